@@ -1,0 +1,156 @@
+/*
+ * libsbp -- C-ABI of the GB300 (sm_103a) SBP-SAT solver for the 2-D anisotropic elastic
+ * wave equation on curvilinear multiblock grids (Almquist & Dunham, "Elastic wave propagation
+ * in anisotropic solids using energy-stable finite differences with weakly enforced boundary
+ * and interface conditions").
+ *
+ * The semidiscrete scheme per block is (Sec. 5, eq. semidiscrete_general; Theorem 1)
+ *     rho u_J'' = J^-1 [ DD_ik(c_iJkL) u_L + J SAT_J ] + f_J
+ * with c_ijkl = F_Ii J C_IjKl F_Kk (eq. transf_density_stiffness) and the Robin, displacement
+ * (Sec. 5) and interface (Sec. 6) SATs.  Time stepping is the explicit leapfrog scheme
+ *     u^{n+1} = 2 u^n - u^{n-1} + dt^2 (rho J)^-1 [ DD(c) u^n + J SAT(u^n, t_n) + J f(t_n) ].
+ *
+ * Conventions
+ *  - Every call returns an int status: SBP_OK (0) or a negative SBP_E_* code.  No call aborts.
+ *    Everything is validated before any device work; sbp_last_error() describes the last failure.
+ *  - A block has n1 x n2 nodes; node (i1, i2) of a host array sits at index i2*n1 + i1
+ *    (x1 fastest).  Faces: 0: x1=0, 1: x1=1, 2: x2=0, 3: x2=1; the tangential index along
+ *    faces 0/1 is i2, along faces 2/3 it is i1.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Host arrays written out
+ *    are caller-allocated.  All host values are double precision.
+ *  - Device memory is owned by the handle (allocated at create / set time, freed by
+ *    sbp_destroy).  Fields are stored in the handle's precision (FP64 or FP32).
+ *  - Time-dependent data (boundary data, body force) is separable: value(t) =
+ *    sum_k coef_k * T_k(t), T_k from sbp_set_time_basis.
+ */
+#ifndef SBP_H
+#define SBP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SBP_OK 0
+#define SBP_E_INVALID_ARG (-1)
+#define SBP_E_JACOBIAN_NONPOSITIVE (-2)      /* J <= 0 at some node (Sec. 3.3 stability requirement) */
+#define SBP_E_NONCONFORMING_INTERFACE (-3)   /* interface sides differ in node count or pairing */
+#define SBP_E_OOM (-4)
+#define SBP_E_CUDA (-5)
+#define SBP_E_TIMEOUT (-6)
+#define SBP_E_UNSTABLE (-7)                  /* non-finite energy */
+#define SBP_E_STATE (-8)                     /* call out of order (e.g. step before material) */
+
+/* precision */
+#define SBP_FP64 0
+#define SBP_FP32 1
+
+/* face kinds */
+#define SBP_BC_DISPLACEMENT 0    /* u = g, SAT of eq. dirichlet_ansatz with Z of Theorem 3 */
+#define SBP_BC_ROBIN 1           /* T u + U u = g, SAT of eq. sat_traction (traction when U = 0) */
+#define SBP_BC_INTERFACE 2       /* welded interface, SATs of eq. scheme_interface (V = Theta = 0) */
+
+/* fields for sbp_get_field */
+#define SBP_FIELD_PREV 0         /* u^{n-1} (after a step: the previous level) */
+#define SBP_FIELD_CUR 1          /* u^n (current level) */
+#define SBP_FIELD_APPLY 2        /* result of the last sbp_apply */
+
+typedef struct sbp_handle sbp_handle;
+
+typedef struct {
+    int kind;                    /* SBP_BC_* */
+    int nbr_block;               /* interface: neighbour block */
+    int nbr_face;                /* interface: neighbour face */
+    int reversed;                /* interface: node s meets neighbour node nf-1-s (else s) */
+} sbp_face_desc;
+
+typedef struct {
+    int n1, n2;                  /* nodes per direction (>= 5 / 18 / 27 for order 2 / 4 / 6) */
+    const double* x1;            /* physical coordinates X_1 of the nodes (n1*n2, host) */
+    const double* x2;            /* physical coordinates X_2 */
+    double h1, h2;               /* reference spacing; <= 0 selects 1/(n-1) */
+    sbp_face_desc faces[4];
+} sbp_block_desc;
+
+typedef struct {
+    int order;                   /* interior order 2q: 2, 4 or 6 (Sec. 4) */
+    int precision;               /* SBP_FP64 or SBP_FP32 */
+    int nblocks;
+    const sbp_block_desc* blocks;
+    double beta;                 /* SAT penalty factor beta >= 1 (Sec. 5.2, 6); 0 selects 1 */
+} sbp_grid_desc;
+
+/* Create a solver for a multiblock curvilinear grid.  Computes the numerical metric on the
+ * device (Sec. 3.3: dX/dx by the SBP first derivative, J = det, F = inverse, face scale factor
+ * J^ = |a_t|).  Errors: SBP_E_INVALID_ARG, SBP_E_NONCONFORMING_INTERFACE,
+ * SBP_E_JACOBIAN_NONPOSITIVE, SBP_E_OOM, SBP_E_CUDA.  On error *out is NULL. */
+int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out);
+
+/* Release every device and host resource of the handle (NULL is accepted). */
+int sbp_destroy(sbp_handle* h);
+
+/* Message of the last failing call on h (h may be NULL: last sbp_grid_create failure). */
+const char* sbp_last_error(const sbp_handle* h);
+
+/* Density and stiffness of one block (Sec. 3, eq. transf_density_stiffness).
+ * rho: n1*n2 values.  C: 10 planes of n1*n2 values, the upper triangle of the symmetric 4x4
+ * pair matrix M[p][q] = C_IJKL, p = 2I+J, q = 2K+L (I,J,K,L in {0,1}) in the order
+ * (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3).  Major symmetry is implied;
+ * minor symmetry is not assumed (Cosserat).  Forms c_ijkl and 1/(rho J) on the device. */
+int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* C);
+
+/* Robin matrix U (Sec. 5.1) of a ROBIN face: 3 planes of nf values (U11, U12, U22), physical. */
+int sbp_set_robin(sbp_handle* h, int block, int face, const double* U);
+
+/* Time basis of separable data: T_k(t) = sin(omega_k t) (kind 0) or cos(omega_k t) (kind 1);
+ * nbasis <= 8. */
+int sbp_set_time_basis(sbp_handle* h, int nbasis, const int* kinds, const double* omegas);
+
+/* Boundary data of a DISPLACEMENT (g_J = prescribed displacement) or ROBIN (g_J = physical
+ * traction data) face: g[(J*nbasis + k)*nf + s]. */
+int sbp_set_boundary_data(sbp_handle* h, int block, int face, const double* g);
+
+/* Body force f_J of one block (physical, per unit volume): f[(J*nbasis + k)*n1*n2 + node]. */
+int sbp_set_forcing(sbp_handle* h, int block, const double* f);
+
+/* Point force f_J = (f1, f2)_J * amplitude * W(t) * delta(X - X0) (Sec. 7.4), W the Ricker
+ * wavelet with peak frequency alpha_p centred at t0.  (x1, x2) is the position in the block's
+ * reference coordinates [0,1]^2.  The discrete delta uses, per direction, the Lagrange weights
+ * of the 2q nodes nearest x (start = clamp(floor(x/h) - q + 1, 0, n - 2q)) divided by H. */
+int sbp_add_point_source(sbp_handle* h, int block, double x1, double x2, double f1, double f2,
+                         double amplitude, double alpha_p, double t0);
+
+/* Initial state of one block: u_prev = u^{-1}, u_cur = u^0, each 2 planes (u_1, u_2) of
+ * n1*n2 values (host).  t is the time of u_cur (same for all blocks; the last call wins). */
+int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* u_cur, double t);
+
+/* Advance all blocks by nsteps leapfrog steps of size dt, asynchronously on `stream`
+ * (a cudaStream_t; NULL = default stream). */
+int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream);
+
+/* Apply the spatial operator to the current level of every block (synchronous):
+ * r = DD(c) u + J SAT(u) (+ J f(t) + point sources when with_data != 0, SAT data at t).
+ * The result is read with sbp_get_field(..., SBP_FIELD_APPLY, ...). */
+int sbp_apply(sbp_handle* h, int with_data, double t);
+
+/* Copy a field of one block to host (2 planes of n1*n2 doubles).  Synchronous. */
+int sbp_get_field(sbp_handle* h, int block, int which, double* dst);
+
+/* Leapfrog energy E^{n+1/2} = 1/2 |u^{n+1}-u^n|^2_{rho J H}/dt^2 - 1/2 (u^{n+1})^T H A u^n
+ * with u^n = PREV, u^{n+1} = CUR and A the homogeneous operator (Sec. 5-6 energies); FP64
+ * reductions.  Returns SBP_E_UNSTABLE if the result is not finite. */
+int sbp_energy(sbp_handle* h, double dt, double* E_out);
+
+/* dt = cfl * min over nodes of min(h1,h2) / v_max, v_max the largest quasi-P speed from the
+ * Christoffel equation in the reference domain (Sec. 7, eq. christoffel), maximised over
+ * 720 sampled directions refined by golden-section search.  Needs all materials set. */
+int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out);
+
+/* Current simulation time and number of resident nodes. */
+int sbp_get_time(const sbp_handle* h, double* t_out);
+int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, int* order_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBP_H */

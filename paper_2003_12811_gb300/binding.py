@@ -1,0 +1,226 @@
+"""ctypes binding of libsbp (include/sbp.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts numpy arrays to the
+C layouts, calls the C entry points by the same names, and raises on non-zero status.
+The library must be built (``paper_2003_12811_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsbp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sbp.h")
+
+SBP_OK = 0
+STATUS = {0: "SBP_OK", -1: "SBP_E_INVALID_ARG", -2: "SBP_E_JACOBIAN_NONPOSITIVE",
+          -3: "SBP_E_NONCONFORMING_INTERFACE", -4: "SBP_E_OOM", -5: "SBP_E_CUDA", -6: "SBP_E_TIMEOUT",
+          -7: "SBP_E_UNSTABLE", -8: "SBP_E_STATE"}
+FP64, FP32 = 0, 1
+BC = {"displacement": 0, "robin": 1, "interface": 2}
+FIELD_PREV, FIELD_CUR, FIELD_APPLY = 0, 1, 2
+
+
+class SbpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class FaceDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nbr_block", C.c_int), ("nbr_face", C.c_int), ("reversed", C.c_int)]
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("x1", C.POINTER(C.c_double)), ("x2", C.POINTER(C.c_double)),
+                ("h1", C.c_double), ("h2", C.c_double), ("faces", FaceDesc * 4)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("order", C.c_int), ("precision", C.c_int), ("nblocks", C.c_int),
+                ("blocks", C.POINTER(BlockDesc)), ("beta", C.c_double)]
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+
+
+def header_functions():
+    """Names of the functions declared in include/sbp.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s+(sbp_\w+)\s*\(", txt, re.M)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsbp.so is not built (run __graft_entry__.build()); no fallback exists")
+        L = C.CDLL(LIB_PATH)
+        L.sbp_grid_create.argtypes = [C.POINTER(GridDesc), C.POINTER(C.c_void_p)]
+        L.sbp_destroy.argtypes = [C.c_void_p]
+        L.sbp_last_error.argtypes = [C.c_void_p]
+        L.sbp_last_error.restype = C.c_char_p
+        L.sbp_set_material.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
+        L.sbp_set_robin.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
+        L.sbp_set_time_basis.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), _DP]
+        L.sbp_set_boundary_data.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
+        L.sbp_set_forcing.argtypes = [C.c_void_p, C.c_int, _DP]
+        L.sbp_add_point_source.argtypes = [C.c_void_p, C.c_int] + [C.c_double] * 7
+        L.sbp_set_state.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_double]
+        L.sbp_step.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+        L.sbp_apply.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.sbp_get_field.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
+        L.sbp_energy.argtypes = [C.c_void_p, C.c_double, _DP]
+        L.sbp_suggest_dt.argtypes = [C.c_void_p, C.c_double, _DP]
+        L.sbp_get_time.argtypes = [C.c_void_p, _DP]
+        L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def pair10(Cfull):
+    """Full tensor C[I,J,K,L,...] -> 10 planes: upper triangle of M[p][q], p = 2I+J, q = 2K+L."""
+    planes = []
+    for p in range(4):
+        for q in range(p, 4):
+            planes.append(Cfull[p // 2, p % 2, q // 2, q % 2])
+    return np.stack(planes)
+
+
+class Solver:
+    """A libsbp handle built from a ``workloads.Problem``."""
+
+    def __init__(self, problem, precision="fp64"):
+        self.L = lib()
+        self.problem = problem
+        self.precision = FP64 if precision == "fp64" else FP32
+        self._keep = []
+        blocks = (BlockDesc * len(problem.blocks))()
+        for b, blk in enumerate(problem.blocks):
+            x1, x2 = _f64(blk.X[0]), _f64(blk.X[1])
+            self._keep += [x1, x2]
+            bd = blocks[b]
+            bd.n1, bd.n2 = blk.N1, blk.N2
+            bd.x1, bd.x2 = _ptr(x1), _ptr(x2)
+            bd.h1, bd.h2 = blk.spacing
+            for f, face in enumerate(blk.faces):
+                if face.kind not in BC:
+                    raise ValueError(f"face kind {face.kind!r} is not supported by libsbp")
+                fd = bd.faces[f]
+                fd.kind = BC[face.kind]
+                if face.kind == "interface":
+                    fd.nbr_block, fd.nbr_face, fd.reversed = face.nbr[0], face.nbr[1], int(bool(face.nbr[2]))
+                else:
+                    fd.nbr_block, fd.nbr_face, fd.reversed = -1, -1, 0
+        desc = GridDesc(problem.order, self.precision, len(problem.blocks), blocks, problem.beta)
+        h = C.c_void_p()
+        rc = self.L.sbp_grid_create(C.byref(desc), C.byref(h))
+        if rc != SBP_OK:
+            raise SbpError(rc, self.L.sbp_last_error(None).decode())
+        self.h = h
+        try:
+            self._setup()
+        except Exception:
+            self.close()
+            raise
+
+    def _check(self, rc):
+        if rc != SBP_OK:
+            raise SbpError(rc, self.L.sbp_last_error(self.h).decode())
+
+    def _setup(self):
+        P = self.problem
+        if P.time_basis:
+            kinds = (C.c_int * len(P.time_basis))(*[0 if k == "sin" else 1 for k, _ in P.time_basis])
+            om = _f64([w for _, w in P.time_basis])
+            self._check(self.L.sbp_set_time_basis(self.h, len(P.time_basis), kinds, _ptr(om)))
+        for b, blk in enumerate(P.blocks):
+            rho = _f64(blk.rho)
+            Cp = _f64(pair10(blk.C))
+            self._check(self.L.sbp_set_material(self.h, b, _ptr(rho), _ptr(Cp)))
+            for f, face in enumerate(blk.faces):
+                if face.kind == "robin" and face.U is not None:
+                    U = _f64(face.U)
+                    self._check(self.L.sbp_set_robin(self.h, b, f, _ptr(U)))
+                if face.g is not None and face.kind in ("robin", "displacement"):
+                    g = _f64(face.g)
+                    self._check(self.L.sbp_set_boundary_data(self.h, b, f, _ptr(g)))
+            if blk.forcing is not None:
+                fo = _f64(blk.forcing)
+                self._check(self.L.sbp_set_forcing(self.h, b, _ptr(fo)))
+        for s in P.sources:
+            self._check(self.L.sbp_add_point_source(self.h, s.block, s.x_ref[0], s.x_ref[1], s.direction[0],
+                                                    s.direction[1], s.amplitude, s.alpha_p, s.t0))
+
+    # ---------------------------------------------------------------- C entry points
+    def sbp_set_state(self, u_prev, u_cur, t):
+        for b, (up, uc) in enumerate(zip(u_prev, u_cur)):
+            a, c = _f64(up), _f64(uc)
+            self._check(self.L.sbp_set_state(self.h, b, _ptr(a), _ptr(c), float(t)))
+
+    def sbp_step(self, nsteps, dt, stream=None):
+        s = None if stream is None else C.c_void_p(stream)
+        self._check(self.L.sbp_step(self.h, int(nsteps), float(dt), s))
+
+    def sbp_apply(self, with_data=False, t=0.0):
+        self._check(self.L.sbp_apply(self.h, int(bool(with_data)), float(t)))
+
+    def sbp_get_field(self, which):
+        out = []
+        for b, blk in enumerate(self.problem.blocks):
+            dst = np.empty((2, blk.N2, blk.N1))
+            self._check(self.L.sbp_get_field(self.h, b, which, _ptr(dst)))
+            out.append(dst)
+        return out
+
+    def sbp_energy(self, dt):
+        E = C.c_double()
+        self._check(self.L.sbp_energy(self.h, float(dt), C.byref(E)))
+        return E.value
+
+    def sbp_suggest_dt(self, cfl):
+        dt = C.c_double()
+        self._check(self.L.sbp_suggest_dt(self.h, float(cfl), C.byref(dt)))
+        return dt.value
+
+    def sbp_get_time(self):
+        t = C.c_double()
+        self._check(self.L.sbp_get_time(self.h, C.byref(t)))
+        return t.value
+
+    # ---------------------------------------------------------------- conveniences
+    set_state = sbp_set_state
+    step = sbp_step
+    energy = sbp_energy
+    suggest_dt = sbp_suggest_dt
+
+    def apply(self, with_data=False, t=0.0):
+        self.sbp_apply(with_data, t)
+        return self.sbp_get_field(FIELD_APPLY)
+
+    def state(self):
+        return self.sbp_get_field(FIELD_PREV), self.sbp_get_field(FIELD_CUR)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sbp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,667 @@
+// libsbp host implementation: handle, validation, device memory, setup and the leapfrog step
+// loop.  The declarations and their documentation are in include/sbp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sbp.h"
+#include "sbp_kernels.cuh"
+
+namespace sbphost {
+#define SBP_TABLE static const
+#include "sbp_tables.inc"
+#undef SBP_TABLE
+}  // namespace sbphost
+
+using namespace sbp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct HostFace {
+    int kind = -1, nbr_block = -1, nbr_face = -1, reversed = 0;
+    int nf = 0;
+    double* jhat = nullptr;
+    void* ju = nullptr;
+    void* g = nullptr;
+    void* tr = nullptr;
+    void* sat = nullptr;
+};
+
+struct HostBlock {
+    int n1 = 0, n2 = 0, pitch = 0;
+    double h1 = 0, h2 = 0;
+    void* u[2] = {nullptr, nullptr};
+    void* c = nullptr;
+    void* w = nullptr;
+    void* jf = nullptr;
+    void* r = nullptr;
+    double* X = nullptr;
+    double* G = nullptr;
+    double* J = nullptr;
+    bool material = false;
+    HostFace f[4];
+};
+
+int order_nb(int o) { return o == 2 ? SBP2_NB : (o == 4 ? SBP4_NB : SBP6_NB); }
+int order_ncol(int o) { return o == 2 ? SBP2_NCOL : (o == 4 ? SBP4_NCOL : SBP6_NCOL); }
+int order_nclos(int o) { return o == 2 ? SBP2_NCLOS : (o == 4 ? SBP4_NCLOS : SBP6_NCLOS); }
+int order_q(int o) { return o / 2; }
+int order_min_n(int o) { return o == 2 ? 5 : (o == 4 ? 18 : 27); }
+double order_hw(int o, int i) {
+    return o == 2 ? sbphost::sbp2_HW[i] : (o == 4 ? sbphost::sbp4_HW[i] : sbphost::sbp6_HW[i]);
+}
+double host_hweight(int o, int N, int i) {
+    const int nb = order_nb(o);
+    if (i < nb) return order_hw(o, i);
+    if (i >= N - nb) return order_hw(o, N - 1 - i);
+    return 1.0;
+}
+
+}  // namespace
+
+struct sbp_handle {
+    int order = 0, precision = 0, nblocks = 0;
+    double beta = 1.0;
+    size_t esize = 8;
+    std::vector<HostBlock> blocks;
+    BlockDev* d_blocks = nullptr;
+    FaceRef* d_refs = nullptr;
+    int nrefs = 0, nface_nodes = 0;
+    int cur = 0;
+    double t = 0.0;
+    int nbasis = 0;
+    int basis_kind[8] = {0};
+    double basis_omega[8] = {0};
+    std::vector<SrcNode> src_nodes;
+    std::vector<SrcParam> src_params;
+    SrcNode* d_src_nodes = nullptr;
+    SrcParam* d_src_params = nullptr;
+    bool src_dirty = false;
+    double* d_scalar = nullptr;
+    int* d_flag = nullptr;
+    std::string err;
+    std::vector<void*> allocs;
+
+    int fail(int code, const std::string& msg) {
+        err = msg;
+        return code;
+    }
+    void* dalloc(size_t bytes) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, bytes);
+        allocs.push_back(p);
+        return p;
+    }
+    void dfree(void* p) {
+        if (!p) return;
+        for (auto& a : allocs)
+            if (a == p) a = nullptr;
+        cudaFree(p);
+    }
+};
+
+namespace {
+
+int check_cuda(sbp_handle* h, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return SBP_OK;
+}
+
+BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
+    BlockDev b{};
+    b.n1 = hb.n1;
+    b.n2 = hb.n2;
+    b.pitch = hb.pitch;
+    b.strip = std::max(order_nclos(h->order), order_ncol(h->order));
+    b.h1 = hb.h1;
+    b.h2 = hb.h2;
+    b.u[0] = hb.u[0];
+    b.u[1] = hb.u[1];
+    b.c = hb.c;
+    b.w = hb.w;
+    b.jf = hb.jf;
+    b.r = hb.r;
+    b.X = hb.X;
+    b.G = hb.G;
+    b.J = hb.J;
+    for (int f = 0; f < 4; ++f) {
+        const HostFace& F = hb.f[f];
+        FaceDev& D = b.f[f];
+        D.kind = F.kind;
+        D.m = f / 2;
+        D.side = f % 2;
+        D.nf = F.nf;
+        D.nbr_block = F.nbr_block;
+        D.nbr_face = F.nbr_face;
+        D.reversed = F.reversed;
+        D.nu = (f % 2 == 0) ? -1.0 : 1.0;
+        const int Nm = (f / 2 == 0) ? hb.n1 : hb.n2;
+        const double hm = (f / 2 == 0) ? hb.h1 : hb.h2;
+        D.hm0 = hm * host_hweight(h->order, Nm, 0);
+        D.jhat = F.jhat;
+        D.ju = F.ju;
+        D.g = F.g;
+        D.tr = F.tr;
+        D.sat = F.sat;
+    }
+    return b;
+}
+
+int sync_views(sbp_handle* h) {
+    std::vector<BlockDev> v;
+    for (auto& hb : h->blocks) v.push_back(make_view(h, hb));
+    if (cudaMemcpy(h->d_blocks, v.data(), sizeof(BlockDev) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "upload of block views failed");
+    return SBP_OK;
+}
+
+inline unsigned grid_for(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T, int O>
+int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
+    const int total = h->nface_nodes;
+    if (total > 0) {
+        k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, total, a.cur);
+        k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, total, a, h->beta);
+    }
+    constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
+    for (auto& hb : h->blocks) {
+        BlockDev b = make_view(h, hb);
+        const int S = b.strip;
+        const int ni1 = hb.n1 - 2 * S, ni2 = hb.n2 - 2 * S;
+        dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
+        if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
+        else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
+        const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)ni1 * ni2;
+        if (mode == 0) k_boundary<T, O, 0><<<grid_for(nstrip), 256, 0, st>>>(b, a);
+        else k_boundary<T, O, 1><<<grid_for(nstrip), 256, 0, st>>>(b, a);
+    }
+    if (!h->src_nodes.empty()) {
+        const int ns = (int)h->src_nodes.size();
+        if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
+        else k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
+    }
+    return check_cuda(h, "operator launch");
+}
+
+template <typename T>
+int dispatch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
+    switch (h->order) {
+        case 2: return launch_operator<T, 2>(h, a, mode, st);
+        case 4: return launch_operator<T, 4>(h, a, mode, st);
+        default: return launch_operator<T, 6>(h, a, mode, st);
+    }
+}
+
+int run_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
+    return h->precision == SBP_FP64 ? dispatch_operator<double>(h, a, mode, st) : dispatch_operator<float>(h, a, mode, st);
+}
+
+template <typename T, int O> void set_smem_attr() {
+    constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
+    cudaFuncSetAttribute(k_interior<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_interior<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+void fill_basis(const sbp_handle* h, double t, StepArgs& a) {
+    a.K = h->nbasis;
+    for (int k = 0; k < h->nbasis; ++k) a.Tk[k] = h->basis_kind[k] == 0 ? sin(h->basis_omega[k] * t) : cos(h->basis_omega[k] * t);
+}
+
+int upload_sources(sbp_handle* h) {
+    if (!h->src_dirty) return SBP_OK;
+    h->dfree(h->d_src_nodes);
+    h->dfree(h->d_src_params);
+    h->d_src_nodes = (SrcNode*)h->dalloc(sizeof(SrcNode) * h->src_nodes.size());
+    h->d_src_params = (SrcParam*)h->dalloc(sizeof(SrcParam) * h->src_params.size());
+    if (!h->d_src_nodes || !h->d_src_params) return h->fail(SBP_E_OOM, "source tables");
+    cudaMemcpy(h->d_src_nodes, h->src_nodes.data(), sizeof(SrcNode) * h->src_nodes.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_src_params, h->src_params.data(), sizeof(SrcParam) * h->src_params.size(), cudaMemcpyHostToDevice);
+    h->src_dirty = false;
+    return check_cuda(h, "source upload");
+}
+
+bool all_materials(const sbp_handle* h) {
+    for (auto& b : h->blocks)
+        if (!b.material) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sbp_last_error(const sbp_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
+    if (!out) return SBP_E_INVALID_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    auto bad = [&](int code, const std::string& m) {
+        g_create_error = m;
+        return code;
+    };
+    if (!desc) return bad(SBP_E_INVALID_ARG, "null descriptor");
+    if (desc->order != 2 && desc->order != 4 && desc->order != 6) return bad(SBP_E_INVALID_ARG, "order must be 2, 4 or 6");
+    if (desc->precision != SBP_FP64 && desc->precision != SBP_FP32) return bad(SBP_E_INVALID_ARG, "bad precision");
+    if (desc->nblocks < 1 || !desc->blocks) return bad(SBP_E_INVALID_ARG, "need at least one block");
+    if (desc->beta < 0 || (desc->beta > 0 && desc->beta < 1)) return bad(SBP_E_INVALID_ARG, "beta must be >= 1");
+    const int o = desc->order;
+    for (int b = 0; b < desc->nblocks; ++b) {
+        const sbp_block_desc& bd = desc->blocks[b];
+        if (bd.n1 < order_min_n(o) || bd.n2 < order_min_n(o))
+            return bad(SBP_E_INVALID_ARG, "block " + std::to_string(b) + ": too few nodes for this order");
+        if ((long long)bd.n1 * bd.n2 > (1LL << 31) - 1) return bad(SBP_E_INVALID_ARG, "block too large");
+        if (!bd.x1 || !bd.x2) return bad(SBP_E_INVALID_ARG, "null coordinates");
+        for (int f = 0; f < 4; ++f) {
+            const sbp_face_desc& fd = bd.faces[f];
+            if (fd.kind < 0 || fd.kind > 2) return bad(SBP_E_INVALID_ARG, "bad face kind");
+            if (fd.kind == SBP_BC_INTERFACE) {
+                if (fd.nbr_block < 0 || fd.nbr_block >= desc->nblocks || fd.nbr_face < 0 || fd.nbr_face > 3)
+                    return bad(SBP_E_INVALID_ARG, "bad interface neighbour");
+                const sbp_block_desc& nb = desc->blocks[fd.nbr_block];
+                const sbp_face_desc& back = nb.faces[fd.nbr_face];
+                const int nf = f < 2 ? bd.n2 : bd.n1;
+                const int nfv = fd.nbr_face < 2 ? nb.n2 : nb.n1;
+                const double ht = f < 2 ? (bd.h2 > 0 ? bd.h2 : 1.0 / (bd.n2 - 1)) : (bd.h1 > 0 ? bd.h1 : 1.0 / (bd.n1 - 1));
+                const double htv = fd.nbr_face < 2 ? (nb.h2 > 0 ? nb.h2 : 1.0 / (nb.n2 - 1)) : (nb.h1 > 0 ? nb.h1 : 1.0 / (nb.n1 - 1));
+                if (nf != nfv || back.kind != SBP_BC_INTERFACE || back.nbr_block != b || back.nbr_face != f ||
+                    (back.reversed != 0) != (fd.reversed != 0) || fabs(ht - htv) > 1e-12 * ht || (fd.nbr_block == b && fd.nbr_face == f))
+                    return bad(SBP_E_NONCONFORMING_INTERFACE, "interface of block " + std::to_string(b) + " face " +
+                                                                  std::to_string(f) + " does not conform");
+            }
+        }
+    }
+    sbp_handle* h = new sbp_handle();
+    h->order = o;
+    h->precision = desc->precision;
+    h->esize = desc->precision == SBP_FP64 ? 8 : 4;
+    h->beta = desc->beta > 0 ? desc->beta : 1.0;
+    h->nblocks = desc->nblocks;
+    h->blocks.resize(desc->nblocks);
+    auto cleanup = [&](int code, const std::string& m) {
+        g_create_error = m;
+        sbp_destroy(h);
+        return code;
+    };
+    if (desc->precision == SBP_FP64) { set_smem_attr<double, 2>(); set_smem_attr<double, 4>(); set_smem_attr<double, 6>(); }
+    else { set_smem_attr<float, 2>(); set_smem_attr<float, 4>(); set_smem_attr<float, 6>(); }
+    h->d_scalar = (double*)h->dalloc(64);
+    h->d_flag = (int*)h->dalloc(64);
+    if (!h->d_scalar || !h->d_flag) return cleanup(SBP_E_OOM, "scalar buffers");
+    std::vector<FaceRef> refs;
+    int start = 0;
+    for (int b = 0; b < desc->nblocks; ++b) {
+        const sbp_block_desc& bd = desc->blocks[b];
+        HostBlock& hb = h->blocks[b];
+        hb.n1 = bd.n1;
+        hb.n2 = bd.n2;
+        hb.pitch = (bd.n1 + 31) / 32 * 32;
+        hb.h1 = bd.h1 > 0 ? bd.h1 : 1.0 / (bd.n1 - 1);
+        hb.h2 = bd.h2 > 0 ? bd.h2 : 1.0 / (bd.n2 - 1);
+        const size_t plane = (size_t)hb.n2 * hb.pitch;
+        const size_t es = h->esize;
+        hb.u[0] = h->dalloc(2 * plane * es);
+        hb.u[1] = h->dalloc(2 * plane * es);
+        hb.c = h->dalloc(10 * plane * es);
+        hb.w = h->dalloc(plane * es);
+        hb.r = h->dalloc(2 * plane * es);
+        hb.X = (double*)h->dalloc(2 * plane * sizeof(double));
+        hb.G = (double*)h->dalloc(4 * plane * sizeof(double));
+        hb.J = (double*)h->dalloc(plane * sizeof(double));
+        if (!hb.u[0] || !hb.u[1] || !hb.c || !hb.w || !hb.r || !hb.X || !hb.G || !hb.J)
+            return cleanup(SBP_E_OOM, "device allocation failed for block " + std::to_string(b));
+        for (int f = 0; f < 4; ++f) {
+            HostFace& F = hb.f[f];
+            F.kind = bd.faces[f].kind;
+            F.nbr_block = bd.faces[f].nbr_block;
+            F.nbr_face = bd.faces[f].nbr_face;
+            F.reversed = bd.faces[f].reversed ? 1 : 0;
+            F.nf = f < 2 ? hb.n2 : hb.n1;
+            F.jhat = (double*)h->dalloc(F.nf * sizeof(double));
+            F.tr = h->dalloc(4 * (size_t)F.nf * es);
+            F.sat = h->dalloc(4 * (size_t)F.nf * es);
+            if (!F.jhat || !F.tr || !F.sat) return cleanup(SBP_E_OOM, "face buffers");
+            refs.push_back(FaceRef{b, f, start, F.nf});
+            start += F.nf;
+        }
+        // coordinates -> pitched device planes
+        double* tmp = (double*)h->dalloc(2 * (size_t)bd.n1 * bd.n2 * sizeof(double));
+        if (!tmp) return cleanup(SBP_E_OOM, "staging buffer");
+        const size_t n = (size_t)bd.n1 * bd.n2;
+        cudaMemcpy(tmp, bd.x1, n * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(tmp + n, bd.x2, n * sizeof(double), cudaMemcpyHostToDevice);
+        k_to_pitched<double><<<grid_for(2 * (long long)n), 256>>>(hb.X, tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+        cudaDeviceSynchronize();
+        h->dfree(tmp);
+    }
+    h->nrefs = (int)refs.size();
+    h->nface_nodes = start;
+    h->d_refs = (FaceRef*)h->dalloc(sizeof(FaceRef) * refs.size());
+    h->d_blocks = (BlockDev*)h->dalloc(sizeof(BlockDev) * h->blocks.size());
+    if (!h->d_refs || !h->d_blocks) return cleanup(SBP_E_OOM, "tables");
+    cudaMemcpy(h->d_refs, refs.data(), sizeof(FaceRef) * refs.size(), cudaMemcpyHostToDevice);
+    if (sync_views(h) != SBP_OK) return cleanup(SBP_E_CUDA, h->err);
+    // metric
+    cudaMemset(h->d_flag, 0, sizeof(int));
+    for (auto& hb : h->blocks) {
+        BlockDev b = make_view(h, hb);
+        const long long n = (long long)hb.n1 * hb.n2;
+        if (o == 2) k_metric<2><<<grid_for(n), 256>>>(b, h->d_flag);
+        else if (o == 4) k_metric<4><<<grid_for(n), 256>>>(b, h->d_flag);
+        else k_metric<6><<<grid_for(n), 256>>>(b, h->d_flag);
+        for (int f = 0; f < 4; ++f) k_face_jhat<<<grid_for(hb.f[f].nf), 256>>>(b, f, hb.f[f].jhat);
+    }
+    int flag = 0;
+    cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return cleanup(SBP_E_CUDA, "metric setup failed");
+    if (flag) return cleanup(SBP_E_JACOBIAN_NONPOSITIVE, "non-positive Jacobian determinant");
+    *out = h;
+    return SBP_OK;
+}
+
+int sbp_destroy(sbp_handle* h) {
+    if (!h) return SBP_OK;
+    for (void* p : h->allocs)
+        if (p) cudaFree(p);
+    delete h;
+    return SBP_OK;
+}
+
+int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* C) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks) return h->fail(SBP_E_INVALID_ARG, "bad block index");
+    if (!rho || !C) return h->fail(SBP_E_INVALID_ARG, "null material arrays");
+    HostBlock& hb = h->blocks[block];
+    const size_t n = (size_t)hb.n1 * hb.n2;
+    for (size_t i = 0; i < n; ++i)
+        if (!(rho[i] > 0.0) || !std::isfinite(rho[i])) return h->fail(SBP_E_INVALID_ARG, "density must be positive and finite");
+    double* d_rho = (double*)h->dalloc(n * sizeof(double));
+    double* d_C = (double*)h->dalloc(10 * n * sizeof(double));
+    if (!d_rho || !d_C) {
+        h->dfree(d_rho);
+        h->dfree(d_C);
+        return h->fail(SBP_E_OOM, "material staging");
+    }
+    cudaMemcpy(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_C, C, 10 * n * sizeof(double), cudaMemcpyHostToDevice);
+    BlockDev b = make_view(h, hb);
+    if (h->precision == SBP_FP64) k_material<double><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
+    else k_material<float><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
+    cudaError_t e = cudaDeviceSynchronize();
+    h->dfree(d_rho);
+    h->dfree(d_C);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, std::string("material: ") + cudaGetErrorString(e));
+    hb.material = true;
+    return SBP_OK;
+}
+
+int sbp_set_robin(sbp_handle* h, int block, int face, const double* U) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || face < 0 || face > 3 || !U) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostFace& F = h->blocks[block].f[face];
+    if (F.kind != SBP_BC_ROBIN) return h->fail(SBP_E_INVALID_ARG, "face is not a Robin face");
+    for (int s = 0; s < F.nf; ++s) {
+        const double a = U[s], b = U[F.nf + s], c = U[2 * F.nf + s];
+        if (!(a >= 0 && c >= 0 && a * c - b * b >= -1e-12 * (a * c + b * b))) return h->fail(SBP_E_INVALID_ARG, "U must be symmetric positive semidefinite");
+    }
+    if (!F.ju) F.ju = h->dalloc(3 * (size_t)F.nf * h->esize);
+    double* tmp = (double*)h->dalloc(3 * (size_t)F.nf * sizeof(double));
+    if (!F.ju || !tmp) return h->fail(SBP_E_OOM, "robin buffers");
+    cudaMemcpy(tmp, U, 3 * (size_t)F.nf * sizeof(double), cudaMemcpyHostToDevice);
+    if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for(3LL * F.nf), 256>>>((double*)F.ju, tmp, F.jhat, F.nf, 3);
+    else k_scale_copy<float><<<grid_for(3LL * F.nf), 256>>>((float*)F.ju, tmp, F.jhat, F.nf, 3);
+    cudaError_t e = cudaDeviceSynchronize();
+    h->dfree(tmp);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "robin upload");
+    return sync_views(h);
+}
+
+int sbp_set_time_basis(sbp_handle* h, int nbasis, const int* kinds, const double* omegas) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nbasis < 0 || nbasis > 8 || (nbasis > 0 && (!kinds || !omegas))) return h->fail(SBP_E_INVALID_ARG, "bad time basis");
+    for (int k = 0; k < nbasis; ++k)
+        if (kinds[k] != 0 && kinds[k] != 1) return h->fail(SBP_E_INVALID_ARG, "basis kind must be 0 (sin) or 1 (cos)");
+    if (h->nbasis != 0 && h->nbasis != nbasis) {
+        for (auto& hb : h->blocks) {
+            if (hb.jf) return h->fail(SBP_E_STATE, "time basis size fixed once data is set");
+            for (auto& F : hb.f)
+                if (F.g) return h->fail(SBP_E_STATE, "time basis size fixed once data is set");
+        }
+    }
+    h->nbasis = nbasis;
+    for (int k = 0; k < nbasis; ++k) {
+        h->basis_kind[k] = kinds[k];
+        h->basis_omega[k] = omegas[k];
+    }
+    return SBP_OK;
+}
+
+int sbp_set_boundary_data(sbp_handle* h, int block, int face, const double* g) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || face < 0 || face > 3 || !g) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    if (h->nbasis == 0) return h->fail(SBP_E_STATE, "set the time basis first");
+    HostFace& F = h->blocks[block].f[face];
+    if (F.kind == SBP_BC_INTERFACE) return h->fail(SBP_E_INVALID_ARG, "interfaces take no boundary data");
+    const size_t cnt = 2 * (size_t)h->nbasis * F.nf;
+    if (!F.g) F.g = h->dalloc(cnt * h->esize);
+    double* tmp = (double*)h->dalloc(cnt * sizeof(double));
+    if (!F.g || !tmp) return h->fail(SBP_E_OOM, "boundary data");
+    cudaMemcpy(tmp, g, cnt * sizeof(double), cudaMemcpyHostToDevice);
+    const double* scale = F.kind == SBP_BC_ROBIN ? F.jhat : nullptr;
+    if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for((long long)cnt), 256>>>((double*)F.g, tmp, scale, F.nf, 2 * h->nbasis);
+    else k_scale_copy<float><<<grid_for((long long)cnt), 256>>>((float*)F.g, tmp, scale, F.nf, 2 * h->nbasis);
+    cudaError_t e = cudaDeviceSynchronize();
+    h->dfree(tmp);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "boundary data upload");
+    return sync_views(h);
+}
+
+int sbp_set_forcing(sbp_handle* h, int block, const double* f) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || !f) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    if (h->nbasis == 0) return h->fail(SBP_E_STATE, "set the time basis first");
+    HostBlock& hb = h->blocks[block];
+    const size_t n = (size_t)hb.n1 * hb.n2, planes = 2 * (size_t)h->nbasis;
+    const size_t plane = (size_t)hb.n2 * hb.pitch;
+    if (!hb.jf) hb.jf = h->dalloc(planes * plane * h->esize);
+    double* tmp = (double*)h->dalloc(planes * n * sizeof(double));
+    if (!hb.jf || !tmp) return h->fail(SBP_E_OOM, "forcing");
+    cudaMemcpy(tmp, f, planes * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for((long long)(planes * n)), 256>>>((double*)hb.jf, tmp, hb.n1, hb.n2, hb.pitch, (int)planes, hb.J);
+    else k_to_pitched<float><<<grid_for((long long)(planes * n)), 256>>>((float*)hb.jf, tmp, hb.n1, hb.n2, hb.pitch, (int)planes, hb.J);
+    cudaError_t e = cudaDeviceSynchronize();
+    h->dfree(tmp);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "forcing upload");
+    return sync_views(h);
+}
+
+int sbp_add_point_source(sbp_handle* h, int block, double x1, double x2, double f1, double f2, double amplitude,
+                         double alpha_p, double t0) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks) return h->fail(SBP_E_INVALID_ARG, "bad block");
+    if (!(x1 >= 0 && x1 <= 1 && x2 >= 0 && x2 <= 1)) return h->fail(SBP_E_INVALID_ARG, "source outside the block");
+    if (!std::isfinite(alpha_p) || !std::isfinite(t0) || !std::isfinite(amplitude)) return h->fail(SBP_E_INVALID_ARG, "non-finite source");
+    const HostBlock& hb = h->blocks[block];
+    const int q = order_q(h->order);
+    auto weights = [&](int N, double hh, double x0, std::vector<int>& nodes, std::vector<double>& w) {
+        const double xi = x0 / hh;
+        int st = (int)floor(xi) - q + 1;
+        st = std::max(0, std::min(st, N - 2 * q));
+        for (int i = st; i < st + 2 * q; ++i) nodes.push_back(i);
+        for (int i : nodes) {
+            double l = 1.0;
+            for (int j : nodes)
+                if (j != i) l *= (x0 - j * hh) / (i * hh - j * hh);
+            w.push_back(l);
+        }
+    };
+    std::vector<int> n1v, n2v;
+    std::vector<double> w1, w2;
+    weights(hb.n1, hb.h1, x1, n1v, w1);
+    weights(hb.n2, hb.h2, x2, n2v, w2);
+    const int sid = (int)h->src_params.size();
+    h->src_params.push_back(SrcParam{alpha_p, t0});
+    for (size_t a = 0; a < n1v.size(); ++a)
+        for (size_t c = 0; c < n2v.size(); ++c) {
+            const double H = hb.h1 * host_hweight(h->order, hb.n1, n1v[a]) * hb.h2 * host_hweight(h->order, hb.n2, n2v[c]);
+            const double wt = amplitude * w1[a] * w2[c] / H;
+            SrcNode nd{};
+            nd.block = block;
+            nd.src = sid;
+            nd.gi = (long long)n2v[c] * hb.pitch + n1v[a];
+            nd.wt0 = f1 * wt;
+            nd.wt1 = f2 * wt;
+            h->src_nodes.push_back(nd);
+        }
+    h->src_dirty = true;
+    return upload_sources(h);
+}
+
+int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* u_cur, double t) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || !u_prev || !u_cur) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostBlock& hb = h->blocks[block];
+    const size_t n = (size_t)hb.n1 * hb.n2;
+    double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
+    if (!tmp) return h->fail(SBP_E_OOM, "state staging");
+    const double* src[2] = {u_prev, u_cur};
+    const int dst_idx[2] = {1 - h->cur, h->cur};
+    for (int k = 0; k < 2; ++k) {
+        cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice);
+        if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+        else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    h->dfree(tmp);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
+    h->t = t;
+    return SBP_OK;
+}
+
+int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return h->fail(SBP_E_INVALID_ARG, "bad step arguments");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    cudaStream_t st = (cudaStream_t)stream;
+    StepArgs a{};
+    a.with_data = 1;
+    a.dt2 = dt * dt;
+    for (int n = 0; n < nsteps; ++n) {
+        a.cur = h->cur;
+        a.t = h->t;
+        fill_basis(h, h->t, a);
+        int rc = run_operator(h, a, 0, st);
+        if (rc != SBP_OK) return rc;
+        h->cur = 1 - h->cur;
+        h->t += dt;
+    }
+    return SBP_OK;
+}
+
+int sbp_apply(sbp_handle* h, int with_data, double t) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    StepArgs a{};
+    a.cur = h->cur;
+    a.with_data = with_data ? 1 : 0;
+    a.t = t;
+    fill_basis(h, t, a);
+    int rc = run_operator(h, a, 1, 0);
+    if (rc != SBP_OK) return rc;
+    if (cudaDeviceSynchronize() != cudaSuccess) return h->fail(SBP_E_CUDA, "apply failed");
+    return SBP_OK;
+}
+
+int sbp_get_field(sbp_handle* h, int block, int which, double* dst) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || !dst || which < 0 || which > 2) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostBlock& hb = h->blocks[block];
+    const size_t n = (size_t)hb.n1 * hb.n2;
+    void* src = which == SBP_FIELD_APPLY ? hb.r : hb.u[which == SBP_FIELD_CUR ? h->cur : 1 - h->cur];
+    double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
+    if (!tmp) return h->fail(SBP_E_OOM, "download staging");
+    cudaDeviceSynchronize();
+    if (h->precision == SBP_FP64) k_from_pitched<double><<<grid_for(2LL * n), 256>>>(tmp, (const double*)src, hb.n1, hb.n2, hb.pitch, 2);
+    else k_from_pitched<float><<<grid_for(2LL * n), 256>>>(tmp, (const float*)src, hb.n1, hb.n2, hb.pitch, 2);
+    cudaError_t e = cudaMemcpy(dst, tmp, 2 * n * sizeof(double), cudaMemcpyDeviceToHost);
+    h->dfree(tmp);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "download failed");
+    return SBP_OK;
+}
+
+int sbp_energy(sbp_handle* h, double dt, double* E_out) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (!E_out || !(dt > 0)) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    StepArgs a{};
+    a.cur = 1 - h->cur;          // apply A to u^n (the previous level)
+    a.with_data = 0;
+    int rc = run_operator(h, a, 1, 0);
+    if (rc != SBP_OK) return rc;
+    cudaMemset(h->d_scalar, 0, sizeof(double));
+    for (auto& hb : h->blocks) {
+        BlockDev b = make_view(h, hb);
+        const int o = h->order;
+        const double idt2 = 1.0 / (dt * dt);
+        if (h->precision == SBP_FP64) {
+            if (o == 2) k_energy<double, 2><<<1024, 256>>>(b, h->cur, idt2, h->d_scalar);
+            else if (o == 4) k_energy<double, 4><<<1024, 256>>>(b, h->cur, idt2, h->d_scalar);
+            else k_energy<double, 6><<<1024, 256>>>(b, h->cur, idt2, h->d_scalar);
+        } else {
+            if (o == 2) k_energy<float, 2><<<1024, 256>>>(b, h->cur, idt2, h->d_scalar);
+            else if (o == 4) k_energy<float, 4><<<1024, 256>>>(b, h->cur, idt2, h->d_scalar);
+            else k_energy<float, 6><<<1024, 256>>>(b, h->cur, idt2, h->d_scalar);
+        }
+    }
+    double E = 0;
+    if (cudaMemcpy(&E, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return h->fail(SBP_E_CUDA, "energy");
+    *E_out = E;
+    if (!std::isfinite(E)) return h->fail(SBP_E_UNSTABLE, "non-finite energy");
+    return SBP_OK;
+}
+
+int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (!dt_out || !(cfl > 0)) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    unsigned long long init = 0x7FF0000000000000ULL;   // +inf
+    cudaMemcpy(h->d_scalar, &init, sizeof(init), cudaMemcpyHostToDevice);
+    for (auto& hb : h->blocks) {
+        BlockDev b = make_view(h, hb);
+        const long long n = (long long)hb.n1 * hb.n2;
+        if (h->precision == SBP_FP64) k_cfl<double><<<grid_for(n), 256>>>(b, (unsigned long long*)h->d_scalar);
+        else k_cfl<float><<<grid_for(n), 256>>>(b, (unsigned long long*)h->d_scalar);
+    }
+    double r = 0;
+    if (cudaMemcpy(&r, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return h->fail(SBP_E_CUDA, "cfl");
+    *dt_out = cfl * r;
+    return SBP_OK;
+}
+
+int sbp_get_time(const sbp_handle* h, double* t_out) {
+    if (!h || !t_out) return SBP_E_INVALID_ARG;
+    *t_out = h->t;
+    return SBP_OK;
+}
+
+int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, int* order_out) {
+    if (!h) return SBP_E_INVALID_ARG;
+    long long n = 0;
+    for (auto& b : h->blocks) n += (long long)b.n1 * b.n2;
+    if (nodes_out) *nodes_out = n;
+    if (precision_out) *precision_out = h->precision;
+    if (order_out) *order_out = h->order;
+    return SBP_OK;
+}
+
+}  // extern "C"

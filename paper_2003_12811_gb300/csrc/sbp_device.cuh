@@ -1,0 +1,186 @@
+// Device-side SBP building blocks shared by the libsbp kernels: coefficient tables in constant
+// memory, 1-D first-derivative rows, fully compatible narrow second-derivative rows, and the
+// block / face views the kernels receive.  Sec. 4 (operators), 4.3-4.7 (multi-D operator).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sbpdev {
+#define SBP_TABLE static __constant__
+#include "sbp_tables.inc"
+#undef SBP_TABLE
+}  // namespace sbpdev
+
+namespace sbp {
+
+// ------------------------------------------------------------------ order traits
+template <int O> struct Ord;
+#define SBP_ORD(O)                                                                                     \
+    template <> struct Ord<O> {                                                                        \
+        static constexpr int Q = SBP##O##_Q, NB = SBP##O##_NB, NCOL = SBP##O##_NCOL,                   \
+                             NCLOS = SBP##O##_NCLOS;                                                   \
+        static __device__ __forceinline__ double hw(int i) { return sbpdev::sbp##O##_HW[i]; }          \
+        static __device__ __forceinline__ double dq(int r, int c) { return sbpdev::sbp##O##_DQ[r][c]; } \
+        static __device__ __forceinline__ double a(int k) { return sbpdev::sbp##O##_A[k]; }            \
+        static __device__ __forceinline__ int cstart(int r) { return sbpdev::sbp##O##_CLOS_START[r]; }  \
+        static __device__ __forceinline__ int cj(int t) { return sbpdev::sbp##O##_CLOS_J[t]; }          \
+        static __device__ __forceinline__ int ck(int t) { return sbpdev::sbp##O##_CLOS_K[t]; }          \
+        static __device__ __forceinline__ double cc(int t) { return sbpdev::sbp##O##_CLOS_C[t]; }      \
+    };
+SBP_ORD(2)
+SBP_ORD(4)
+SBP_ORD(6)
+#undef SBP_ORD
+
+// interior edge weights E_m(i) = sum_k e_{m,k} b_{i+k} (m = 1..Q) of the narrow operator
+template <int O> struct Edge;
+template <> struct Edge<2> {
+    template <typename T, class F> __device__ static __forceinline__ T e(int m, F B) { return SBP2_E1(B); }
+};
+template <> struct Edge<4> {
+    template <typename T, class F> __device__ static __forceinline__ T e(int m, F B) {
+        return m == 1 ? SBP4_E1(B) : SBP4_E2(B);
+    }
+};
+template <> struct Edge<6> {
+    template <typename T, class F> __device__ static __forceinline__ T e(int m, F B) {
+        return m == 1 ? SBP6_E1(B) : (m == 2 ? SBP6_E2(B) : SBP6_E3(B));
+    }
+};
+
+// lowest b offset used by E_m (E_m is evaluated at i only if i + elo(m) stays in range)
+template <int O> __host__ __device__ constexpr int edge_lo(int m) {
+    return O == 2 ? 0 : (O == 4 ? (m == 1 ? -1 : 0) : (m == 1 ? -2 : (m == 2 ? -1 : 0)));
+}
+
+// ------------------------------------------------------------------ 1-D first derivative
+// D[row][col] * h  (row-major SBP operator with mirrored right closure)
+template <int O> __device__ __forceinline__ double dcoef(int N, int row, int col) {
+    using P = Ord<O>;
+    if (row < P::NB) return (col >= 0 && col < P::NCOL) ? P::dq(row, col) : 0.0;
+    if (row >= N - P::NB) {
+        int r = N - 1 - row, c = N - 1 - col;
+        return (c >= 0 && c < P::NCOL) ? -P::dq(r, c) : 0.0;
+    }
+    int k = col - row;
+    if (k == 0 || k > P::Q || k < -P::Q) return 0.0;
+    return k > 0 ? P::a(k - 1) : -P::a(-k - 1);
+}
+
+// norm weight H_ii / h
+template <int O> __device__ __forceinline__ double hweight(int N, int i) {
+    using P = Ord<O>;
+    if (i < P::NB) return P::hw(i);
+    if (i >= N - P::NB) return P::hw(N - 1 - i);
+    return 1.0;
+}
+
+// first and last column of row `row` of D
+template <int O> __device__ __forceinline__ void drow_range(int N, int row, int& lo, int& hi) {
+    using P = Ord<O>;
+    if (row < P::NB) { lo = 0; hi = P::NCOL - 1; }
+    else if (row >= N - P::NB) { lo = N - P::NCOL; hi = N - 1; }
+    else { lo = row - P::Q; hi = row + P::Q; }
+}
+
+// sum_j D[row][j] v(j) * h, accumulated in type T
+template <int O, typename T, class F> __device__ __forceinline__ T dsum(int N, int row, F v) {
+    using P = Ord<O>;
+    T s = T(0);
+    if (row < P::NB) {
+#pragma unroll
+        for (int j = 0; j < P::NCOL; ++j) s += T(P::dq(row, j)) * v(j);
+    } else if (row >= N - P::NB) {
+        const int r = N - 1 - row;
+#pragma unroll
+        for (int j = 0; j < P::NCOL; ++j) s -= T(P::dq(r, j)) * v(N - 1 - j);
+    } else {
+#pragma unroll
+        for (int k = 1; k <= P::Q; ++k) s += T(P::a(k - 1)) * (v(row + k) - v(row - k));
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ narrow second derivative
+// Row i of h^2 D_xx^FC applied to the 2-component field with the 3 coefficient fields
+// (b0 = c_d1d1, b1 = c_d1d2 = c_d2d1, b2 = c_d2d2):
+//   r0 += D_xx(b0) u0 + D_xx(b1) u1,   r1 += D_xx(b1) u0 + D_xx(b2) u1
+template <int O, typename T, class FU0, class FU1, class FB0, class FB1, class FB2>
+__device__ __forceinline__ void dxx_vec(int N, int i, FU0 u0, FU1 u1, FB0 b0, FB1 b1, FB2 b2, T& r0, T& r1) {
+    using P = Ord<O>;
+    if (i < P::NCLOS || i >= N - P::NCLOS) {
+        const bool right = i >= N - P::NCLOS;
+        const int row = right ? N - 1 - i : i;
+        for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
+            int j = P::cj(t), k = P::ck(t);
+            if (right) { j = N - 1 - j; k = N - 1 - k; }
+            const T c = T(P::cc(t));
+            const T bb0 = b0(k), bb1 = b1(k), bb2 = b2(k);
+            const T uu0 = u0(j), uu1 = u1(j);
+            r0 += c * (bb0 * uu0 + bb1 * uu1);
+            r1 += c * (bb1 * uu0 + bb2 * uu1);
+        }
+        return;
+    }
+    const T uc0 = u0(i), uc1 = u1(i);
+#pragma unroll
+    for (int m = 1; m <= P::Q; ++m) {
+        auto B0p = [&](int k) { return b0(i + k); };
+        auto B1p = [&](int k) { return b1(i + k); };
+        auto B2p = [&](int k) { return b2(i + k); };
+        auto B0m = [&](int k) { return b0(i - m + k); };
+        auto B1m = [&](int k) { return b1(i - m + k); };
+        auto B2m = [&](int k) { return b2(i - m + k); };
+        const T e0p = Edge<O>::template e<T>(m, B0p), e1p = Edge<O>::template e<T>(m, B1p),
+                e2p = Edge<O>::template e<T>(m, B2p);
+        const T e0m = Edge<O>::template e<T>(m, B0m), e1m = Edge<O>::template e<T>(m, B1m),
+                e2m = Edge<O>::template e<T>(m, B2m);
+        const T dp0 = u0(i + m) - uc0, dp1 = u1(i + m) - uc1;
+        const T dm0 = u0(i - m) - uc0, dm1 = u1(i - m) - uc1;
+        r0 += e0p * dp0 + e1p * dp1 + e0m * dm0 + e1m * dm1;
+        r1 += e1p * dp0 + e2p * dp1 + e1m * dm0 + e2m * dm1;
+    }
+}
+
+// ------------------------------------------------------------------ views
+// Coefficient planes (10), in terms of c_ijkl (0-based indices):
+//  0 c0000  1 c0001  2 c0101 | 3 c1010  4 c1011  5 c1111 | 6 c0010  7 c0011  8 c0110  9 c0111
+// i.e. narrow x1 (c_1j1l), narrow x2 (c_2j2l), mixed c_1j2l (plane 6 + 2j + l); c_2j1l = c_1l2j.
+enum { FACE_DISP = 0, FACE_ROBIN = 1, FACE_INTF = 2 };
+
+struct FaceDev {
+    int kind, m, side, nf;
+    int nbr_block, nbr_face, reversed, pad;
+    double nu, hm0;           // outward reference normal component, H_m[0] (includes h_m)
+    const double* jhat;       // surface scale factor per face node
+    const void* ju;           // robin: J^ U (3 x nf), type T
+    const void* g;            // data: displacement g (2 x K x nf) or robin J^ g, type T
+    void* tr;                 // scratch: u1, u2, J^ tau1, J^ tau2 (4 x nf), type T
+    void* sat;                // scratch: face term (2 x nf), normal-spread amplitude (2 x nf), type T
+};
+
+struct BlockDev {
+    int n1, n2, pitch, strip;  // strip = width of the boundary strips handled by k_boundary
+    double h1, h2;
+    void* u[2];               // state buffers, 2 planes each
+    const void* c;            // 10 planes
+    const void* w;            // 1/(rho J)
+    const void* jf;           // J f harmonic planes (2 x K) or null
+    void* r;                  // operator output (apply mode), 2 planes
+    const double* X;          // coordinates (2 planes)
+    double* G;                // metric dX_I/dx_i (4 planes, [2 i + I])
+    double* J;                // Jacobian
+    FaceDev f[4];
+};
+
+struct StepArgs {
+    int cur;                  // index of the current level in BlockDev::u
+    int K;                    // number of time-basis functions
+    int with_data;            // include boundary data / forcing / sources
+    int pad;
+    double dt2;               // dt^2 (step mode)
+    double t;                 // time of the current level
+    double Tk[8];             // basis values T_k(t)
+};
+
+}  // namespace sbp

@@ -1,0 +1,734 @@
+// libsbp kernels: one leapfrog step of the SBP-SAT anisotropic elastic scheme (interior
+// stencil, boundary strips with closures and SATs, face traces, interface/boundary SAT terms,
+// point sources), the FP64 energy reduction, and the setup kernels (metric, material, CFL).
+#pragma once
+#include "sbp_device.cuh"
+
+namespace sbp {
+
+// ============================================================================ interior
+// Tile of TX x TY output nodes, 256 threads (32 x 8), every thread computes TY/8 nodes.
+// Nodes of the interior region are at least `strip` >= NCLOS, NCOL away from every face, so
+// every row uses the interior stencils and no SAT reaches them.
+//   r_j = sum_d [ D_dd^FC(c_djdl) u_l ] + D_1 (c_1j2l D_2 u_l) + D_2 (c_2j1l D_1 u_l)   (Sec. 4.6)
+// with the narrow rows written through edge weights:
+//   D_xx(b) u |_i = h^-2 sum_m E_m(i) (u_{i+m} - u_i) + E_m(i-m) (u_{i-m} - u_i).
+constexpr int ITX = 32, ITY = 16, ITHREADS = 256;
+
+template <typename T, int O> constexpr size_t interior_smem_elems() {
+    constexpr int Q = Ord<O>::Q, SX = ITX + 2 * Q, SY = ITY + 2 * Q;
+    return 2 * SY * SX + 3 * ITY * SX + 3 * SY * ITX + 4 * SY * SX + 2 * ITY * SX + 2 * SY * ITX +
+           3 * Q * ITY * (ITX + Q) + 3 * Q * (ITY + Q) * ITX;
+}
+
+template <typename T, int O, int MODE>
+__global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
+    constexpr int Q = Ord<O>::Q;
+    constexpr int TX = ITX, TY = ITY, SX = TX + 2 * Q, SY = TY + 2 * Q, EX = TX + Q, EY = TY + Q;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* su = reinterpret_cast<T*>(smem_raw);   // [2][SY][SX]
+    T* snx = su + 2 * SY * SX;                 // [3][TY][SX]
+    T* sny = snx + 3 * TY * SX;                // [3][SY][TX]
+    T* smx = sny + 3 * SY * TX;                // [4][SY][SX]
+    T* sg1 = smx + 4 * SY * SX;                // [2][TY][SX]
+    T* sg2 = sg1 + 2 * TY * SX;                // [2][SY][TX]
+    T* sex = sg2 + 2 * SY * TX;                // [3][Q][TY][EX]   E_m at i = ii - Q
+    T* sey = sex + 3 * Q * TY * EX;            // [3][Q][EY][TX]   E_m at j = jj - Q
+
+    const int S = B.strip;
+    const int n1 = B.n1, n2 = B.n2, P = B.pitch;
+    const int lim1 = n1 - S, lim2 = n2 - S;
+    const int x0 = S + blockIdx.x * TX, y0 = S + blockIdx.y * TY;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const size_t plane = (size_t)n2 * P;
+    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+
+    auto load = [&](T* dst, const T* __restrict__ src, int rows, int cols, int gy0, int gx0) {
+        for (int idx = tid; idx < rows * cols; idx += ITHREADS) {
+            const int r = idx / cols, c = idx - r * cols;
+            const int gy = gy0 + r, gx = gx0 + c;
+            dst[idx] = (gy < n2 && gx < n1) ? __ldg(src + (size_t)gy * P + gx) : T(0);
+        }
+    };
+    load(su, U, SY, SX, y0 - Q, x0 - Q);
+    load(su + SY * SX, U + plane, SY, SX, y0 - Q, x0 - Q);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) load(snx + f * TY * SX, C + f * plane, TY, SX, y0, x0 - Q);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) load(sny + f * SY * TX, C + (3 + f) * plane, SY, TX, y0 - Q, x0);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) load(smx + f * SY * SX, C + (6 + f) * plane, SY, SX, y0 - Q, x0 - Q);
+    __syncthreads();
+
+    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    // mixed fluxes g1_j = c_1j2l D_2 u_l on tile rows x (tile cols + x-halo)
+    for (int idx = tid; idx < TY * SX; idx += ITHREADS) {
+        const int r = idx / SX, c = idx - r * SX;
+        const T* p0 = su + (r + Q) * SX + c;
+        const T* p1 = p0 + SY * SX;
+        T d0 = T(0), d1 = T(0);
+#pragma unroll
+        for (int k = 1; k <= Q; ++k) {
+            const T ak = T(Ord<O>::a(k - 1));
+            d0 += ak * (p0[k * SX] - p0[-k * SX]);
+            d1 += ak * (p1[k * SX] - p1[-k * SX]);
+        }
+        d0 *= ih2;
+        d1 *= ih2;
+        const int mi = (r + Q) * SX + c;
+        const T m6 = smx[mi], m7 = smx[SY * SX + mi], m8 = smx[2 * SY * SX + mi], m9 = smx[3 * SY * SX + mi];
+        sg1[r * SX + c] = m6 * d0 + m7 * d1;
+        sg1[TY * SX + r * SX + c] = m8 * d0 + m9 * d1;
+    }
+    // mixed fluxes g2_j = c_2j1l D_1 u_l = c_1l2j D_1 u_l on (tile rows + y-halo) x tile cols
+    for (int idx = tid; idx < SY * TX; idx += ITHREADS) {
+        const int r = idx / TX, c = idx - r * TX;
+        const T* p0 = su + r * SX + c + Q;
+        const T* p1 = p0 + SY * SX;
+        T d0 = T(0), d1 = T(0);
+#pragma unroll
+        for (int k = 1; k <= Q; ++k) {
+            const T ak = T(Ord<O>::a(k - 1));
+            d0 += ak * (p0[k] - p0[-k]);
+            d1 += ak * (p1[k] - p1[-k]);
+        }
+        d0 *= ih1;
+        d1 *= ih1;
+        const int mi = r * SX + c + Q;
+        const T m6 = smx[mi], m7 = smx[SY * SX + mi], m8 = smx[2 * SY * SX + mi], m9 = smx[3 * SY * SX + mi];
+        sg2[r * TX + c] = m6 * d0 + m8 * d1;
+        sg2[SY * TX + r * TX + c] = m7 * d0 + m9 * d1;
+    }
+    // edge weights along x1 at i in [-Q, TX)
+    for (int idx = tid; idx < 3 * TY * EX; idx += ITHREADS) {
+        const int f = idx / (TY * EX);
+        const int rem = idx - f * TY * EX;
+        const int r = rem / EX, ii = rem - r * EX;
+        const int i = ii - Q;
+        const T* bl = snx + f * TY * SX + r * SX + (i + Q);
+        auto Bf = [&](int k) { return bl[k]; };
+#pragma unroll
+        for (int m = 1; m <= Q; ++m)
+            sex[((f * Q + (m - 1)) * TY + r) * EX + ii] = (i + Q + edge_lo<O>(m) >= 0) ? Edge<O>::template e<T>(m, Bf) : T(0);
+    }
+    // edge weights along x2 at j in [-Q, TY)
+    for (int idx = tid; idx < 3 * EY * TX; idx += ITHREADS) {
+        const int f = idx / (EY * TX);
+        const int rem = idx - f * EY * TX;
+        const int jj = rem / TX, c = rem - jj * TX;
+        const int j = jj - Q;
+        const T* bl = sny + f * SY * TX + (j + Q) * TX + c;
+        auto Bf = [&](int k) { return bl[k * TX]; };
+#pragma unroll
+        for (int m = 1; m <= Q; ++m)
+            sey[((f * Q + (m - 1)) * EY + jj) * TX + c] = (j + Q + edge_lo<O>(m) >= 0) ? Edge<O>::template e<T>(m, Bf) : T(0);
+    }
+    __syncthreads();
+
+    const T* __restrict__ Wp = reinterpret_cast<const T*>(B.w);
+#pragma unroll
+    for (int rr = 0; rr < TY / 8; ++rr) {
+        const int r = threadIdx.y + 8 * rr, c = threadIdx.x;
+        const int gx = x0 + c, gy = y0 + r;
+        if (gx >= lim1 || gy >= lim2) continue;
+        const T* u0 = su + (r + Q) * SX + (c + Q);
+        const T* u1 = u0 + SY * SX;
+        const T uc0 = u0[0], uc1 = u1[0];
+        T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0);
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            const T* ex0 = sex + ((0 * Q + (m - 1)) * TY + r) * EX + (c + Q);
+            const T* ex1 = ex0 + Q * TY * EX;
+            const T* ex2 = ex1 + Q * TY * EX;
+            const T dp0 = u0[m] - uc0, dp1 = u1[m] - uc1, dm0 = u0[-m] - uc0, dm1 = u1[-m] - uc1;
+            rx0 += ex0[0] * dp0 + ex1[0] * dp1 + ex0[-m] * dm0 + ex1[-m] * dm1;
+            rx1 += ex1[0] * dp0 + ex2[0] * dp1 + ex1[-m] * dm0 + ex2[-m] * dm1;
+            const T* ey0 = sey + ((0 * Q + (m - 1)) * EY + (r + Q)) * TX + c;
+            const T* ey1 = ey0 + Q * EY * TX;
+            const T* ey2 = ey1 + Q * EY * TX;
+            const T qp0 = u0[m * SX] - uc0, qp1 = u1[m * SX] - uc1, qm0 = u0[-m * SX] - uc0, qm1 = u1[-m * SX] - uc1;
+            ry0 += ey0[0] * qp0 + ey1[0] * qp1 + ey0[-m * TX] * qm0 + ey1[-m * TX] * qm1;
+            ry1 += ey1[0] * qp0 + ey2[0] * qp1 + ey1[-m * TX] * qm0 + ey2[-m * TX] * qm1;
+        }
+        T r0 = rx0 * ih1 * ih1 + ry0 * ih2 * ih2;
+        T r1 = rx1 * ih1 * ih1 + ry1 * ih2 * ih2;
+        const T* g10 = sg1 + r * SX + (c + Q);
+        const T* g11 = g10 + TY * SX;
+        const T* g20 = sg2 + (r + Q) * TX + c;
+        const T* g21 = g20 + SY * TX;
+        T m10 = T(0), m11 = T(0), m20 = T(0), m21 = T(0);
+#pragma unroll
+        for (int k = 1; k <= Q; ++k) {
+            const T ak = T(Ord<O>::a(k - 1));
+            m10 += ak * (g10[k] - g10[-k]);
+            m11 += ak * (g11[k] - g11[-k]);
+            m20 += ak * (g20[k * TX] - g20[-k * TX]);
+            m21 += ak * (g21[k * TX] - g21[-k * TX]);
+        }
+        r0 += m10 * ih1 + m20 * ih2;
+        r1 += m11 * ih1 + m21 * ih2;
+        const size_t gi = (size_t)gy * P + gx;
+        if (a.with_data && B.jf) {
+            const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
+            for (int k = 0; k < a.K; ++k) {
+                r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
+                r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
+            }
+        }
+        if (MODE == 0) {
+            T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+            const T wv = Wp[gi], dt2 = T(a.dt2);
+            Un[gi] = T(2) * uc0 - Un[gi] + dt2 * wv * r0;
+            Un[gi + plane] = T(2) * uc1 - Un[gi + plane] + dt2 * wv * r1;
+        } else {
+            T* __restrict__ R = reinterpret_cast<T*>(B.r);
+            R[gi] = r0;
+            R[gi + plane] = r1;
+        }
+    }
+}
+
+// ============================================================================ boundary strips
+// Every node within `strip` of a face: generic rows (closures from the tables), mixed terms
+// with the boundary rows of D, plus the SAT contributions prepared by k_face_sat:
+//   at depth d < NCOL from face f:  D_m[face row][i_m] / H_m[i_m] * a_J(s)   (D_m^T spread)
+//   on the face itself:             the face term of k_face_sat
+template <typename T, int O, int MODE>
+__global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
+    const int n1 = B.n1, n2 = B.n2, P = B.pitch, S = B.strip;
+    const long long nstrip = (long long)n1 * n2 - (long long)(n1 - 2 * S) * (n2 - 2 * S);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nstrip) return;
+    int i1, i2;
+    {
+        const long long top = (long long)S * n1;
+        if (t < top) { i2 = (int)(t / n1); i1 = (int)(t - (long long)i2 * n1); }
+        else if (t < 2 * top) { long long u = t - top; i2 = n2 - S + (int)(u / n1); i1 = (int)(u - (long long)(i2 - n2 + S) * n1); }
+        else {
+            long long u = t - 2 * top;
+            const int row = (int)(u / (2 * S)), k = (int)(u - (long long)row * 2 * S);
+            i2 = S + row;
+            i1 = k < S ? k : n1 - 2 * S + k;
+        }
+    }
+    const size_t plane = (size_t)n2 * P;
+    const T* __restrict__ U0 = reinterpret_cast<const T*>(B.u[a.cur]);
+    const T* __restrict__ U1 = U0 + plane;
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    const size_t row2 = (size_t)i2 * P;
+
+    // narrow terms along x1 (line i2) and x2 (column i1)
+    T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0);
+    dxx_vec<O, T>(n1, i1,
+                  [&](int j) { return __ldg(U0 + row2 + j); }, [&](int j) { return __ldg(U1 + row2 + j); },
+                  [&](int k) { return __ldg(C + row2 + k); }, [&](int k) { return __ldg(C + plane + row2 + k); },
+                  [&](int k) { return __ldg(C + 2 * plane + row2 + k); }, rx0, rx1);
+    dxx_vec<O, T>(n2, i2,
+                  [&](int j) { return __ldg(U0 + (size_t)j * P + i1); }, [&](int j) { return __ldg(U1 + (size_t)j * P + i1); },
+                  [&](int k) { return __ldg(C + 3 * plane + (size_t)k * P + i1); },
+                  [&](int k) { return __ldg(C + 4 * plane + (size_t)k * P + i1); },
+                  [&](int k) { return __ldg(C + 5 * plane + (size_t)k * P + i1); }, ry0, ry1);
+    T r0 = rx0 * ih1 * ih1 + ry0 * ih2 * ih2;
+    T r1 = rx1 * ih1 * ih1 + ry1 * ih2 * ih2;
+
+    // mixed: D_1 (c_1j2l D_2 u_l) + D_2 (c_2j1l D_1 u_l)
+    {
+        int lo, hi;
+        drow_range<O>(n1, i1, lo, hi);
+        T s0 = T(0), s1 = T(0);
+        for (int aa = lo; aa <= hi; ++aa) {
+            const T d = T(dcoef<O>(n1, i1, aa));
+            if (d == T(0)) continue;
+            const T du0 = dsum<O, T>(n2, i2, [&](int bb) { return __ldg(U0 + (size_t)bb * P + aa); }) * ih2;
+            const T du1 = dsum<O, T>(n2, i2, [&](int bb) { return __ldg(U1 + (size_t)bb * P + aa); }) * ih2;
+            const size_t gi = row2 + aa;
+            const T m6 = __ldg(C + 6 * plane + gi), m7 = __ldg(C + 7 * plane + gi),
+                    m8 = __ldg(C + 8 * plane + gi), m9 = __ldg(C + 9 * plane + gi);
+            s0 += d * (m6 * du0 + m7 * du1);
+            s1 += d * (m8 * du0 + m9 * du1);
+        }
+        r0 += s0 * ih1;
+        r1 += s1 * ih1;
+        drow_range<O>(n2, i2, lo, hi);
+        s0 = T(0);
+        s1 = T(0);
+        for (int bb = lo; bb <= hi; ++bb) {
+            const T d = T(dcoef<O>(n2, i2, bb));
+            if (d == T(0)) continue;
+            const size_t rowb = (size_t)bb * P;
+            const T du0 = dsum<O, T>(n1, i1, [&](int aa) { return __ldg(U0 + rowb + aa); }) * ih1;
+            const T du1 = dsum<O, T>(n1, i1, [&](int aa) { return __ldg(U1 + rowb + aa); }) * ih1;
+            const size_t gi = rowb + i1;
+            const T m6 = __ldg(C + 6 * plane + gi), m7 = __ldg(C + 7 * plane + gi),
+                    m8 = __ldg(C + 8 * plane + gi), m9 = __ldg(C + 9 * plane + gi);
+            s0 += d * (m6 * du0 + m8 * du1);
+            s1 += d * (m7 * du0 + m9 * du1);
+        }
+        r0 += s0 * ih2;
+        r1 += s1 * ih2;
+    }
+
+    // SAT contributions
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const FaceDev& F = B.f[f];
+        const int m = F.m;
+        const int im = m == 0 ? i1 : i2, Nm = m == 0 ? n1 : n2;
+        const int d = F.side ? Nm - 1 - im : im;
+        if (d >= Ord<O>::NCOL) continue;
+        const int s = m == 0 ? i2 : i1;
+        const T* __restrict__ sat = reinterpret_cast<const T*>(F.sat);
+        const int nf = F.nf;
+        const double hm = m == 0 ? B.h1 : B.h2;
+        const T fac = T(dcoef<O>(Nm, F.side ? Nm - 1 : 0, im) / (hm * hm * hweight<O>(Nm, im)));
+        r0 += fac * sat[2 * nf + s];
+        r1 += fac * sat[3 * nf + s];
+        if (d == 0) {
+            r0 += sat[s];
+            r1 += sat[nf + s];
+        }
+    }
+    const size_t gi = row2 + i1;
+    if (a.with_data && B.jf) {
+        const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
+        for (int k = 0; k < a.K; ++k) {
+            r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
+            r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
+        }
+    }
+    if (MODE == 0) {
+        T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = T(a.dt2);
+        Un[gi] = T(2) * U0[gi] - Un[gi] + dt2 * wv * r0;
+        Un[gi + plane] = T(2) * U1[gi] - Un[gi + plane] + dt2 * wv * r1;
+    } else {
+        T* __restrict__ R = reinterpret_cast<T*>(B.r);
+        R[gi] = r0;
+        R[gi + plane] = r1;
+    }
+}
+
+// ============================================================================ faces
+struct FaceRef {
+    int block, face, start, nf;
+};
+
+__device__ __forceinline__ int find_face(const FaceRef* refs, int nrefs, int t) {
+    int k = 0;
+    while (k + 1 < nrefs && t >= refs[k + 1].start) ++k;
+    return k;
+}
+
+// c planes at a face node: narrow of the normal direction m (c_mJmL) and the mixed c_mJtL
+__device__ __forceinline__ int plane_nn(int m, int J, int L) { return 3 * m + J + L; }
+__device__ __forceinline__ int plane_nt(int m, int J, int L) { return m == 0 ? 6 + 2 * J + L : 6 + 2 * L + J; }
+
+// trace u_L and J^ tau_J = nu_i c_iJkL D_k u_L (eq. n-C_conversion) at every face node
+template <typename T, int O>
+__global__ void k_face_trace(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
+                             int total, int cur) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const FaceRef fr = refs[find_face(refs, nrefs, t)];
+    const int s = t - fr.start;
+    const BlockDev& B = blocks[fr.block];
+    const FaceDev& F = B.f[fr.face];
+    const int m = F.m, P = B.pitch;
+    const int n1 = B.n1, n2 = B.n2;
+    const size_t plane = (size_t)n2 * P;
+    const T* __restrict__ U0 = reinterpret_cast<const T*>(B.u[cur]);
+    const T* __restrict__ U1 = U0 + plane;
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+    int i1, i2;
+    if (m == 0) { i1 = F.side ? n1 - 1 : 0; i2 = s; }
+    else { i2 = F.side ? n2 - 1 : 0; i1 = s; }
+    const size_t gi = (size_t)i2 * P + i1;
+    T dn0, dn1, dt0, dt1;
+    if (m == 0) {
+        const size_t row = (size_t)i2 * P;
+        dn0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(1.0 / B.h1);
+        dn1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(1.0 / B.h1);
+        dt0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
+        dt1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
+    } else {
+        const size_t row = (size_t)i2 * P;
+        dn0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
+        dn1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
+        dt0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(1.0 / B.h1);
+        dt1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(1.0 / B.h1);
+    }
+    const T nu = T(F.nu);
+    T tau[2];
+#pragma unroll
+    for (int J = 0; J < 2; ++J) {
+        tau[J] = nu * (C[plane_nn(m, J, 0) * plane + gi] * dn0 + C[plane_nn(m, J, 1) * plane + gi] * dn1 +
+                       C[plane_nt(m, J, 0) * plane + gi] * dt0 + C[plane_nt(m, J, 1) * plane + gi] * dt1);
+    }
+    T* tr = reinterpret_cast<T*>(F.tr);
+    const int nf = F.nf;
+    tr[s] = U0[gi];
+    tr[nf + s] = U1[gi];
+    tr[2 * nf + s] = tau[0];
+    tr[3 * nf + s] = tau[1];
+}
+
+// value of c_{plane} at tangential face index s of face F of block B
+template <typename T>
+__device__ __forceinline__ T face_c(const BlockDev& B, const FaceDev& F, int pl, int s) {
+    int i1, i2;
+    if (F.m == 0) { i1 = F.side ? B.n1 - 1 : 0; i2 = s; }
+    else { i2 = F.side ? B.n2 - 1 : 0; i1 = s; }
+    return reinterpret_cast<const T*>(B.c)[(size_t)pl * B.n2 * B.pitch + (size_t)i2 * B.pitch + i1];
+}
+
+// jump w_L at face node s (displacement: u - g(t); interface: u - v)
+template <typename T>
+__device__ __forceinline__ void face_jump(const BlockDev* blocks, const BlockDev& B, const FaceDev& F, int s,
+                                          const StepArgs& a, T& w0, T& w1) {
+    const T* tr = reinterpret_cast<const T*>(F.tr);
+    const int nf = F.nf;
+    w0 = tr[s];
+    w1 = tr[nf + s];
+    if (F.kind == FACE_DISP) {
+        if (a.with_data && F.g) {
+            const T* g = reinterpret_cast<const T*>(F.g);
+            for (int k = 0; k < a.K; ++k) {
+                w0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
+                w1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
+            }
+        }
+    } else if (F.kind == FACE_INTF) {
+        const BlockDev& V = blocks[F.nbr_block];
+        const FaceDev& FV = V.f[F.nbr_face];
+        const int sv = F.reversed ? nf - 1 - s : s;
+        const T* trv = reinterpret_cast<const T*>(FV.tr);
+        w0 -= trv[sv];
+        w1 -= trv[nf + sv];
+    }
+}
+
+// SAT terms of every face node (Sec. 5.1 eq. sat_traction, Sec. 5.2 eq. dirichlet_ansatz with
+// Z of Theorem 3, Sec. 6 eq. scheme_interface with V = Theta = 0), using
+// J^ Z_JL = beta d / h1 * c_mJmL (boundary) and beta d / 4 (c^u_mJmL / h1^u + c^v / h1^v) (interface).
+template <typename T, int O>
+__global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
+                           int total, StepArgs a, double beta) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const FaceRef fr = refs[find_face(refs, nrefs, t)];
+    const int s = t - fr.start;
+    const BlockDev& B = blocks[fr.block];
+    const FaceDev& F = B.f[fr.face];
+    const int m = F.m, nf = F.nf;
+    const T* tr = reinterpret_cast<const T*>(F.tr);
+    T* sat = reinterpret_cast<T*>(F.sat);
+    const T inv_h0 = T(1.0 / F.hm0);
+    const T nu = T(F.nu);
+    const double dd = 2.0;   // spatial dimension d
+    if (F.kind == FACE_ROBIN) {
+        T u0 = tr[s], u1 = tr[nf + s];
+        T f0 = tr[2 * nf + s], f1 = tr[3 * nf + s];
+        if (F.ju) {
+            const T* ju = reinterpret_cast<const T*>(F.ju);
+            const T a11 = ju[s], a12 = ju[nf + s], a22 = ju[2 * nf + s];
+            f0 += a11 * u0 + a12 * u1;
+            f1 += a12 * u0 + a22 * u1;
+        }
+        if (a.with_data && F.g) {
+            const T* g = reinterpret_cast<const T*>(F.g);
+            for (int k = 0; k < a.K; ++k) {
+                f0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
+                f1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
+            }
+        }
+        sat[s] = -inv_h0 * f0;
+        sat[nf + s] = -inv_h0 * f1;
+        sat[2 * nf + s] = T(0);
+        sat[3 * nf + s] = T(0);
+        return;
+    }
+    const bool intf = F.kind == FACE_INTF;
+    const T half = intf ? T(0.5) : T(1);
+    T w0, w1;
+    face_jump<T>(blocks, B, F, s, a, w0, w1);
+    // penalty J^ Z
+    const T c00 = face_c<T>(B, F, plane_nn(m, 0, 0), s), c01 = face_c<T>(B, F, plane_nn(m, 0, 1), s),
+            c11 = face_c<T>(B, F, plane_nn(m, 1, 1), s);
+    T z00, z01, z11;
+    if (!intf) {
+        const T k = T(beta * dd / F.hm0);
+        z00 = k * c00; z01 = k * c01; z11 = k * c11;
+    } else {
+        const BlockDev& V = blocks[F.nbr_block];
+        const FaceDev& FV = V.f[F.nbr_face];
+        const int sv = F.reversed ? nf - 1 - s : s;
+        const int mv = FV.m;
+        const T ku = T(beta * dd / 4.0 / F.hm0), kv = T(beta * dd / 4.0 / FV.hm0);
+        z00 = ku * c00 + kv * face_c<T>(V, FV, plane_nn(mv, 0, 0), sv);
+        z01 = ku * c01 + kv * face_c<T>(V, FV, plane_nn(mv, 0, 1), sv);
+        z11 = ku * c11 + kv * face_c<T>(V, FV, plane_nn(mv, 1, 1), sv);
+    }
+    // normal-spread amplitude a_J = half * nu c_mJmL w_L
+    sat[2 * nf + s] = half * nu * (c00 * w0 + c01 * w1);
+    sat[3 * nf + s] = half * nu * (c01 * w0 + c11 * w1);
+    // tangential transpose term (1/H_t(s)) sum_s' D_t[s'][s] H_t(s') b_J(s'),  b_J = nu c_mLtJ w_L
+    const int Nt = nf;
+    const double ht = m == 0 ? B.h2 : B.h1;
+    int lo = s - Ord<O>::Q, hi = s + Ord<O>::Q;
+    if (s < Ord<O>::NCOL) lo = 0;
+    if (s >= Nt - Ord<O>::NCOL) hi = Nt - 1;
+    if (lo < 0) lo = 0;
+    if (hi > Nt - 1) hi = Nt - 1;
+    T tt0 = T(0), tt1 = T(0);
+    for (int sp = lo; sp <= hi; ++sp) {
+        const double dc = dcoef<O>(Nt, sp, s);
+        if (dc == 0.0) continue;
+        T v0, v1;
+        face_jump<T>(blocks, B, F, sp, a, v0, v1);
+        const T b0 = nu * (face_c<T>(B, F, plane_nt(m, 0, 0), sp) * v0 + face_c<T>(B, F, plane_nt(m, 1, 0), sp) * v1);
+        const T b1 = nu * (face_c<T>(B, F, plane_nt(m, 0, 1), sp) * v0 + face_c<T>(B, F, plane_nt(m, 1, 1), sp) * v1);
+        const T wgt = T(dc * hweight<O>(Nt, sp));
+        tt0 += wgt * b0;
+        tt1 += wgt * b1;
+    }
+    const T tfac = T(1.0 / (ht * hweight<O>(Nt, s)));
+    T f0 = half * tt0 * tfac - (z00 * w0 + z01 * w1);
+    T f1 = half * tt1 * tfac - (z01 * w0 + z11 * w1);
+    if (intf) {
+        const BlockDev& V = blocks[F.nbr_block];
+        const FaceDev& FV = V.f[F.nbr_face];
+        const int sv = F.reversed ? nf - 1 - s : s;
+        const T* trv = reinterpret_cast<const T*>(FV.tr);
+        f0 -= T(0.5) * (tr[2 * nf + s] + trv[2 * nf + sv]);
+        f1 -= T(0.5) * (tr[3 * nf + s] + trv[3 * nf + sv]);
+    }
+    sat[s] = inv_h0 * f0;
+    sat[nf + s] = inv_h0 * f1;
+}
+
+// ============================================================================ point sources
+struct SrcNode {
+    int block, src;
+    long long gi;             // node offset in the planes
+    double wt0, wt1;          // dir_J * amplitude * w1 w2 / H
+};
+struct SrcParam {
+    double alpha_p, t0;
+};
+
+template <typename T, int MODE>
+__global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __restrict__ nodes, int nnodes,
+                          const SrcParam* __restrict__ par, StepArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnodes || !a.with_data) return;
+    const SrcNode nd = nodes[t];
+    const SrcParam p = par[nd.src];
+    const double x = 3.14159265358979323846 * p.alpha_p * (a.t - p.t0);
+    const double Wt = (1.0 - 2.0 * x * x) * exp(-x * x);        // Ricker wavelet (Sec. 7.4)
+    const BlockDev& B = blocks[nd.block];
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    if (MODE == 0) {
+        T* Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+        const double fac = a.dt2 * (double)reinterpret_cast<const T*>(B.w)[nd.gi] * Wt;
+        atomicAdd(Un + nd.gi, T(fac * nd.wt0));
+        atomicAdd(Un + plane + nd.gi, T(fac * nd.wt1));
+    } else {
+        T* R = reinterpret_cast<T*>(B.r);
+        atomicAdd(R + nd.gi, T(Wt * nd.wt0));
+        atomicAdd(R + plane + nd.gi, T(Wt * nd.wt1));
+    }
+}
+
+// ============================================================================ energy
+// E = 1/2 sum H/w |u1 - u0|^2 / dt^2 - 1/2 sum H u1 . r   (FP64 accumulation)
+template <typename T, int O>
+__global__ void k_energy(BlockDev B, int cur, double inv_dt2, double* out) {
+    const long long n = (long long)B.n1 * B.n2;
+    double acc = 0.0;
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    const T* U1 = reinterpret_cast<const T*>(B.u[cur]);
+    const T* U0 = reinterpret_cast<const T*>(B.u[1 - cur]);
+    const T* R = reinterpret_cast<const T*>(B.r);
+    const T* Wp = reinterpret_cast<const T*>(B.w);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+        const size_t gi = (size_t)i2 * B.pitch + i1;
+        const double H = B.h1 * hweight<O>(B.n1, i1) * B.h2 * hweight<O>(B.n2, i2);
+        const double d0 = (double)U1[gi] - (double)U0[gi], d1 = (double)U1[gi + plane] - (double)U0[gi + plane];
+        const double mass = H / (double)Wp[gi];
+        acc += 0.5 * mass * (d0 * d0 + d1 * d1) * inv_dt2 -
+               0.5 * H * ((double)U1[gi] * (double)R[gi] + (double)U1[gi + plane] * (double)R[gi + plane]);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+
+// ============================================================================ setup
+// numerical metric (Sec. 3.3): G[2i+I] = D_i X_I, J = det; flags J <= 0
+template <int O>
+__global__ void k_metric(BlockDev B, int* flag) {
+    const long long n = (long long)B.n1 * B.n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+    const size_t P = B.pitch, plane = (size_t)B.n2 * P, gi = (size_t)i2 * P + i1;
+    const double* X0 = B.X;
+    const double* X1 = B.X + plane;
+    const double g00 = dsum<O, double>(B.n1, i1, [&](int j) { return X0[(size_t)i2 * P + j]; }) / B.h1;
+    const double g01 = dsum<O, double>(B.n1, i1, [&](int j) { return X1[(size_t)i2 * P + j]; }) / B.h1;
+    const double g10 = dsum<O, double>(B.n2, i2, [&](int j) { return X0[(size_t)j * P + i1]; }) / B.h2;
+    const double g11 = dsum<O, double>(B.n2, i2, [&](int j) { return X1[(size_t)j * P + i1]; }) / B.h2;
+    B.G[gi] = g00;
+    B.G[plane + gi] = g01;
+    B.G[2 * plane + gi] = g10;
+    B.G[3 * plane + gi] = g11;
+    const double J = g00 * g11 - g01 * g10;
+    B.J[gi] = J;
+    if (!(J > 0.0)) atomicOr(flag, 1);
+}
+
+// transformed stiffness c_ijkl = F_Ii J C_IjKl F_Kk and w = 1/(rho J) (eq. transf_density_stiffness)
+template <typename T>
+__global__ void k_material(BlockDev B, const double* __restrict__ rho, const double* __restrict__ Cp) {
+    const long long n = (long long)B.n1 * B.n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+    const size_t P = B.pitch, plane = (size_t)B.n2 * P, gi = (size_t)i2 * P + i1;
+    const double g00 = B.G[gi], g01 = B.G[plane + gi], g10 = B.G[2 * plane + gi], g11 = B.G[3 * plane + gi];
+    const double J = B.J[gi];
+    double F[2][2];   // F[I][i]
+    F[0][0] = g11 / J;
+    F[0][1] = -g01 / J;
+    F[1][0] = -g10 / J;
+    F[1][1] = g00 / J;
+    // pair matrix M[p][q], p = 2I + J, upper triangle in 10 planes (host layout, n = n1*n2)
+    double M[4][4];
+    int idx = 0;
+    for (int p = 0; p < 4; ++p)
+        for (int q = p; q < 4; ++q) {
+            M[p][q] = M[q][p] = Cp[(size_t)idx * n + t];
+            ++idx;
+        }
+    auto cijkl = [&](int i, int j, int k, int l) {
+        double s = 0.0;
+        for (int I = 0; I < 2; ++I)
+            for (int K = 0; K < 2; ++K) s = s + F[I][i] * M[2 * I + j][2 * K + l] * F[K][k];
+        return J * s;
+    };
+    T* c = reinterpret_cast<T*>(const_cast<void*>(B.c));
+    const int ijkl[10][4] = {{0, 0, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}, {1, 0, 1, 0}, {1, 0, 1, 1},
+                             {1, 1, 1, 1}, {0, 0, 1, 0}, {0, 0, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
+    for (int pl = 0; pl < 10; ++pl)
+        c[pl * plane + gi] = T(cijkl(ijkl[pl][0], ijkl[pl][1], ijkl[pl][2], ijkl[pl][3]));
+    reinterpret_cast<T*>(const_cast<void*>(B.w))[gi] = T(1.0 / (rho[t] * J));
+}
+
+// face scale factor J^ = |a_t|, a_t = dX/dx_t on the face (eq. surfj_app_2d)
+__global__ void k_face_jhat(BlockDev B, int face, double* jhat) {
+    const FaceDev& F = B.f[face];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= F.nf) return;
+    int i1, i2;
+    if (F.m == 0) { i1 = F.side ? B.n1 - 1 : 0; i2 = s; }
+    else { i2 = F.side ? B.n2 - 1 : 0; i1 = s; }
+    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
+    const int tdir = 1 - F.m;
+    const double a0 = B.G[(2 * tdir) * plane + gi], a1 = B.G[(2 * tdir + 1) * plane + gi];
+    jhat[s] = sqrt(a0 * a0 + a1 * a1);
+}
+
+// out[k*n + s] = T(scale[s] * in[k*n + s])   (scale may be null)
+template <typename T>
+__global__ void k_scale_copy(T* out, const double* __restrict__ in, const double* __restrict__ scale, int n, int planes) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * planes) return;
+    const int s = (int)(t % n);
+    out[t] = T(scale ? scale[s] * in[t] : in[t]);
+}
+
+// pitched plane <-> dense double (optionally multiplied by the block's J)
+template <typename T>
+__global__ void k_to_pitched(T* dst, const double* __restrict__ src, int n1, int n2, int pitch, int planes,
+                             const double* __restrict__ Jmul) {
+    const long long n = (long long)n1 * n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * planes) return;
+    const int p = (int)(t / n);
+    const long long node = t - (long long)p * n;
+    const int i2 = (int)(node / n1), i1 = (int)(node - (long long)i2 * n1);
+    const size_t gi = (size_t)i2 * pitch + i1;
+    double v = src[t];
+    if (Jmul) v *= Jmul[gi];
+    dst[(size_t)p * n2 * pitch + gi] = T(v);
+}
+
+template <typename T>
+__global__ void k_from_pitched(double* dst, const T* __restrict__ src, int n1, int n2, int pitch, int planes) {
+    const long long n = (long long)n1 * n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * planes) return;
+    const int p = (int)(t / n);
+    const long long node = t - (long long)p * n;
+    const int i2 = (int)(node / n1), i1 = (int)(node - (long long)i2 * n1);
+    dst[t] = (double)src[(size_t)p * n2 * pitch + (size_t)i2 * pitch + i1];
+}
+
+// CFL (Sec. 7): per node min(h1,h2) / v_max with v_max^2 = max_theta lambda_max(Gamma(theta)) / (rho J),
+// Gamma_jl = xi_i c_ijkl xi_k; 720 samples in [0, pi) then 40 golden-section steps around the best.
+template <typename T>
+__device__ __forceinline__ double christoffel_lmax(const double* c, double th) {
+    const double x1 = cos(th), x2 = sin(th);
+    const double g00 = x1 * x1 * c[0] + 2.0 * x1 * x2 * c[6] + x2 * x2 * c[3];
+    const double g01 = x1 * x1 * c[1] + x1 * x2 * (c[7] + c[8]) + x2 * x2 * c[4];
+    const double g11 = x1 * x1 * c[2] + 2.0 * x1 * x2 * c[9] + x2 * x2 * c[5];
+    const double hm = 0.5 * (g00 - g11);
+    return 0.5 * (g00 + g11) + sqrt(hm * hm + g01 * g01);
+}
+
+template <typename T>
+__global__ void k_cfl(BlockDev B, unsigned long long* out_bits) {
+    const long long n = (long long)B.n1 * B.n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
+    double c[10];
+    const T* C = reinterpret_cast<const T*>(B.c);
+    for (int p = 0; p < 10; ++p) c[p] = (double)C[p * plane + gi];
+    const double rhoJ = 1.0 / (double)reinterpret_cast<const T*>(B.w)[gi];
+    const double PI = 3.14159265358979323846;
+    double best = -1.0, bth = 0.0;
+    for (int k = 0; k < 720; ++k) {
+        const double th = k * PI / 720;
+        const double l = christoffel_lmax<T>(c, th);
+        if (l > best) { best = l; bth = th; }
+    }
+    double lo = bth - PI / 720, hi = bth + PI / 720;
+    const double gr = (sqrt(5.0) - 1.0) / 2.0;
+    double cc = hi - gr * (hi - lo), dd = lo + gr * (hi - lo);
+    double fc = christoffel_lmax<T>(c, cc), fd = christoffel_lmax<T>(c, dd);
+    for (int it = 0; it < 40; ++it) {
+        if (fc > fd) hi = dd; else lo = cc;
+        cc = hi - gr * (hi - lo);
+        dd = lo + gr * (hi - lo);
+        fc = christoffel_lmax<T>(c, cc);
+        fd = christoffel_lmax<T>(c, dd);
+    }
+    const double lmax = fmax(fmax(fc, fd), best);
+    const double v = sqrt(lmax / rhoJ);
+    const double hmin = fmin(B.h1, B.h2);
+    const double r = hmin / v;
+    atomicMin(out_bits, (unsigned long long)__double_as_longlong(r));
+}
+
+}  // namespace sbp

@@ -457,12 +457,12 @@ def config3(n1: int = 4001, n2: int = 2001, order: int = 6, window=None,
         _remap_window_interfaces(blocks, sorted(window))
     srcs = []
     if window is None or 1 in window:
-        bidx = 0 if window is None else sorted(window).index(1)
+        bidx = 1 if window is None else sorted(window).index(1)
         xr = (0.5, 1.0)
         if window is not None:   # re-express the reference position in the crop
             lo1, hi1, lo2, hi2 = window[1]
             xr = ((0.5 * (n1 - 1) - lo1) / (n1 - 1), ((n2 - 1) - lo2) / (n2 - 1))
-        srcs.append(PointSource(block=bidx if window is None else bidx, x_ref=xr, direction=(0.0, -1.0),
+        srcs.append(PointSource(block=bidx, x_ref=xr, direction=(0.0, -1.0),
                                 amplitude=1.0, alpha_p=f_peak, t0=1.0 / f_peak))
     return Problem("config3", order, blocks, sources=srcs)
 
