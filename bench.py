@@ -1,0 +1,292 @@
+"""Benchmark of one leapfrog step of the SBP-SAT anisotropic elastic scheme on GB300.
+
+Workload (default): the topography model -- 2 stacked curvilinear blocks of 4001 x 2001 nodes
+(16,012,002 nodes), interior order 6, tilted VTI stiffness, traction-free surface, Robin sides,
+welded interface, vertical Ricker point force at the surface, FP32 fields.  A "step" is one
+leapfrog time step over all blocks (interior stencil, boundary strips, face SAT terms, source).
+
+Prints ONE JSON line (rank 0).  Metric: grid-point updates per second (nodes x steps / s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp32|fp64]
+
+--impl reference times the FP64 CPU oracle (the reference implementation of this build) on a
+bounded crop of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "grid-pt updates/s"
+UNIT = "node-updates/s"
+BYTES_PER_NODE = {"fp32": 68, "fp64": 136}     # 17 words: u^n 2, u^{n-1} 2, u^{n+1} 2, c 10, 1/(rho J) 1
+FALLBACK_HBM_GBS = 6800.0
+N1, N2 = 4001, 2001
+# crop of the workload the oracle is timed on: a 401-column window around the source spanning
+# the interface (block 0 top 161 rows, block 1 bottom 161 rows)
+CROP = {0: (1800, 2201, N2 - 161, N2), 1: (1800, 2201, 0, 161)}
+
+
+def workload_name(prec):
+    return (f"topography 2x({N1}x{N2}) curvilinear blocks, order 6, tilted VTI, traction-free top, "
+            f"Robin sides, interface, Ricker 8 Hz point force, {prec.upper()}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    v = d[k]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_steps(prec_unused, steps, warmup):
+    """Time the FP64 oracle's leapfrog steps on the bounded crop; returns (node-updates/s, detail)."""
+    from oracle.scheme import Oracle
+    P = W.config3(window=CROP)
+    O = Oracle(P)
+    dt = O.suggest_dt(0.3)
+    u = O.pack(W.smooth_state(P))
+    up = u.copy()
+    for _ in range(warmup):
+        up, u, _ = O.leapfrog(up, u, 0.0, dt, 1)
+    t0 = time.perf_counter()
+    up, u, _ = O.leapfrog(up, u, 0.0, dt, steps)
+    el = time.perf_counter() - t0
+    nodes = P.n_nodes
+    return nodes * steps / el, dict(nodes=nodes, seconds=el, steps=steps)
+
+
+def cpu_baseline(target_seconds=12.0):
+    """The oracle as it stands, on a bounded crop of the workload (single host thread)."""
+    t0 = time.perf_counter()
+    rate, d = run_oracle_steps(None, 3, 1)
+    # scale the number of timed steps to ~target_seconds of stepping
+    per = d["seconds"] / d["steps"]
+    n = max(3, min(60, int(target_seconds / max(per, 1e-6))))
+    rate, d = run_oracle_steps(None, n, 0)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} leapfrog steps of the FP64 oracle on a crop of the workload: 2 blocks "
+                      f"of 401x161 nodes ({d['nodes']} nodes) around the source and interface; "
+                      f"{time.perf_counter() - t0:.1f} s incl. assembly"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    K, Wm = max(1, args.steps), max(0, args.warmup)
+    # keep the whole run within a few minutes: cap the stepping at ~120 s
+    rate, d = run_oracle_steps(None, 2, 0)
+    per = d["seconds"] / 2
+    K = max(1, min(K, int(120 / max(per, 1e-6))))
+    Wm = min(Wm, 3)
+    rate, d = run_oracle_steps(None, K, Wm)
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": K, "warmup": Wm, "ms_per_step": 1e3 * d["seconds"] / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name("fp64") + " -- oracle on a bounded crop", "nodes": d["nodes"]},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{K} steps on a crop of {d['nodes']} nodes (2 blocks of 401x161)"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n1", type=int, default=N1, help="nodes per block along x1 (profiling runs use smaller)")
+    ap.add_argument("--n2", type=int, default=N2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2003_12811_gb300 import Solver
+
+    prec = args.precision
+    P = W.config3(n1=args.n1, n2=args.n2)
+    S = Solver(P, prec)
+    dt = S.suggest_dt(0.3)
+    zero = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+    S.set_state(zero, zero, 0.0)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    nodes = P.n_nodes
+    interior_nodes = sum((b.N1 - 18) * (b.N2 - 18) for b in P.blocks)
+
+    # warm-up (the first steps also run the source ramp-up)
+    S.sbp_step(args.warmup, dt, sh)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region (value): K steps, CUDA events on the launch stream
+    S.sbp_profile(False)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        S.sbp_step(args.steps, dt, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    _, launches = S.sbp_profile_read()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * nodes * args.steps / (ms / 1e3)
+
+    # ---- per-kernel timing (roofline of the dominant kernel): same K steps with events per family
+    S.sbp_profile(True)
+    S.sbp_step(args.steps, dt, sh)
+    torch.cuda.synchronize()
+    fam_ms, _ = S.sbp_profile_read()
+    S.sbp_profile(False)
+    interior_ms = fam_ms[0] / args.steps         # both blocks' interior launches per step
+    bpn = BYTES_PER_NODE[prec]
+    achieved = bpn * interior_nodes / (interior_ms / 1e3) / 1e9
+    peak, peak_src = peaks()
+
+    # ---- end to end through the C-ABI with host buffers: upload the state, K steps, read back
+    up_h = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.sbp_set_state(up_h, up_h, 0.0)
+    S.sbp_step(args.steps, dt, sh)
+    out = S.sbp_get_field(1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(2 * u.nbytes for u in up_h)
+    d2h = sum(o.nbytes for o in out)
+    e2e = {"value": world * nodes * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "note": "one request: host->device upload of (u^{n-1}, u^n) as FP64 host arrays, K steps, "
+                   "device->host read of u^n; bytes amortised over the K steps"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(prec).replace(f"{N1}x{N2}", f"{args.n1}x{args.n2}"), "nodes": nodes, "order": 6, "dt": dt,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": f"inputs larger than L2 ({bpn * nodes / 1e9:.2f} GB moved per step vs 129 MB L2)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_interior", "peak_source": peak_src,
+                         "bytes_per_node": bpn, "units_per_launch": interior_nodes // len(P.blocks),
+                         "kernel_ms_per_step": interior_ms,
+                         "family_ms_per_step": {"interior": fam_ms[0] / args.steps, "boundary": fam_ms[1] / args.steps,
+                                                "faces": fam_ms[2] / args.steps, "sources": fam_ms[3] / args.steps}},
+            "gpu_launches": int(launches.sum()),
+            "clocks": clk.summary(),
+            "e2e": e2e}
+    S.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

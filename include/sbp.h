@@ -146,6 +146,15 @@ int sbp_energy(sbp_handle* h, double dt, double* E_out);
  * 720 sampled directions refined by golden-section search.  Needs all materials set. */
 int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out);
 
+/* Kernel timing for benchmarks.  sbp_profile(h, 1) resets the counters and, until
+ * sbp_profile(h, 0), makes every operator launch record CUDA events (on the launch stream)
+ * around four kernel families: [0] interior stencil, [1] boundary strips (closures + SATs),
+ * [2] face traces and SAT terms, [3] point sources.  sbp_profile_read returns the accumulated
+ * milliseconds per family (ms[4], needs profiling on) and the number of kernel launches per
+ * family since the last reset (launches[4], always counted).  Either pointer may be NULL. */
+int sbp_profile(sbp_handle* h, int enable);
+int sbp_profile_read(sbp_handle* h, double* ms, long long* launches);
+
 /* Current simulation time and number of resident nodes. */
 int sbp_get_time(const sbp_handle* h, double* t_out);
 int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, int* order_out);

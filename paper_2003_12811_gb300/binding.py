@@ -78,6 +78,8 @@ def lib():
         L.sbp_energy.argtypes = [C.c_void_p, C.c_double, _DP]
         L.sbp_suggest_dt.argtypes = [C.c_void_p, C.c_double, _DP]
         L.sbp_get_time.argtypes = [C.c_void_p, _DP]
+        L.sbp_profile.argtypes = [C.c_void_p, C.c_int]
+        L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -200,6 +202,15 @@ class Solver:
         t = C.c_double()
         self._check(self.L.sbp_get_time(self.h, C.byref(t)))
         return t.value
+
+    def sbp_profile(self, enable):
+        self._check(self.L.sbp_profile(self.h, int(bool(enable))))
+
+    def sbp_profile_read(self):
+        ms = np.zeros(4)
+        n = (C.c_longlong * 4)()
+        self._check(self.L.sbp_profile_read(self.h, _ptr(ms), n))
+        return ms, np.array(list(n), dtype=np.int64)
 
     # ---------------------------------------------------------------- conveniences
     set_state = sbp_set_state

@@ -88,6 +88,24 @@ struct sbp_handle {
     int* d_flag = nullptr;
     std::string err;
     std::vector<void*> allocs;
+    // kernel timing (benchmarks): families 0 interior, 1 boundary strips, 2 faces, 3 sources
+    bool prof = false;
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long launches[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int fam; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+
+    cudaEvent_t get_event() {
+        if (!ev_pool.empty()) {
+            cudaEvent_t e = ev_pool.back();
+            ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
 
     int fail(int code, const std::string& msg) {
         err = msg;
@@ -109,6 +127,28 @@ struct sbp_handle {
 };
 
 namespace {
+
+// records CUDA events around one kernel family when profiling is on; counts launches always
+struct ProfScope {
+    sbp_handle* h;
+    int fam;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(sbp_handle* h_, int fam_, cudaStream_t st_, int nlaunch) : h(h_), fam(fam_), st(st_) {
+        h->launches[fam] += nlaunch;
+        if (h->prof) {
+            a = h->get_event();
+            b = h->get_event();
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (h->prof) {
+            cudaEventRecord(b, st);
+            h->pending.push_back({fam, a, b});
+        }
+    }
+};
 
 int check_cuda(sbp_handle* h, const char* where) {
     cudaError_t e = cudaGetLastError();
@@ -170,6 +210,7 @@ template <typename T, int O>
 int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
     const int total = h->nface_nodes;
     if (total > 0) {
+        ProfScope ps(h, 2, st, 2);
         k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, total, a.cur);
         k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, total, a, h->beta);
     }
@@ -179,13 +220,20 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
         const int S = b.strip;
         const int ni1 = hb.n1 - 2 * S, ni2 = hb.n2 - 2 * S;
         dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
-        if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
-        else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
+        {
+            ProfScope ps(h, 0, st, 1);
+            if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
+            else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
+        }
         const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)ni1 * ni2;
-        if (mode == 0) k_boundary<T, O, 0><<<grid_for(nstrip), 256, 0, st>>>(b, a);
-        else k_boundary<T, O, 1><<<grid_for(nstrip), 256, 0, st>>>(b, a);
+        {
+            ProfScope ps(h, 1, st, 1);
+            if (mode == 0) k_boundary<T, O, 0><<<grid_for(nstrip), 256, 0, st>>>(b, a);
+            else k_boundary<T, O, 1><<<grid_for(nstrip), 256, 0, st>>>(b, a);
+        }
     }
     if (!h->src_nodes.empty()) {
+        ProfScope ps(h, 3, st, 1);
         const int ns = (int)h->src_nodes.size();
         if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
         else k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
@@ -373,6 +421,11 @@ int sbp_destroy(sbp_handle* h) {
     if (!h) return SBP_OK;
     for (void* p : h->allocs)
         if (p) cudaFree(p);
+    for (auto& pd : h->pending) {
+        cudaEventDestroy(pd.a);
+        cudaEventDestroy(pd.b);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
     delete h;
     return SBP_OK;
 }
@@ -645,6 +698,40 @@ int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out) {
     double r = 0;
     if (cudaMemcpy(&r, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return h->fail(SBP_E_CUDA, "cfl");
     *dt_out = cfl * r;
+    return SBP_OK;
+}
+
+int sbp_profile(sbp_handle* h, int enable) {
+    if (!h) return SBP_E_INVALID_ARG;
+    cudaDeviceSynchronize();
+    for (auto& pd : h->pending) {
+        h->ev_pool.push_back(pd.a);
+        h->ev_pool.push_back(pd.b);
+    }
+    h->pending.clear();
+    for (int k = 0; k < 4; ++k) {
+        h->prof_ms[k] = 0;
+        h->launches[k] = 0;
+    }
+    h->prof = enable != 0;
+    return SBP_OK;
+}
+
+int sbp_profile_read(sbp_handle* h, double* ms, long long* launches) {
+    if (!h) return SBP_E_INVALID_ARG;
+    for (auto& pd : h->pending) {
+        float t = 0;
+        if (cudaEventSynchronize(pd.b) != cudaSuccess || cudaEventElapsedTime(&t, pd.a, pd.b) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "event timing failed");
+        h->prof_ms[pd.fam] += t;
+        h->ev_pool.push_back(pd.a);
+        h->ev_pool.push_back(pd.b);
+    }
+    h->pending.clear();
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->launches[k];
+    }
     return SBP_OK;
 }
 

@@ -476,9 +476,11 @@ __global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* _
     // tangential transpose term (1/H_t(s)) sum_s' D_t[s'][s] H_t(s') b_J(s'),  b_J = nu c_mLtJ w_L
     const int Nt = nf;
     const double ht = m == 0 ? B.h2 : B.h1;
+    // rows of D with a non-zero in column s: the interior band s-Q..s+Q plus, near an end, every
+    // boundary row (boundary rows span columns 0..NCOL-1, which can reach past s+Q)
     int lo = s - Ord<O>::Q, hi = s + Ord<O>::Q;
-    if (s < Ord<O>::NCOL) lo = 0;
-    if (s >= Nt - Ord<O>::NCOL) hi = Nt - 1;
+    if (s < Ord<O>::NCOL) { lo = 0; hi = max(hi, Ord<O>::NB - 1); }
+    if (s >= Nt - Ord<O>::NCOL) { hi = Nt - 1; lo = min(lo, Nt - Ord<O>::NB); }
     if (lo < 0) lo = 0;
     if (hi > Nt - 1) hi = Nt - 1;
     T tt0 = T(0), tt1 = T(0);

@@ -117,39 +117,36 @@ def face_slice(f: int):
 
 # ----------------------------------------------------------------------------- materials
 def voigt_to_tensor(cv: np.ndarray) -> np.ndarray:
-    """2-D Voigt (3x3: 1 <-> 11, 2 <-> 22, 3 <-> 12/21) to the full tensor C_IJKL."""
-    v = {(0, 0): 0, (1, 1): 1, (0, 1): 2, (1, 0): 2}
-    shape = cv.shape[2:]
-    C = np.zeros((2, 2, 2, 2) + shape, dtype=cv.dtype)
-    for I in range(2):
-        for J in range(2):
-            for K in range(2):
-                for L in range(2):
-                    C[I, J, K, L] = cv[v[I, J], v[K, L]]
-    return C
+    """2-D Voigt (3x3: 1 <-> 11, 2 <-> 22, 3 <-> 12/21) to the full tensor C_IJKL.
+
+    The result is a view of the 4x4 pair matrix M[2I+J, 2K+L] reshaped to (2, 2, 2, 2, ...)."""
+    v = [0, 2, 2, 1]                       # pair index p = 2I+J -> Voigt index
+    M = np.empty((4, 4) + cv.shape[2:], dtype=cv.dtype)
+    for p in range(4):
+        for q in range(4):
+            M[p, q] = cv[v[p], v[q]]
+    return M.reshape((2, 2, 2, 2) + cv.shape[2:])
 
 
 def pair10_to_tensor(m: np.ndarray) -> np.ndarray:
     """Symmetric 4x4 pair matrix over (IJ) in order 11, 12, 21, 22 -> C_IJKL (Cosserat)."""
-    p = {(0, 0): 0, (0, 1): 1, (1, 0): 2, (1, 1): 3}
-    shape = m.shape[2:]
-    C = np.zeros((2, 2, 2, 2) + shape, dtype=m.dtype)
-    for I in range(2):
-        for J in range(2):
-            for K in range(2):
-                for L in range(2):
-                    C[I, J, K, L] = m[p[I, J], p[K, L]]
-    return C
+    return np.ascontiguousarray(m).reshape((2, 2, 2, 2) + m.shape[2:])
 
 
 def rotate_tensor(C: np.ndarray, theta) -> np.ndarray:
-    """C'_IJKL = R_Ia R_Jb R_Kc R_Ld C_abcd, R the rotation by theta (array or scalar)."""
+    """C'_IJKL = R_Ia R_Jb R_Kc R_Ld C_abcd, R the rotation by theta (array or scalar),
+    evaluated in pair form M' = Rp M Rp^T with Rp[2I+J, 2a+b] = R_Ia R_Jb."""
     c, s = np.cos(theta), np.sin(theta)
-    R = np.array([[c, -s], [s, c]], dtype=np.result_type(c, C))
-    if np.ndim(theta) == 0:
-        R = R.reshape((2, 2) + (1,) * (C.ndim - 4)) * np.ones((2, 2) + C.shape[4:])
-    out = np.einsum("ia...,jb...,kc...,ld...,abcd...->ijkl...", R, R, R, R, C, optimize=True)
-    return out
+    R = [[c, -s], [s, c]]
+    M = C.reshape((4, 4) + C.shape[4:])
+    Rp = [[R[p // 2][a // 2] * R[p % 2][a % 2] for a in range(4)] for p in range(4)]
+    T = [[sum(Rp[p][a] * M[a, b] for a in range(4)) for b in range(4)] for p in range(4)]
+    out = np.empty(np.broadcast(M[0, 0], np.asarray(c)).shape, dtype=np.result_type(c, C))
+    out = np.empty((4, 4) + out.shape, dtype=out.dtype)
+    for p in range(4):
+        for q in range(4):
+            out[p, q] = sum(T[p][b] * Rp[q][b] for b in range(4))
+    return out.reshape((2, 2, 2, 2) + out.shape[2:])
 
 
 def vti_voigt(rho, vp, vs, eps, delta):
@@ -456,12 +453,13 @@ def config3(n1: int = 4001, n2: int = 2001, order: int = 6, window=None,
     if window is not None:
         _remap_window_interfaces(blocks, sorted(window))
     srcs = []
-    if window is None or 1 in window:
+    src_i1, src_i2 = 0.5 * (n1 - 1), float(n2 - 1)          # surface, mid-width, in block 1
+    keep = window is None or (1 in window and window[1][0] <= src_i1 < window[1][1] - 1
+                              and window[1][2] <= src_i2 < window[1][3])
+    if keep:
         bidx = 1 if window is None else sorted(window).index(1)
-        xr = (0.5, 1.0)
-        if window is not None:   # re-express the reference position in the crop
-            lo1, hi1, lo2, hi2 = window[1]
-            xr = ((0.5 * (n1 - 1) - lo1) / (n1 - 1), ((n2 - 1) - lo2) / (n2 - 1))
+        lo1, lo2 = (0, 0) if window is None else (window[1][0], window[1][2])
+        xr = ((src_i1 - lo1) / (n1 - 1), (src_i2 - lo2) / (n2 - 1))
         srcs.append(PointSource(block=bidx, x_ref=xr, direction=(0.0, -1.0),
                                 amplitude=1.0, alpha_p=f_peak, t0=1.0 / f_peak))
     return Problem("config3", order, blocks, sources=srcs)
