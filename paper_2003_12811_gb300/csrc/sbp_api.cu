@@ -7,9 +7,14 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/sbp.h"
+#include "sbp_interior_tma.cuh"
 #include "sbp_kernels.cuh"
 
 namespace sbphost {
@@ -47,6 +52,7 @@ struct HostBlock {
     double* J = nullptr;
     bool material = false;
     HostFace f[4];
+    TmaMaps maps;             // FP32 interior kernel tensor maps
 };
 
 int order_nb(int o) { return o == 2 ? SBP2_NB : (o == 4 ? SBP4_NB : SBP6_NB); }
@@ -86,6 +92,8 @@ struct sbp_handle {
     bool src_dirty = false;
     double* d_scalar = nullptr;
     int* d_flag = nullptr;
+    int* d_err = nullptr;       // kernel error flags (bounded waits that ran out)
+    int num_sms = 0;
     std::string err;
     std::vector<void*> allocs;
     // kernel timing (benchmarks): families 0 interior, 1 boundary strips, 2 faces, 3 sources
@@ -206,6 +214,32 @@ int sync_views(sbp_handle* h) {
 
 inline unsigned grid_for(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 3-D map over `planes` consecutive float planes of n2 x pitch, box [planes][rows][TBOXW]
+bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)n2, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * n2 * 4};
+    cuuint32_t box[3] = {(cuuint32_t)TBOXW, (cuuint32_t)rows, (cuuint32_t)planes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int O> int tma_rows() { return TmaTile<O>::SY; }
+
 template <typename T, int O>
 int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
     const int total = h->nface_nodes;
@@ -222,8 +256,18 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
         dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
         {
             ProfScope ps(h, 0, st, 1);
-            if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
-            else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
+            if constexpr (std::is_same<T, float>::value) {
+                const int S2 = b.strip;
+                const int ntx = (hb.n1 - S2 - tile_x0(S2) + TTX - 1) / TTX, nty = (hb.n2 - 2 * S2 + TTY - 1) / TTY;
+                const int ntiles = ntx * nty;
+                const int nct = std::min(ntiles, 2 * h->num_sms);
+                constexpr size_t tsm = TmaTile<O>::BYTES;
+                if (mode == 0) k_interior_tma<O, 0><<<nct, TTHREADS, tsm, st>>>(hb.maps, b, a, h->d_err);
+                else k_interior_tma<O, 1><<<nct, TTHREADS, tsm, st>>>(hb.maps, b, a, h->d_err);
+            } else {
+                if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
+                else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
+            }
         }
         const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)ni1 * ni2;
         {
@@ -258,6 +302,22 @@ template <typename T, int O> void set_smem_attr() {
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
     cudaFuncSetAttribute(k_interior<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_interior<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (std::is_same<T, float>::value) {
+        cudaFuncSetAttribute(k_interior_tma<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaTile<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_tma<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaTile<O>::BYTES);
+    }
+}
+
+// kernel error flags: bit 1 = a bounded wait in the interior kernel ran out
+int check_kernel_errors(sbp_handle* h) {
+    int e = 0;
+    if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, std::string("device error: ") + cudaGetErrorString(cudaGetLastError()));
+    if (e) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        return h->fail(SBP_E_TIMEOUT, "a bounded wait in a kernel ran out; results of the last steps are invalid");
+    }
+    return SBP_OK;
 }
 
 void fill_basis(const sbp_handle* h, double t, StepArgs& a) {
@@ -345,7 +405,14 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     else { set_smem_attr<float, 2>(); set_smem_attr<float, 4>(); set_smem_attr<float, 6>(); }
     h->d_scalar = (double*)h->dalloc(64);
     h->d_flag = (int*)h->dalloc(64);
-    if (!h->d_scalar || !h->d_flag) return cleanup(SBP_E_OOM, "scalar buffers");
+    h->d_err = (int*)h->dalloc(64);
+    if (!h->d_scalar || !h->d_flag || !h->d_err) return cleanup(SBP_E_OOM, "scalar buffers");
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->num_sms <= 0) h->num_sms = 1;
+    }
     std::vector<FaceRef> refs;
     int start = 0;
     for (int b = 0; b < desc->nblocks; ++b) {
@@ -381,6 +448,13 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             if (!F.jhat || !F.tr || !F.sat) return cleanup(SBP_E_OOM, "face buffers");
             refs.push_back(FaceRef{b, f, start, F.nf});
             start += F.nf;
+        }
+        if (h->precision == SBP_FP32) {
+            const int rows = o == 2 ? tma_rows<2>() : (o == 4 ? tma_rows<4>() : tma_rows<6>());
+            if (!make_map(&hb.maps.u[0], hb.u[0], hb.pitch, hb.n2, 2, rows) ||
+                !make_map(&hb.maps.u[1], hb.u[1], hb.pitch, hb.n2, 2, rows) ||
+                !make_map(&hb.maps.c, hb.c, hb.pitch, hb.n2, 10, rows))
+                return cleanup(SBP_E_CUDA, "tensor map encoding failed");
         }
         // coordinates -> pitched device planes
         double* tmp = (double*)h->dalloc(2 * (size_t)bd.n1 * bd.n2 * sizeof(double));
@@ -632,7 +706,7 @@ int sbp_apply(sbp_handle* h, int with_data, double t) {
     int rc = run_operator(h, a, 1, 0);
     if (rc != SBP_OK) return rc;
     if (cudaDeviceSynchronize() != cudaSuccess) return h->fail(SBP_E_CUDA, "apply failed");
-    return SBP_OK;
+    return check_kernel_errors(h);
 }
 
 int sbp_get_field(sbp_handle* h, int block, int which, double* dst) {
@@ -649,7 +723,7 @@ int sbp_get_field(sbp_handle* h, int block, int which, double* dst) {
     cudaError_t e = cudaMemcpy(dst, tmp, 2 * n * sizeof(double), cudaMemcpyDeviceToHost);
     h->dfree(tmp);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "download failed");
-    return SBP_OK;
+    return check_kernel_errors(h);
 }
 
 int sbp_energy(sbp_handle* h, double dt, double* E_out) {
@@ -679,6 +753,8 @@ int sbp_energy(sbp_handle* h, double dt, double* E_out) {
     double E = 0;
     if (cudaMemcpy(&E, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return h->fail(SBP_E_CUDA, "energy");
     *E_out = E;
+    int rc2 = check_kernel_errors(h);
+    if (rc2 != SBP_OK) return rc2;
     if (!std::isfinite(E)) return h->fail(SBP_E_UNSTABLE, "non-finite energy");
     return SBP_OK;
 }
