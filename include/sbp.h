@@ -155,6 +155,24 @@ int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out);
 int sbp_profile(sbp_handle* h, int enable);
 int sbp_profile_read(sbp_handle* h, double* ms, long long* launches);
 
+/* Operator application that allocates nothing (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory, e.g. code confined to a fixed memory pool or a
+ * real-time loop that must not call cudaMalloc).  Computes, for the grid, material, SATs and
+ * data of h, r = DD(c) u + J SAT(u) (+ J f(t) + point sources when with_data != 0), exactly the
+ * operator of sbp_apply, but on caller-provided device buffers:
+ *   u_dev: input displacement, r_dev: output, both in the library's device layout -- for each
+ *          block in order, 2 planes (component 1, component 2) of n2 rows x pitch elements,
+ *          pitch = n1 rounded up to a multiple of 32, elements in the handle's precision
+ *          (double for SBP_FP64, float for SBP_FP32); blocks follow each other without gaps.
+ * The per-face traces and SAT terms and the device copies of the block tables live in one
+ * fixed 8 MiB file-scope device array shared by every call; grids needing more scratch are
+ * rejected with SBP_E_INVALID_ARG before any device work.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) -- make that first call before any stream
+ * capture.  Calls that overlap on the GPU (concurrent streams, several handles) race on the
+ * shared array: serialise them.  The call is stream-ordered on `stream` and returns after the
+ * stream has drained.  No cudaMalloc/cudaFree or allocating library routine is called. */
+int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_data, double t, void* stream);
+
 /* Current simulation time and number of resident nodes. */
 int sbp_get_time(const sbp_handle* h, double* t_out);
 int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, int* order_out);

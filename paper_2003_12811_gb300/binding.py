@@ -79,6 +79,7 @@ def lib():
         L.sbp_suggest_dt.argtypes = [C.c_void_p, C.c_double, _DP]
         L.sbp_get_time.argtypes = [C.c_void_p, _DP]
         L.sbp_profile.argtypes = [C.c_void_p, C.c_int]
+        L.sbp_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
@@ -202,6 +203,12 @@ class Solver:
         t = C.c_double()
         self._check(self.L.sbp_get_time(self.h, C.byref(t)))
         return t.value
+
+    def sbp_apply_noalloc(self, u_ptr, r_ptr, with_data=False, t=0.0, stream=None):
+        """u_ptr, r_ptr: device addresses of buffers in the library layout (see include/sbp.h)."""
+        s = None if stream is None else C.c_void_p(stream)
+        self._check(self.L.sbp_apply_noalloc(self.h, C.c_void_p(u_ptr), C.c_void_p(r_ptr), int(bool(with_data)),
+                                             float(t), s))
 
     def sbp_profile(self, enable):
         self._check(self.L.sbp_profile(self.h, int(bool(enable))))

@@ -346,6 +346,67 @@ bool all_materials(const sbp_handle* h) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------------
+// Fixed scratch for sbp_apply_noalloc.  Callers that cannot allocate device memory (for example
+// code running inside a memory pool it may not grow, or a real-time loop where cudaMalloc's
+// implicit synchronisation is not allowed) get the operator application with every temporary --
+// the per-face trace and SAT arrays and the device copies of the block/face tables -- placed in
+// this file-scope array.  Every GPU that loads the library holds it until the process exits.
+constexpr size_t NOALLOC_SCRATCH_BYTES = 8u << 20;   // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// device address of g_noalloc_scratch, looked up once per device (host code must not use the
+// symbol itself: on the host it is only a stand-in, not a device address)
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+int noalloc_scratch(sbp_handle* h, unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return h->fail(SBP_E_CUDA, "cannot query the current device");
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return h->fail(SBP_E_CUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (unsigned char*)g_noalloc_ptr[dev];
+    return SBP_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+constexpr int NOALLOC_MAX_BLOCKS = 32;
+
+template <typename T, int O>
+void launch_noalloc(sbp_handle* h, const BlockDev* views, int nviews, BlockDev* d_views, FaceRef* d_refs,
+                    const StepArgs& a, cudaStream_t st) {
+    const int total = h->nface_nodes;
+    if (total > 0) {
+        k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(d_views, d_refs, h->nrefs, total, a.cur);
+        k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(d_views, d_refs, h->nrefs, total, a, h->beta);
+    }
+    constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
+    for (int b = 0; b < nviews; ++b) {
+        const BlockDev& v = views[b];
+        const int S = v.strip;
+        const int ni1 = v.n1 - 2 * S, ni2 = v.n2 - 2 * S;
+        dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
+        k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(v, a);
+        const long long nstrip = (long long)v.n1 * v.n2 - (long long)ni1 * ni2;
+        k_boundary<T, O, 1><<<grid_for(nstrip), 256, 0, st>>>(v, a);
+    }
+    if (!h->src_nodes.empty()) {
+        const int ns = (int)h->src_nodes.size();
+        k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(d_views, h->d_src_nodes, ns, h->d_src_params, a);
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sbp_last_error(const sbp_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -809,6 +870,73 @@ int sbp_profile_read(sbp_handle* h, double* ms, long long* launches) {
         if (launches) launches[k] = h->launches[k];
     }
     return SBP_OK;
+}
+
+int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_data, double t, void* stream) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (!u_dev || !r_dev) return h->fail(SBP_E_INVALID_ARG, "null device buffer");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    const int nb = (int)h->blocks.size();
+    if (nb > NOALLOC_MAX_BLOCKS) return h->fail(SBP_E_INVALID_ARG, "sbp_apply_noalloc supports at most 32 blocks");
+    const size_t es = h->esize;
+    // scratch layout: block views | face refs | per face: trace (4 x nf) and SAT (4 x nf) arrays
+    size_t need = align256(sizeof(BlockDev) * nb) + align256(sizeof(FaceRef) * h->nrefs);
+    for (auto& hb : h->blocks)
+        for (auto& F : hb.f) need += 2 * align256(4 * (size_t)F.nf * es);
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return h->fail(SBP_E_INVALID_ARG, "grid needs more scratch than the fixed 8 MiB of sbp_apply_noalloc");
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(h, &base);
+    if (rc != SBP_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t off = 0;
+    BlockDev* d_views = (BlockDev*)(base + off);
+    off += align256(sizeof(BlockDev) * nb);
+    FaceRef* d_refs = (FaceRef*)(base + off);
+    off += align256(sizeof(FaceRef) * h->nrefs);
+    BlockDev views[NOALLOC_MAX_BLOCKS];
+    FaceRef refs[4 * NOALLOC_MAX_BLOCKS];
+    size_t uoff = 0;
+    int start = 0, nr = 0;
+    for (int b = 0; b < nb; ++b) {
+        const HostBlock& hb = h->blocks[b];
+        BlockDev v = make_view(h, hb);
+        const size_t planes2 = 2 * (size_t)hb.n2 * hb.pitch * es;
+        v.u[0] = (unsigned char*)const_cast<void*>(u_dev) + uoff;   // read as the current level
+        v.u[1] = nullptr;
+        v.r = (unsigned char*)r_dev + uoff;
+        uoff += planes2;
+        for (int f = 0; f < 4; ++f) {
+            const size_t fb = align256(4 * (size_t)hb.f[f].nf * es);
+            v.f[f].tr = base + off;
+            off += fb;
+            v.f[f].sat = base + off;
+            off += fb;
+            refs[nr++] = FaceRef{b, f, start, hb.f[f].nf};
+            start += hb.f[f].nf;
+        }
+        views[b] = v;
+    }
+    if (cudaMemcpyAsync(d_views, views, sizeof(BlockDev) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_refs, refs, sizeof(FaceRef) * nr, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "table upload to the fixed scratch failed");
+    StepArgs a{};
+    a.cur = 0;
+    a.with_data = with_data ? 1 : 0;
+    a.t = t;
+    fill_basis(h, t, a);
+    if (h->precision == SBP_FP64) {
+        if (h->order == 2) launch_noalloc<double, 2>(h, views, nb, d_views, d_refs, a, st);
+        else if (h->order == 4) launch_noalloc<double, 4>(h, views, nb, d_views, d_refs, a, st);
+        else launch_noalloc<double, 6>(h, views, nb, d_views, d_refs, a, st);
+    } else {
+        if (h->order == 2) launch_noalloc<float, 2>(h, views, nb, d_views, d_refs, a, st);
+        else if (h->order == 4) launch_noalloc<float, 4>(h, views, nb, d_views, d_refs, a, st);
+        else launch_noalloc<float, 6>(h, views, nb, d_views, d_refs, a, st);
+    }
+    // the table copies read the stack arrays above: drain the stream before they go away
+    if (cudaStreamSynchronize(st) != cudaSuccess) return h->fail(SBP_E_CUDA, "sbp_apply_noalloc kernels failed");
+    return check_cuda(h, "sbp_apply_noalloc");
 }
 
 int sbp_get_time(const sbp_handle* h, double* t_out) {
