@@ -15,6 +15,7 @@
 
 #include "../../include/sbp.h"
 #include "sbp_interior_tma.cuh"
+#include "sbp_interior_march.cuh"
 #include "sbp_kernels.cuh"
 
 namespace sbphost {
@@ -52,7 +53,8 @@ struct HostBlock {
     double* J = nullptr;
     bool material = false;
     HostFace f[4];
-    TmaMaps maps;             // FP32 interior kernel tensor maps
+    TmaMaps maps;             // FP32 tile interior kernel tensor maps
+    MarchMaps mmaps;          // FP32 column-marching interior kernel tensor maps
 };
 
 int order_nb(int o) { return o == 2 ? SBP2_NB : (o == 4 ? SBP4_NB : SBP6_NB); }
@@ -226,13 +228,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D map over `planes` consecutive float planes of n2 x pitch, box [planes][rows][TBOXW]
-bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows) {
+// 3-D map over `planes` consecutive float planes of n2 x pitch, box [planes][rows][width]
+bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows, int width = TBOXW) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)n2, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * n2 * 4};
-    cuuint32_t box[3] = {(cuuint32_t)TBOXW, (cuuint32_t)rows, (cuuint32_t)planes};
+    cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -257,23 +259,29 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
         {
             ProfScope ps(h, 0, st, 1);
             if constexpr (std::is_same<T, float>::value) {
+                // column-marching kernel: one wave of ~4 CTAs per SM, rows split evenly
                 const int S2 = b.strip;
-                const int ntx = (hb.n1 - S2 - tile_x0(S2) + TTX - 1) / TTX, nty = (hb.n2 - 2 * S2 + TTY - 1) / TTY;
-                const int ntiles = ntx * nty;
-                const int nct = std::min(ntiles, 2 * h->num_sms);
-                constexpr size_t tsm = TmaTile<O>::BYTES;
-                if (mode == 0) k_interior_tma<O, 0><<<nct, TTHREADS, tsm, st>>>(hb.maps, b, a, h->d_err);
-                else k_interior_tma<O, 1><<<nct, TTHREADS, tsm, st>>>(hb.maps, b, a, h->d_err);
+                const int ncx = (hb.n1 - S2 - march_x0(S2) + MTHREADS - 1) / MTHREADS;
+                const int n2i = hb.n2 - 2 * S2;
+                int ncy = std::max(1, (4 * h->num_sms + ncx / 2) / ncx);
+                int rows = (n2i + ncy - 1) / ncy;
+                if (rows < 16) rows = std::min(16, n2i);
+                ncy = (n2i + rows - 1) / rows;
+                constexpr size_t msm = MarchCfg<O>::BYTES;
+                if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, st>>>(hb.mmaps, b, a, rows, h->d_err);
+                else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, st>>>(hb.mmaps, b, a, rows, h->d_err);
             } else {
                 if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
                 else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
             }
         }
-        const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)ni1 * ni2;
         {
             ProfScope ps(h, 1, st, 1);
-            if (mode == 0) k_boundary<T, O, 0><<<grid_for(nstrip), 256, 0, st>>>(b, a);
-            else k_boundary<T, O, 1><<<grid_for(nstrip), 256, 0, st>>>(b, a);
+            using ST = StripTile<O>;
+            const int ntile = 2 * ((hb.n1 + 31) / 32) + 2 * ((hb.n2 - 2 * ST::S + 31) / 32);
+            constexpr size_t ssm = (size_t)ST::ELEMS * sizeof(T);
+            if (mode == 0) k_strip_tile<T, O, 0><<<ntile, ST::THREADS, ssm, st>>>(b, a);
+            else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, st>>>(b, a);
         }
     }
     if (!h->src_nodes.empty()) {
@@ -300,15 +308,20 @@ int run_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
 
 template <typename T, int O> void set_smem_attr() {
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
+    constexpr size_t ssm = (size_t)StripTile<O>::ELEMS * sizeof(T);
+    cudaFuncSetAttribute(k_strip_tile<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    cudaFuncSetAttribute(k_strip_tile<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     cudaFuncSetAttribute(k_interior<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_interior<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (std::is_same<T, float>::value) {
+        cudaFuncSetAttribute(k_interior_march<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_march<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_tma<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaTile<O>::BYTES);
         cudaFuncSetAttribute(k_interior_tma<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaTile<O>::BYTES);
     }
 }
 
-// kernel error flags: bit 1 = a bounded wait in the interior kernel ran out
+// kernel error flags: bits 2 (tile kernel) and 4 (marching kernel) = a bounded wait ran out
 int check_kernel_errors(sbp_handle* h) {
     int e = 0;
     if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -514,7 +527,10 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             const int rows = o == 2 ? tma_rows<2>() : (o == 4 ? tma_rows<4>() : tma_rows<6>());
             if (!make_map(&hb.maps.u[0], hb.u[0], hb.pitch, hb.n2, 2, rows) ||
                 !make_map(&hb.maps.u[1], hb.u[1], hb.pitch, hb.n2, 2, rows) ||
-                !make_map(&hb.maps.c, hb.c, hb.pitch, hb.n2, 10, rows))
+                !make_map(&hb.maps.c, hb.c, hb.pitch, hb.n2, 10, rows) ||
+                !make_map(&hb.mmaps.u[0], hb.u[0], hb.pitch, hb.n2, 2, MR, MBOXW) ||
+                !make_map(&hb.mmaps.u[1], hb.u[1], hb.pitch, hb.n2, 2, MR, MBOXW) ||
+                !make_map(&hb.mmaps.c, hb.c, hb.pitch, hb.n2, 10, MR, MBOXW))
                 return cleanup(SBP_E_CUDA, "tensor map encoding failed");
         }
         // coordinates -> pitched device planes

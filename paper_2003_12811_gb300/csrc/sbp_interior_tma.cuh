@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(TTHREADS, 2)
 k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int* err) {
     using TT = TmaTile<O>;
     constexpr int Q = TT::Q, SY = TT::SY, SX = TT::SX, EX = TT::EX, EY = TT::EY, W = TBOXW;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* cbuf = reinterpret_cast<float*>(smem_raw);     // [10][SY][W]
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    float* cbuf = reinterpret_cast<float*>(tma_smem);     // [10][SY][W]
     float* ubuf = cbuf + TT::CBUF;                         // [2 stages][2][SY][W]
     float* sg1 = ubuf + 2 * TT::UBUF;                      // [2][TY][SX]   col index c + Q
     float* sg2 = sg1 + TT::G1;                             // [2][SY][TX]
@@ -151,39 +151,74 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
         int x0, y0;
         tile_origin(tile, x0, y0);
         const float* su = ubuf + s * TT::UBUF;
-        // ---- phase 2: mixed fluxes and edge weights
-        // g1_j = c_1j2l D_2 u_l at tile rows, columns c in [-Q, TX+Q)
+        // early global loads of this thread's 1/(rho J) and u^{n-1} (two adjacent rows): they
+        // complete while phase 2 runs
+        const int pr0 = 2 * ty;                       // phase-3 rows pr0, pr0 + 1
+        const int gx = x0 + tx;
+        float wv[2] = {0.f, 0.f}, up0[2] = {0.f, 0.f}, up1[2] = {0.f, 0.f};
+        bool act[2];
 #pragma unroll
-        for (int rr = 0; rr < TTY / 8; ++rr) {
-            const int r = ty + 8 * rr;
-#pragma unroll
-            for (int cb = 0; cb < 2; ++cb) {
-                const int c = tx + 32 * cb;          // c - Q is the tile column
-                if (c < SX) {
-                    const int col = c - Q + TXOFF;
-                    const float* p0 = su + (r + Q) * W + col;
-                    const float* p1 = p0 + SY * W;
-                    float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-                    for (int k = 1; k <= Q; ++k) {
-                        d0 += ak[k - 1] * (p0[k * W] - p0[-k * W]);
-                        d1 += ak[k - 1] * (p1[k * W] - p1[-k * W]);
-                    }
-                    d0 *= ih2;
-                    d1 *= ih2;
-                    const int mi = (r + Q) * W + col;
-                    const float m6 = cbuf[6 * SY * W + mi], m7 = cbuf[7 * SY * W + mi],
-                                m8 = cbuf[8 * SY * W + mi], m9 = cbuf[9 * SY * W + mi];
-                    sg1[r * SX + c] = m6 * d0 + m7 * d1;
-                    sg1[TTY * SX + r * SX + c] = m8 * d0 + m9 * d1;
-                }
+        for (int k = 0; k < 2; ++k) {
+            const int gy = y0 + pr0 + k;
+            act[k] = gx >= S && gx < lim1 && gy < lim2;
+            if (MODE == 0 && act[k]) {
+                const size_t gi = (size_t)gy * P + gx;
+                wv[k] = __ldg(reinterpret_cast<const float*>(B.w) + gi);
+                const float* Un = reinterpret_cast<const float*>(B.u[1 - a.cur]);
+                up0[k] = Un[gi];
+                up1[k] = Un[gi + plane];
             }
         }
-        // g2_j = c_1l2j D_1 u_l at rows [-Q, TY+Q), tile columns
+        // ---- phase 2: mixed fluxes and edge weights, as warp-uniform tasks of 32 lanes:
+        //   [0,16)      g1 = c_1j2l D_2 u_l, tile row t, tile columns
+        //   [16,19)     g1 at the 2Q halo columns (96 lanes: row, halo column)
+        //   [19,19+SY)  g2 = c_1l2j D_1 u_l, rows [-Q, TY+Q), tile columns
+        //   next 16     x edge weights, tile row, i in [0, TX)
+        //   next 2      x edge weights at i in [-Q, 0) (16 x Q lanes)
+        //   next EY     y edge weights, j in [-Q, TY), tile columns
+        constexpr int T_G1 = 0, T_G1H = TTY, T_G2 = T_G1H + (TTY * 2 * Q + 31) / 32, T_EX = T_G2 + SY,
+                      T_EXH = T_EX + TTY, T_EY = T_EXH + (TTY * Q + 31) / 32, T_END = T_EY + EY;
+        auto g1_at = [&](int r, int c) {           // c: column index in [0, SX) (tile column c - Q)
+            const int col = c - Q + TXOFF;
+            const float* p0 = su + (r + Q) * W + col;
+            const float* p1 = p0 + SY * W;
+            float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-        for (int rr = 0; rr < (SY + 7) / 8; ++rr) {
-            const int r = ty + 8 * rr;
-            if (r < SY) {
+            for (int k = 1; k <= Q; ++k) {
+                d0 += ak[k - 1] * (p0[k * W] - p0[-k * W]);
+                d1 += ak[k - 1] * (p1[k * W] - p1[-k * W]);
+            }
+            d0 *= ih2;
+            d1 *= ih2;
+            const int mi = (r + Q) * W + col;
+            const float m6 = cbuf[6 * SY * W + mi], m7 = cbuf[7 * SY * W + mi], m8 = cbuf[8 * SY * W + mi],
+                        m9 = cbuf[9 * SY * W + mi];
+            sg1[r * SX + c] = m6 * d0 + m7 * d1;
+            sg1[TTY * SX + r * SX + c] = m8 * d0 + m9 * d1;
+        };
+        auto ex_at = [&](int r, int ii) {          // ii = i + Q
+            const int col = ii - Q + TXOFF;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const float* bl = cbuf + f * SY * W + (r + Q) * W + col;
+                auto Bf = [&](int k) { return bl[k]; };
+#pragma unroll
+                for (int m = 1; m <= Q; ++m)
+                    sex[((f * Q + (m - 1)) * TTY + r) * EX + ii] =
+                        (ii + edge_lo<O>(m) >= 0) ? Edge<O>::template e<float>(m, Bf) : 0.f;
+            }
+        };
+        for (int task = ty; task < T_END; task += 8) {
+            if (task < T_G1H) {
+                g1_at(task - T_G1, tx + Q);
+            } else if (task < T_G2) {
+                const int lane = (task - T_G1H) * 32 + tx;
+                if (lane < TTY * 2 * Q) {
+                    const int r = lane / (2 * Q), h = lane - r * (2 * Q);
+                    g1_at(r, h < Q ? h : TTX + h);
+                }
+            } else if (task < T_EX) {
+                const int r = task - T_G2;
                 const int col = tx + TXOFF;
                 const float* p0 = su + r * W + col;
                 const float* p1 = p0 + SY * W;
@@ -196,38 +231,20 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
                 d0 *= ih1;
                 d1 *= ih1;
                 const int mi = r * W + col;
-                const float m6 = cbuf[6 * SY * W + mi], m7 = cbuf[7 * SY * W + mi],
-                            m8 = cbuf[8 * SY * W + mi], m9 = cbuf[9 * SY * W + mi];
+                const float m6 = cbuf[6 * SY * W + mi], m7 = cbuf[7 * SY * W + mi], m8 = cbuf[8 * SY * W + mi],
+                            m9 = cbuf[9 * SY * W + mi];
                 sg2[r * TTX + tx] = m6 * d0 + m8 * d1;
                 sg2[SY * TTX + r * TTX + tx] = m7 * d0 + m9 * d1;
-            }
-        }
-        // x edge weights at i in [-Q, TX), fields c_1j1l (planes 0..2), rows of the tile
-#pragma unroll
-        for (int rr = 0; rr < TTY / 8; ++rr) {
-            const int r = ty + 8 * rr;
-#pragma unroll
-            for (int cb = 0; cb < 2; ++cb) {
-                const int ii = tx + 32 * cb;     // i = ii - Q
-                if (ii < EX) {
-                    const int col = ii - Q + TXOFF;
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        const float* bl = cbuf + f * SY * W + (r + Q) * W + col;
-                        auto Bf = [&](int k) { return bl[k]; };
-#pragma unroll
-                        for (int m = 1; m <= Q; ++m)
-                            sex[((f * Q + (m - 1)) * TTY + r) * EX + ii] =
-                                (ii + edge_lo<O>(m) >= 0) ? Edge<O>::template e<float>(m, Bf) : 0.f;
-                    }
+            } else if (task < T_EXH) {
+                ex_at(task - T_EX, tx + Q);
+            } else if (task < T_EY) {
+                const int lane = (task - T_EXH) * 32 + tx;
+                if (lane < TTY * Q) {
+                    const int r = lane / Q, ii = lane - r * Q;
+                    ex_at(r, ii);
                 }
-            }
-        }
-        // y edge weights at j in [-Q, TY), fields c_2j2l (planes 3..5), tile columns
-#pragma unroll
-        for (int rr = 0; rr < (EY + 7) / 8; ++rr) {
-            const int jj = ty + 8 * rr;          // j = jj - Q
-            if (jj < EY) {
+            } else {
+                const int jj = task - T_EY;        // j = jj - Q
                 const int col = tx + TXOFF;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
@@ -248,12 +265,12 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
             fence_proxy_async();
             issue(next, s ^ 1, true);
         }
-        // ---- phase 3: outputs
+        // ---- phase 3: outputs at rows pr0 and pr0 + 1 of column tx
 #pragma unroll
-        for (int rr = 0; rr < TTY / 8; ++rr) {
-            const int r = ty + 8 * rr;
-            const int gx = x0 + tx, gy = y0 + r;
-            if (gx < S || gx >= lim1 || gy >= lim2) continue;
+        for (int k = 0; k < 2; ++k) {
+            const int r = pr0 + k;
+            if (!act[k]) continue;
+            const int gy = y0 + r;
             const float* u0 = su + (r + Q) * W + tx + TXOFF;
             const float* u1 = u0 + SY * W;
             const float uc0 = u0[0], uc1 = u1[0];
@@ -282,28 +299,29 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
             const float* g21 = g20 + SY * TTX;
             float m10 = 0.f, m11 = 0.f, m20 = 0.f, m21 = 0.f;
 #pragma unroll
-            for (int k = 1; k <= Q; ++k) {
-                m10 += ak[k - 1] * (g10[k] - g10[-k]);
-                m11 += ak[k - 1] * (g11[k] - g11[-k]);
-                m20 += ak[k - 1] * (g20[k * TTX] - g20[-k * TTX]);
-                m21 += ak[k - 1] * (g21[k * TTX] - g21[-k * TTX]);
+            for (int kk = 1; kk <= Q; ++kk) {
+                m10 += ak[kk - 1] * (g10[kk] - g10[-kk]);
+                m11 += ak[kk - 1] * (g11[kk] - g11[-kk]);
+                m20 += ak[kk - 1] * (g20[kk * TTX] - g20[-kk * TTX]);
+                m21 += ak[kk - 1] * (g21[kk * TTX] - g21[-kk * TTX]);
             }
             r0 += m10 * ih1 + m20 * ih2;
             r1 += m11 * ih1 + m21 * ih2;
             const size_t gi = (size_t)gy * P + gx;
             if (a.with_data && B.jf) {
                 const float* __restrict__ JF = reinterpret_cast<const float*>(B.jf);
-                for (int k = 0; k < a.K; ++k) {
-                    r0 += (float)a.Tk[k] * JF[(size_t)k * plane + gi];
-                    r1 += (float)a.Tk[k] * JF[(size_t)(a.K + k) * plane + gi];
+                #pragma unroll
+                for (int kb = 0; kb < 8; ++kb) {
+                    if (kb >= a.K) break;
+                    r0 += (float)a.Tk[kb] * JF[(size_t)kb * plane + gi];
+                    r1 += (float)a.Tk[kb] * JF[(size_t)(a.K + kb) * plane + gi];
                 }
             }
             if (MODE == 0) {
                 float* __restrict__ Un = reinterpret_cast<float*>(B.u[1 - a.cur]);
-                const float wv = __ldg(reinterpret_cast<const float*>(B.w) + gi);
                 const float dt2 = (float)a.dt2;
-                Un[gi] = 2.f * uc0 - Un[gi] + dt2 * wv * r0;
-                Un[gi + plane] = 2.f * uc1 - Un[gi + plane] + dt2 * wv * r1;
+                Un[gi] = 2.f * uc0 - up0[k] + dt2 * wv[k] * r0;
+                Un[gi + plane] = 2.f * uc1 - up1[k] + dt2 * wv[k] * r1;
             } else {
                 float* __restrict__ R = reinterpret_cast<float*>(B.r);
                 R[gi] = r0;

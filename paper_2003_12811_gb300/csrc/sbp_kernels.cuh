@@ -171,7 +171,9 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
         const size_t gi = (size_t)gy * P + gx;
         if (a.with_data && B.jf) {
             const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
-            for (int k = 0; k < a.K; ++k) {
+            #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= a.K) break;
                 r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
                 r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
             }
@@ -194,6 +196,92 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
 // with the boundary rows of D, plus the SAT contributions prepared by k_face_sat:
 //   at depth d < NCOL from face f:  D_m[face row][i_m] / H_m[i_m] * a_J(s)   (D_m^T spread)
 //   on the face itself:             the face term of k_face_sat
+// One strip node: narrow terms (closure triples or interior edge weights), mixed terms with the
+// boundary rows of D, SAT contributions of k_face_sat, forcing, and the leapfrog update.
+// u0(j1, j2), u1(j1, j2): displacement components; cc(plane, j1, j2): coefficient planes.
+template <typename T, int O, int MODE, class FU0, class FU1, class FC>
+__device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a, int i1, int i2, FU0 u0, FU1 u1, FC cc) {
+    const int n1 = B.n1, n2 = B.n2, P = B.pitch;
+    const size_t plane = (size_t)n2 * P;
+    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0);
+    dxx_vec<O, T>(n1, i1, [&](int j) { return u0(j, i2); }, [&](int j) { return u1(j, i2); },
+                  [&](int k) { return cc(0, k, i2); }, [&](int k) { return cc(1, k, i2); },
+                  [&](int k) { return cc(2, k, i2); }, rx0, rx1);
+    dxx_vec<O, T>(n2, i2, [&](int j) { return u0(i1, j); }, [&](int j) { return u1(i1, j); },
+                  [&](int k) { return cc(3, i1, k); }, [&](int k) { return cc(4, i1, k); },
+                  [&](int k) { return cc(5, i1, k); }, ry0, ry1);
+    T r0 = rx0 * ih1 * ih1 + ry0 * ih2 * ih2;
+    T r1 = rx1 * ih1 * ih1 + ry1 * ih2 * ih2;
+    {
+        int lo, hi;
+        drow_range<O>(n1, i1, lo, hi);
+        T s0 = T(0), s1 = T(0);
+        for (int aa = lo; aa <= hi; ++aa) {
+            const T d = T(dcoef<O>(n1, i1, aa));
+            if (d == T(0)) continue;
+            const T du0 = dsum<O, T>(n2, i2, [&](int bb) { return u0(aa, bb); }) * ih2;
+            const T du1 = dsum<O, T>(n2, i2, [&](int bb) { return u1(aa, bb); }) * ih2;
+            s0 += d * (cc(6, aa, i2) * du0 + cc(7, aa, i2) * du1);
+            s1 += d * (cc(8, aa, i2) * du0 + cc(9, aa, i2) * du1);
+        }
+        r0 += s0 * ih1;
+        r1 += s1 * ih1;
+        drow_range<O>(n2, i2, lo, hi);
+        s0 = T(0);
+        s1 = T(0);
+        for (int bb = lo; bb <= hi; ++bb) {
+            const T d = T(dcoef<O>(n2, i2, bb));
+            if (d == T(0)) continue;
+            const T du0 = dsum<O, T>(n1, i1, [&](int aa) { return u0(aa, bb); }) * ih1;
+            const T du1 = dsum<O, T>(n1, i1, [&](int aa) { return u1(aa, bb); }) * ih1;
+            s0 += d * (cc(6, i1, bb) * du0 + cc(8, i1, bb) * du1);
+            s1 += d * (cc(7, i1, bb) * du0 + cc(9, i1, bb) * du1);
+        }
+        r0 += s0 * ih2;
+        r1 += s1 * ih2;
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const FaceDev& F = B.f[f];
+        const int m = F.m;
+        const int im = m == 0 ? i1 : i2, Nm = m == 0 ? n1 : n2;
+        const int d = F.side ? Nm - 1 - im : im;
+        if (d >= Ord<O>::NCOL) continue;
+        const int s = m == 0 ? i2 : i1;
+        const T* __restrict__ sat = reinterpret_cast<const T*>(F.sat);
+        const int nf = F.nf;
+        const double hm = m == 0 ? B.h1 : B.h2;
+        const T fac = T(dcoef<O>(Nm, F.side ? Nm - 1 : 0, im) / (hm * hm * hweight<O>(Nm, im)));
+        r0 += fac * sat[2 * nf + s];
+        r1 += fac * sat[3 * nf + s];
+        if (d == 0) {
+            r0 += sat[s];
+            r1 += sat[nf + s];
+        }
+    }
+    const size_t gi = (size_t)i2 * P + i1;
+    if (a.with_data && B.jf) {
+        const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
+        #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= a.K) break;
+            r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
+            r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
+        }
+    }
+    if (MODE == 0) {
+        T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = T(a.dt2);
+        Un[gi] = T(2) * u0(i1, i2) - Un[gi] + dt2 * wv * r0;
+        Un[gi + plane] = T(2) * u1(i1, i2) - Un[gi + plane] + dt2 * wv * r1;
+    } else {
+        T* __restrict__ R = reinterpret_cast<T*>(B.r);
+        R[gi] = r0;
+        R[gi + plane] = r1;
+    }
+}
+
 template <typename T, int O, int MODE>
 __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
     const int n1 = B.n1, n2 = B.n2, P = B.pitch, S = B.strip;
@@ -216,61 +304,117 @@ __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
     const T* __restrict__ U0 = reinterpret_cast<const T*>(B.u[a.cur]);
     const T* __restrict__ U1 = U0 + plane;
     const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
-    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
-    const size_t row2 = (size_t)i2 * P;
+    strip_node<T, O, MODE>(
+        B, a, i1, i2, [&](int j1, int j2) { return __ldg(U0 + (size_t)j2 * P + j1); },
+        [&](int j1, int j2) { return __ldg(U1 + (size_t)j2 * P + j1); },
+        [&](int pl, int j1, int j2) { return __ldg(C + pl * plane + (size_t)j2 * P + j1); });
+}
 
-    // narrow terms along x1 (line i2) and x2 (column i1)
-    T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0);
-    dxx_vec<O, T>(n1, i1,
-                  [&](int j) { return __ldg(U0 + row2 + j); }, [&](int j) { return __ldg(U1 + row2 + j); },
-                  [&](int k) { return __ldg(C + row2 + k); }, [&](int k) { return __ldg(C + plane + row2 + k); },
-                  [&](int k) { return __ldg(C + 2 * plane + row2 + k); }, rx0, rx1);
-    dxx_vec<O, T>(n2, i2,
-                  [&](int j) { return __ldg(U0 + (size_t)j * P + i1); }, [&](int j) { return __ldg(U1 + (size_t)j * P + i1); },
-                  [&](int k) { return __ldg(C + 3 * plane + (size_t)k * P + i1); },
-                  [&](int k) { return __ldg(C + 4 * plane + (size_t)k * P + i1); },
-                  [&](int k) { return __ldg(C + 5 * plane + (size_t)k * P + i1); }, ry0, ry1);
-    T r0 = rx0 * ih1 * ih1 + ry0 * ih2 * ih2;
-    T r1 = rx1 * ih1 * ih1 + ry1 * ih2 * ih2;
+// ============================================================================ boundary strips, tiled
+// The strips are cut into tiles of 32 nodes along the face x (strip width) nodes across it:
+// bottom and top bands (tiles along x1), left and right bands (tiles along x2, between the
+// bands).  A tile and a halo of HALO nodes (>= the widest closure stencil) are staged in shared
+// memory (2 displacement + 10 coefficient planes).  The mixed fluxes g1_j = c_1j2l D_2 u_l and
+// g2_j = c_1l2j D_1 u_l are formed once per staged node (where their stencils fit), so every
+// output node needs only the narrow rows, two <= NCOL-tap sums and its SAT terms.
+template <int O> struct StripTile {
+    static constexpr int HALO = O == 2 ? 3 : (O == 4 ? 8 : 12);
+    static constexpr int S = Ord<O>::NCLOS > Ord<O>::NCOL ? Ord<O>::NCLOS : Ord<O>::NCOL;
+    static constexpr int RLONG = 32 + 2 * HALO;
+    static constexpr int RMAX = RLONG * (S + HALO);     // one side of the region is the face
+    static constexpr int ELEMS = 16 * RMAX;             // 12 staged planes + 4 flux planes
+    static constexpr int THREADS = 32 * S;
+};
 
-    // mixed: D_1 (c_1j2l D_2 u_l) + D_2 (c_2j1l D_1 u_l)
-    {
-        int lo, hi;
-        drow_range<O>(n1, i1, lo, hi);
-        T s0 = T(0), s1 = T(0);
-        for (int aa = lo; aa <= hi; ++aa) {
-            const T d = T(dcoef<O>(n1, i1, aa));
-            if (d == T(0)) continue;
-            const T du0 = dsum<O, T>(n2, i2, [&](int bb) { return __ldg(U0 + (size_t)bb * P + aa); }) * ih2;
-            const T du1 = dsum<O, T>(n2, i2, [&](int bb) { return __ldg(U1 + (size_t)bb * P + aa); }) * ih2;
-            const size_t gi = row2 + aa;
-            const T m6 = __ldg(C + 6 * plane + gi), m7 = __ldg(C + 7 * plane + gi),
-                    m8 = __ldg(C + 8 * plane + gi), m9 = __ldg(C + 9 * plane + gi);
-            s0 += d * (m6 * du0 + m7 * du1);
-            s1 += d * (m8 * du0 + m9 * du1);
-        }
-        r0 += s0 * ih1;
-        r1 += s1 * ih1;
-        drow_range<O>(n2, i2, lo, hi);
-        s0 = T(0);
-        s1 = T(0);
-        for (int bb = lo; bb <= hi; ++bb) {
-            const T d = T(dcoef<O>(n2, i2, bb));
-            if (d == T(0)) continue;
-            const size_t rowb = (size_t)bb * P;
-            const T du0 = dsum<O, T>(n1, i1, [&](int aa) { return __ldg(U0 + rowb + aa); }) * ih1;
-            const T du1 = dsum<O, T>(n1, i1, [&](int aa) { return __ldg(U1 + rowb + aa); }) * ih1;
-            const size_t gi = rowb + i1;
-            const T m6 = __ldg(C + 6 * plane + gi), m7 = __ldg(C + 7 * plane + gi),
-                    m8 = __ldg(C + 8 * plane + gi), m9 = __ldg(C + 9 * plane + gi);
-            s0 += d * (m6 * du0 + m8 * du1);
-            s1 += d * (m7 * du0 + m9 * du1);
-        }
-        r0 += s0 * ih2;
-        r1 += s1 * ih2;
+template <typename T, int O, int MODE>
+__global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B, StepArgs a) {
+    using ST = StripTile<O>;
+    constexpr int S = ST::S, H = ST::HALO, NT = ST::THREADS;
+    extern __shared__ __align__(16) unsigned char strip_smem[];
+    T* sm = reinterpret_cast<T*>(strip_smem);
+    const int n1 = B.n1, n2 = B.n2, P = B.pitch;
+    const int nbx = (n1 + 31) / 32, nby = (n2 - 2 * S + 31) / 32;
+    int t = blockIdx.x, x0, y0, w, h;
+    bool along_x;
+    if (t < 2 * nbx) {
+        along_x = true;
+        const int band = t / nbx;
+        x0 = (t - band * nbx) * 32;
+        w = min(32, n1 - x0);
+        y0 = band ? n2 - S : 0;
+        h = S;
+    } else {
+        t -= 2 * nbx;
+        along_x = false;
+        const int side = t / nby;
+        y0 = S + (t - side * nby) * 32;
+        h = min(32, n2 - S - y0);
+        x0 = side ? n1 - S : 0;
+        w = S;
     }
-
-    // SAT contributions
+    const int rx0 = max(0, x0 - H), rx1 = min(n1, x0 + w + H);
+    const int ry0 = max(0, y0 - H), ry1 = min(n2, y0 + h + H);
+    const int RW = rx1 - rx0, RH = ry1 - ry0, RN = RW * RH;
+    const size_t plane = (size_t)n2 * P;
+    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+    // stage: asynchronous element copies (cp.async), all in flight before the single wait
+    for (int pl = 0; pl < 12; ++pl) {
+        const T* src = pl < 2 ? U + pl * plane : C + (pl - 2) * plane;
+        T* dst = sm + pl * ST::RMAX;
+        for (int r = threadIdx.x / 32; r < RH; r += NT / 32) {
+            const T* srow = src + (size_t)(ry0 + r) * P + rx0;
+            for (int c = threadIdx.x & 31; c < RW; c += 32) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + r * RW + c);
+                if (sizeof(T) == 8)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(srow + c) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(srow + c) : "memory");
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    auto at = [&](int pl, int j1, int j2) -> T& { return sm[pl * ST::RMAX + (j2 - ry0) * RW + (j1 - rx0)]; };
+    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    // fluxes at every staged node whose D stencils lie inside the staged region
+    for (int idx = threadIdx.x; idx < RN; idx += NT) {
+        const int r = idx / RW, c = idx - r * RW;
+        const int j1 = rx0 + c, j2 = ry0 + r;
+        int lo, hi;
+        drow_range<O>(n2, j2, lo, hi);
+        if (lo >= ry0 && hi < ry1) {     // g1 needs D_2 u
+            const T d0 = dsum<O, T>(n2, j2, [&](int bb) { return at(0, j1, bb); }) * ih2;
+            const T d1 = dsum<O, T>(n2, j2, [&](int bb) { return at(1, j1, bb); }) * ih2;
+            at(12, j1, j2) = at(8, j1, j2) * d0 + at(9, j1, j2) * d1;
+            at(13, j1, j2) = at(10, j1, j2) * d0 + at(11, j1, j2) * d1;
+        }
+        drow_range<O>(n1, j1, lo, hi);
+        if (lo >= rx0 && hi < rx1) {     // g2 needs D_1 u
+            const T d0 = dsum<O, T>(n1, j1, [&](int aa) { return at(0, aa, j2); }) * ih1;
+            const T d1 = dsum<O, T>(n1, j1, [&](int aa) { return at(1, aa, j2); }) * ih1;
+            at(14, j1, j2) = at(8, j1, j2) * d0 + at(10, j1, j2) * d1;
+            at(15, j1, j2) = at(9, j1, j2) * d0 + at(11, j1, j2) * d1;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i1 = along_x ? x0 + lane : x0 + wid;
+    const int i2 = along_x ? y0 + wid : y0 + lane;
+    if (i1 >= x0 + w || i2 >= y0 + h) return;
+    T rx0v = T(0), rx1v = T(0), ry0v = T(0), ry1v = T(0);
+    dxx_vec<O, T>(n1, i1, [&](int j) { return at(0, j, i2); }, [&](int j) { return at(1, j, i2); },
+                  [&](int k) { return at(2, k, i2); }, [&](int k) { return at(3, k, i2); },
+                  [&](int k) { return at(4, k, i2); }, rx0v, rx1v);
+    dxx_vec<O, T>(n2, i2, [&](int j) { return at(0, i1, j); }, [&](int j) { return at(1, i1, j); },
+                  [&](int k) { return at(5, i1, k); }, [&](int k) { return at(6, i1, k); },
+                  [&](int k) { return at(7, i1, k); }, ry0v, ry1v);
+    T r0 = rx0v * ih1 * ih1 + ry0v * ih2 * ih2;
+    T r1 = rx1v * ih1 * ih1 + ry1v * ih2 * ih2;
+    r0 += dsum<O, T>(n1, i1, [&](int aa) { return at(12, aa, i2); }) * ih1 +
+          dsum<O, T>(n2, i2, [&](int bb) { return at(14, i1, bb); }) * ih2;
+    r1 += dsum<O, T>(n1, i1, [&](int aa) { return at(13, aa, i2); }) * ih1 +
+          dsum<O, T>(n2, i2, [&](int bb) { return at(15, i1, bb); }) * ih2;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const FaceDev& F = B.f[f];
@@ -290,10 +434,12 @@ __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
             r1 += sat[nf + s];
         }
     }
-    const size_t gi = row2 + i1;
+    const size_t gi = (size_t)i2 * P + i1;
     if (a.with_data && B.jf) {
         const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
-        for (int k = 0; k < a.K; ++k) {
+        #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= a.K) break;
             r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
             r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
         }
@@ -301,8 +447,8 @@ __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
     if (MODE == 0) {
         T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
         const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = T(a.dt2);
-        Un[gi] = T(2) * U0[gi] - Un[gi] + dt2 * wv * r0;
-        Un[gi + plane] = T(2) * U1[gi] - Un[gi + plane] + dt2 * wv * r1;
+        Un[gi] = T(2) * at(0, i1, i2) - Un[gi] + dt2 * wv * r0;
+        Un[gi + plane] = T(2) * at(1, i1, i2) - Un[gi + plane] + dt2 * wv * r1;
     } else {
         T* __restrict__ R = reinterpret_cast<T*>(B.r);
         R[gi] = r0;
@@ -394,7 +540,9 @@ __device__ __forceinline__ void face_jump(const BlockDev* blocks, const BlockDev
     if (F.kind == FACE_DISP) {
         if (a.with_data && F.g) {
             const T* g = reinterpret_cast<const T*>(F.g);
-            for (int k = 0; k < a.K; ++k) {
+            #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= a.K) break;
                 w0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
                 w1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
             }
@@ -438,7 +586,9 @@ __global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* _
         }
         if (a.with_data && F.g) {
             const T* g = reinterpret_cast<const T*>(F.g);
-            for (int k = 0; k < a.K; ++k) {
+            #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= a.K) break;
                 f0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
                 f1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
             }
