@@ -143,6 +143,50 @@ def cpu_baseline(target_seconds=12.0):
                       f"{time.perf_counter() - t0:.1f} s incl. assembly"}
 
 
+def serving_bench(nshots=32, side_range=(201, 801), rate=64.0, tick=32):
+    """Served batch (reduced config 4): nshots single-block curvilinear shots, side ~ U(side_range),
+    steps = side, Poisson arrivals; FP32 continuous batching under an HBM cap that binds, against
+    the plain FP64 one-solve-at-a-time GPU path on the same shots.  Setup (grid, material, CFL)
+    is inside both timings."""
+    import numpy as np
+    import torch
+    from paper_2003_12811_gb300 import Solver
+    from paper_2003_12811_gb300.binding import footprint_bytes
+    from paper_2003_12811_gb300.serve import ServingEngine, Request, GpuBackend, percentile
+    specs = W.config4_requests(nshots, side_range, rate=rate, steps_per_side=1.0, step_multiple=2)
+    probs = [W.shot_problem(side, seed) for (_, side, seed, _) in specs]
+    fps = [footprint_bytes(p, "fp32") for p in probs]
+    cap = int(8 * np.mean(fps))
+    reqs = [Request(rid=i, arrival=a, problem=p, nsteps=n) for i, ((a, _, _, n), p) in enumerate(zip(specs, probs))]
+    eng = ServingEngine(cap, backend=GpuBackend("fp32"), tick_steps=tick, max_active=32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = eng.run(reqs)
+    torch.cuda.synchronize()
+    served = time.perf_counter() - t0
+    lat = [r.latency for r in res]
+    # plain FP64 path: one solve at a time, in arrival order, same dt rule
+    t0 = time.perf_counter()
+    for (a, _, _, n), p in zip(specs, probs):
+        S = Solver(p, "fp64")
+        dt = S.suggest_dt(0.3)
+        z = [np.zeros((2, b.N2, b.N1)) for b in p.blocks]
+        S.set_state(z, z, 0.0)
+        S.sbp_step(n, dt)
+        S.state()
+        S.close()
+    torch.cuda.synchronize()
+    seq64 = time.perf_counter() - t0
+    return {"workload": f"served batch (config 4 reduced): {nshots} shots, side U{list(side_range)}, steps = side, "
+                        f"Poisson arrivals {rate}/s, FP32, HBM cap {cap / 1e9:.2f} GB (8 x mean footprint), tick {tick}",
+            "solves_per_s": nshots / served, "makespan_s": served,
+            "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
+            "fp64_sequential_solves_per_s": nshots / seq64,
+            "speedup_vs_fp64_sequential": seq64 / served,
+            "peak_active": eng.peak_active, "peak_bytes": eng.peak_bytes,
+            "node_updates": int(sum((p.blocks[0].N1 * p.blocks[0].N2) * n for (_, _, _, n), p in zip(specs, probs)))}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -175,6 +219,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n1", type=int, default=N1, help="nodes per block along x1 (profiling runs use smaller)")
     ap.add_argument("--n2", type=int, default=N2)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -279,6 +324,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e}
     S.close()
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = serving_bench()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -128,6 +128,28 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
  * (a cudaStream_t; NULL = default stream). */
 int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream);
 
+/* The same leapfrog steps as sbp_step, replayed from a CUDA graph: the first call (and any call
+ * with a different nsteps or dt) captures nsteps launches of the step kernels into a graph,
+ * later calls only update the device-side time and launch the graph on `stream`.  nsteps must
+ * be even (the displacement buffers return to the same parity).  Supports point sources; a
+ * handle with time-basis data (sbp_set_time_basis) is rejected with SBP_E_STATE.  Results are
+ * bitwise identical to sbp_step. */
+int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream);
+
+/* Device bytes a handle for `desc` holds after sbp_grid_create, sbp_set_material and
+ * sbp_set_state (fields, coefficients, metric, face buffers), used to admit solves by HBM
+ * footprint.  No device work. */
+int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out);
+
+/* Pick the FP32 interior kernel's rows per CTA for this grid by timing candidate shapes
+ * (operator applications on the current state, which is left unchanged); the choice is kept
+ * by the handle and written to *rows_out (0 = the built-in heuristic).  FP64 handles: no-op. */
+int sbp_autotune(sbp_handle* h, int* rows_out);
+
+/* Set the FP32 interior kernel's rows per CTA directly (e.g. a choice sbp_autotune made for
+ * another handle with the same grid); 0 restores the heuristic. */
+int sbp_set_tuning(sbp_handle* h, int rows_per_cta);
+
 /* Apply the spatial operator to the current level of every block (synchronous):
  * r = DD(c) u + J SAT(u) (+ J f(t) + point sources when with_data != 0, SAT data at t).
  * The result is read with sbp_get_field(..., SBP_FIELD_APPLY, ...). */

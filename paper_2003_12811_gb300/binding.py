@@ -79,6 +79,10 @@ def lib():
         L.sbp_suggest_dt.argtypes = [C.c_void_p, C.c_double, _DP]
         L.sbp_get_time.argtypes = [C.c_void_p, _DP]
         L.sbp_profile.argtypes = [C.c_void_p, C.c_int]
+        L.sbp_step_graph.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+        L.sbp_grid_footprint.argtypes = [C.POINTER(GridDesc), C.POINTER(C.c_longlong)]
+        L.sbp_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+        L.sbp_set_tuning.argtypes = [C.c_void_p, C.c_int]
         L.sbp_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -101,6 +105,41 @@ def pair10(Cfull):
         for q in range(p, 4):
             planes.append(Cfull[p // 2, p % 2, q // 2, q % 2])
     return np.stack(planes)
+
+
+def grid_desc(problem, precision="fp64"):
+    """Build the C grid descriptor of a ``workloads.Problem``; returns (desc, arrays kept alive)."""
+    keep = []
+    blocks = (BlockDesc * len(problem.blocks))()
+    for b, blk in enumerate(problem.blocks):
+        x1, x2 = _f64(blk.X[0]), _f64(blk.X[1])
+        keep += [x1, x2]
+        bd = blocks[b]
+        bd.n1, bd.n2 = blk.N1, blk.N2
+        bd.x1, bd.x2 = _ptr(x1), _ptr(x2)
+        bd.h1, bd.h2 = blk.spacing
+        for f, face in enumerate(blk.faces):
+            if face.kind not in BC:
+                raise ValueError(f"face kind {face.kind!r} is not supported by libsbp")
+            fd = bd.faces[f]
+            fd.kind = BC[face.kind]
+            if face.kind == "interface":
+                fd.nbr_block, fd.nbr_face, fd.reversed = face.nbr[0], face.nbr[1], int(bool(face.nbr[2]))
+            else:
+                fd.nbr_block, fd.nbr_face, fd.reversed = -1, -1, 0
+    keep.append(blocks)
+    prec = FP64 if precision == "fp64" else FP32
+    return GridDesc(problem.order, prec, len(problem.blocks), blocks, problem.beta), keep
+
+
+def footprint_bytes(problem, precision="fp32"):
+    """Device bytes a Solver for ``problem`` will hold (sbp_grid_footprint)."""
+    desc, keep = grid_desc(problem, precision)
+    out = C.c_longlong()
+    rc = lib().sbp_grid_footprint(C.byref(desc), C.byref(out))
+    if rc != SBP_OK:
+        raise SbpError(rc, "footprint query failed")
+    return int(out.value)
 
 
 class Solver:
@@ -177,6 +216,18 @@ class Solver:
     def sbp_step(self, nsteps, dt, stream=None):
         s = None if stream is None else C.c_void_p(stream)
         self._check(self.L.sbp_step(self.h, int(nsteps), float(dt), s))
+
+    def sbp_step_graph(self, nsteps, dt, stream=None):
+        s = None if stream is None else C.c_void_p(stream)
+        self._check(self.L.sbp_step_graph(self.h, int(nsteps), float(dt), s))
+
+    def sbp_autotune(self):
+        r = C.c_int()
+        self._check(self.L.sbp_autotune(self.h, C.byref(r)))
+        return r.value
+
+    def sbp_set_tuning(self, rows_per_cta):
+        self._check(self.L.sbp_set_tuning(self.h, int(rows_per_cta)))
 
     def sbp_apply(self, with_data=False, t=0.0):
         self._check(self.L.sbp_apply(self.h, int(bool(with_data)), float(t)))

@@ -105,6 +105,13 @@ struct sbp_handle {
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int fam; cudaEvent_t a, b; };
     std::vector<Pending> pending;
+    // CUDA-graph step loop (sbp_step_graph): graph of `graph_steps` steps of size `graph_dt`
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_steps = 0;
+    double graph_dt = 0.0;
+    double* d_time = nullptr;     // device copy of the time of the first step of a graph launch
+    // marching-kernel rows per CTA chosen by sbp_autotune (0 = default heuristic)
+    int rows_per_cta = 0;
 
     cudaEvent_t get_event() {
         if (!ev_pool.empty()) {
@@ -266,6 +273,7 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
                 int ncy = std::max(1, (4 * h->num_sms + ncx / 2) / ncx);
                 int rows = (n2i + ncy - 1) / ncy;
                 if (rows < 16) rows = std::min(16, n2i);
+                if (h->rows_per_cta > 0) rows = std::min(h->rows_per_cta, n2i);
                 ncy = (n2i + rows - 1) / rows;
                 constexpr size_t msm = MarchCfg<O>::BYTES;
                 if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, st>>>(hb.mmaps, b, a, rows, h->d_err);
@@ -577,6 +585,7 @@ int sbp_destroy(sbp_handle* h) {
         cudaEventDestroy(pd.b);
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     delete h;
     return SBP_OK;
 }
@@ -953,6 +962,167 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
     // the table copies read the stack arrays above: drain the stream before they go away
     if (cudaStreamSynchronize(st) != cudaSuccess) return h->fail(SBP_E_CUDA, "sbp_apply_noalloc kernels failed");
     return check_cuda(h, "sbp_apply_noalloc");
+}
+
+int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nsteps <= 0 || (nsteps & 1) || !(dt > 0) || !std::isfinite(dt))
+        return h->fail(SBP_E_INVALID_ARG, "sbp_step_graph needs an even positive step count and dt > 0");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    if (h->nbasis != 0) return h->fail(SBP_E_STATE, "sbp_step_graph supports point sources only (no time-basis data)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!h->d_time) {
+        h->d_time = (double*)h->dalloc(sizeof(double));
+        if (!h->d_time) return h->fail(SBP_E_OOM, "graph time buffer");
+    }
+    if (!h->graph_exec || h->graph_steps != nsteps || h->graph_dt != dt) {
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        // capture on a private stream: the captured launches read the time from d_time and
+        // use fixed buffer parities, so the graph can be replayed from any state with the same
+        // parity (nsteps is even)
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return h->fail(SBP_E_CUDA, "stream");
+        const bool prof = h->prof;
+        h->prof = false;
+        long long saved[4];
+        for (int k = 0; k < 4; ++k) saved[k] = h->launches[k];
+        cudaGraph_t g = nullptr;
+        int rc = SBP_OK;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = SBP_E_CUDA;
+        for (int n = 0; n < nsteps && rc == SBP_OK; ++n) {
+            StepArgs a{};
+            a.with_data = 1;
+            a.dt2 = dt * dt;
+            a.cur = (h->cur + n) & 1;
+            a.tstep = n;
+            a.tdev = h->d_time;
+            a.dt = dt;
+            rc = run_operator(h, a, 0, cs);
+        }
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) rc = SBP_E_CUDA;
+        cudaStreamDestroy(cs);
+        h->prof = prof;
+        for (int k = 0; k < 4; ++k) h->launches[k] = saved[k];
+        if (rc != SBP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return h->fail(SBP_E_CUDA, "graph capture failed");
+        }
+        if (cudaGraphInstantiate(&h->graph_exec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            h->graph_exec = nullptr;
+            return h->fail(SBP_E_CUDA, "graph instantiation failed");
+        }
+        cudaGraphDestroy(g);
+        h->graph_steps = nsteps;
+        h->graph_dt = dt;
+    }
+    double t0 = h->t;   // pageable source: the value is staged at call time
+    if (cudaMemcpyAsync(h->d_time, &t0, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaGraphLaunch(h->graph_exec, st) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "graph launch failed");
+    // launches in the graph, per family (counted as if launched one by one)
+    {
+        const int nb = (int)h->blocks.size();
+        h->launches[0] += (long long)nsteps * nb;
+        h->launches[1] += (long long)nsteps * nb;
+        if (h->nface_nodes > 0) h->launches[2] += 2LL * nsteps;
+        if (!h->src_nodes.empty()) h->launches[3] += nsteps;
+    }
+    h->t += nsteps * dt;
+    return SBP_OK;
+}
+
+int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out) {
+    if (!desc || !bytes_out || desc->nblocks < 1 || !desc->blocks) return SBP_E_INVALID_ARG;
+    if (desc->precision != SBP_FP64 && desc->precision != SBP_FP32) return SBP_E_INVALID_ARG;
+    const long long es = desc->precision == SBP_FP64 ? 8 : 4;
+    long long total = 3 * 256;   // scalars
+    auto al = [](long long b) { return (b + 255) / 256 * 256; };
+    for (int b = 0; b < desc->nblocks; ++b) {
+        const sbp_block_desc& bd = desc->blocks[b];
+        if (bd.n1 < 2 || bd.n2 < 2) return SBP_E_INVALID_ARG;
+        const long long pitch = (bd.n1 + 31) / 32 * 32;
+        const long long plane = (long long)bd.n2 * pitch;
+        // u (2 x 2), c (10), w (1), r (2) in the field precision; X (2), G (4), J (1) in FP64
+        total += al(2 * plane * es) * 2 + al(10 * plane * es) + al(plane * es) + al(2 * plane * es);
+        total += al(2 * plane * 8) + al(4 * plane * 8) + al(plane * 8);
+        for (int f = 0; f < 4; ++f) {
+            const long long nf = f < 2 ? bd.n2 : bd.n1;
+            total += al(nf * 8) + 2 * al(4 * nf * es) + al(3 * nf * es) + al(2 * 8 * nf * es);
+        }
+    }
+    total += 4096;   // block views, face tables, source tables
+    *bytes_out = total;
+    return SBP_OK;
+}
+
+int sbp_set_tuning(sbp_handle* h, int rows_per_cta) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (rows_per_cta < 0) return h->fail(SBP_E_INVALID_ARG, "rows per CTA must be >= 0");
+    if (rows_per_cta != h->rows_per_cta && h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    h->rows_per_cta = rows_per_cta;
+    return SBP_OK;
+}
+
+int sbp_autotune(sbp_handle* h, int* rows_out) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    if (h->precision != SBP_FP32) {
+        if (rows_out) *rows_out = 0;
+        return SBP_OK;   // only the FP32 marching kernel has a tunable shape
+    }
+    // candidates for the marching kernel's rows per CTA; 0 = heuristic (one wave at 4 CTAs/SM)
+    const int cand[] = {0, 16, 32, 64, 128, 256};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    StepArgs a{};
+    a.cur = h->cur;
+    a.with_data = 0;
+    const int saved = h->rows_per_cta;
+    long long saved_l[4];
+    for (int k = 0; k < 4; ++k) saved_l[k] = h->launches[k];
+    for (int c : cand) {
+        h->rows_per_cta = c;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, 0);
+            int rc = run_operator(h, a, 1, 0);   // apply mode: the state is left untouched
+            cudaEventRecord(e1, 0);
+            if (rc != SBP_OK) {
+                h->rows_per_cta = saved;
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rc;
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;            // first repetition is a warm-up
+        }
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = c;
+        }
+    }
+    for (int k = 0; k < 4; ++k) h->launches[k] = saved_l[k];
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->rows_per_cta = best;
+    if (h->graph_exec) {   // the captured graph used the previous shape
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    if (rows_out) *rows_out = best;
+    return check_kernel_errors(h);
 }
 
 int sbp_get_time(const sbp_handle* h, double* t_out) {

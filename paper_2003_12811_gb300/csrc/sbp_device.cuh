@@ -177,10 +177,12 @@ struct StepArgs {
     int cur;                  // index of the current level in BlockDev::u
     int K;                    // number of time-basis functions
     int with_data;            // include boundary data / forcing / sources
-    int pad;
+    int tstep;                // graph mode: step index inside the captured sequence
     double dt2;               // dt^2 (step mode)
     double t;                 // time of the current level
     double Tk[8];             // basis values T_k(t)
+    const double* tdev;       // graph mode: device time of the first captured step (else null)
+    double dt;                // graph mode: step size
 };
 
 }  // namespace sbp

@@ -673,11 +673,12 @@ struct SrcParam {
 template <typename T, int MODE>
 __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __restrict__ nodes, int nnodes,
                           const SrcParam* __restrict__ par, StepArgs a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nnodes || !a.with_data) return;
-    const SrcNode nd = nodes[t];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nnodes || !a.with_data) return;
+    const SrcNode nd = nodes[tid];
     const SrcParam p = par[nd.src];
-    const double x = 3.14159265358979323846 * p.alpha_p * (a.t - p.t0);
+    const double tnow = a.tdev ? *a.tdev + a.tstep * a.dt : a.t;   // graph mode reads the time on the device
+    const double x = 3.14159265358979323846 * p.alpha_p * (tnow - p.t0);
     const double Wt = (1.0 - 2.0 * x * x) * exp(-x * x);        // Ricker wavelet (Sec. 7.4)
     const BlockDev& B = blocks[nd.block];
     const size_t plane = (size_t)B.n2 * B.pitch;

@@ -1,0 +1,193 @@
+"""Continuous batching of independent forward solves ("shots") on one GPU.
+
+Requests arrive over time (each with its own grid, material, sources and step count).  The
+engine admits a waiting request as soon as a slot is free and its device footprint
+(``sbp_grid_footprint``) fits under the HBM cap, keeps every admitted shot's wavefield resident,
+and advances all active shots in ticks of ``tick_steps`` leapfrog steps.  Each shot runs on its
+own CUDA stream and its ticks are replayed from a CUDA graph (``sbp_step_graph``), so the
+kernels of different shots overlap on the device; when a shot finishes, its result is read
+back, its memory is released and the next request is admitted -- while the others keep running.
+
+All arithmetic is in libsbp; this module only schedules.  The scheduling logic is written
+against a small backend interface so that it can be exercised without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Any, Callable, List, Optional
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the engine starts
+    problem: Any                   # workloads.Problem
+    nsteps: int
+    dt: Optional[float] = None     # None: dt = suggest_dt(cfl) of the shot
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    nsteps: int
+    dt: float
+    fields: Any                    # final displacement per block (host arrays), or backend data
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class GpuBackend:
+    """libsbp shots on CUDA streams (torch streams/events are used only as handles)."""
+
+    def __init__(self, precision="fp32", autotune=True):
+        import torch
+        from .binding import Solver, footprint_bytes
+        self.torch = torch
+        self.Solver = Solver
+        self.footprint_bytes = footprint_bytes
+        self.precision = precision
+        self.autotune = autotune
+        self._tuned = {}
+
+    def footprint(self, problem) -> int:
+        return self.footprint_bytes(problem, self.precision)
+
+    def create(self, problem, cfl, dt=None):
+        import numpy as np
+        torch = self.torch
+        S = self.Solver(problem, self.precision)
+        if dt is None:
+            dt = S.suggest_dt(cfl)
+        z = [np.zeros((2, b.N2, b.N1)) for b in problem.blocks]
+        S.set_state(z, z, 0.0)
+        if self.autotune:
+            key = tuple((b.N1, b.N2) for b in problem.blocks) + (problem.order,)
+            if key not in self._tuned:
+                self._tuned[key] = S.sbp_autotune()
+            else:
+                S.sbp_set_tuning(self._tuned[key])
+        return _GpuShot(S, torch.cuda.Stream(), dt, torch)
+
+
+class _GpuShot:
+    def __init__(self, solver, stream, dt, torch):
+        self.S = solver
+        self.stream = stream
+        self.dt = dt
+        self.torch = torch
+        self.event = None
+
+    def launch(self, nsteps):
+        h = self.stream.cuda_stream
+        if nsteps % 2 == 0:
+            self.S.sbp_step_graph(nsteps, self.dt, h)
+        else:
+            self.S.sbp_step(nsteps, self.dt, h)
+        self.event = self.torch.cuda.Event()
+        self.event.record(self.stream)
+
+    def busy(self) -> bool:
+        return self.event is not None and not self.event.query()
+
+    def result(self):
+        self.stream.synchronize()
+        _, u = self.S.state()
+        return u
+
+    def close(self):
+        self.S.close()
+
+
+class ServingEngine:
+    def __init__(self, hbm_cap_bytes: int, backend=None, tick_steps: int = 32, max_active: int = 16,
+                 cfl: float = 0.3, clock: Callable[[], float] = time.perf_counter,
+                 idle_sleep: float = 2e-4, sleep: Callable[[float], None] = time.sleep):
+        if tick_steps < 2 or tick_steps % 2:
+            raise ValueError("tick_steps must be an even number >= 2")
+        self.cap = int(hbm_cap_bytes)
+        self.backend = backend if backend is not None else GpuBackend()
+        self.tick = tick_steps
+        self.max_active = max_active
+        self.cfl = cfl
+        self.clock = clock
+        self.idle_sleep = idle_sleep
+        self.sleep = sleep
+        self.peak_bytes = 0           # largest admitted footprint sum seen
+        self.peak_active = 0
+        self.trace: List[tuple] = []  # (time, event, rid) for inspection
+
+    def run(self, requests: List[Request]) -> List[Result]:
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        waiting: collections.deque = collections.deque()
+        active = []
+        used = 0
+        results = []
+        t0 = self.clock()
+        while pending or waiting or active:
+            now = self.clock() - t0
+            progressed = False
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            # admission: first come, first served, by device footprint
+            while waiting and len(active) < self.max_active:
+                req = waiting[0]
+                fp = self.backend.footprint(req.problem)
+                if fp > self.cap:
+                    raise ValueError(f"request {req.rid} needs {fp} bytes, more than the cap {self.cap}")
+                if used + fp > self.cap:
+                    break
+                waiting.popleft()
+                shot = self.backend.create(req.problem, self.cfl, req.dt)
+                used += fp
+                self.peak_bytes = max(self.peak_bytes, used)
+                active.append(dict(req=req, shot=shot, fp=fp, done=0, admitted=self.clock() - t0))
+                self.peak_active = max(self.peak_active, len(active))
+                self.trace.append((self.clock() - t0, "admit", req.rid))
+                progressed = True
+            # progress every active shot whose previous tick has finished
+            still = []
+            for slot in active:
+                shot, req = slot["shot"], slot["req"]
+                if shot.busy():
+                    still.append(slot)
+                    continue
+                if slot["done"] >= req.nsteps:
+                    fields = shot.result()
+                    shot.close()
+                    used -= slot["fp"]
+                    t = self.clock() - t0
+                    results.append(Result(req.rid, req.arrival, slot["admitted"], t, req.nsteps, shot.dt, fields))
+                    self.trace.append((t, "finish", req.rid))
+                    progressed = True
+                    continue
+                n = min(self.tick, req.nsteps - slot["done"])
+                shot.launch(n)
+                slot["done"] += n
+                still.append(slot)
+                progressed = True
+            active = still
+            if not progressed:
+                if pending and not waiting and not active:
+                    # nothing resident: jump to the next arrival instead of spinning
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(min(wait, 0.05))
+                else:
+                    self.sleep(self.idle_sleep)
+        return sorted(results, key=lambda r: r.rid)
+
+
+def percentile(values, q):
+    v = sorted(values)
+    if not v:
+        return float("nan")
+    k = (len(v) - 1) * q / 100.0
+    lo, hi = int(k), min(int(k) + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)

@@ -1,0 +1,81 @@
+"""Serving layer on the GPU: graph-replayed steps equal plain steps, the autotuner's choice does
+not change results, and every shot served in a mix of concurrent shots equals the same shot run
+alone (bitwise: the same kernels on the same data)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _zero(P):
+    return [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+
+
+@pytest.mark.parametrize("prec", ("fp32", "fp64"))
+def test_graph_steps_equal_plain_steps(prec):
+    from paper_2003_12811_gb300 import Solver
+    P = W.config3(n1=101, n2=51, order=6)
+    A, B = Solver(P, prec), Solver(P, prec)
+    dt = A.suggest_dt(0.3)
+    A.set_state(_zero(P), _zero(P), 0.0)
+    B.set_state(_zero(P), _zero(P), 0.0)
+    A.step(40, dt)
+    B.sbp_step_graph(20, dt)
+    B.sbp_step_graph(20, dt)          # replay of the same graph
+    ua, ub = A.state(), B.state()
+    assert B.sbp_get_time() == pytest.approx(40 * dt)
+    for x, y in zip(ua[1] + ua[0], ub[1] + ub[0]):
+        assert np.array_equal(x, y)
+    assert max(np.abs(x).max() for x in ua[1]) > 0     # the source did inject something
+    A.close()
+    B.close()
+
+
+def test_autotune_choice_does_not_change_results():
+    from paper_2003_12811_gb300 import Solver
+    P = W.config3(n1=161, n2=81, order=6)
+    A, B = Solver(P, "fp32"), Solver(P, "fp32")
+    dt = A.suggest_dt(0.3)
+    for S in (A, B):
+        S.set_state(_zero(P), _zero(P), 0.0)
+    rows = B.sbp_autotune()
+    assert rows in (0, 16, 32, 64, 128, 256)
+    B.sbp_set_tuning(16 if rows != 16 else 32)
+    A.step(30, dt)
+    B.step(30, dt)
+    for x, y in zip(A.state()[1], B.state()[1]):
+        assert np.array_equal(x, y)
+    A.close()
+    B.close()
+
+
+def test_served_mix_equals_alone():
+    from paper_2003_12811_gb300 import Solver
+    from paper_2003_12811_gb300.binding import footprint_bytes
+    from paper_2003_12811_gb300.serve import ServingEngine, Request, GpuBackend
+    sides = [41, 61, 47, 73, 55]
+    probs = [W.shot_problem(s, seed=30 + i) for i, s in enumerate(sides)]
+    nsteps = [40, 66, 50, 30, 44]
+    fps = [footprint_bytes(p, "fp32") for p in probs]
+    cap = int(2.5 * max(fps))          # at most two or three resident at a time
+    reqs = [Request(rid=i, arrival=0.002 * i, problem=p, nsteps=n) for i, (p, n) in enumerate(zip(probs, nsteps))]
+    eng = ServingEngine(cap, backend=GpuBackend("fp32"), tick_steps=8, max_active=8)
+    res = eng.run(reqs)
+    assert eng.peak_bytes <= cap and eng.peak_active >= 2
+    for r in res:
+        S = Solver(probs[r.rid], "fp32")
+        S.set_state(_zero(probs[r.rid]), _zero(probs[r.rid]), 0.0)
+        S.step(r.nsteps, r.dt)
+        alone = S.state()[1]
+        S.close()
+        for x, y in zip(alone, r.fields):
+            assert np.array_equal(x, y), r.rid
+        assert max(np.abs(x).max() for x in alone) > 0

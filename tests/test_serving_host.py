@@ -1,0 +1,105 @@
+"""Host logic of the continuous-batching engine (no GPU): admission by footprint, FIFO order,
+concurrency, completion and latency accounting, with a simulated backend on a virtual clock."""
+import pytest
+
+from paper_2003_12811_gb300.serve import ServingEngine, Request, percentile
+
+
+class VClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+class FakeShot:
+    def __init__(self, clock, cost_per_step, dt, log, rid):
+        self.clock, self.cost, self.dt, self.log, self.rid = clock, cost_per_step, dt, log, rid
+        self.ready_at = 0.0
+        self.steps = 0
+
+    def launch(self, n):
+        self.ready_at = max(self.ready_at, self.clock()) + n * self.cost
+        self.steps += n
+        self.log.append(("launch", self.rid, n))
+
+    def busy(self):
+        return self.clock() < self.ready_at
+
+    def result(self):
+        return self.steps
+
+    def close(self):
+        self.log.append(("close", self.rid))
+
+
+class FakeBackend:
+    def __init__(self, clock, sizes):
+        self.clock, self.sizes, self.log = clock, sizes, []
+
+    def footprint(self, problem):
+        return self.sizes[problem]
+
+    def create(self, problem, cfl, dt=None):
+        self.log.append(("create", problem))
+        return FakeShot(self.clock, 1e-3, 0.01, self.log, problem)
+
+
+def _run(sizes, arrivals, nsteps, cap, max_active=8, tick=4):
+    clk = VClock()
+    be = FakeBackend(clk, sizes)
+    eng = ServingEngine(cap, backend=be, tick_steps=tick, max_active=max_active, clock=clk, sleep=clk.sleep,
+                        idle_sleep=1e-4)
+    reqs = [Request(rid=i, arrival=a, problem=i, nsteps=n) for i, (a, n) in enumerate(zip(arrivals, nsteps))]
+    return eng, be, eng.run(reqs)
+
+
+def test_all_requests_complete_with_their_steps():
+    eng, be, res = _run({i: 10 for i in range(6)}, [0.0, 0.001, 0.002, 0.01, 0.02, 0.5], [8, 12, 6, 4, 10, 2], cap=100)
+    assert [r.rid for r in res] == list(range(6))
+    assert [r.fields for r in res] == [8, 12, 6, 4, 10, 2]
+    assert all(r.finished >= r.admitted >= r.arrival for r in res)
+
+
+def test_footprint_cap_is_never_exceeded_and_admission_waits():
+    sizes = {0: 60, 1: 50, 2: 30, 3: 70}
+    eng, be, res = _run(sizes, [0.0, 0.0, 0.0, 0.0], [40, 40, 40, 40], cap=100)
+    assert eng.peak_bytes <= 100
+    # FIFO: request 1 (50) cannot join request 0 (60); it is admitted only after 0 finishes,
+    # and request 2 is not admitted ahead of it
+    order = [e[1] for e in be.log if e[0] == "create"]
+    assert order == [0, 1, 2, 3]
+    r = {x.rid: x for x in res}
+    assert r[1].admitted >= r[0].finished - 1e-12
+
+
+def test_work_overlaps_when_memory_allows():
+    eng, be, res = _run({i: 10 for i in range(5)}, [0.0] * 5, [20] * 5, cap=100)
+    assert eng.peak_active == 5
+    # all five run concurrently: the last finishes long before 5 sequential runs would
+    assert max(r.finished for r in res) < 5 * 20 * 1e-3
+
+
+def test_max_active_limits_concurrency():
+    eng, be, res = _run({i: 1 for i in range(6)}, [0.0] * 6, [8] * 6, cap=100, max_active=2)
+    assert eng.peak_active == 2
+
+
+def test_oversized_request_is_rejected():
+    with pytest.raises(ValueError):
+        _run({0: 500}, [0.0], [4], cap=100)
+
+
+def test_odd_remainders_and_ticks():
+    eng, be, res = _run({0: 1}, [0.0], [11], cap=10, tick=4)
+    launches = [e[2] for e in be.log if e[0] == "launch"]
+    assert launches == [4, 4, 3]
+
+
+def test_percentile():
+    assert percentile([1, 2, 3, 4], 50) == 2.5
+    assert percentile([5], 99) == 5

@@ -579,3 +579,53 @@ def _mms_tangent(gx, gy, curved, along):
         return (1 + 0.06 * np.sin(np.pi * gy) * np.pi * np.cos(np.pi * gx),
                 0.05 * np.pi * np.cos(np.pi * gx) + 0.04 * gy)
     return (0.06 * np.pi * np.cos(np.pi * gy) * np.sin(np.pi * gx), 1 + 0.04 * gx)
+
+
+# ----------------------------------------------------------------------------- config 4 (served batch)
+def _smooth_field(X1, X2, rng, nmodes=3, kmax=3.0):
+    """Seeded smooth field in [0, 1]: normalised sum of low Fourier modes of X."""
+    f = np.zeros_like(X1)
+    for _ in range(nmodes):
+        k1, k2 = rng.uniform(-kmax, kmax, 2) * np.pi
+        f += np.sin(k1 * X1 + k2 * X2 + rng.uniform(0, 2 * np.pi))
+    return 0.5 + 0.5 * f / nmodes
+
+
+def shot_problem(side: int, seed: int, order: int = 6, f_peak: float = 4.0) -> Problem:
+    """One served shot: a single curvilinear block side x side on a unit square perturbed by a
+    seeded smooth mapping; smooth random material after the Sec. 7.2 recipe (rho = 1 + r,
+    the 10 independent pair entries of C~ smooth in [0,1], +4 on I=K, J=L); traction-free top,
+    displacement elsewhere; a vertical Ricker point force at a seeded interior point."""
+    rng = np.random.default_rng(seed)
+    x1, x2 = ref_grid(side, side)
+    a1, a2 = rng.uniform(0.02, 0.05, 2)
+    X1 = x1 + a1 * np.sin(np.pi * x1) * np.sin(2 * np.pi * x2)
+    X2 = x2 + a2 * np.sin(2 * np.pi * x1) * np.sin(np.pi * x2)
+    rho = 1 + _smooth_field(X1, X2, rng)
+    m = np.zeros((4, 4) + X1.shape)
+    for a in range(4):
+        for b in range(a, 4):
+            m[a, b] = m[b, a] = _smooth_field(X1, X2, rng)
+    for a in range(4):
+        m[a, a] += 4
+    C = pair10_to_tensor(m)
+    faces = [Face("displacement"), Face("displacement"), Face("displacement"), Face("robin")]
+    src = PointSource(block=0, x_ref=(float(rng.uniform(0.3, 0.7)), float(rng.uniform(0.3, 0.7))),
+                      direction=(0.0, -1.0), amplitude=1.0, alpha_p=f_peak, t0=1.0 / f_peak)
+    return Problem(f"shot{seed}", order, [Block(X=np.stack([X1, X2]), rho=rho, C=C, faces=faces)], sources=[src])
+
+
+def config4_requests(nshots: int = 256, side_range=(201, 2001), rate: float = 1.0, seed: int = SEED,
+                     steps_per_side: float = 2.0, step_multiple: int = 2):
+    """Served batch: nshots requests with Poisson arrivals (rate per second), side lengths uniform
+    in side_range, steps = steps_per_side * side (rounded up to step_multiple).  Returns a list of
+    (arrival, problem, nsteps); problems are built lazily by calling the returned factory."""
+    rng = np.random.default_rng(seed + 4)
+    t = 0.0
+    out = []
+    for i in range(nshots):
+        t += rng.exponential(1.0 / rate)
+        side = int(rng.integers(side_range[0], side_range[1] + 1))
+        n = int(np.ceil(steps_per_side * side / step_multiple) * step_multiple)
+        out.append((t, side, seed + 100 + i, n))
+    return out
