@@ -109,7 +109,8 @@ struct sbp_handle {
     cudaGraphExec_t graph_exec = nullptr;
     int graph_steps = 0;
     double graph_dt = 0.0;
-    double* d_time = nullptr;     // device copy of the time of the first step of a graph launch
+    double* d_time = nullptr;     // device copies of the step times of a graph launch
+    int d_time_cap = 0;
     // marching-kernel rows per CTA chosen by sbp_autotune (0 = default heuristic)
     int rows_per_cta = 0;
 
@@ -971,9 +972,15 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
     if (h->nbasis != 0) return h->fail(SBP_E_STATE, "sbp_step_graph supports point sources only (no time-basis data)");
     cudaStream_t st = (cudaStream_t)stream;
-    if (!h->d_time) {
-        h->d_time = (double*)h->dalloc(sizeof(double));
+    if (h->d_time_cap < nsteps) {
+        h->dfree(h->d_time);
+        h->d_time = (double*)h->dalloc(sizeof(double) * nsteps);
+        h->d_time_cap = h->d_time ? nsteps : 0;
         if (!h->d_time) return h->fail(SBP_E_OOM, "graph time buffer");
+        if (h->graph_exec) {   // the captured launches point at the old buffer
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
     }
     if (!h->graph_exec || h->graph_steps != nsteps || h->graph_dt != dt) {
         if (h->graph_exec) {
@@ -1019,8 +1026,14 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         h->graph_steps = nsteps;
         h->graph_dt = dt;
     }
-    double t0 = h->t;   // pageable source: the value is staged at call time
-    if (cudaMemcpyAsync(h->d_time, &t0, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+    // the step times, accumulated exactly as sbp_step does (pageable source: staged at call time)
+    std::vector<double> times(nsteps);
+    double tt = h->t;
+    for (int n = 0; n < nsteps; ++n) {
+        times[n] = tt;
+        tt += dt;
+    }
+    if (cudaMemcpyAsync(h->d_time, times.data(), sizeof(double) * nsteps, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaGraphLaunch(h->graph_exec, st) != cudaSuccess)
         return h->fail(SBP_E_CUDA, "graph launch failed");
     // launches in the graph, per family (counted as if launched one by one)
@@ -1031,7 +1044,7 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         if (h->nface_nodes > 0) h->launches[2] += 2LL * nsteps;
         if (!h->src_nodes.empty()) h->launches[3] += nsteps;
     }
-    h->t += nsteps * dt;
+    h->t = tt;
     return SBP_OK;
 }
 

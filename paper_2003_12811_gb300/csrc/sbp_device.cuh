@@ -181,8 +181,8 @@ struct StepArgs {
     double dt2;               // dt^2 (step mode)
     double t;                 // time of the current level
     double Tk[8];             // basis values T_k(t)
-    const double* tdev;       // graph mode: device time of the first captured step (else null)
-    double dt;                // graph mode: step size
+    const double* tdev;       // graph mode: device array of the times of the captured steps (else null)
+    double dt;                // step size
 };
 
 }  // namespace sbp

@@ -677,7 +677,7 @@ __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __
     if (tid >= nnodes || !a.with_data) return;
     const SrcNode nd = nodes[tid];
     const SrcParam p = par[nd.src];
-    const double tnow = a.tdev ? *a.tdev + a.tstep * a.dt : a.t;   // graph mode reads the time on the device
+    const double tnow = a.tdev ? a.tdev[a.tstep] : a.t;   // graph mode: per-step times uploaded by the host
     const double x = 3.14159265358979323846 * p.alpha_p * (tnow - p.t0);
     const double Wt = (1.0 - 2.0 * x * x) * exp(-x * x);        // Ricker wavelet (Sec. 7.4)
     const BlockDev& B = blocks[nd.block];
