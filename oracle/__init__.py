@@ -16,6 +16,8 @@ scheme  metric (Sec. 3.2-3.3), transformed stiffness, the discrete elastic opera
         (Sec. 4.6-4.7), boundary SATs (Sec. 5), interface SATs (Sec. 6), leapfrog and RK4
         time stepping, discrete energy, CFL time step (Sec. 7), Ricker wavelet and
         discrete delta point sources (Sec. 7.4).
+adjoint discrete adjoint of the leapfrog scheme with explicit transposes, receiver misfit and its
+        gradient with respect to density and stiffness (Sec. 5.2 remark, Theorems 3 and 5).
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``.
 """

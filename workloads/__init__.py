@@ -629,3 +629,35 @@ def config4_requests(nshots: int = 256, side_range=(201, 2001), rate: float = 1.
         n = int(np.ceil(steps_per_side * side / step_multiple) * step_multiple)
         out.append((t, side, seed + 100 + i, n))
     return out
+
+
+# ----------------------------------------------------------------------------- misfit-gradient workload
+def config5(n: int = 1001, order: int = 6, blob: bool = False, nrec: int = 64, seed: int = SEED,
+            f_peak: float = 15.0):
+    """Misfit-gradient workload: one curvilinear block n x n on a perturbed unit square; smooth
+    tilted VTI stiffness (Thomsen eps = 0.2, delta = 0.1) and density 2.3 scaled by a smooth
+    seeded field within +-10 %; with ``blob`` a Gaussian inclusion (radius 0.08, centre 0.3 below
+    the surface) raises rho and C by 10 % at its centre.  Traction-free top, displacement (no data)
+    elsewhere; a vertical Ricker point force 0.05 below the surface at mid-width; ``nrec`` receivers
+    evenly spaced on the surface nodes.  Returns (problem, receivers) with receivers as
+    (block, i1, i2) node indices."""
+    rng = np.random.default_rng(seed + 5)
+    x1, x2 = ref_grid(n, n)
+    X1 = x1 + 0.03 * np.sin(np.pi * x1) * np.sin(2 * np.pi * x2)
+    X2 = x2 + 0.02 * np.sin(2 * np.pi * x1) * np.sin(np.pi * x2)
+    scale = 0.9 + 0.2 * _smooth_field(X1, X2, rng)
+    tilt = (np.pi / 8) * (2 * _smooth_field(X1, X2, rng) - 1)
+    if blob:
+        cx, cy, r = 0.5, float(X2.max()) - 0.3, 0.08
+        scale = scale * (1 + 0.1 * np.exp(-((X1 - cx) ** 2 + (X2 - cy) ** 2) / (2 * r * r)))
+    rho = C3_RHO * scale
+    cv = vti_voigt(rho, C3_VP, C3_VS, C3_EPS, C3_DELTA)
+    C = rotate_tensor(voigt_to_tensor(cv), tilt)
+    faces = [Face("displacement"), Face("displacement"), Face("displacement"), Face("robin")]
+    src = PointSource(block=0, x_ref=(0.5, 0.95), direction=(0.0, -1.0), amplitude=1.0,
+                      alpha_p=f_peak, t0=1.0 / f_peak)
+    prob = Problem("config5" + ("_blob" if blob else ""), order,
+                   [Block(X=np.stack([X1, X2]), rho=rho, C=C, faces=faces)], sources=[src])
+    idx = np.unique(np.round(np.linspace(0.05, 0.95, nrec) * (n - 1)).astype(int))
+    receivers = [(0, int(i), n - 1) for i in idx]
+    return prob, receivers
