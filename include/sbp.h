@@ -199,6 +199,41 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
 int sbp_get_time(const sbp_handle* h, double* t_out);
 int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, int* order_out);
 
+/* ---- misfit gradient (adjoint) --------------------------------------------------------------
+ * Sec. 5.2 remarks that self-adjointness (Theorems 3 and 5) lets an adjoint solver reuse the
+ * forward solver; these calls build that adjoint for the leapfrog scheme.
+ *
+ * Receivers: `rec` holds nrec triples (block, i1, i2) of node indices (host, copied); nodes must be
+ * distinct.  nrec = 0 removes them.  Errors: SBP_E_INVALID_ARG (bad index, duplicate node). */
+int sbp_set_receivers(sbp_handle* h, int nrec, const int* rec);
+
+/* Advance nsteps leapfrog steps exactly as sbp_step does and record, after every step, both
+ * displacement components at every receiver: traces[(n * nrec + r) * 2 + J] (host, FP64,
+ * nsteps * nrec * 2 values; may be null).  Synchronous.  SBP_E_STATE without receivers. */
+int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces);
+
+/* Misfit Phi = 1/2 dt sum_n sum_r sum_J (u_{n+1}[J, x_r] - observed[n, r, J])^2 over nsteps
+ * leapfrog steps from the current state (the levels sbp_record would record), and its exact
+ * discrete gradient with respect to the density and the stiffness of every node:
+ *   grad_rho[b]: n1*n2 doubles (x1 fastest), dPhi/drho;
+ *   grad_C[b]:   10 planes of n1*n2 doubles, dPhi/dC in the pair layout of sbp_set_material
+ *                (plane P = entry P of the upper triangle of M[2I+J][2K+L] = C_IJKL, which stands
+ *                for both M[p][q] and M[q][p]).
+ * Either array pointer (or an entry) may be null to skip that output; `observed` is host FP64
+ * [nsteps][nrec][2]; *misfit receives Phi.  Method: a forward pass that stores the state every
+ * `checkpoint_every` steps (0: ceil(sqrt(nsteps))), then, segment by segment from the last, a
+ * recomputation of the segment's levels and the adjoint recursion psi_n = 2 psi_{n+1} - psi_{n+2}
+ * + dt^2 W L psi_{n+1} + H^-1 W dPhi/du_{n+1} with the forward kernels (psi = H^-1 W lambda, lambda
+ * the Lagrange multipliers of the step equations), accumulating
+ *   dPhi/dc_p(x) += dt^2 (H psi_n)^T dL/dc_p(x) u_n,  dPhi/drho(x) -= H J psi_n . (u_{n+1} - 2u_n + u_{n-1}),
+ * and finally dPhi/dC from dPhi/dc through c_ijkl = J F_Ii C_IjKl F_Kk.  Device workspace: about
+ * (2 nsteps / K + K + 16) field levels per block plus 11 accumulator planes, allocated for the call.
+ * On return the state is the one after nsteps steps (as sbp_step would leave it).  Synchronous.
+ * Errors: SBP_E_STATE without receivers or when a displacement face carries boundary data (the
+ * data would then depend on C); SBP_E_OOM when the workspace does not fit. */
+int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* observed, int checkpoint_every,
+                        double* misfit, double* const* grad_rho, double* const* grad_C);
+
 #ifdef __cplusplus
 }
 #endif

@@ -139,13 +139,14 @@ def _with_stiffness(problem: W.Problem, stiff: List[np.ndarray]) -> W.Problem:
     return dataclasses.replace(problem, blocks=blocks, sources=[], time_basis=[])
 
 
-def stiffness_derivative(problem: W.Problem, block: int, P: int, i1: int, i2: int):
-    """dA_glob/dC_P(x) = A(E) - A(0) (A_glob is affine in C)."""
+def stiffness_derivative(problem: W.Problem, block: int, P: int, i1: int, i2: int, A0=None):
+    """dA_glob/dC_P(x) = A(E) - A(0) (A_glob is affine in C); A0 = A(0) may be passed in."""
     zero = [np.zeros_like(b.C) for b in problem.blocks]
     unit = [z.copy() for z in zero]
     unit[block][..., i2, i1] = W.pair10_to_tensor(pair_unit(P)[:, :, None, None])[..., 0, 0]
     A1 = Oracle(_with_stiffness(problem, unit)).A
-    A0 = Oracle(_with_stiffness(problem, zero)).A
+    if A0 is None:
+        A0 = Oracle(_with_stiffness(problem, zero)).A
     return (A1 - A0).tocsr()
 
 
@@ -153,9 +154,10 @@ def grad_stiffness(oracle: Oracle, levels, lams, dt: float, params):
     """dPhi/dC_P(x) for params given as (block, P, i1, i2)."""
     U = np.stack(levels[1:len(lams) + 1], axis=1)              # u_1 .. u_N as columns
     WL = np.stack(lams, axis=1) * oracle.wvec[:, None]          # diag(w) lambda_n
+    A0 = Oracle(_with_stiffness(oracle.problem, [np.zeros_like(b.C) for b in oracle.problem.blocks])).A
     out = []
     for (b, P, i1, i2) in params:
-        dA = stiffness_derivative(oracle.problem, b, P, i1, i2)
+        dA = stiffness_derivative(oracle.problem, b, P, i1, i2, A0)
         out.append(dt * dt * float(np.sum(WL * (dA @ U))))
     return np.array(out)
 

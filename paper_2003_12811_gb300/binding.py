@@ -86,6 +86,10 @@ def lib():
         L.sbp_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sbp_set_receivers.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
+        L.sbp_record.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP]
+        L.sbp_misfit_gradient.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP, C.c_int, _DP,
+                                          C.POINTER(_DP), C.POINTER(_DP)]
         _lib = L
     return _lib
 
@@ -260,6 +264,31 @@ class Solver:
         s = None if stream is None else C.c_void_p(stream)
         self._check(self.L.sbp_apply_noalloc(self.h, C.c_void_p(u_ptr), C.c_void_p(r_ptr), int(bool(with_data)),
                                              float(t), s))
+
+    def sbp_set_receivers(self, receivers):
+        """receivers: sequence of (block, i1, i2) node indices."""
+        rec = np.ascontiguousarray(np.asarray(receivers, dtype=np.int32).reshape(-1, 3))
+        self._nrec = rec.shape[0]
+        self._check(self.L.sbp_set_receivers(self.h, self._nrec, rec.ctypes.data_as(C.POINTER(C.c_int))))
+
+    def sbp_record(self, nsteps, dt):
+        """Step nsteps times; returns the receiver traces (nsteps, nrec, 2)."""
+        out = np.empty((int(nsteps), getattr(self, "_nrec", 0), 2))
+        self._check(self.L.sbp_record(self.h, int(nsteps), float(dt), _ptr(out)))
+        return out
+
+    def sbp_misfit_gradient(self, nsteps, dt, observed, checkpoint_every=0, rho=True, stiffness=True):
+        """Returns (misfit, [dPhi/drho (N2, N1)] or None, [dPhi/dC (10, N2, N1) pair layout] or None)."""
+        obs = _f64(observed)
+        nb = len(self.problem.blocks)
+        gr = [np.empty((b.N2, b.N1)) for b in self.problem.blocks] if rho else None
+        gc = [np.empty((10, b.N2, b.N1)) for b in self.problem.blocks] if stiffness else None
+        pr = (_DP * nb)(*[_ptr(a) for a in gr]) if rho else None
+        pc = (_DP * nb)(*[_ptr(a) for a in gc]) if stiffness else None
+        phi = C.c_double()
+        self._check(self.L.sbp_misfit_gradient(self.h, int(nsteps), float(dt), _ptr(obs), int(checkpoint_every),
+                                               C.byref(phi), pr, pc))
+        return phi.value, gr, gc
 
     def sbp_profile(self, enable):
         self._check(self.L.sbp_profile(self.h, int(bool(enable))))

@@ -1,0 +1,536 @@
+// libsbp adjoint kernels: receiver recording, misfit residuals, adjoint source injection, and the
+// accumulation of the misfit gradient with respect to the transformed stiffness c and the density.
+//
+// The scheme is u'' = W L(c) u + W data with W = 1/(rho J) and H L symmetric (Theorems 3 and 5,
+// H = H_1 (x) H_2).  For the leapfrog recursion u_{n+1} = 2u_n - u_{n-1} + dt^2 W (L u_n + data_n)
+// the multipliers lambda_n of the discrete Lagrangian give psi_n = H^-1 W lambda_n, and psi obeys
+// the same recursion run backwards with the homogeneous operator plus the source
+// H^-1 W dPhi/du_{n+1} (the paper's remark in Sec. 5.2 that the adjoint reuses the forward solver).
+// The gradient is
+//   dPhi/dc_p(x) = sum_n dt^2 (H psi_n)^T dL/dc_p(x) u_n,
+//   dPhi/drho(x) = -sum_n H(x) J(x) psi_n(x) . (u_{n+1} - 2u_n + u_{n-1})(x).
+// L is linear in c, so dL/dc_p(x) is read off the operator term by term: the narrow rows of
+// D_ii^FC(b) (closure triples and interior edge weights, Sec. 4.4), the mixed terms D_i c D_k
+// (Sec. 4.6), and the SAT terms of Sec. 5.1, 5.2 and 6, which involve c only at face nodes.
+#pragma once
+#include "sbp_kernels.cuh"
+
+namespace sbp {
+
+struct GradDev {
+    const void* seg;          // recomputed forward levels: level l (2 planes) at seg + l * lvl_elems
+    long long lvl_elems;
+    void* gc;                 // 10 accumulator planes (dPhi/dc, plane layout of BlockDev::c)
+    void* grho;               // 1 accumulator plane (dPhi/drho)
+    void* gsat[4];            // per face: 7 x nf SAT contributions (planes 3m, 3m+1, 3m+2, 6..9)
+};
+
+struct RecDev {
+    int block, pad;
+    long long gi;             // node offset in the planes
+    double hinv;              // 1 / H at the node
+};
+
+// ------------------------------------------------------------------ receivers and misfit
+template <typename T>
+__global__ void k_record(const BlockDev* __restrict__ blocks, const RecDev* __restrict__ rec, int nrec, int cur,
+                         double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    const RecDev d = rec[r];
+    const BlockDev& B = blocks[d.block];
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    const T* U = reinterpret_cast<const T*>(B.u[cur]);
+    out[2 * r] = (double)U[d.gi];
+    out[2 * r + 1] = (double)U[d.gi + plane];
+}
+
+// res = traces - observed per step (one CTA per step) and the per-step sum of squares
+__global__ void k_residual(const double* __restrict__ tr, const double* __restrict__ obs, double* __restrict__ res,
+                           int per_step, double* __restrict__ partial) {
+    const size_t base = (size_t)blockIdx.x * per_step;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < per_step; k += blockDim.x) {
+        const double r = tr[base + k] - obs[base + k];
+        res[base + k] = r;
+        acc += r * r;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// out = scale * sum(partial[0..n))   (one CTA of 256 threads, fixed summation order)
+__global__ void k_sum_scaled(const double* __restrict__ partial, int n, double scale, double* out) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partial[k];
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = scale * red[0];
+}
+
+// psi_n += H^-1 W dt res at the receivers (receiver nodes are distinct)
+template <typename T>
+__global__ void k_inject(const BlockDev* __restrict__ adj, const RecDev* __restrict__ rec, int nrec, int pcur,
+                         const double* __restrict__ res_row, double dt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    const RecDev d = rec[r];
+    const BlockDev& B = adj[d.block];
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    T* P = reinterpret_cast<T*>(B.u[pcur]);
+    const double s = d.hinv * (double)reinterpret_cast<const T*>(B.w)[d.gi] * dt;
+    P[d.gi] += T(s * res_row[2 * r]);
+    P[d.gi + plane] += T(s * res_row[2 * r + 1]);
+}
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ void face_node(const BlockDev& B, const FaceDev& F, int s, int& i1, int& i2) {
+    if (F.m == 0) { i1 = F.side ? B.n1 - 1 : 0; i2 = s; }
+    else { i2 = F.side ? B.n2 - 1 : 0; i1 = s; }
+}
+
+template <int O> __device__ __forceinline__ double node_h(const BlockDev& B, int i1, int i2) {
+    return B.h1 * hweight<O>(B.n1, i1) * B.h2 * hweight<O>(B.n2, i2);
+}
+
+// coefficient e_{m,kk} of b_{i+kk} in the interior edge weight E_m(i) (0 outside its support)
+template <int O> __device__ __forceinline__ double edge_coef(int m, int kk) {
+    return Edge<O>::template e<double>(m, [&](int q) { return q == kk ? 1.0 : 0.0; });
+}
+
+// d(h^2 D_xx(b) U |_row i) / d b_k  on a line of N nodes, for the two displacement components
+template <int O, typename T, class FU0, class FU1>
+__device__ __forceinline__ void narrow_dcoef(int N, int i, int k, FU0 u0, FU1 u1, T& m0, T& m1) {
+    using P = Ord<O>;
+    m0 = T(0);
+    m1 = T(0);
+    if (i < P::NCLOS || i >= N - P::NCLOS) {
+        const bool right = i >= N - P::NCLOS;
+        const int row = right ? N - 1 - i : i;
+        for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
+            int j = P::cj(t), kk = P::ck(t);
+            if (right) { j = N - 1 - j; kk = N - 1 - kk; }
+            if (kk != k) continue;
+            const T c = T(P::cc(t));
+            m0 += c * u0(j);
+            m1 += c * u1(j);
+        }
+        return;
+    }
+    const T uc0 = u0(i), uc1 = u1(i);
+#pragma unroll
+    for (int m = 1; m <= P::Q; ++m) {
+        const T ep = T(edge_coef<O>(m, k - i)), em = T(edge_coef<O>(m, k - i + m));
+        if (ep != T(0)) { m0 += ep * (u0(i + m) - uc0); m1 += ep * (u1(i + m) - uc1); }
+        if (em != T(0)) { m0 += em * (u0(i - m) - uc0); m1 += em * (u1(i - m) - uc1); }
+    }
+}
+
+// (D^T v)(x) * h = sum_row D[row][x] h v(row) on a line of N nodes
+template <int O, typename T, class F>
+__device__ __forceinline__ T dtsum(int N, int x, F v) {
+    constexpr int R = Ord<O>::NCOL + Ord<O>::Q;
+    const int lo = max(0, x - R), hi = min(N - 1, x + R);
+    T s = T(0);
+    for (int row = lo; row <= hi; ++row) {
+        const double d = dcoef<O>(N, row, x);
+        if (d != 0.0) s += T(d) * v(row);
+    }
+    return s;
+}
+
+template <int O> struct GradCfg {
+    // nodes at least GS from every face see only interior rows of every operator (rows within
+    // Q of the node are interior narrow rows, D^T is -D there, and H = h1 h2)
+    static constexpr int GS = Ord<O>::NCLOS + Ord<O>::Q;
+    // rows whose narrow coefficients can reach a node (closure triples reach |k - row| <= 1, 3, 5)
+    static constexpr int RR = O == 2 ? 2 : (O == 4 ? 4 : 6);
+    // support of the interior edge weights E_m (offsets of b relative to the edge's left node)
+    static constexpr int ELO = O == 2 ? SBP2_ELO : (O == 4 ? SBP4_ELO : SBP6_ELO);
+    static constexpr int EHI = O == 2 ? SBP2_EHI : (O == 4 ? SBP4_EHI : SBP6_EHI);
+};
+
+// ------------------------------------------------------------------ SAT part of the gradient
+// One thread per face node: the derivatives of (H psi)^T SAT(c, u) with respect to the c planes
+// at that node (the SATs involve c only at face nodes).  Terms, for face F with normal direction
+// m, outward sign nu, phi = H psi, and w = u - v (interface) or u (displacement):
+//   normal-spread amplitude  a_J = half nu c_mJmL w_L          -> phi_a,J = sum_d phi_J D_m[f][d] / H_m(d)
+//   tangential transpose     b_J = nu c_mLtJ w_L               -> eta_J = half H_t (D_t xi_J), xi = phi_f / (H_m0 H_t)
+//   penalty                  -J^Z_JL w_L                        -> own side and the neighbour's SAT
+//   traction (Robin, and the interface average) tau_J = nu (c_mJmL D_m u_L + c_mJtL D_t u_L)
+template <typename T, int O>
+__global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __restrict__ gd,
+                            const FaceRef* __restrict__ refs, int nrefs, int total, int pcur, int lvl, double beta) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const FaceRef fr = refs[find_face(refs, nrefs, t)];
+    const int s = t - fr.start;
+    const BlockDev& B = adj[fr.block];
+    const FaceDev& F = B.f[fr.face];
+    const GradDev& G = gd[fr.block];
+    T* out = reinterpret_cast<T*>(G.gsat[fr.face]);
+    const int nf = F.nf;
+    T g[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) g[k] = T(0);
+    if (F.kind != FACE_DISP && F.kind != FACE_ROBIN && F.kind != FACE_INTF) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) out[k * nf + s] = T(0);
+        return;
+    }
+    const int m = F.m, n1 = B.n1, n2 = B.n2, P = B.pitch;
+    const int Nm = m == 0 ? n1 : n2, Nt = m == 0 ? n2 : n1;
+    const double hm = m == 0 ? B.h1 : B.h2, ht = m == 0 ? B.h2 : B.h1;
+    const size_t plane = (size_t)n2 * P;
+    const T* __restrict__ Ps = reinterpret_cast<const T*>(B.u[pcur]);
+    const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)lvl * G.lvl_elems;
+    const T nu = T(F.nu);
+    const double inv_h0 = 1.0 / F.hm0;
+    // node at tangential index sp and depth d from the face
+    auto node = [&](int sp, int d) -> size_t {
+        int i1, i2;
+        if (m == 0) { i1 = F.side ? n1 - 1 - d : d; i2 = sp; }
+        else { i2 = F.side ? n2 - 1 - d : d; i1 = sp; }
+        return (size_t)i2 * P + i1;
+    };
+    auto hnode = [&](int sp, int d) -> double {
+        int i1, i2;
+        if (m == 0) { i1 = F.side ? n1 - 1 - d : d; i2 = sp; }
+        else { i2 = F.side ? n2 - 1 - d : d; i1 = sp; }
+        return node_h<O>(B, i1, i2);
+    };
+    const size_t gi = node(s, 0);
+    const double Hs = hnode(s, 0);
+    const T pf0 = T(Hs * (double)Ps[gi]), pf1 = T(Hs * (double)Ps[gi + plane]);
+    // the neighbour's scaled face adjoint (interface)
+    T pv0 = T(0), pv1 = T(0), v0 = T(0), v1 = T(0);
+    double inv_h0v = 0.0;
+    if (F.kind == FACE_INTF) {
+        const BlockDev& V = adj[F.nbr_block];
+        const FaceDev& FV = V.f[F.nbr_face];
+        const GradDev& GV = gd[F.nbr_block];
+        const int sv = F.reversed ? nf - 1 - s : s;
+        int j1, j2;
+        face_node(V, FV, sv, j1, j2);
+        const size_t gv = (size_t)j2 * V.pitch + j1, planev = (size_t)V.n2 * V.pitch;
+        const T* Pv = reinterpret_cast<const T*>(V.u[pcur]);
+        const T* Uv = reinterpret_cast<const T*>(GV.seg) + (size_t)lvl * GV.lvl_elems;
+        const double Hv = node_h<O>(V, j1, j2);
+        pv0 = T(Hv * (double)Pv[gv]);
+        pv1 = T(Hv * (double)Pv[gv + planev]);
+        v0 = Uv[gv];
+        v1 = Uv[gv + planev];
+        inv_h0v = 1.0 / FV.hm0;
+    }
+    // derivatives of u at the face node (true derivatives)
+    auto ucomp = [&](int L, int sp, int d) { return U[node(sp, d) + (size_t)L * plane]; };
+    T dn[2], dtg[2];
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+        const int fr_row = F.side ? Nm - 1 : 0;
+        dn[L] = dsum<O, T>(Nm, fr_row, [&](int j) { return ucomp(L, s, F.side ? Nm - 1 - j : j); }) * T(1.0 / hm);
+        dtg[L] = dsum<O, T>(Nt, s, [&](int j) { return ucomp(L, j, 0); }) * T(1.0 / ht);
+    }
+    // traction coefficient Theta_J (tau enters with -Theta_J)
+    T th0 = T(0), th1 = T(0);
+    if (F.kind == FACE_ROBIN) {
+        th0 = T(inv_h0) * pf0;
+        th1 = T(inv_h0) * pf1;
+    } else if (F.kind == FACE_INTF) {
+        th0 = T(0.5) * (T(inv_h0) * pf0 + T(inv_h0v) * pv0);
+        th1 = T(0.5) * (T(inv_h0) * pf1 + T(inv_h0v) * pv1);
+    }
+    if (F.kind != FACE_DISP) {
+        const T th[2] = {th0, th1};
+        // nn planes: c_mJmL with (0,1) and (1,0) sharing plane 3m+1
+        g[0] -= nu * th[0] * dn[0];
+        g[1] -= nu * (th[0] * dn[1] + th[1] * dn[0]);
+        g[2] -= nu * th[1] * dn[1];
+#pragma unroll
+        for (int J = 0; J < 2; ++J)
+#pragma unroll
+            for (int L = 0; L < 2; ++L) g[plane_nt(m, J, L) - 6 + 3] -= nu * th[J] * dtg[L];
+    }
+    if (F.kind != FACE_ROBIN) {
+        const bool intf = F.kind == FACE_INTF;
+        const T half = intf ? T(0.5) : T(1);
+        const T w0 = U[gi] - v0, w1 = U[gi + plane] - v1;
+        const T w[2] = {w0, w1};
+        // normal-spread amplitude: phi_a,J = sum_d phi_J(d) D_m[face row][i_m] / H_m(i_m)
+        T pa0 = T(0), pa1 = T(0);
+        for (int d = 0; d < Ord<O>::NCOL; ++d) {
+            const int im = F.side ? Nm - 1 - d : d;
+            const double fac = dcoef<O>(Nm, F.side ? Nm - 1 : 0, im) / (hm * hm * hweight<O>(Nm, im));
+            if (fac == 0.0) continue;
+            const size_t q = node(s, d);
+            const double Hq = hnode(s, d);
+            pa0 += T(fac * Hq * (double)Ps[q]);
+            pa1 += T(fac * Hq * (double)Ps[q + plane]);
+        }
+        g[0] += half * nu * pa0 * w0;
+        g[1] += half * nu * (pa0 * w1 + pa1 * w0);
+        g[2] += half * nu * pa1 * w1;
+        // tangential transpose: eta_J(s) = half hw(s) sum_s' D_t[s][s'] h_t xi_J(s')
+        const double hs = hweight<O>(Nt, s);
+        const T e0 = half * T(hs) * dsum<O, T>(Nt, s, [&](int sp) {
+            return T(hnode(sp, 0) * (double)Ps[node(sp, 0)] * inv_h0 / (ht * hweight<O>(Nt, sp)));
+        });
+        const T e1 = half * T(hs) * dsum<O, T>(Nt, s, [&](int sp) {
+            return T(hnode(sp, 0) * (double)Ps[node(sp, 0) + plane] * inv_h0 / (ht * hweight<O>(Nt, sp)));
+        });
+        const T eta[2] = {e0, e1};
+#pragma unroll
+        for (int J = 0; J < 2; ++J)
+#pragma unroll
+            for (int L = 0; L < 2; ++L) g[plane_nt(m, L, J) - 6 + 3] += nu * eta[J] * w[L];
+        // penalty J^Z = k_own c_mJmL (+ neighbour part): own SAT and, at an interface, the
+        // neighbour's SAT (whose jump is -w) both carry this node's c
+        const double dd = 2.0;
+        const T kown = T(intf ? beta * dd / 4.0 / F.hm0 : beta * dd / F.hm0);
+        const T k0 = kown * (T(inv_h0) * pf0 - (intf ? T(inv_h0v) * pv0 : T(0)));
+        const T k1 = kown * (T(inv_h0) * pf1 - (intf ? T(inv_h0v) * pv1 : T(0)));
+        g[0] -= k0 * w0;
+        g[1] -= k0 * w1 + k1 * w0;
+        g[2] -= k1 * w1;
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) out[k * nf + s] = g[k];
+}
+
+// ------------------------------------------------------------------ bulk part of the gradient
+// One node x: dL/dc_p(x) contracted with phi = H psi_n and u_n, for the narrow rows of both
+// directions (planes 0-2 along x1, 3-5 along x2), the mixed terms (planes 6-9), plus the SAT
+// contributions of k_grad_face at face nodes; accumulates dt^2 times that into gc and the density
+// term into grho.
+template <typename T, int O, bool INTERIOR>
+__device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, int pcur, int lvl, double dt2, int i1,
+                                          int i2) {
+    using PO = Ord<O>;
+    const int n1 = B.n1, n2 = B.n2, P = B.pitch;
+    const size_t plane = (size_t)n2 * P;
+    const T* __restrict__ Ps = reinterpret_cast<const T*>(B.u[pcur]);
+    const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)lvl * G.lvl_elems;
+    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    auto ps = [&](int L, int j1, int j2) { return __ldg(Ps + (size_t)L * plane + (size_t)j2 * P + j1); };
+    auto uu = [&](int L, int j1, int j2) { return __ldg(U + (size_t)L * plane + (size_t)j2 * P + j1); };
+    T acc[10];
+    if (INTERIOR) {
+        // phi = h1 h2 psi in the interior: edge-pair form of the narrow rows,
+        //   dPhi/db(x) = -sum_m sum_k e_{m,k} (phi(j+m) - phi(j)) (u(j+m) - u(j)),  j = x - k
+        T a00 = T(0), a01 = T(0), a11 = T(0), b00 = T(0), b01 = T(0), b11 = T(0);
+#pragma unroll
+        for (int m = 1; m <= PO::Q; ++m) {
+#pragma unroll
+            for (int k = GradCfg<O>::ELO; k <= GradCfg<O>::EHI; ++k) {
+                const double e = edge_coef<O>(m, k);
+                if (e == 0.0) continue;
+                const T ee = T(e);
+                {
+                    const int j = i1 - k;
+                    const T dp0 = ps(0, j + m, i2) - ps(0, j, i2), dp1 = ps(1, j + m, i2) - ps(1, j, i2);
+                    const T du0 = uu(0, j + m, i2) - uu(0, j, i2), du1 = uu(1, j + m, i2) - uu(1, j, i2);
+                    a00 += ee * dp0 * du0;
+                    a01 += ee * (dp0 * du1 + dp1 * du0);
+                    a11 += ee * dp1 * du1;
+                }
+                {
+                    const int j = i2 - k;
+                    const T dp0 = ps(0, i1, j + m) - ps(0, i1, j), dp1 = ps(1, i1, j + m) - ps(1, i1, j);
+                    const T du0 = uu(0, i1, j + m) - uu(0, i1, j), du1 = uu(1, i1, j + m) - uu(1, i1, j);
+                    b00 += ee * dp0 * du0;
+                    b01 += ee * (dp0 * du1 + dp1 * du0);
+                    b11 += ee * dp1 * du1;
+                }
+            }
+        }
+        const T hh = T(B.h1 * B.h2);
+        acc[0] = -hh * ih1 * ih1 * a00;
+        acc[1] = -hh * ih1 * ih1 * a01;
+        acc[2] = -hh * ih1 * ih1 * a11;
+        acc[3] = -hh * ih2 * ih2 * b00;
+        acc[4] = -hh * ih2 * ih2 * b01;
+        acc[5] = -hh * ih2 * ih2 * b11;
+        // mixed: D^T = -D on interior rows
+        T d1p[2], d2p[2], d1u[2], d2u[2];
+#pragma unroll
+        for (int L = 0; L < 2; ++L) {
+            T s1 = T(0), s2 = T(0), s3 = T(0), s4 = T(0);
+#pragma unroll
+            for (int k = 1; k <= PO::Q; ++k) {
+                const T ak = T(PO::a(k - 1));
+                s1 += ak * (ps(L, i1 + k, i2) - ps(L, i1 - k, i2));
+                s2 += ak * (ps(L, i1, i2 + k) - ps(L, i1, i2 - k));
+                s3 += ak * (uu(L, i1 + k, i2) - uu(L, i1 - k, i2));
+                s4 += ak * (uu(L, i1, i2 + k) - uu(L, i1, i2 - k));
+            }
+            d1p[L] = -hh * s1 * ih1;
+            d2p[L] = -hh * s2 * ih2;
+            d1u[L] = s3 * ih1;
+            d2u[L] = s4 * ih2;
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] = d1p[a] * d2u[b] + d2p[b] * d1u[a];
+    } else {
+        auto phi = [&](int L, int j1, int j2) { return T(node_h<O>(B, j1, j2) * (double)ps(L, j1, j2)); };
+        constexpr int RR = GradCfg<O>::RR;
+        T s00 = T(0), s01 = T(0), s11 = T(0);
+        for (int i = max(0, i1 - RR); i <= min(n1 - 1, i1 + RR); ++i) {
+            T m0, m1;
+            narrow_dcoef<O, T>(n1, i, i1, [&](int j) { return uu(0, j, i2); }, [&](int j) { return uu(1, j, i2); }, m0, m1);
+            if (m0 == T(0) && m1 == T(0)) continue;
+            const T p0 = phi(0, i, i2), p1 = phi(1, i, i2);
+            s00 += p0 * m0;
+            s01 += p0 * m1 + p1 * m0;
+            s11 += p1 * m1;
+        }
+        acc[0] = s00 * ih1 * ih1;
+        acc[1] = s01 * ih1 * ih1;
+        acc[2] = s11 * ih1 * ih1;
+        s00 = s01 = s11 = T(0);
+        for (int i = max(0, i2 - RR); i <= min(n2 - 1, i2 + RR); ++i) {
+            T m0, m1;
+            narrow_dcoef<O, T>(n2, i, i2, [&](int j) { return uu(0, i1, j); }, [&](int j) { return uu(1, i1, j); }, m0, m1);
+            if (m0 == T(0) && m1 == T(0)) continue;
+            const T p0 = phi(0, i1, i), p1 = phi(1, i1, i);
+            s00 += p0 * m0;
+            s01 += p0 * m1 + p1 * m0;
+            s11 += p1 * m1;
+        }
+        acc[3] = s00 * ih2 * ih2;
+        acc[4] = s01 * ih2 * ih2;
+        acc[5] = s11 * ih2 * ih2;
+        T d1p[2], d2p[2], d1u[2], d2u[2];
+#pragma unroll
+        for (int L = 0; L < 2; ++L) {
+            d1p[L] = dtsum<O, T>(n1, i1, [&](int j) { return phi(L, j, i2); }) * ih1;
+            d2p[L] = dtsum<O, T>(n2, i2, [&](int j) { return phi(L, i1, j); }) * ih2;
+            d1u[L] = dsum<O, T>(n1, i1, [&](int j) { return uu(L, j, i2); }) * ih1;
+            d2u[L] = dsum<O, T>(n2, i2, [&](int j) { return uu(L, i1, j); }) * ih2;
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] = d1p[a] * d2u[b] + d2p[b] * d1u[a];
+        // SAT contributions at face nodes
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const FaceDev& F = B.f[f];
+            const int m = F.m;
+            const int im = m == 0 ? i1 : i2, Nm = m == 0 ? n1 : n2;
+            const int d = F.side ? Nm - 1 - im : im;
+            if (d != 0) continue;
+            const int s = m == 0 ? i2 : i1;
+            const T* gs = reinterpret_cast<const T*>(G.gsat[f]);
+            const int nf = F.nf;
+            acc[3 * m] += gs[s];
+            acc[3 * m + 1] += gs[nf + s];
+            acc[3 * m + 2] += gs[2 * nf + s];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[6 + k] += gs[(3 + k) * nf + s];
+        }
+    }
+    const size_t gi = (size_t)i2 * P + i1;
+    T* __restrict__ GC = reinterpret_cast<T*>(G.gc);
+    const T d2 = T(dt2);
+#pragma unroll
+    for (int p = 0; p < 10; ++p) GC[(size_t)p * plane + gi] += d2 * acc[p];
+    // density: -H J psi . (u_{n+1} - 2 u_n + u_{n-1})
+    const T* Up = U + G.lvl_elems;
+    const T* Um = U - G.lvl_elems;
+    T dd = T(0);
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+        const size_t q = (size_t)L * plane + gi;
+        dd += Ps[q] * (Up[q] - T(2) * U[q] + Um[q]);
+    }
+    T* __restrict__ GR = reinterpret_cast<T*>(G.grho);
+    GR[gi] -= T(node_h<O>(B, i1, i2) * B.J[gi]) * dd;
+}
+
+template <typename T, int O>
+__global__ void __launch_bounds__(256) k_grad_interior(BlockDev B, GradDev G, int pcur, int lvl, double dt2) {
+    constexpr int GS = GradCfg<O>::GS;
+    const int i1 = GS + blockIdx.x * 32 + threadIdx.x;
+    const int i2 = GS + blockIdx.y * 8 + threadIdx.y;
+    if (i1 >= B.n1 - GS || i2 >= B.n2 - GS) return;
+    grad_node<T, O, true>(B, G, pcur, lvl, dt2, i1, i2);
+}
+
+template <typename T, int O>
+__global__ void __launch_bounds__(256) k_grad_strip(BlockDev B, GradDev G, int pcur, int lvl, double dt2) {
+    constexpr int S = GradCfg<O>::GS;       // every admissible block has n > 2 GS in both directions
+    const int n1 = B.n1, n2 = B.n2;
+    const int s1 = S, s2 = S;
+    const long long inner = (long long)(n1 - 2 * s1) * (n2 - 2 * s2);
+    const long long nstrip = (long long)n1 * n2 - inner;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nstrip) return;
+    int i1, i2;
+    const long long top = (long long)s2 * n1;
+    if (t < top) { i2 = (int)(t / n1); i1 = (int)(t - (long long)i2 * n1); }
+    else if (t < 2 * top) { const long long u = t - top; i2 = n2 - s2 + (int)(u / n1); i1 = (int)(u - (long long)(i2 - n2 + s2) * n1); }
+    else {
+        const long long u = t - 2 * top;
+        const int row = (int)(u / (2 * s1)), k = (int)(u - (long long)row * 2 * s1);
+        i2 = s2 + row;
+        i1 = k < s1 ? k : n1 - 2 * s1 + k;
+    }
+    grad_node<T, O, false>(B, G, pcur, lvl, dt2, i1, i2);
+}
+
+// dPhi/dC (pair layout, 10 planes of the upper triangle of M[2I+J][2K+L]) and dPhi/drho as dense
+// FP64 arrays: g_C[P] = sum_p g_c[p] dc_p/dC_P with c_ijkl = J F_Ii C_IjKl F_Kk.
+template <typename T>
+__global__ void k_grad_to_C(BlockDev B, const T* __restrict__ gc, const T* __restrict__ grho, double* __restrict__ outC,
+                            double* __restrict__ outR) {
+    const long long n = (long long)B.n1 * B.n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+    const size_t P = B.pitch, plane = (size_t)B.n2 * P, gi = (size_t)i2 * P + i1;
+    const double g00 = B.G[gi], g01 = B.G[plane + gi], g10 = B.G[2 * plane + gi], g11 = B.G[3 * plane + gi];
+    const double J = B.J[gi];
+    double F[2][2];
+    F[0][0] = g11 / J;
+    F[0][1] = -g01 / J;
+    F[1][0] = -g10 / J;
+    F[1][1] = g00 / J;
+    double g[10];
+    for (int p = 0; p < 10; ++p) g[p] = (double)gc[(size_t)p * plane + gi];
+    const int ijkl[10][4] = {{0, 0, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}, {1, 0, 1, 0}, {1, 0, 1, 1},
+                             {1, 1, 1, 1}, {0, 0, 1, 0}, {0, 0, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
+    int idx = 0;
+    for (int p = 0; p < 4; ++p)
+        for (int q = p; q < 4; ++q) {
+            // unit pair entry (p, q) and its mirror
+            double s = 0.0;
+            for (int pl = 0; pl < 10; ++pl) {
+                const int i = ijkl[pl][0], j = ijkl[pl][1], k = ijkl[pl][2], l = ijkl[pl][3];
+                double c = 0.0;
+                for (int I = 0; I < 2; ++I)
+                    for (int K = 0; K < 2; ++K) {
+                        const int a = 2 * I + j, b = 2 * K + l;
+                        if ((a == p && b == q) || (a == q && b == p)) c += F[I][i] * F[K][k];
+                    }
+                s += g[pl] * J * c;
+            }
+            outC[(size_t)idx * n + t] = s;
+            ++idx;
+        }
+    outR[t] = (double)grho[gi];
+}
+
+}  // namespace sbp

@@ -17,6 +17,7 @@
 #include "sbp_interior_tma.cuh"
 #include "sbp_interior_march.cuh"
 #include "sbp_kernels.cuh"
+#include "sbp_adjoint.cuh"
 
 namespace sbphost {
 #define SBP_TABLE static const
@@ -55,6 +56,8 @@ struct HostBlock {
     HostFace f[4];
     TmaMaps maps;             // FP32 tile interior kernel tensor maps
     MarchMaps mmaps;          // FP32 column-marching interior kernel tensor maps
+    void* psi[2] = {nullptr, nullptr};   // adjoint fields (sbp_misfit_gradient), allocated on first use
+    MarchMaps pmaps;          // marching-kernel maps over the adjoint fields
 };
 
 int order_nb(int o) { return o == 2 ? SBP2_NB : (o == 4 ? SBP4_NB : SBP6_NB); }
@@ -113,6 +116,10 @@ struct sbp_handle {
     int d_time_cap = 0;
     // marching-kernel rows per CTA chosen by sbp_autotune (0 = default heuristic)
     int rows_per_cta = 0;
+    // adjoint: block views whose state buffers are the adjoint fields; receivers
+    BlockDev* d_blocks_adj = nullptr;
+    std::vector<RecDev> recs;
+    RecDev* d_recs = nullptr;
 
     cudaEvent_t get_event() {
         if (!ev_pool.empty()) {
@@ -138,8 +145,7 @@ struct sbp_handle {
     }
     void dfree(void* p) {
         if (!p) return;
-        for (auto& a : allocs)
-            if (a == p) a = nullptr;
+        allocs.erase(std::remove(allocs.begin(), allocs.end(), p), allocs.end());
         cudaFree(p);
     }
 };
@@ -214,11 +220,25 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
     return b;
 }
 
+// the same view with the adjoint fields as its state buffers
+BlockDev make_view_adj(const sbp_handle* h, const HostBlock& hb) {
+    BlockDev b = make_view(h, hb);
+    b.u[0] = hb.psi[0];
+    b.u[1] = hb.psi[1];
+    return b;
+}
+
 int sync_views(sbp_handle* h) {
     std::vector<BlockDev> v;
     for (auto& hb : h->blocks) v.push_back(make_view(h, hb));
     if (cudaMemcpy(h->d_blocks, v.data(), sizeof(BlockDev) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return h->fail(SBP_E_CUDA, "upload of block views failed");
+    if (h->d_blocks_adj) {
+        v.clear();
+        for (auto& hb : h->blocks) v.push_back(make_view_adj(h, hb));
+        if (cudaMemcpy(h->d_blocks_adj, v.data(), sizeof(BlockDev) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "upload of adjoint block views failed");
+    }
     return SBP_OK;
 }
 
@@ -250,17 +270,21 @@ bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int row
 
 template <int O> int tma_rows() { return TmaTile<O>::SY; }
 
+// one operator application (mode 1) or leapfrog step (mode 0) on the state fields, or, with adj,
+// on the adjoint fields (the same kernels; the sources are skipped)
 template <typename T, int O>
-int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
+int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj) {
     const int total = h->nface_nodes;
+    const BlockDev* tab = adj ? h->d_blocks_adj : h->d_blocks;
     if (total > 0) {
         ProfScope ps(h, 2, st, 2);
-        k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, total, a.cur);
-        k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, total, a, h->beta);
+        k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(tab, h->d_refs, h->nrefs, total, a.cur);
+        k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(tab, h->d_refs, h->nrefs, total, a, h->beta);
     }
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
     for (auto& hb : h->blocks) {
-        BlockDev b = make_view(h, hb);
+        BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
+        const MarchMaps& mm = adj ? hb.pmaps : hb.mmaps;
         const int S = b.strip;
         const int ni1 = hb.n1 - 2 * S, ni2 = hb.n2 - 2 * S;
         dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
@@ -277,8 +301,8 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
                 if (h->rows_per_cta > 0) rows = std::min(h->rows_per_cta, n2i);
                 ncy = (n2i + rows - 1) / rows;
                 constexpr size_t msm = MarchCfg<O>::BYTES;
-                if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, st>>>(hb.mmaps, b, a, rows, h->d_err);
-                else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, st>>>(hb.mmaps, b, a, rows, h->d_err);
+                if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, st>>>(mm, b, a, rows, h->d_err);
+                else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, st>>>(mm, b, a, rows, h->d_err);
             } else {
                 if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
                 else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
@@ -293,7 +317,7 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
             else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, st>>>(b, a);
         }
     }
-    if (!h->src_nodes.empty()) {
+    if (!adj && !h->src_nodes.empty()) {
         ProfScope ps(h, 3, st, 1);
         const int ns = (int)h->src_nodes.size();
         if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
@@ -303,16 +327,17 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st)
 }
 
 template <typename T>
-int dispatch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
+int dispatch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj) {
     switch (h->order) {
-        case 2: return launch_operator<T, 2>(h, a, mode, st);
-        case 4: return launch_operator<T, 4>(h, a, mode, st);
-        default: return launch_operator<T, 6>(h, a, mode, st);
+        case 2: return launch_operator<T, 2>(h, a, mode, st, adj);
+        case 4: return launch_operator<T, 4>(h, a, mode, st, adj);
+        default: return launch_operator<T, 6>(h, a, mode, st, adj);
     }
 }
 
-int run_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
-    return h->precision == SBP_FP64 ? dispatch_operator<double>(h, a, mode, st) : dispatch_operator<float>(h, a, mode, st);
+int run_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj = false) {
+    return h->precision == SBP_FP64 ? dispatch_operator<double>(h, a, mode, st, adj)
+                                    : dispatch_operator<float>(h, a, mode, st, adj);
 }
 
 template <typename T, int O> void set_smem_attr() {
@@ -426,6 +451,104 @@ void launch_noalloc(sbp_handle* h, const BlockDev* views, int nviews, BlockDev* 
         k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(d_views, h->d_src_nodes, ns, h->d_src_params, a);
     }
 }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// misfit gradient: helpers
+namespace {
+
+int ensure_adjoint_buffers(sbp_handle* h) {
+    bool fresh = false;
+    for (auto& hb : h->blocks) {
+        if (hb.psi[0]) continue;
+        const size_t bytes = 2 * (size_t)hb.n2 * hb.pitch * h->esize;
+        hb.psi[0] = h->dalloc(bytes);
+        hb.psi[1] = h->dalloc(bytes);
+        if (!hb.psi[0] || !hb.psi[1]) return h->fail(SBP_E_OOM, "adjoint fields");
+        if (h->precision == SBP_FP32) {
+            if (!make_map(&hb.pmaps.u[0], hb.psi[0], hb.pitch, hb.n2, 2, MR, MBOXW) ||
+                !make_map(&hb.pmaps.u[1], hb.psi[1], hb.pitch, hb.n2, 2, MR, MBOXW))
+                return h->fail(SBP_E_CUDA, "tensor map encoding failed (adjoint fields)");
+            hb.pmaps.c = hb.mmaps.c;
+        }
+        fresh = true;
+    }
+    if (!h->d_blocks_adj) {
+        h->d_blocks_adj = (BlockDev*)h->dalloc(sizeof(BlockDev) * h->blocks.size());
+        if (!h->d_blocks_adj) return h->fail(SBP_E_OOM, "adjoint block views");
+        fresh = true;
+    }
+    return fresh ? sync_views(h) : SBP_OK;
+}
+
+// one leapfrog step of the state (the body of sbp_step)
+int step_once(sbp_handle* h, double dt, cudaStream_t st) {
+    StepArgs a{};
+    a.with_data = 1;
+    a.dt2 = dt * dt;
+    a.cur = h->cur;
+    a.t = h->t;
+    fill_basis(h, h->t, a);
+    const int rc = run_operator(h, a, 0, st);
+    if (rc != SBP_OK) return rc;
+    h->cur = 1 - h->cur;
+    h->t += dt;
+    return SBP_OK;
+}
+
+int record_receivers(sbp_handle* h, double* d_row, cudaStream_t st) {
+    const int nr = (int)h->recs.size();
+    if (h->precision == SBP_FP64) k_record<double><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks, h->d_recs, nr, h->cur, d_row);
+    else k_record<float><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks, h->d_recs, nr, h->cur, d_row);
+    return SBP_OK;
+}
+
+template <typename T, int O>
+void launch_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int pc, int lvl, double dt2,
+                 cudaStream_t st) {
+    const int total = h->nface_nodes;
+    if (total > 0)
+        k_grad_face<T, O><<<grid_for(total), 128, 0, st>>>(h->d_blocks_adj, d_grad, h->d_refs, h->nrefs, total, pc, lvl, h->beta);
+    constexpr int GS = GradCfg<O>::GS;
+    for (size_t b = 0; b < h->blocks.size(); ++b) {
+        const HostBlock& hb = h->blocks[b];
+        const BlockDev v = make_view_adj(h, hb);
+        dim3 gi((hb.n1 - 2 * GS + 31) / 32, (hb.n2 - 2 * GS + 7) / 8);
+        k_grad_interior<T, O><<<gi, dim3(32, 8), 0, st>>>(v, grads[b], pc, lvl, dt2);
+        const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)(hb.n1 - 2 * GS) * (hb.n2 - 2 * GS);
+        k_grad_strip<T, O><<<grid_for(nstrip), 256, 0, st>>>(v, grads[b], pc, lvl, dt2);
+    }
+}
+
+void run_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int pc, int lvl, double dt2,
+              cudaStream_t st) {
+    if (h->precision == SBP_FP64) {
+        if (h->order == 2) launch_grad<double, 2>(h, d_grad, grads, pc, lvl, dt2, st);
+        else if (h->order == 4) launch_grad<double, 4>(h, d_grad, grads, pc, lvl, dt2, st);
+        else launch_grad<double, 6>(h, d_grad, grads, pc, lvl, dt2, st);
+    } else {
+        if (h->order == 2) launch_grad<float, 2>(h, d_grad, grads, pc, lvl, dt2, st);
+        else if (h->order == 4) launch_grad<float, 4>(h, d_grad, grads, pc, lvl, dt2, st);
+        else launch_grad<float, 6>(h, d_grad, grads, pc, lvl, dt2, st);
+    }
+}
+
+// temporaries of one sbp_misfit_gradient call, released on every exit path
+struct GradScratch {
+    sbp_handle* h;
+    std::vector<void*> ptrs;
+    explicit GradScratch(sbp_handle* hh) : h(hh) {}
+    void* get(size_t bytes) {
+        void* p = h->dalloc(bytes);
+        if (p) ptrs.push_back(p);
+        return p;
+    }
+    ~GradScratch() {
+        cudaDeviceSynchronize();
+        for (void* p : ptrs) h->dfree(p);
+    }
+};
 
 }  // namespace
 
@@ -1152,6 +1275,214 @@ int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, 
     if (precision_out) *precision_out = h->precision;
     if (order_out) *order_out = h->order;
     return SBP_OK;
+}
+
+int sbp_set_receivers(sbp_handle* h, int nrec, const int* rec) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nrec < 0 || (nrec > 0 && !rec)) return h->fail(SBP_E_INVALID_ARG, "bad receiver arguments");
+    std::vector<RecDev> v;
+    std::vector<std::pair<int, long long>> seen;
+    for (int r = 0; r < nrec; ++r) {
+        const int b = rec[3 * r], i1 = rec[3 * r + 1], i2 = rec[3 * r + 2];
+        if (b < 0 || b >= h->nblocks) return h->fail(SBP_E_INVALID_ARG, "receiver " + std::to_string(r) + ": bad block");
+        const HostBlock& hb = h->blocks[b];
+        if (i1 < 0 || i1 >= hb.n1 || i2 < 0 || i2 >= hb.n2)
+            return h->fail(SBP_E_INVALID_ARG, "receiver " + std::to_string(r) + ": node outside the block");
+        RecDev d{};
+        d.block = b;
+        d.gi = (long long)i2 * hb.pitch + i1;
+        d.hinv = 1.0 / (hb.h1 * host_hweight(h->order, hb.n1, i1) * hb.h2 * host_hweight(h->order, hb.n2, i2));
+        seen.push_back({b, d.gi});
+        v.push_back(d);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return h->fail(SBP_E_INVALID_ARG, "receivers must sit on distinct nodes");
+    h->dfree(h->d_recs);
+    h->d_recs = nullptr;
+    h->recs = v;
+    if (nrec > 0) {
+        h->d_recs = (RecDev*)h->dalloc(sizeof(RecDev) * nrec);
+        if (!h->d_recs) return h->fail(SBP_E_OOM, "receiver table");
+        if (cudaMemcpy(h->d_recs, v.data(), sizeof(RecDev) * nrec, cudaMemcpyHostToDevice) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "receiver upload");
+    }
+    return SBP_OK;
+}
+
+int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return h->fail(SBP_E_INVALID_ARG, "bad step arguments");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    if (h->recs.empty()) return h->fail(SBP_E_STATE, "set the receivers first");
+    const size_t per = 2 * h->recs.size();
+    GradScratch sc(h);
+    double* d_tr = (double*)sc.get(sizeof(double) * per * std::max(nsteps, 1));
+    if (!d_tr) return h->fail(SBP_E_OOM, "trace buffer");
+    for (int n = 0; n < nsteps; ++n) {
+        int rc = step_once(h, dt, 0);
+        if (rc != SBP_OK) return rc;
+        record_receivers(h, d_tr + (size_t)n * per, 0);
+    }
+    if (traces && nsteps > 0 &&
+        cudaMemcpy(traces, d_tr, sizeof(double) * per * nsteps, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "trace download");
+    int rc = check_cuda(h, "sbp_record");
+    return rc != SBP_OK ? rc : check_kernel_errors(h);
+}
+
+int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* observed, int checkpoint_every,
+                        double* misfit, double* const* grad_rho, double* const* grad_C) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nsteps < 1 || !(dt > 0) || !std::isfinite(dt) || !observed || !misfit || checkpoint_every < 0)
+        return h->fail(SBP_E_INVALID_ARG, "bad misfit-gradient arguments");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    if (h->recs.empty()) return h->fail(SBP_E_STATE, "set the receivers first");
+    for (auto& hb : h->blocks)
+        for (auto& F : hb.f)
+            if (F.kind == SBP_BC_DISPLACEMENT && F.g)
+                return h->fail(SBP_E_STATE, "displacement faces with boundary data make the data depend on C; not supported");
+    int rc = ensure_adjoint_buffers(h);
+    if (rc != SBP_OK) return rc;
+    const int K = checkpoint_every > 0 ? std::min(checkpoint_every, nsteps)
+                                       : std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+    const int nseg = (nsteps + K - 1) / K;
+    const size_t es = h->esize;
+    const size_t per = 2 * h->recs.size();
+    const int nb = (int)h->blocks.size();
+    GradScratch sc(h);
+    std::vector<void*> ck(nb), seg(nb), fin(nb);
+    std::vector<size_t> lvl_bytes(nb);
+    std::vector<GradDev> grads(nb);
+    for (int b = 0; b < nb; ++b) {
+        HostBlock& hb = h->blocks[b];
+        const size_t plane = (size_t)hb.n2 * hb.pitch;
+        lvl_bytes[b] = 2 * plane * es;
+        ck[b] = sc.get((size_t)nseg * 2 * lvl_bytes[b]);
+        seg[b] = sc.get((size_t)(K + 2) * lvl_bytes[b]);
+        fin[b] = sc.get(2 * lvl_bytes[b]);
+        GradDev& G = grads[b];
+        G.seg = seg[b];
+        G.lvl_elems = (long long)(2 * plane);
+        G.gc = sc.get(10 * plane * es);
+        G.grho = sc.get(plane * es);
+        for (int f = 0; f < 4; ++f) G.gsat[f] = sc.get(7 * (size_t)hb.f[f].nf * es);
+        if (!ck[b] || !seg[b] || !fin[b] || !G.gc || !G.grho || !G.gsat[0] || !G.gsat[1] || !G.gsat[2] || !G.gsat[3])
+            return h->fail(SBP_E_OOM, "misfit-gradient workspace (checkpoints every " + std::to_string(K) + " steps)");
+    }
+    GradDev* d_grad = (GradDev*)sc.get(sizeof(GradDev) * nb);
+    double* d_tr = (double*)sc.get(sizeof(double) * per * nsteps);
+    double* d_obs = (double*)sc.get(sizeof(double) * per * nsteps);
+    double* d_res = (double*)sc.get(sizeof(double) * per * nsteps);
+    double* d_part = (double*)sc.get(sizeof(double) * nsteps);
+    double* d_phi = (double*)sc.get(sizeof(double));
+    if (!d_grad || !d_tr || !d_obs || !d_res || !d_part || !d_phi) return h->fail(SBP_E_OOM, "misfit-gradient tables");
+    cudaMemcpy(d_grad, grads.data(), sizeof(GradDev) * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_obs, observed, sizeof(double) * per * nsteps, cudaMemcpyHostToDevice);
+    cudaStream_t st = 0;
+    auto copy = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    };
+    auto lvl_ptr = [&](std::vector<void*>& base, int b, size_t l) { return (unsigned char*)base[b] + l * lvl_bytes[b]; };
+    // forward pass: checkpoints (u_{n-1}, u_n) at the start of every segment, receiver traces
+    std::vector<double> ck_t(nseg);
+    for (int n = 0; n < nsteps; ++n) {
+        if (n % K == 0) {
+            const int c = n / K;
+            for (int b = 0; b < nb; ++b)
+                if (!copy(lvl_ptr(ck, b, 2 * c), h->blocks[b].u[1 - h->cur], lvl_bytes[b]) ||
+                    !copy(lvl_ptr(ck, b, 2 * c + 1), h->blocks[b].u[h->cur], lvl_bytes[b]))
+                    return h->fail(SBP_E_CUDA, "checkpoint copy");
+            ck_t[c] = h->t;
+        }
+        rc = step_once(h, dt, st);
+        if (rc != SBP_OK) return rc;
+        record_receivers(h, d_tr + (size_t)n * per, st);
+    }
+    const int cur_final = h->cur;
+    const double t_final = h->t;
+    for (int b = 0; b < nb; ++b)
+        if (!copy(lvl_ptr(fin, b, 0), h->blocks[b].u[1 - h->cur], lvl_bytes[b]) ||
+            !copy(lvl_ptr(fin, b, 1), h->blocks[b].u[h->cur], lvl_bytes[b]))
+            return h->fail(SBP_E_CUDA, "final state copy");
+    // misfit: 1/2 dt sum (traces - observed)^2
+    k_residual<<<nsteps, 256, 0, st>>>(d_tr, d_obs, d_res, (int)per, d_part);
+    k_sum_scaled<<<1, 256, 0, st>>>(d_part, nsteps, 0.5 * dt, d_phi);
+    // backward pass: psi_{N+1} = psi_{N+2} = 0, accumulators zero
+    for (int b = 0; b < nb; ++b) {
+        HostBlock& hb = h->blocks[b];
+        const size_t plane = (size_t)hb.n2 * hb.pitch;
+        cudaMemsetAsync(hb.psi[0], 0, lvl_bytes[b], st);
+        cudaMemsetAsync(hb.psi[1], 0, lvl_bytes[b], st);
+        cudaMemsetAsync(grads[b].gc, 0, 10 * plane * es, st);
+        cudaMemsetAsync(grads[b].grho, 0, plane * es, st);
+    }
+    int pc = 0;
+    StepArgs aa{};
+    aa.with_data = 0;
+    aa.dt2 = dt * dt;
+    const int nr = (int)h->recs.size();
+    for (int s = nseg - 1; s >= 0; --s) {
+        const int a0 = s * K, a1 = std::min(a0 + K, nsteps) - 1;   // 0-based steps of the segment
+        // recompute the segment's levels u_{a0} .. u_{a1+2} from its checkpoint
+        for (int b = 0; b < nb; ++b) {
+            if (!copy(h->blocks[b].u[1 - h->cur], lvl_ptr(ck, b, 2 * s), lvl_bytes[b]) ||
+                !copy(h->blocks[b].u[h->cur], lvl_ptr(ck, b, 2 * s + 1), lvl_bytes[b]) ||
+                !copy(lvl_ptr(seg, b, 0), lvl_ptr(ck, b, 2 * s), lvl_bytes[b]) ||
+                !copy(lvl_ptr(seg, b, 1), lvl_ptr(ck, b, 2 * s + 1), lvl_bytes[b]))
+                return h->fail(SBP_E_CUDA, "checkpoint restore");
+        }
+        h->t = ck_t[s];
+        for (int q = a0; q <= a1; ++q) {
+            rc = step_once(h, dt, st);
+            if (rc != SBP_OK) return rc;
+            for (int b = 0; b < nb; ++b)
+                if (!copy(lvl_ptr(seg, b, (size_t)(q - a0 + 2)), h->blocks[b].u[h->cur], lvl_bytes[b]))
+                    return h->fail(SBP_E_CUDA, "segment copy");
+        }
+        // adjoint steps n = q + 1 (1-based) from the last step of the segment down to the first
+        for (int q = a1; q >= a0; --q) {
+            aa.cur = pc;
+            rc = run_operator(h, aa, 0, st, true);          // psi_n = 2 psi_{n+1} - psi_{n+2} + dt^2 W L psi_{n+1}
+            if (rc != SBP_OK) return rc;
+            pc = 1 - pc;
+            if (h->precision == SBP_FP64)
+                k_inject<double><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
+            else
+                k_inject<float><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
+            run_grad(h, d_grad, grads, pc, q - a0 + 1, dt * dt, st);
+        }
+    }
+    rc = check_cuda(h, "misfit gradient");
+    if (rc != SBP_OK) return rc;
+    // outputs: dPhi/dC (pair layout) and dPhi/drho as dense FP64 arrays
+    for (int b = 0; b < nb; ++b) {
+        HostBlock& hb = h->blocks[b];
+        const size_t n = (size_t)hb.n1 * hb.n2;
+        double* dC = (double*)sc.get(10 * n * sizeof(double));
+        double* dR = (double*)sc.get(n * sizeof(double));
+        if (!dC || !dR) return h->fail(SBP_E_OOM, "gradient download staging");
+        const BlockDev v = make_view(h, hb);
+        if (h->precision == SBP_FP64)
+            k_grad_to_C<double><<<grid_for((long long)n), 256, 0, st>>>(v, (const double*)grads[b].gc, (const double*)grads[b].grho, dC, dR);
+        else
+            k_grad_to_C<float><<<grid_for((long long)n), 256, 0, st>>>(v, (const float*)grads[b].gc, (const float*)grads[b].grho, dC, dR);
+        if (grad_C && grad_C[b] && cudaMemcpy(grad_C[b], dC, 10 * n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "gradient download");
+        if (grad_rho && grad_rho[b] && cudaMemcpy(grad_rho[b], dR, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "gradient download");
+    }
+    // leave the state where the forward pass ended
+    h->cur = cur_final;
+    h->t = t_final;
+    for (int b = 0; b < nb; ++b)
+        if (!copy(h->blocks[b].u[1 - h->cur], lvl_ptr(fin, b, 0), lvl_bytes[b]) ||
+            !copy(h->blocks[b].u[h->cur], lvl_ptr(fin, b, 1), lvl_bytes[b]))
+            return h->fail(SBP_E_CUDA, "final state restore");
+    if (cudaMemcpy(misfit, d_phi, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "misfit download");
+    rc = check_cuda(h, "misfit gradient");
+    return rc != SBP_OK ? rc : check_kernel_errors(h);
 }
 
 }  // extern "C"

@@ -1,0 +1,166 @@
+"""Misfit gradient on the GPU (sbp_set_receivers, sbp_record, sbp_misfit_gradient) against the
+oracle's explicit-transpose adjoint: receiver traces, misfit, dPhi/drho at every node and dPhi/dC at
+sampled nodes (corners, face nodes of every kind, interface nodes on both sides, closure depths,
+interior); checkpoint-interval invariance; the state left behind."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint as AD
+from oracle.scheme import Oracle
+
+pytestmark = pytest.mark.gpu
+
+SIZES = {2: (13, 11), 4: (21, 19), 6: (29, 27)}
+NSTEPS = 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _setup(order, seed=5, nsteps=NSTEPS):
+    n = SIZES[order]
+    kinds = ("displacement", "robin", "robin", "displacement")
+    src = [W.PointSource(block=0, x_ref=(0.45, 0.55), direction=(0.3, -1.0), amplitude=1.0, alpha_p=3.0, t0=0.3)]
+    P = W.random_problem(kinds=kinds, n=n, order=order, seed=seed, two_blocks=True)
+    P.sources = src
+    Q = W.random_problem(kinds=kinds, n=n, order=order, seed=seed + 1, two_blocks=True)
+    Q.sources = src
+    dt = Oracle(P).suggest_dt(0.5)
+    u0 = W.smooth_state(P, seed=1, amplitude=0.1)
+    rec = [(b, i1, i2) for b in (0, 1) for i1 in range(1, n[0], 3) for i2 in range(2, n[1], 4)]
+    rec += [(0, 0, 0), (1, n[0] - 1, n[1] - 1)]
+    oq = Oracle(Q)
+    lv, _ = AD.forward(oq, u0, u0, 0.0, dt, nsteps)
+    obs = AD.traces(oq, lv, rec)
+    return P, u0, dt, rec, obs
+
+
+def _params(order):
+    n1, n2 = SIZES[order]
+    out = []
+    for P in range(10):
+        out += [(0, P, 0, 0), (1, P, n1 - 1, n2 - 1)]                    # corners
+    out += [(0, 4, n1 - 1, 3), (1, 9, 0, 5), (0, 3, n1 - 1, n2 // 2), (1, 1, 0, n2 // 2)]   # interface, both sides
+    out += [(0, 2, 3, n2 - 1), (1, 5, n1 // 2, 0), (0, 7, 0, n2 // 2), (1, 8, n1 - 1, 4)]  # displacement / Robin faces
+    out += [(0, 5, 2, 1), (1, 6, 4, n2 - 3), (0, 0, n1 // 2, 5)]         # closure depths
+    out += [(1, 7, n1 // 2, n2 // 2), (0, 9, n1 // 2 + 1, n2 // 2)]     # interior
+    return out
+
+
+def _solver(P, prec, u0, rec):
+    from paper_2003_12811_gb300 import Solver
+    S = Solver(P, prec)
+    S.set_state(u0, u0, 0.0)
+    S.sbp_set_receivers(rec)
+    return S
+
+
+@pytest.mark.parametrize("order", (2, 4, 6))
+def test_record_matches_oracle(order):
+    P, u0, dt, rec, _ = _setup(order)
+    S = _solver(P, "fp64", u0, rec)
+    tr = S.sbp_record(NSTEPS, dt)
+    S.close()
+    orc = Oracle(P)
+    lv, _ = AD.forward(orc, u0, u0, 0.0, dt, NSTEPS)
+    ref = AD.traces(orc, lv, rec)
+    assert np.max(np.abs(tr - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("order", (2, 4, 6))
+def test_gradient_matches_oracle_fp64(order):
+    P, u0, dt, rec, obs = _setup(order)
+    params = _params(order)
+    ref = AD.gradient(P, u0, u0, 0.0, dt, NSTEPS, rec, obs, params)
+    S = _solver(P, "fp64", u0, rec)
+    phi, gr, gc = S.sbp_misfit_gradient(NSTEPS, dt, obs, checkpoint_every=7)
+    S.close()
+    assert phi == pytest.approx(ref["misfit"], rel=1e-12)
+    for b in range(2):
+        scale = np.max(np.abs(ref["grad_rho"][b]))
+        assert np.max(np.abs(gr[b] - ref["grad_rho"][b])) <= 1e-9 * scale, b
+    got = np.array([gc[b][Pp, i2, i1] for (b, Pp, i1, i2) in params])
+    scale = np.max(np.abs(ref["grad_C"]))
+    err = np.abs(got - ref["grad_C"])
+    assert np.all(err <= 1e-9 * scale), [(params[k], got[k], ref["grad_C"][k]) for k in np.argsort(-err)[:5]]
+
+
+@pytest.mark.parametrize("order", (4, 6))
+def test_gradient_fp32_close_to_oracle(order):
+    P, u0, dt, rec, obs = _setup(order)
+    params = _params(order)
+    ref = AD.gradient(P, u0, u0, 0.0, dt, NSTEPS, rec, obs, params)
+    S = _solver(P, "fp32", u0, rec)
+    phi, gr, gc = S.sbp_misfit_gradient(NSTEPS, dt, obs)
+    S.close()
+    assert phi == pytest.approx(ref["misfit"], rel=1e-4)
+    for b in range(2):
+        scale = np.max(np.abs(ref["grad_rho"][b]))
+        e = np.max(np.abs(gr[b] - ref["grad_rho"][b])) / scale
+        assert e <= 2e-3, (b, e)
+    got = np.array([gc[b][Pp, i2, i1] for (b, Pp, i1, i2) in params])
+    e = np.max(np.abs(got - ref["grad_C"])) / np.max(np.abs(ref["grad_C"]))
+    assert e <= 2e-3, e
+
+
+@pytest.mark.parametrize("prec", ("fp64", "fp32"))
+def test_checkpoint_interval_invariance_and_final_state(prec):
+    P, u0, dt, rec, obs = _setup(6)
+    res = []
+    for K in (1, 6, 0, NSTEPS):
+        S = _solver(P, prec, u0, rec)
+        res.append(S.sbp_misfit_gradient(NSTEPS, dt, obs, checkpoint_every=K))
+        st = S.state()
+        S.close()
+        A = _solver(P, prec, u0, rec)
+        A.step(NSTEPS, dt)
+        ref = A.state()
+        A.close()
+        for x, y in zip(st[0] + st[1], ref[0] + ref[1]):
+            assert np.array_equal(x, y)
+    for phi, gr, gc in res[1:]:
+        assert phi == res[0][0]
+        for b in range(2):
+            assert np.array_equal(gr[b], res[0][1][b]) and np.array_equal(gc[b], res[0][2][b])
+
+
+def test_gradient_rejects_displacement_data():
+    from paper_2003_12811_gb300 import Solver
+    from paper_2003_12811_gb300.binding import SbpError
+    P = W.mms_problem(20, 4)
+    S = Solver(P, "fp64")
+    z = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+    S.set_state(z, z, 0.0)
+    S.sbp_set_receivers([(0, 3, 3)])
+    with pytest.raises(SbpError):
+        S.sbp_misfit_gradient(4, 1e-3, np.zeros((4, 1, 2)))
+    with pytest.raises(SbpError):
+        S.sbp_set_receivers([(0, 3, 3), (0, 3, 3)])
+    S.close()
+
+
+def test_misfit_gradient_workload_small():
+    """The misfit-gradient workload at n = 41: observations from the model with the inclusion,
+    gradient at the background model, checked against the oracle at sampled nodes."""
+    Pb, rec = W.config5(n=41, nrec=8, blob=False)
+    Pt, _ = W.config5(n=41, nrec=8, blob=True)
+    z = [np.zeros((2, 41, 41))]
+    nsteps = 60
+    dt = Oracle(Pb).suggest_dt(0.5)
+    ot = Oracle(Pt)
+    lv, _ = AD.forward(ot, z[0], z[0], 0.0, dt, nsteps)
+    obs = AD.traces(ot, lv, rec)
+    params = [(0, 0, 20, 40), (0, 9, 20, 30), (0, 5, 0, 0), (0, 2, 40, 20), (0, 7, 20, 38)]
+    ref = AD.gradient(Pb, z[0], z[0], 0.0, dt, nsteps, rec, obs, params)
+    S = _solver(Pb, "fp64", z, rec)
+    phi, gr, gc = S.sbp_misfit_gradient(nsteps, dt, obs)
+    S.close()
+    assert ref["misfit"] > 0 and phi == pytest.approx(ref["misfit"], rel=1e-12)
+    scale = np.max(np.abs(ref["grad_rho"][0]))
+    assert np.max(np.abs(gr[0] - ref["grad_rho"][0])) <= 1e-9 * scale
+    got = np.array([gc[0][Pp, i2, i1] for (_, Pp, i1, i2) in params])
+    assert np.max(np.abs(got - ref["grad_C"])) <= 1e-9 * np.max(np.abs(ref["grad_C"]))
