@@ -509,7 +509,7 @@ void launch_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev
                  cudaStream_t st) {
     const int total = h->nface_nodes;
     if (total > 0)
-        k_grad_face<T, O><<<grid_for(total), 128, 0, st>>>(h->d_blocks_adj, d_grad, h->d_refs, h->nrefs, total, pc, lvl, h->beta);
+        k_grad_face<T, O><<<grid_for(total, 128), 128, 0, st>>>(h->d_blocks_adj, d_grad, h->d_refs, h->nrefs, total, pc, lvl, h->beta);
     constexpr int GS = GradCfg<O>::GS;
     for (size_t b = 0; b < h->blocks.size(); ++b) {
         const HostBlock& hb = h->blocks[b];

@@ -32,7 +32,7 @@ def _setup(order, seed=5, nsteps=NSTEPS):
     dt = Oracle(P).suggest_dt(0.5)
     u0 = W.smooth_state(P, seed=1, amplitude=0.1)
     rec = [(b, i1, i2) for b in (0, 1) for i1 in range(1, n[0], 3) for i2 in range(2, n[1], 4)]
-    rec += [(0, 0, 0), (1, n[0] - 1, n[1] - 1)]
+    rec = sorted(set(rec) | {(0, 0, 0), (1, n[0] - 1, n[1] - 1)})
     oq = Oracle(Q)
     lv, _ = AD.forward(oq, u0, u0, 0.0, dt, nsteps)
     obs = AD.traces(oq, lv, rec)
@@ -152,10 +152,10 @@ def test_misfit_gradient_workload_small():
     nsteps = 60
     dt = Oracle(Pb).suggest_dt(0.5)
     ot = Oracle(Pt)
-    lv, _ = AD.forward(ot, z[0], z[0], 0.0, dt, nsteps)
+    lv, _ = AD.forward(ot, z, z, 0.0, dt, nsteps)
     obs = AD.traces(ot, lv, rec)
     params = [(0, 0, 20, 40), (0, 9, 20, 30), (0, 5, 0, 0), (0, 2, 40, 20), (0, 7, 20, 38)]
-    ref = AD.gradient(Pb, z[0], z[0], 0.0, dt, nsteps, rec, obs, params)
+    ref = AD.gradient(Pb, z, z, 0.0, dt, nsteps, rec, obs, params)
     S = _solver(Pb, "fp64", z, rec)
     phi, gr, gc = S.sbp_misfit_gradient(nsteps, dt, obs)
     S.close()
