@@ -187,6 +187,69 @@ def serving_bench(nshots=32, side_range=(201, 801), rate=64.0, tick=32):
             "node_updates": int(sum((p.blocks[0].N1 * p.blocks[0].N2) * n for (_, _, _, n), p in zip(specs, probs)))}
 
 
+GRAD_BYTES_PER_NODE = {"fp32": 128, "fp64": 248}   # psi 2, u_n 2, u_{n+1} 2, u_{n-1} 2, g_c 10 r+w, g_rho r+w, J (FP64)
+
+
+def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
+    """Misfit gradient (config 5): one curvilinear block n x n, 64 surface receivers, nsteps
+    leapfrog steps; observations made by the model with the Gaussian inclusion, gradient of the L2
+    misfit at the background model through the checkpointed discrete adjoint (sqrt(nsteps)
+    checkpoints).  Also times the forward solve alone and profiles the gradient kernels."""
+    import torch
+    from paper_2003_12811_gb300 import Solver
+    Pb, rec = W.config5(n=n, blob=False)
+    Pt, _ = W.config5(n=n, blob=True)
+    z = [np.zeros((2, n, n))]
+    St = Solver(Pt, prec)
+    dt = St.suggest_dt(0.3)
+    St.set_state(z, z, 0.0)
+    St.sbp_set_receivers(rec)
+    obs = St.sbp_record(nsteps, dt)
+    St.close()
+    S = Solver(Pb, prec)
+    S.set_state(z, z, 0.0)
+    S.sbp_set_receivers(rec)
+    S.sbp_misfit_gradient(20, dt, obs[:20])                   # warm-up (workspace, adjoint fields)
+    S.set_state(z, z, 0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi, gr, gc = S.sbp_misfit_gradient(nsteps, dt, obs)
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
+    # forward alone, same steps
+    S.set_state(z, z, 0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.sbp_step(nsteps, dt)
+    torch.cuda.synchronize()
+    fwd_s = time.perf_counter() - t0
+    # kernel families of one profiled gradient
+    S.set_state(z, z, 0.0)
+    S.sbp_profile(True)
+    S.sbp_misfit_gradient(nsteps, dt, obs)
+    fam_ms, fam_n = S.sbp_profile_read()
+    S.sbp_profile(False)
+    S.close()
+    GS = 12                                                    # gradient interior starts 12 nodes from a face (order 6)
+    inner = (n - 2 * GS) ** 2
+    k_ms = fam_ms[4] / max(1, fam_n[4])
+    bpn = GRAD_BYTES_PER_NODE[prec]
+    achieved = bpn * inner / (k_ms / 1e3) / 1e9
+    peak, src = peaks()
+    names = ["interior", "boundary", "faces", "sources", "grad_interior", "grad_strips", "grad_faces_receivers", "misfit_output"]
+    return {"workload": f"misfit gradient (config 5): 1 curvilinear block {n}x{n}, order 6, tilted VTI + Gaussian "
+                        f"inclusion, 64 surface receivers, {nsteps} steps, {prec.upper()}, "
+                        f"checkpoints every {int(math.ceil(math.sqrt(nsteps)))} steps",
+            "gradients_per_s": 1.0 / grad_s, "ms_per_gradient": 1e3 * grad_s,
+            "forward_ms": 1e3 * fwd_s, "gradient_over_forward": grad_s / fwd_s,
+            "misfit": phi, "grad_rho_absmax": float(np.abs(gr[0]).max()), "grad_C_absmax": float(np.abs(gc[0]).max()),
+            "family_ms": {k: float(v) for k, v in zip(names, fam_ms)},
+            "family_launches": {k: int(v) for k, v in zip(names, fam_n)},
+            "roofline": {"kernel": "k_grad_interior", "bound": "hbm", "bytes_per_node": bpn, "units_per_launch": inner,
+                         "kernel_ms": k_ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src, "traffic": None}}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -220,6 +283,8 @@ def main():
     ap.add_argument("--n1", type=int, default=N1, help="nodes per block along x1 (profiling runs use smaller)")
     ap.add_argument("--n2", type=int, default=N2)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true", help="print the misfit-gradient measurement alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -242,6 +307,9 @@ def main():
     from paper_2003_12811_gb300 import Solver
 
     prec = args.precision
+    if args.adjoint_only:
+        print(json.dumps(adjoint_bench(prec=prec)), flush=True)
+        return 0
     P = W.config3(n1=args.n1, n2=args.n2)
     S = Solver(P, prec)
     dt = S.suggest_dt(0.3)
@@ -326,6 +394,8 @@ def main():
     S.close()
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_bench()
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_bench(prec=prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

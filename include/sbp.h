@@ -169,11 +169,14 @@ int sbp_energy(sbp_handle* h, double dt, double* E_out);
 int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out);
 
 /* Kernel timing for benchmarks.  sbp_profile(h, 1) resets the counters and, until
- * sbp_profile(h, 0), makes every operator launch record CUDA events (on the launch stream)
- * around four kernel families: [0] interior stencil, [1] boundary strips (closures + SATs),
- * [2] face traces and SAT terms, [3] point sources.  sbp_profile_read returns the accumulated
- * milliseconds per family (ms[4], needs profiling on) and the number of kernel launches per
- * family since the last reset (launches[4], always counted).  Either pointer may be NULL. */
+ * sbp_profile(h, 0), makes every kernel launch record CUDA events (on the launch stream)
+ * around its family: [0] interior stencil, [1] boundary strips (closures + SATs), [2] face
+ * traces and SAT terms, [3] point sources, [4] gradient interior, [5] gradient strips,
+ * [6] gradient face terms, receiver recording and adjoint injection, [7] misfit reduction and
+ * gradient output.  sbp_profile_read returns the accumulated milliseconds per family
+ * (ms[SBP_PROF_FAMILIES], needs profiling on) and the number of kernel launches per family since
+ * the last reset (launches[SBP_PROF_FAMILIES], always counted).  Either pointer may be NULL. */
+#define SBP_PROF_FAMILIES 8
 int sbp_profile(sbp_handle* h, int enable);
 int sbp_profile_read(sbp_handle* h, double* ms, long long* launches);
 

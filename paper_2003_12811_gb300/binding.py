@@ -23,6 +23,7 @@ STATUS = {0: "SBP_OK", -1: "SBP_E_INVALID_ARG", -2: "SBP_E_JACOBIAN_NONPOSITIVE"
 FP64, FP32 = 0, 1
 BC = {"displacement": 0, "robin": 1, "interface": 2}
 FIELD_PREV, FIELD_CUR, FIELD_APPLY = 0, 1, 2
+PROF_FAMILIES = 8      # SBP_PROF_FAMILIES
 
 
 class SbpError(RuntimeError):
@@ -294,8 +295,8 @@ class Solver:
         self._check(self.L.sbp_profile(self.h, int(bool(enable))))
 
     def sbp_profile_read(self):
-        ms = np.zeros(4)
-        n = (C.c_longlong * 4)()
+        ms = np.zeros(PROF_FAMILIES)
+        n = (C.c_longlong * PROF_FAMILIES)()
         self._check(self.L.sbp_profile_read(self.h, _ptr(ms), n))
         return ms, np.array(list(n), dtype=np.int64)
 

@@ -18,7 +18,10 @@ What is derived (Sec. 4 and 4.1 of Almquist & Dunham; coefficients are not print
 * Tables emitted: the D boundary block, the norm weights, the closure rows of D_xx^FC(b) as
   sparse (u-column, b-column, coefficient) triples, and the interior row written through
   "edge weights": row i = sum_{m=1..q} E_m(i) (u_{i+m} - u_i) + E_m(i-m) (u_{i-m} - u_i),
-  E_m(i) = sum_k e_{m,k} b_{i+k}.
+  E_m(i) = sum_k e_{m,k} b_{i+k}.  For gradients with respect to b near an end: per node k the
+  (row, u-column, coefficient) list of d(row)/d b_k, and per column k the non-zeros of D.
+  Every FP64 table has an FP32 twin (suffix _F) holding exactly the values a cast of the FP64
+  entry gives, so FP32 kernels read single-precision constants without converting them.
 """
 import os
 from math import comb
@@ -179,12 +182,42 @@ def analyse(order):
             tot[k - m] = tot.get(k - m, 0) - v
     assert {k: v for k, v in tot.items() if v != 0} == diag
     clos = [sorted(W[i].items()) for i in range(nclos)]
-    return dict(hw=hw, Dq=Dq, a=a, nclos=nclos, clos=clos, edges=edges)
+    # transposed views for the gradient with respect to b near the left end (node k < GS = nclos + q):
+    # every (row, u-column, coefficient) with d(row of h^2 D_xx(b) u)/d b_k = sum coefficient * u_j,
+    # and every (row, D[row][k] h) of the column k of D
+    gs = nclos + q
+    D, _, _, _, _ = full_D(order, N)
+    gn, dt = [], []
+    for k in range(gs):
+        gn.append(sorted((i, j, v) for i in range(N) for (j, kk), v in W[i].items() if kk == k))
+        dt.append([(r, D[r, k]) for r in range(N) if D[r, k] != 0])
+    return dict(hw=hw, Dq=Dq, a=a, nclos=nclos, clos=clos, edges=edges, gs=gs, gn=gn, dt=dt)
 
 
 def cnum(v):
     v = sp.Rational(v)
     return "(%d.0/%d.0)" % (v.p, v.q) if v.q != 1 else "%d.0" % v.p
+
+
+def fnum(v):
+    """The FP32 value a CUDA cast of the FP64 table entry produces (round to nearest), exactly."""
+    import numpy as np
+    f = np.float32(float(sp.Rational(v)))
+    return "%sf" % np.format_float_scientific(f, unique=True, exp_digits=2) if f != 0 else "0.0f"
+
+
+def table(out, typ, name, vals, dims):
+    """Emit a double table and its FP32 twin (name_F)."""
+    shape = "".join("[%d]" % d for d in dims)
+    if len(dims) == 2:
+        n = dims[1]
+        body = ", ".join("{%s}" % ", ".join(cnum(v) for v in vals[r * n:(r + 1) * n]) for r in range(dims[0]))
+        fbody = ", ".join("{%s}" % ", ".join(fnum(v) for v in vals[r * n:(r + 1) * n]) for r in range(dims[0]))
+    else:
+        body = ", ".join(cnum(v) for v in vals)
+        fbody = ", ".join(fnum(v) for v in vals)
+    out.append("SBP_TABLE double %s%s = {%s};" % (name, shape, body))
+    out.append("SBP_TABLE float %s_F%s = {%s};" % (name, shape, fbody))
 
 
 def emit():
@@ -200,26 +233,42 @@ def emit():
         out.append("#define %s_NB %d" % (P, nb))
         out.append("#define %s_NCOL %d" % (P, ncol))
         out.append("#define %s_NCLOS %d" % (P, t["nclos"]))
-        out.append("SBP_TABLE double %s_HW[%d] = {%s};" % (P.lower(), nb, ", ".join(cnum(v) for v in t["hw"])))
-        out.append("SBP_TABLE double %s_A[%d] = {%s};" % (P.lower(), q, ", ".join(cnum(v) for v in t["a"])))
-        rows = ["{%s}" % ", ".join(cnum(v) for v in r) for r in t["Dq"]]
-        out.append("SBP_TABLE double %s_DQ[%d][%d] = {%s};" % (P.lower(), nb, ncol, ", ".join(rows)))
+        table(out, "double", "%s_HW" % P.lower(), t["hw"], [nb])
+        table(out, "double", "%s_A" % P.lower(), t["a"], [q])
+        table(out, "double", "%s_DQ" % P.lower(), [v for r in t["Dq"] for v in r], [nb, ncol])
         starts, js, ks, cs = [0], [], [], []
         for row in t["clos"]:
             for (j, k), v in row:
                 js.append(j)
                 ks.append(k)
-                cs.append(cnum(v))
+                cs.append(v)
             starts.append(len(js))
         out.append("SBP_TABLE int %s_CLOS_START[%d] = {%s};" % (P.lower(), len(starts), ", ".join(map(str, starts))))
         out.append("SBP_TABLE int %s_CLOS_J[%d] = {%s};" % (P.lower(), len(js), ", ".join(map(str, js))))
         out.append("SBP_TABLE int %s_CLOS_K[%d] = {%s};" % (P.lower(), len(ks), ", ".join(map(str, ks))))
-        out.append("SBP_TABLE double %s_CLOS_C[%d] = {%s};" % (P.lower(), len(cs), ", ".join(cs)))
+        table(out, "double", "%s_CLOS_C" % P.lower(), cs, [len(cs)])
         # edge weights as an inline device function
         out.append("// interior edge weights E_m(i) = sum_k e_{m,k} b_{i+k}; B(k) reads b_{i+k}")
         for m, e in enumerate(t["edges"], start=1):
             terms = " + ".join("T(%s) * B(%d)" % (cnum(v), k) for k, v in sorted(e.items()))
             out.append("#define %s_E%d(B) (%s)" % (P, m, terms))
+        # gradient tables: node k < GS from the left end (the right end is the mirror image, with
+        # the sign of D flipped)
+        out.append("#define %s_GS %d" % (P, t["gs"]))
+        for name, tab in (("GN", t["gn"]), ("DT", t["dt"])):
+            starts, rows, js, cs = [0], [], [], []
+            for ent in tab:
+                for e in ent:
+                    rows.append(e[0])
+                    if name == "GN":
+                        js.append(e[1])
+                    cs.append(e[-1])
+                starts.append(len(rows))
+            out.append("SBP_TABLE int %s_%s_START[%d] = {%s};" % (P.lower(), name, len(starts), ", ".join(map(str, starts))))
+            out.append("SBP_TABLE int %s_%s_ROW[%d] = {%s};" % (P.lower(), name, len(rows), ", ".join(map(str, rows))))
+            if name == "GN":
+                out.append("SBP_TABLE int %s_GN_J[%d] = {%s};" % (P.lower(), len(js), ", ".join(map(str, js))))
+            table(out, "double", "%s_%s_C" % (P.lower(), name), cs, [len(cs)])
         lo = min(min(e) for e in t["edges"])
         hi = max(max(e) for e in t["edges"])
         out.append("#define %s_ELO %d" % (P, lo))

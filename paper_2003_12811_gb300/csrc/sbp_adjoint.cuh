@@ -109,66 +109,87 @@ template <int O> __device__ __forceinline__ double edge_coef(int m, int kk) {
     return Edge<O>::template e<double>(m, [&](int q) { return q == kk ? 1.0 : 0.0; });
 }
 
-// d(h^2 D_xx(b) U |_row i) / d b_k  on a line of N nodes, for the two displacement components
-template <int O, typename T, class FU0, class FU1>
-__device__ __forceinline__ void narrow_dcoef(int N, int i, int k, FU0 u0, FU1 u1, T& m0, T& m1) {
-    using P = Ord<O>;
-    m0 = T(0);
-    m1 = T(0);
-    if (i < P::NCLOS || i >= N - P::NCLOS) {
-        const bool right = i >= N - P::NCLOS;
-        const int row = right ? N - 1 - i : i;
-        for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
-            int j = P::cj(t), kk = P::ck(t);
-            if (right) { j = N - 1 - j; kk = N - 1 - kk; }
-            if (kk != k) continue;
-            const T c = T(P::cc(t));
-            m0 += c * u0(j);
-            m1 += c * u1(j);
-        }
-        return;
-    }
-    const T uc0 = u0(i), uc1 = u1(i);
-#pragma unroll
-    for (int m = 1; m <= P::Q; ++m) {
-        const T ep = T(edge_coef<O>(m, k - i)), em = T(edge_coef<O>(m, k - i + m));
-        if (ep != T(0)) { m0 += ep * (u0(i + m) - uc0); m1 += ep * (u1(i + m) - uc1); }
-        if (em != T(0)) { m0 += em * (u0(i - m) - uc0); m1 += em * (u1(i - m) - uc1); }
-    }
-}
-
-// (D^T v)(x) * h = sum_row D[row][x] h v(row) on a line of N nodes
-template <int O, typename T, class F>
-__device__ __forceinline__ T dtsum(int N, int x, F v) {
-    constexpr int R = Ord<O>::NCOL + Ord<O>::Q;
-    const int lo = max(0, x - R), hi = min(N - 1, x + R);
-    T s = T(0);
-    for (int row = lo; row <= hi; ++row) {
-        const double d = dcoef<O>(N, row, x);
-        if (d != 0.0) s += T(d) * v(row);
-    }
-    return s;
-}
-
 template <int O> struct GradCfg {
     // nodes at least GS from every face see only interior rows of every operator (rows within
     // Q of the node are interior narrow rows, D^T is -D there, and H = h1 h2)
     static constexpr int GS = Ord<O>::NCLOS + Ord<O>::Q;
-    // rows whose narrow coefficients can reach a node (closure triples reach |k - row| <= 1, 3, 5)
-    static constexpr int RR = O == 2 ? 2 : (O == 4 ? 4 : 6);
+    static_assert(GS == Ord<O>::GS, "gradient tables cover the nodes within GS of an end");
     // support of the interior edge weights E_m (offsets of b relative to the edge's left node)
     static constexpr int ELO = O == 2 ? SBP2_ELO : (O == 4 ? SBP4_ELO : SBP6_ELO);
     static constexpr int EHI = O == 2 ? SBP2_EHI : (O == 4 ? SBP4_EHI : SBP6_EHI);
 };
 
+// Gradient of the narrow rows of one grid line with respect to b at line index x, contracted with
+// phi (per row) and u: s_JL = sum_rows phi_J(row) d(row of h^2 D_xx(b) u_L)/d b_x, with s01
+// collecting (J, L) = (0, 1) and (1, 0).  Nodes at least GS from both ends: the edge-pair form
+//   -sum_m sum_k e_{m,k} (phi(j+m) - phi(j)) (u(j+m) - u(j)),  j = x - k;
+// nodes near an end: the tabulated (row, u-column, coefficient) lists (mirrored at the high end).
+template <int O, typename T, class FP, class FU>
+__device__ __forceinline__ void narrow_grad_line(int N, int x, FP phi, FU u, T& s00, T& s01, T& s11) {
+    using P = Ord<O>;
+    s00 = s01 = s11 = T(0);
+    if (x >= P::GS && x < N - P::GS) {
+#pragma unroll
+        for (int m = 1; m <= P::Q; ++m) {
+#pragma unroll
+            for (int k = GradCfg<O>::ELO; k <= GradCfg<O>::EHI; ++k) {
+                const double e = edge_coef<O>(m, k);
+                if (e == 0.0) continue;
+                const T ee = T(e);
+                const int j = x - k;
+                const T dp0 = phi(0, j + m) - phi(0, j), dp1 = phi(1, j + m) - phi(1, j);
+                const T du0 = u(0, j + m) - u(0, j), du1 = u(1, j + m) - u(1, j);
+                s00 -= ee * dp0 * du0;
+                s01 -= ee * (dp0 * du1 + dp1 * du0);
+                s11 -= ee * dp1 * du1;
+            }
+        }
+        return;
+    }
+    const bool right = x >= N - P::GS;
+    const int kk = right ? N - 1 - x : x;
+    for (int t = P::gn_start(kk); t < P::gn_start(kk + 1); ++t) {
+        int r = P::gn_row(t), j = P::gn_j(t);
+        if (right) { r = N - 1 - r; j = N - 1 - j; }
+        const T c = P::template gn_c<T>(t);
+        const T p0 = phi(0, r), p1 = phi(1, r), u0 = u(0, j), u1 = u(1, j);
+        s00 += c * p0 * u0;
+        s01 += c * (p0 * u1 + p1 * u0);
+        s11 += c * p1 * u1;
+    }
+}
+
+// (D^T phi)(x) * h on a line of N nodes: -D in the interior, tabulated columns near the ends
+// (the high end mirrors the low end with the sign of D flipped)
+template <int O, typename T, class FP>
+__device__ __forceinline__ T dt_line(int N, int x, FP phi) {
+    using P = Ord<O>;
+    T s = T(0);
+    if (x >= P::GS && x < N - P::GS) {
+#pragma unroll
+        for (int k = 1; k <= P::Q; ++k) s += P::template aT<T>(k - 1) * (phi(x - k) - phi(x + k));
+        return s;
+    }
+    const bool right = x >= N - P::GS;
+    const int kk = right ? N - 1 - x : x;
+    for (int t = P::dt_start(kk); t < P::dt_start(kk + 1); ++t) {
+        const int r = P::dt_row(t);
+        s += P::template dt_c<T>(t) * phi(right ? N - 1 - r : r);
+    }
+    return right ? -s : s;
+}
+
 // ------------------------------------------------------------------ SAT part of the gradient
 // One thread per face node: the derivatives of (H psi)^T SAT(c, u) with respect to the c planes
-// at that node (the SATs involve c only at face nodes).  Terms, for face F with normal direction
-// m, outward sign nu, phi = H psi, and w = u - v (interface) or u (displacement):
-//   normal-spread amplitude  a_J = half nu c_mJmL w_L          -> phi_a,J = sum_d phi_J D_m[f][d] / H_m(d)
-//   tangential transpose     b_J = nu c_mLtJ w_L               -> eta_J = half H_t (D_t xi_J), xi = phi_f / (H_m0 H_t)
-//   penalty                  -J^Z_JL w_L                        -> own side and the neighbour's SAT
-//   traction (Robin, and the interface average) tau_J = nu (c_mJmL D_m u_L + c_mJtL D_t u_L)
+// at that node (the SATs involve c only at face nodes).  For face F with normal direction m,
+// tangential direction t, outward sign nu, w = u - v (interface) or u (displacement), and
+// H_t = h_t hw_t(s) (H = H_m H_t on the face, H_m[0] cancels against the SAT's 1/H_m[0]):
+//   normal-spread amplitude a_J = half nu c_mJmL w_L           weight  H_t sum_d D_m[face][d] psi_J(d)
+//   tangential transpose    b_J = nu c_mLtJ w_L                weight  half H_t (D_t psi_J)
+//   penalty                 -J^Z_JL w_L (own side and, at an interface, the neighbour's SAT,
+//                            whose jump is -w)                  weight  k_own H_t (psi_J - psi^v_J)
+//   traction tau_J = nu (c_mJmL D_m u_L + c_mJtL D_t u_L) in the Robin SAT (weight -H_t psi_J) and
+//                    the interface average (weight -H_t (psi_J + psi^v_J) / 2)
 template <typename T, int O>
 __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __restrict__ gd,
                             const FaceRef* __restrict__ refs, int nrefs, int total, int pcur, int lvl, double beta) {
@@ -191,12 +212,12 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
     }
     const int m = F.m, n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int Nm = m == 0 ? n1 : n2, Nt = m == 0 ? n2 : n1;
-    const double hm = m == 0 ? B.h1 : B.h2, ht = m == 0 ? B.h2 : B.h1;
     const size_t plane = (size_t)n2 * P;
     const T* __restrict__ Ps = reinterpret_cast<const T*>(B.u[pcur]);
     const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)lvl * G.lvl_elems;
     const T nu = T(F.nu);
-    const double inv_h0 = 1.0 / F.hm0;
+    const T ihm = T(m == 0 ? B.ih1 : B.ih2), iht = T(m == 0 ? B.ih2 : B.ih1);
+    const T Ht = T(m == 0 ? B.h2 : B.h1) * hweightT<O, T>(Nt, s);
     // node at tangential index sp and depth d from the face
     auto node = [&](int sp, int d) -> size_t {
         int i1, i2;
@@ -204,18 +225,10 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
         else { i2 = F.side ? n2 - 1 - d : d; i1 = sp; }
         return (size_t)i2 * P + i1;
     };
-    auto hnode = [&](int sp, int d) -> double {
-        int i1, i2;
-        if (m == 0) { i1 = F.side ? n1 - 1 - d : d; i2 = sp; }
-        else { i2 = F.side ? n2 - 1 - d : d; i1 = sp; }
-        return node_h<O>(B, i1, i2);
-    };
     const size_t gi = node(s, 0);
-    const double Hs = hnode(s, 0);
-    const T pf0 = T(Hs * (double)Ps[gi]), pf1 = T(Hs * (double)Ps[gi + plane]);
-    // the neighbour's scaled face adjoint (interface)
+    const T ps0 = Ps[gi], ps1 = Ps[gi + plane];
+    // the neighbour's face adjoint and displacement (interface)
     T pv0 = T(0), pv1 = T(0), v0 = T(0), v1 = T(0);
-    double inv_h0v = 0.0;
     if (F.kind == FACE_INTF) {
         const BlockDev& V = adj[F.nbr_block];
         const FaceDev& FV = V.f[F.nbr_face];
@@ -226,33 +239,21 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
         const size_t gv = (size_t)j2 * V.pitch + j1, planev = (size_t)V.n2 * V.pitch;
         const T* Pv = reinterpret_cast<const T*>(V.u[pcur]);
         const T* Uv = reinterpret_cast<const T*>(GV.seg) + (size_t)lvl * GV.lvl_elems;
-        const double Hv = node_h<O>(V, j1, j2);
-        pv0 = T(Hv * (double)Pv[gv]);
-        pv1 = T(Hv * (double)Pv[gv + planev]);
+        pv0 = Pv[gv];
+        pv1 = Pv[gv + planev];
         v0 = Uv[gv];
         v1 = Uv[gv + planev];
-        inv_h0v = 1.0 / FV.hm0;
-    }
-    // derivatives of u at the face node (true derivatives)
-    auto ucomp = [&](int L, int sp, int d) { return U[node(sp, d) + (size_t)L * plane]; };
-    T dn[2], dtg[2];
-#pragma unroll
-    for (int L = 0; L < 2; ++L) {
-        const int fr_row = F.side ? Nm - 1 : 0;
-        dn[L] = dsum<O, T>(Nm, fr_row, [&](int j) { return ucomp(L, s, F.side ? Nm - 1 - j : j); }) * T(1.0 / hm);
-        dtg[L] = dsum<O, T>(Nt, s, [&](int j) { return ucomp(L, j, 0); }) * T(1.0 / ht);
-    }
-    // traction coefficient Theta_J (tau enters with -Theta_J)
-    T th0 = T(0), th1 = T(0);
-    if (F.kind == FACE_ROBIN) {
-        th0 = T(inv_h0) * pf0;
-        th1 = T(inv_h0) * pf1;
-    } else if (F.kind == FACE_INTF) {
-        th0 = T(0.5) * (T(inv_h0) * pf0 + T(inv_h0v) * pv0);
-        th1 = T(0.5) * (T(inv_h0) * pf1 + T(inv_h0v) * pv1);
     }
     if (F.kind != FACE_DISP) {
-        const T th[2] = {th0, th1};
+        // traction weight Theta_J (tau enters with -Theta_J) and the derivatives of u at the node
+        const T th[2] = {F.kind == FACE_ROBIN ? Ht * ps0 : T(0.5) * Ht * (ps0 + pv0),
+                         F.kind == FACE_ROBIN ? Ht * ps1 : T(0.5) * Ht * (ps1 + pv1)};
+        T dn[2], dtg[2];
+#pragma unroll
+        for (int L = 0; L < 2; ++L) {
+            dn[L] = dsum<O, T>(Nm, F.side ? Nm - 1 : 0, [&](int j) { return U[node(s, F.side ? Nm - 1 - j : j) + (size_t)L * plane]; }) * ihm;
+            dtg[L] = dsum<O, T>(Nt, s, [&](int j) { return U[node(j, 0) + (size_t)L * plane]; }) * iht;
+        }
         // nn planes: c_mJmL with (0,1) and (1,0) sharing plane 3m+1
         g[0] -= nu * th[0] * dn[0];
         g[1] -= nu * (th[0] * dn[1] + th[1] * dn[0]);
@@ -267,39 +268,33 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
         const T half = intf ? T(0.5) : T(1);
         const T w0 = U[gi] - v0, w1 = U[gi + plane] - v1;
         const T w[2] = {w0, w1};
-        // normal-spread amplitude: phi_a,J = sum_d phi_J(d) D_m[face row][i_m] / H_m(i_m)
+        // normal-spread weight: H_t sum_d D_m[face row][i_m] psi_J(d)  (D_m mirrored with a sign flip)
         T pa0 = T(0), pa1 = T(0);
+#pragma unroll
         for (int d = 0; d < Ord<O>::NCOL; ++d) {
-            const int im = F.side ? Nm - 1 - d : d;
-            const double fac = dcoef<O>(Nm, F.side ? Nm - 1 : 0, im) / (hm * hm * hweight<O>(Nm, im));
-            if (fac == 0.0) continue;
+            const T dq = Ord<O>::template dqT<T>(0, d);
             const size_t q = node(s, d);
-            const double Hq = hnode(s, d);
-            pa0 += T(fac * Hq * (double)Ps[q]);
-            pa1 += T(fac * Hq * (double)Ps[q + plane]);
+            pa0 += dq * Ps[q];
+            pa1 += dq * Ps[q + plane];
         }
+        const T sg = F.side ? T(-1) : T(1);
+        pa0 *= sg * Ht * ihm;
+        pa1 *= sg * Ht * ihm;
         g[0] += half * nu * pa0 * w0;
         g[1] += half * nu * (pa0 * w1 + pa1 * w0);
         g[2] += half * nu * pa1 * w1;
-        // tangential transpose: eta_J(s) = half hw(s) sum_s' D_t[s][s'] h_t xi_J(s')
-        const double hs = hweight<O>(Nt, s);
-        const T e0 = half * T(hs) * dsum<O, T>(Nt, s, [&](int sp) {
-            return T(hnode(sp, 0) * (double)Ps[node(sp, 0)] * inv_h0 / (ht * hweight<O>(Nt, sp)));
-        });
-        const T e1 = half * T(hs) * dsum<O, T>(Nt, s, [&](int sp) {
-            return T(hnode(sp, 0) * (double)Ps[node(sp, 0) + plane] * inv_h0 / (ht * hweight<O>(Nt, sp)));
-        });
+        // tangential transpose weight: half H_t (D_t psi_J)(s)
+        const T e0 = half * Ht * iht * dsum<O, T>(Nt, s, [&](int sp) { return Ps[node(sp, 0)]; });
+        const T e1 = half * Ht * iht * dsum<O, T>(Nt, s, [&](int sp) { return Ps[node(sp, 0) + plane]; });
         const T eta[2] = {e0, e1};
 #pragma unroll
         for (int J = 0; J < 2; ++J)
 #pragma unroll
             for (int L = 0; L < 2; ++L) g[plane_nt(m, L, J) - 6 + 3] += nu * eta[J] * w[L];
-        // penalty J^Z = k_own c_mJmL (+ neighbour part): own SAT and, at an interface, the
-        // neighbour's SAT (whose jump is -w) both carry this node's c
+        // penalty J^Z = k_own c_mJmL (+ neighbour part)
         const double dd = 2.0;
-        const T kown = T(intf ? beta * dd / 4.0 / F.hm0 : beta * dd / F.hm0);
-        const T k0 = kown * (T(inv_h0) * pf0 - (intf ? T(inv_h0v) * pv0 : T(0)));
-        const T k1 = kown * (T(inv_h0) * pf1 - (intf ? T(inv_h0v) * pv1 : T(0)));
+        const T kown = T(intf ? beta * dd / 4.0 * F.inv_h0 : beta * dd * F.inv_h0);
+        const T k0 = kown * Ht * (ps0 - pv0), k1 = kown * Ht * (ps1 - pv1);
         g[0] -= k0 * w0;
         g[1] -= k0 * w1 + k1 * w0;
         g[2] -= k1 * w1;
@@ -321,7 +316,7 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
     const size_t plane = (size_t)n2 * P;
     const T* __restrict__ Ps = reinterpret_cast<const T*>(B.u[pcur]);
     const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)lvl * G.lvl_elems;
-    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
     auto ps = [&](int L, int j1, int j2) { return __ldg(Ps + (size_t)L * plane + (size_t)j2 * P + j1); };
     auto uu = [&](int L, int j1, int j2) { return __ldg(U + (size_t)L * plane + (size_t)j2 * P + j1); };
     T acc[10];
@@ -384,39 +379,26 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
 #pragma unroll
             for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] = d1p[a] * d2u[b] + d2p[b] * d1u[a];
     } else {
-        auto phi = [&](int L, int j1, int j2) { return T(node_h<O>(B, j1, j2) * (double)ps(L, j1, j2)); };
-        constexpr int RR = GradCfg<O>::RR;
-        T s00 = T(0), s01 = T(0), s11 = T(0);
-        for (int i = max(0, i1 - RR); i <= min(n1 - 1, i1 + RR); ++i) {
-            T m0, m1;
-            narrow_dcoef<O, T>(n1, i, i1, [&](int j) { return uu(0, j, i2); }, [&](int j) { return uu(1, j, i2); }, m0, m1);
-            if (m0 == T(0) && m1 == T(0)) continue;
-            const T p0 = phi(0, i, i2), p1 = phi(1, i, i2);
-            s00 += p0 * m0;
-            s01 += p0 * m1 + p1 * m0;
-            s11 += p1 * m1;
-        }
+        const T hh = T(B.h1 * B.h2);
+        auto phi = [&](int L, int j1, int j2) {
+            return hh * hweightT<O, T>(n1, j1) * hweightT<O, T>(n2, j2) * ps(L, j1, j2);
+        };
+        T s00, s01, s11;
+        narrow_grad_line<O, T>(n1, i1, [&](int L, int j) { return phi(L, j, i2); }, [&](int L, int j) { return uu(L, j, i2); },
+                               s00, s01, s11);
         acc[0] = s00 * ih1 * ih1;
         acc[1] = s01 * ih1 * ih1;
         acc[2] = s11 * ih1 * ih1;
-        s00 = s01 = s11 = T(0);
-        for (int i = max(0, i2 - RR); i <= min(n2 - 1, i2 + RR); ++i) {
-            T m0, m1;
-            narrow_dcoef<O, T>(n2, i, i2, [&](int j) { return uu(0, i1, j); }, [&](int j) { return uu(1, i1, j); }, m0, m1);
-            if (m0 == T(0) && m1 == T(0)) continue;
-            const T p0 = phi(0, i1, i), p1 = phi(1, i1, i);
-            s00 += p0 * m0;
-            s01 += p0 * m1 + p1 * m0;
-            s11 += p1 * m1;
-        }
+        narrow_grad_line<O, T>(n2, i2, [&](int L, int j) { return phi(L, i1, j); }, [&](int L, int j) { return uu(L, i1, j); },
+                               s00, s01, s11);
         acc[3] = s00 * ih2 * ih2;
         acc[4] = s01 * ih2 * ih2;
         acc[5] = s11 * ih2 * ih2;
         T d1p[2], d2p[2], d1u[2], d2u[2];
 #pragma unroll
         for (int L = 0; L < 2; ++L) {
-            d1p[L] = dtsum<O, T>(n1, i1, [&](int j) { return phi(L, j, i2); }) * ih1;
-            d2p[L] = dtsum<O, T>(n2, i2, [&](int j) { return phi(L, i1, j); }) * ih2;
+            d1p[L] = dt_line<O, T>(n1, i1, [&](int j) { return phi(L, j, i2); }) * ih1;
+            d2p[L] = dt_line<O, T>(n2, i2, [&](int j) { return phi(L, i1, j); }) * ih2;
             d1u[L] = dsum<O, T>(n1, i1, [&](int j) { return uu(L, j, i2); }) * ih1;
             d2u[L] = dsum<O, T>(n2, i2, [&](int j) { return uu(L, i1, j); }) * ih2;
         }
@@ -457,7 +439,7 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
         dd += Ps[q] * (Up[q] - T(2) * U[q] + Um[q]);
     }
     T* __restrict__ GR = reinterpret_cast<T*>(G.grho);
-    GR[gi] -= T(node_h<O>(B, i1, i2) * B.J[gi]) * dd;
+    GR[gi] -= T(B.h1 * B.h2) * hweightT<O, T>(n1, i1) * hweightT<O, T>(n2, i2) * T(B.J[gi]) * dd;
 }
 
 template <typename T, int O>
@@ -483,10 +465,12 @@ __global__ void __launch_bounds__(256) k_grad_strip(BlockDev B, GradDev G, int p
     if (t < top) { i2 = (int)(t / n1); i1 = (int)(t - (long long)i2 * n1); }
     else if (t < 2 * top) { const long long u = t - top; i2 = n2 - s2 + (int)(u / n1); i1 = (int)(u - (long long)(i2 - n2 + s2) * n1); }
     else {
+        // side bands column by column: a warp shares its distance from the face
         const long long u = t - 2 * top;
-        const int row = (int)(u / (2 * s1)), k = (int)(u - (long long)row * 2 * s1);
+        const int rows = n2 - 2 * s2;
+        const int col = (int)(u / rows), row = (int)(u - (long long)col * rows);
         i2 = s2 + row;
-        i1 = k < s1 ? k : n1 - 2 * s1 + k;
+        i1 = col < s1 ? col : n1 - 2 * s1 + col;
     }
     grad_node<T, O, false>(B, G, pcur, lvl, dt2, i1, i2);
 }

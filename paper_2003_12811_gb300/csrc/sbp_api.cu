@@ -68,6 +68,9 @@ int order_min_n(int o) { return o == 2 ? 5 : (o == 4 ? 18 : 27); }
 double order_hw(int o, int i) {
     return o == 2 ? sbphost::sbp2_HW[i] : (o == 4 ? sbphost::sbp4_HW[i] : sbphost::sbp6_HW[i]);
 }
+double order_dq0(int o, int c) {
+    return o == 2 ? sbphost::sbp2_DQ[0][c] : (o == 4 ? sbphost::sbp4_DQ[0][c] : sbphost::sbp6_DQ[0][c]);
+}
 double host_hweight(int o, int N, int i) {
     const int nb = order_nb(o);
     if (i < nb) return order_hw(o, i);
@@ -101,10 +104,10 @@ struct sbp_handle {
     int num_sms = 0;
     std::string err;
     std::vector<void*> allocs;
-    // kernel timing (benchmarks): families 0 interior, 1 boundary strips, 2 faces, 3 sources
+    // kernel timing (benchmarks): the families of sbp_profile in include/sbp.h
     bool prof = false;
-    double prof_ms[4] = {0, 0, 0, 0};
-    long long launches[4] = {0, 0, 0, 0};
+    double prof_ms[SBP_PROF_FAMILIES] = {0};
+    long long launches[SBP_PROF_FAMILIES] = {0};
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int fam; cudaEvent_t a, b; };
     std::vector<Pending> pending;
@@ -188,6 +191,8 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
     b.strip = std::max(order_nclos(h->order), order_ncol(h->order));
     b.h1 = hb.h1;
     b.h2 = hb.h2;
+    b.ih1 = 1.0 / hb.h1;
+    b.ih2 = 1.0 / hb.h2;
     b.u[0] = hb.u[0];
     b.u[1] = hb.u[1];
     b.c = hb.c;
@@ -211,6 +216,13 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
         const int Nm = (f / 2 == 0) ? hb.n1 : hb.n2;
         const double hm = (f / 2 == 0) ? hb.h1 : hb.h2;
         D.hm0 = hm * host_hweight(h->order, Nm, 0);
+        D.inv_h0 = 1.0 / D.hm0;
+        // D_m[face row][i_m] / (h_m^2 hw(i_m)) at depth d: the boundary row of D (mirrored with the
+        // opposite sign at the high end) over the norm weight
+        for (int d = 0; d < 12; ++d) {
+            const double dq0 = d < order_ncol(h->order) ? order_dq0(h->order, d) : 0.0;
+            D.fac[d] = ((f % 2) ? -dq0 : dq0) / (hm * hm * host_hweight(h->order, Nm, (f % 2) ? Nm - 1 - d : d));
+        }
         D.jhat = F.jhat;
         D.ju = F.ju;
         D.g = F.g;
@@ -499,6 +511,7 @@ int step_once(sbp_handle* h, double dt, cudaStream_t st) {
 
 int record_receivers(sbp_handle* h, double* d_row, cudaStream_t st) {
     const int nr = (int)h->recs.size();
+    ProfScope ps(h, 6, st, 1);
     if (h->precision == SBP_FP64) k_record<double><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks, h->d_recs, nr, h->cur, d_row);
     else k_record<float><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks, h->d_recs, nr, h->cur, d_row);
     return SBP_OK;
@@ -508,16 +521,24 @@ template <typename T, int O>
 void launch_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int pc, int lvl, double dt2,
                  cudaStream_t st) {
     const int total = h->nface_nodes;
-    if (total > 0)
+    if (total > 0) {
+        ProfScope ps(h, 6, st, 1);
         k_grad_face<T, O><<<grid_for(total, 128), 128, 0, st>>>(h->d_blocks_adj, d_grad, h->d_refs, h->nrefs, total, pc, lvl, h->beta);
+    }
     constexpr int GS = GradCfg<O>::GS;
     for (size_t b = 0; b < h->blocks.size(); ++b) {
         const HostBlock& hb = h->blocks[b];
         const BlockDev v = make_view_adj(h, hb);
-        dim3 gi((hb.n1 - 2 * GS + 31) / 32, (hb.n2 - 2 * GS + 7) / 8);
-        k_grad_interior<T, O><<<gi, dim3(32, 8), 0, st>>>(v, grads[b], pc, lvl, dt2);
-        const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)(hb.n1 - 2 * GS) * (hb.n2 - 2 * GS);
-        k_grad_strip<T, O><<<grid_for(nstrip), 256, 0, st>>>(v, grads[b], pc, lvl, dt2);
+        {
+            ProfScope ps(h, 4, st, 1);
+            dim3 gi((hb.n1 - 2 * GS + 31) / 32, (hb.n2 - 2 * GS + 7) / 8);
+            k_grad_interior<T, O><<<gi, dim3(32, 8), 0, st>>>(v, grads[b], pc, lvl, dt2);
+        }
+        {
+            ProfScope ps(h, 5, st, 1);
+            const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)(hb.n1 - 2 * GS) * (hb.n2 - 2 * GS);
+            k_grad_strip<T, O><<<grid_for(nstrip), 256, 0, st>>>(v, grads[b], pc, lvl, dt2);
+        }
     }
 }
 
@@ -995,7 +1016,7 @@ int sbp_profile(sbp_handle* h, int enable) {
         h->ev_pool.push_back(pd.b);
     }
     h->pending.clear();
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < SBP_PROF_FAMILIES; ++k) {
         h->prof_ms[k] = 0;
         h->launches[k] = 0;
     }
@@ -1014,7 +1035,7 @@ int sbp_profile_read(sbp_handle* h, double* ms, long long* launches) {
         h->ev_pool.push_back(pd.b);
     }
     h->pending.clear();
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < SBP_PROF_FAMILIES; ++k) {
         if (ms) ms[k] = h->prof_ms[k];
         if (launches) launches[k] = h->launches[k];
     }
@@ -1117,8 +1138,8 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return h->fail(SBP_E_CUDA, "stream");
         const bool prof = h->prof;
         h->prof = false;
-        long long saved[4];
-        for (int k = 0; k < 4; ++k) saved[k] = h->launches[k];
+        long long saved[SBP_PROF_FAMILIES];
+        for (int k = 0; k < SBP_PROF_FAMILIES; ++k) saved[k] = h->launches[k];
         cudaGraph_t g = nullptr;
         int rc = SBP_OK;
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = SBP_E_CUDA;
@@ -1135,7 +1156,7 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) rc = SBP_E_CUDA;
         cudaStreamDestroy(cs);
         h->prof = prof;
-        for (int k = 0; k < 4; ++k) h->launches[k] = saved[k];
+        for (int k = 0; k < SBP_PROF_FAMILIES; ++k) h->launches[k] = saved[k];
         if (rc != SBP_OK) {
             if (g) cudaGraphDestroy(g);
             return h->fail(SBP_E_CUDA, "graph capture failed");
@@ -1224,8 +1245,8 @@ int sbp_autotune(sbp_handle* h, int* rows_out) {
     a.cur = h->cur;
     a.with_data = 0;
     const int saved = h->rows_per_cta;
-    long long saved_l[4];
-    for (int k = 0; k < 4; ++k) saved_l[k] = h->launches[k];
+    long long saved_l[SBP_PROF_FAMILIES];
+    for (int k = 0; k < SBP_PROF_FAMILIES; ++k) saved_l[k] = h->launches[k];
     for (int c : cand) {
         h->rows_per_cta = c;
         float tot = 0.f;
@@ -1249,7 +1270,7 @@ int sbp_autotune(sbp_handle* h, int* rows_out) {
             best = c;
         }
     }
-    for (int k = 0; k < 4; ++k) h->launches[k] = saved_l[k];
+    for (int k = 0; k < SBP_PROF_FAMILIES; ++k) h->launches[k] = saved_l[k];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->rows_per_cta = best;
@@ -1406,8 +1427,11 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
             !copy(lvl_ptr(fin, b, 1), h->blocks[b].u[h->cur], lvl_bytes[b]))
             return h->fail(SBP_E_CUDA, "final state copy");
     // misfit: 1/2 dt sum (traces - observed)^2
-    k_residual<<<nsteps, 256, 0, st>>>(d_tr, d_obs, d_res, (int)per, d_part);
-    k_sum_scaled<<<1, 256, 0, st>>>(d_part, nsteps, 0.5 * dt, d_phi);
+    {
+        ProfScope ps(h, 7, st, 2);
+        k_residual<<<nsteps, 256, 0, st>>>(d_tr, d_obs, d_res, (int)per, d_part);
+        k_sum_scaled<<<1, 256, 0, st>>>(d_part, nsteps, 0.5 * dt, d_phi);
+    }
     // backward pass: psi_{N+1} = psi_{N+2} = 0, accumulators zero
     for (int b = 0; b < nb; ++b) {
         HostBlock& hb = h->blocks[b];
@@ -1446,10 +1470,13 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
             rc = run_operator(h, aa, 0, st, true);          // psi_n = 2 psi_{n+1} - psi_{n+2} + dt^2 W L psi_{n+1}
             if (rc != SBP_OK) return rc;
             pc = 1 - pc;
-            if (h->precision == SBP_FP64)
-                k_inject<double><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
-            else
-                k_inject<float><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
+            {
+                ProfScope ps(h, 6, st, 1);
+                if (h->precision == SBP_FP64)
+                    k_inject<double><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
+                else
+                    k_inject<float><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
+            }
             run_grad(h, d_grad, grads, pc, q - a0 + 1, dt * dt, st);
         }
     }
@@ -1463,6 +1490,7 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
         double* dR = (double*)sc.get(n * sizeof(double));
         if (!dC || !dR) return h->fail(SBP_E_OOM, "gradient download staging");
         const BlockDev v = make_view(h, hb);
+        ProfScope ps(h, 7, st, 1);
         if (h->precision == SBP_FP64)
             k_grad_to_C<double><<<grid_for((long long)n), 256, 0, st>>>(v, (const double*)grads[b].gc, (const double*)grads[b].grho, dC, dR);
         else

@@ -15,10 +15,16 @@ namespace sbp {
 
 // ------------------------------------------------------------------ order traits
 template <int O> struct Ord;
+// Every coefficient is also available in the arithmetic type T (FP32 kernels read the FP32 twin
+// tables, which hold exactly the values a cast of the FP64 entries gives).
+#define SBP_TWIN(name, expr64, expr32)                                                                 \
+    template <typename T> static __device__ __forceinline__ T name {                                   \
+        if constexpr (sizeof(T) == 4) return expr32; else return expr64;                               \
+    }
 #define SBP_ORD(O)                                                                                     \
     template <> struct Ord<O> {                                                                        \
         static constexpr int Q = SBP##O##_Q, NB = SBP##O##_NB, NCOL = SBP##O##_NCOL,                   \
-                             NCLOS = SBP##O##_NCLOS;                                                   \
+                             NCLOS = SBP##O##_NCLOS, GS = SBP##O##_GS;                                 \
         static __device__ __forceinline__ double hw(int i) { return sbpdev::sbp##O##_HW[i]; }          \
         static __device__ __forceinline__ double dq(int r, int c) { return sbpdev::sbp##O##_DQ[r][c]; } \
         static __device__ __forceinline__ double a(int k) { return sbpdev::sbp##O##_A[k]; }            \
@@ -26,11 +32,24 @@ template <int O> struct Ord;
         static __device__ __forceinline__ int cj(int t) { return sbpdev::sbp##O##_CLOS_J[t]; }          \
         static __device__ __forceinline__ int ck(int t) { return sbpdev::sbp##O##_CLOS_K[t]; }          \
         static __device__ __forceinline__ double cc(int t) { return sbpdev::sbp##O##_CLOS_C[t]; }      \
+        SBP_TWIN(hwT(int i), sbpdev::sbp##O##_HW[i], sbpdev::sbp##O##_HW_F[i])                          \
+        SBP_TWIN(dqT(int r, int c), sbpdev::sbp##O##_DQ[r][c], sbpdev::sbp##O##_DQ_F[r][c])             \
+        SBP_TWIN(aT(int k), sbpdev::sbp##O##_A[k], sbpdev::sbp##O##_A_F[k])                             \
+        SBP_TWIN(ccT(int t), sbpdev::sbp##O##_CLOS_C[t], sbpdev::sbp##O##_CLOS_C_F[t])                  \
+        /* gradient tables: node k < GS from the left end */                                            \
+        static __device__ __forceinline__ int gn_start(int k) { return sbpdev::sbp##O##_GN_START[k]; }  \
+        static __device__ __forceinline__ int gn_row(int t) { return sbpdev::sbp##O##_GN_ROW[t]; }      \
+        static __device__ __forceinline__ int gn_j(int t) { return sbpdev::sbp##O##_GN_J[t]; }          \
+        SBP_TWIN(gn_c(int t), sbpdev::sbp##O##_GN_C[t], sbpdev::sbp##O##_GN_C_F[t])                     \
+        static __device__ __forceinline__ int dt_start(int k) { return sbpdev::sbp##O##_DT_START[k]; }  \
+        static __device__ __forceinline__ int dt_row(int t) { return sbpdev::sbp##O##_DT_ROW[t]; }      \
+        SBP_TWIN(dt_c(int t), sbpdev::sbp##O##_DT_C[t], sbpdev::sbp##O##_DT_C_F[t])                     \
     };
 SBP_ORD(2)
 SBP_ORD(4)
 SBP_ORD(6)
 #undef SBP_ORD
+#undef SBP_TWIN
 
 // interior edge weights E_m(i) = sum_k e_{m,k} b_{i+k} (m = 1..Q) of the narrow operator
 template <int O> struct Edge;
@@ -67,12 +86,33 @@ template <int O> __device__ __forceinline__ double dcoef(int N, int row, int col
     return k > 0 ? P::a(k - 1) : -P::a(-k - 1);
 }
 
+// the same entry in the arithmetic type T
+template <int O, typename T> __device__ __forceinline__ T dcoefT(int N, int row, int col) {
+    using P = Ord<O>;
+    if (row < P::NB) return (col >= 0 && col < P::NCOL) ? P::template dqT<T>(row, col) : T(0);
+    if (row >= N - P::NB) {
+        int r = N - 1 - row, c = N - 1 - col;
+        return (c >= 0 && c < P::NCOL) ? -P::template dqT<T>(r, c) : T(0);
+    }
+    int k = col - row;
+    if (k == 0 || k > P::Q || k < -P::Q) return T(0);
+    return k > 0 ? P::template aT<T>(k - 1) : -P::template aT<T>(-k - 1);
+}
+
 // norm weight H_ii / h
 template <int O> __device__ __forceinline__ double hweight(int N, int i) {
     using P = Ord<O>;
     if (i < P::NB) return P::hw(i);
     if (i >= N - P::NB) return P::hw(N - 1 - i);
     return 1.0;
+}
+
+// norm weight H_ii / h in the arithmetic type T
+template <int O, typename T> __device__ __forceinline__ T hweightT(int N, int i) {
+    using P = Ord<O>;
+    if (i < P::NB) return P::template hwT<T>(i);
+    if (i >= N - P::NB) return P::template hwT<T>(N - 1 - i);
+    return T(1);
 }
 
 // first and last column of row `row` of D
@@ -89,14 +129,14 @@ template <int O, typename T, class F> __device__ __forceinline__ T dsum(int N, i
     T s = T(0);
     if (row < P::NB) {
 #pragma unroll
-        for (int j = 0; j < P::NCOL; ++j) s += T(P::dq(row, j)) * v(j);
+        for (int j = 0; j < P::NCOL; ++j) s += P::template dqT<T>(row, j) * v(j);
     } else if (row >= N - P::NB) {
         const int r = N - 1 - row;
 #pragma unroll
-        for (int j = 0; j < P::NCOL; ++j) s -= T(P::dq(r, j)) * v(N - 1 - j);
+        for (int j = 0; j < P::NCOL; ++j) s -= P::template dqT<T>(r, j) * v(N - 1 - j);
     } else {
 #pragma unroll
-        for (int k = 1; k <= P::Q; ++k) s += T(P::a(k - 1)) * (v(row + k) - v(row - k));
+        for (int k = 1; k <= P::Q; ++k) s += P::template aT<T>(k - 1) * (v(row + k) - v(row - k));
     }
     return s;
 }
@@ -114,7 +154,7 @@ __device__ __forceinline__ void dxx_vec(int N, int i, FU0 u0, FU1 u1, FB0 b0, FB
         for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
             int j = P::cj(t), k = P::ck(t);
             if (right) { j = N - 1 - j; k = N - 1 - k; }
-            const T c = T(P::cc(t));
+            const T c = P::template ccT<T>(t);
             const T bb0 = b0(k), bb1 = b1(k), bb2 = b2(k);
             const T uu0 = u0(j), uu1 = u1(j);
             r0 += c * (bb0 * uu0 + bb1 * uu1);
@@ -152,6 +192,8 @@ struct FaceDev {
     int kind, m, side, nf;
     int nbr_block, nbr_face, reversed, pad;
     double nu, hm0;           // outward reference normal component, H_m[0] (includes h_m)
+    double inv_h0;            // 1 / H_m[0]
+    double fac[12];           // D_m[face row][i_m] / H_m[i_m] / h_m at depth d = |i_m - face| < NCOL
     const double* jhat;       // surface scale factor per face node
     const void* ju;           // robin: J^ U (3 x nf), type T
     const void* g;            // data: displacement g (2 x K x nf) or robin J^ g, type T
@@ -162,6 +204,7 @@ struct FaceDev {
 struct BlockDev {
     int n1, n2, pitch, strip;  // strip = width of the boundary strips handled by k_boundary
     double h1, h2;
+    double ih1, ih2;          // 1 / h1, 1 / h2
     void* u[2];               // state buffers, 2 planes each
     const void* c;            // 10 planes
     const void* w;            // 1/(rho J)

@@ -103,7 +103,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     float ak[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) ak[k] = (float)Ord<O>::a(k);
-    const float ih1 = (float)(1.0 / B.h1), ih2 = (float)(1.0 / B.h2);
+    const float ih1 = (float)B.ih1, ih2 = (float)B.ih2;
     const float ih11 = ih1 * ih1, ih22 = ih2 * ih2;
 
     // register queues, index 0 = oldest row

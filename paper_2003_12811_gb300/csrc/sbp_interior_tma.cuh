@@ -129,7 +129,7 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
     if (tile >= ntiles) return;
     if (threadIdx.x == 0) issue(tile, 0, true);
 
-    const float ih1 = (float)(1.0 / B.h1), ih2 = (float)(1.0 / B.h2);
+    const float ih1 = (float)B.ih1, ih2 = (float)B.ih2;
     const float ih11 = ih1 * ih1, ih22 = ih2 * ih2;
     float ak[Q];
 #pragma unroll

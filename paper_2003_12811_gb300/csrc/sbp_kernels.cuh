@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
     for (int f = 0; f < 4; ++f) load(smx + f * SY * SX, C + (6 + f) * plane, SY, SX, y0 - Q, x0 - Q);
     __syncthreads();
 
-    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
     // mixed fluxes g1_j = c_1j2l D_2 u_l on tile rows x (tile cols + x-halo)
     for (int idx = tid; idx < TY * SX; idx += ITHREADS) {
         const int r = idx / SX, c = idx - r * SX;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
         T d0 = T(0), d1 = T(0);
 #pragma unroll
         for (int k = 1; k <= Q; ++k) {
-            const T ak = T(Ord<O>::a(k - 1));
+            const T ak = Ord<O>::template aT<T>(k - 1);
             d0 += ak * (p0[k * SX] - p0[-k * SX]);
             d1 += ak * (p1[k * SX] - p1[-k * SX]);
         }
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
         T d0 = T(0), d1 = T(0);
 #pragma unroll
         for (int k = 1; k <= Q; ++k) {
-            const T ak = T(Ord<O>::a(k - 1));
+            const T ak = Ord<O>::template aT<T>(k - 1);
             d0 += ak * (p0[k] - p0[-k]);
             d1 += ak * (p1[k] - p1[-k]);
         }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
         T m10 = T(0), m11 = T(0), m20 = T(0), m21 = T(0);
 #pragma unroll
         for (int k = 1; k <= Q; ++k) {
-            const T ak = T(Ord<O>::a(k - 1));
+            const T ak = Ord<O>::template aT<T>(k - 1);
             m10 += ak * (g10[k] - g10[-k]);
             m11 += ak * (g11[k] - g11[-k]);
             m20 += ak * (g20[k * TX] - g20[-k * TX]);
@@ -203,7 +203,7 @@ template <typename T, int O, int MODE, class FU0, class FU1, class FC>
 __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a, int i1, int i2, FU0 u0, FU1 u1, FC cc) {
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const size_t plane = (size_t)n2 * P;
-    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
     T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0);
     dxx_vec<O, T>(n1, i1, [&](int j) { return u0(j, i2); }, [&](int j) { return u1(j, i2); },
                   [&](int k) { return cc(0, k, i2); }, [&](int k) { return cc(1, k, i2); },
@@ -218,7 +218,7 @@ __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a,
         drow_range<O>(n1, i1, lo, hi);
         T s0 = T(0), s1 = T(0);
         for (int aa = lo; aa <= hi; ++aa) {
-            const T d = T(dcoef<O>(n1, i1, aa));
+            const T d = dcoefT<O, T>(n1, i1, aa);
             if (d == T(0)) continue;
             const T du0 = dsum<O, T>(n2, i2, [&](int bb) { return u0(aa, bb); }) * ih2;
             const T du1 = dsum<O, T>(n2, i2, [&](int bb) { return u1(aa, bb); }) * ih2;
@@ -231,7 +231,7 @@ __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a,
         s0 = T(0);
         s1 = T(0);
         for (int bb = lo; bb <= hi; ++bb) {
-            const T d = T(dcoef<O>(n2, i2, bb));
+            const T d = dcoefT<O, T>(n2, i2, bb);
             if (d == T(0)) continue;
             const T du0 = dsum<O, T>(n1, i1, [&](int aa) { return u0(aa, bb); }) * ih1;
             const T du1 = dsum<O, T>(n1, i1, [&](int aa) { return u1(aa, bb); }) * ih1;
@@ -251,8 +251,7 @@ __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a,
         const int s = m == 0 ? i2 : i1;
         const T* __restrict__ sat = reinterpret_cast<const T*>(F.sat);
         const int nf = F.nf;
-        const double hm = m == 0 ? B.h1 : B.h2;
-        const T fac = T(dcoef<O>(Nm, F.side ? Nm - 1 : 0, im) / (hm * hm * hweight<O>(Nm, im)));
+        const T fac = T(F.fac[d]);
         r0 += fac * sat[2 * nf + s];
         r1 += fac * sat[3 * nf + s];
         if (d == 0) {
@@ -376,7 +375,7 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
     asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
     __syncthreads();
     auto at = [&](int pl, int j1, int j2) -> T& { return sm[pl * ST::RMAX + (j2 - ry0) * RW + (j1 - rx0)]; };
-    const T ih1 = T(1.0 / B.h1), ih2 = T(1.0 / B.h2);
+    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
     // fluxes at every staged node whose D stencils lie inside the staged region
     for (int idx = threadIdx.x; idx < RN; idx += NT) {
         const int r = idx / RW, c = idx - r * RW;
@@ -425,8 +424,7 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
         const int s = m == 0 ? i2 : i1;
         const T* __restrict__ sat = reinterpret_cast<const T*>(F.sat);
         const int nf = F.nf;
-        const double hm = m == 0 ? B.h1 : B.h2;
-        const T fac = T(dcoef<O>(Nm, F.side ? Nm - 1 : 0, im) / (hm * hm * hweight<O>(Nm, im)));
+        const T fac = T(F.fac[d]);
         r0 += fac * sat[2 * nf + s];
         r1 += fac * sat[3 * nf + s];
         if (d == 0) {
@@ -494,16 +492,16 @@ __global__ void k_face_trace(const BlockDev* __restrict__ blocks, const FaceRef*
     T dn0, dn1, dt0, dt1;
     if (m == 0) {
         const size_t row = (size_t)i2 * P;
-        dn0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(1.0 / B.h1);
-        dn1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(1.0 / B.h1);
-        dt0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
-        dt1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
+        dn0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(B.ih1);
+        dn1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(B.ih1);
+        dt0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(B.ih2);
+        dt1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(B.ih2);
     } else {
         const size_t row = (size_t)i2 * P;
-        dn0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
-        dn1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(1.0 / B.h2);
-        dt0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(1.0 / B.h1);
-        dt1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(1.0 / B.h1);
+        dn0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(B.ih2);
+        dn1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(B.ih2);
+        dt0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(B.ih1);
+        dt1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(B.ih1);
     }
     const T nu = T(F.nu);
     T tau[2];
@@ -572,7 +570,7 @@ __global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* _
     const int m = F.m, nf = F.nf;
     const T* tr = reinterpret_cast<const T*>(F.tr);
     T* sat = reinterpret_cast<T*>(F.sat);
-    const T inv_h0 = T(1.0 / F.hm0);
+    const T inv_h0 = T(F.inv_h0);
     const T nu = T(F.nu);
     const double dd = 2.0;   // spatial dimension d
     if (F.kind == FACE_ROBIN) {
