@@ -187,7 +187,11 @@ def serving_bench(nshots=32, side_range=(201, 801), rate=64.0, tick=32):
             "node_updates": int(sum((p.blocks[0].N1 * p.blocks[0].N2) * n for (_, _, _, n), p in zip(specs, probs)))}
 
 
-GRAD_BYTES_PER_NODE = {"fp32": 128, "fp64": 248}   # psi 2, u_n 2, u_{n+1} 2, u_{n-1} 2, g_c 10 r+w, g_rho r+w, J (FP64)
+# gradient interior kernel, per node: every level of the segment reads psi_n (2 words) and u_{n+1}
+# (2 words; u_n, u_{n-1} stay in registers); once per launch g_c (10 r+w), g_rho (r+w), J (FP64)
+# and the first two forward levels (4 words)
+GRAD_BYTES_PER_NODE_LEVEL = {"fp32": 16, "fp64": 32}
+GRAD_BYTES_PER_NODE_LAUNCH = {"fp32": 22 * 4 + 8 + 16, "fp64": 22 * 8 + 8 + 32}
 
 
 def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
@@ -233,7 +237,8 @@ def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
     GS = 12                                                    # gradient interior starts 12 nodes from a face (order 6)
     inner = (n - 2 * GS) ** 2
     k_ms = fam_ms[4] / max(1, fam_n[4])
-    bpn = GRAD_BYTES_PER_NODE[prec]
+    levels = nsteps / max(1, fam_n[4])                         # levels per launch (one launch per segment)
+    bpn = GRAD_BYTES_PER_NODE_LEVEL[prec] * levels + GRAD_BYTES_PER_NODE_LAUNCH[prec]
     achieved = bpn * inner / (k_ms / 1e3) / 1e9
     peak, src = peaks()
     names = ["interior", "boundary", "faces", "sources", "grad_interior", "grad_strips", "grad_faces_receivers", "misfit_output"]
@@ -245,7 +250,8 @@ def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
             "misfit": phi, "grad_rho_absmax": float(np.abs(gr[0]).max()), "grad_C_absmax": float(np.abs(gc[0]).max()),
             "family_ms": {k: float(v) for k, v in zip(names, fam_ms)},
             "family_launches": {k: int(v) for k, v in zip(names, fam_n)},
-            "roofline": {"kernel": "k_grad_interior", "bound": "hbm", "bytes_per_node": bpn, "units_per_launch": inner,
+            "roofline": {"kernel": "k_grad_interior", "bound": "hbm", "bytes_per_node": bpn, "levels_per_launch": levels,
+                         "units_per_launch": inner,
                          "kernel_ms": k_ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src, "traffic": None}}
 

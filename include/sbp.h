@@ -229,8 +229,9 @@ int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces);
  * + dt^2 W L psi_{n+1} + H^-1 W dPhi/du_{n+1} with the forward kernels (psi = H^-1 W lambda, lambda
  * the Lagrange multipliers of the step equations), accumulating
  *   dPhi/dc_p(x) += dt^2 (H psi_n)^T dL/dc_p(x) u_n,  dPhi/drho(x) -= H J psi_n . (u_{n+1} - 2u_n + u_{n-1}),
- * and finally dPhi/dC from dPhi/dc through c_ijkl = J F_Ii C_IjKl F_Kk.  Device workspace: about
- * (2 nsteps / K + K + 16) field levels per block plus 11 accumulator planes, allocated for the call.
+ * (the terms of a segment are accumulated in registers over its levels and added once), and
+ * finally dPhi/dC from dPhi/dc through c_ijkl = J F_Ii C_IjKl F_Kk.  Device workspace: about
+ * (2 nsteps / K + 2 K + 4) field levels per block plus 11 accumulator planes, allocated for the call.
  * On return the state is the one after nsteps steps (as sbp_step would leave it).  Synchronous.
  * Errors: SBP_E_STATE without receivers or when a displacement face carries boundary data (the
  * data would then depend on C); SBP_E_OOM when the workspace does not fit. */

@@ -19,10 +19,12 @@ namespace sbp {
 
 struct GradDev {
     const void* seg;          // recomputed forward levels: level l (2 planes) at seg + l * lvl_elems
+    const void* pseg;         // adjoint levels of the segment: psi level l pairs with forward level l + 1
     long long lvl_elems;
     void* gc;                 // 10 accumulator planes (dPhi/dc, plane layout of BlockDev::c)
     void* grho;               // 1 accumulator plane (dPhi/drho)
     void* gsat[4];            // per face: 7 x nf SAT contributions (planes 3m, 3m+1, 3m+2, 6..9)
+    void* part;               // strip nodes: per level chunk, 11 partial sums (10 c planes, rho)
 };
 
 struct RecDev {
@@ -192,7 +194,7 @@ __device__ __forceinline__ T dt_line(int N, int x, FP phi) {
 //                    the interface average (weight -H_t (psi_J + psi^v_J) / 2)
 template <typename T, int O>
 __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __restrict__ gd,
-                            const FaceRef* __restrict__ refs, int nrefs, int total, int pcur, int lvl, double beta) {
+                            const FaceRef* __restrict__ refs, int nrefs, int total, int nl, double beta) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     const FaceRef fr = refs[find_face(refs, nrefs, t)];
@@ -213,8 +215,6 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
     const int m = F.m, n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int Nm = m == 0 ? n1 : n2, Nt = m == 0 ? n2 : n1;
     const size_t plane = (size_t)n2 * P;
-    const T* __restrict__ Ps = reinterpret_cast<const T*>(B.u[pcur]);
-    const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)lvl * G.lvl_elems;
     const T nu = T(F.nu);
     const T ihm = T(m == 0 ? B.ih1 : B.ih2), iht = T(m == 0 ? B.ih2 : B.ih1);
     const T Ht = T(m == 0 ? B.h2 : B.h1) * hweightT<O, T>(Nt, s);
@@ -226,9 +226,11 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
         return (size_t)i2 * P + i1;
     };
     const size_t gi = node(s, 0);
-    const T ps0 = Ps[gi], ps1 = Ps[gi + plane];
-    // the neighbour's face adjoint and displacement (interface)
-    T pv0 = T(0), pv1 = T(0), v0 = T(0), v1 = T(0);
+    // the neighbour's node (interface)
+    const T* Pv = nullptr;
+    const T* Uv = nullptr;
+    size_t gv = 0, planev = 0;
+    long long lv = 0;
     if (F.kind == FACE_INTF) {
         const BlockDev& V = adj[F.nbr_block];
         const FaceDev& FV = V.f[F.nbr_face];
@@ -236,13 +238,22 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
         const int sv = F.reversed ? nf - 1 - s : s;
         int j1, j2;
         face_node(V, FV, sv, j1, j2);
-        const size_t gv = (size_t)j2 * V.pitch + j1, planev = (size_t)V.n2 * V.pitch;
-        const T* Pv = reinterpret_cast<const T*>(V.u[pcur]);
-        const T* Uv = reinterpret_cast<const T*>(GV.seg) + (size_t)lvl * GV.lvl_elems;
-        pv0 = Pv[gv];
-        pv1 = Pv[gv + planev];
-        v0 = Uv[gv];
-        v1 = Uv[gv + planev];
+        gv = (size_t)j2 * V.pitch + j1;
+        planev = (size_t)V.n2 * V.pitch;
+        Pv = reinterpret_cast<const T*>(GV.pseg);
+        Uv = reinterpret_cast<const T*>(GV.seg) + GV.lvl_elems;
+        lv = GV.lvl_elems;
+    }
+    for (int l = 0; l < nl; ++l) {
+    const T* __restrict__ Ps = reinterpret_cast<const T*>(G.pseg) + (size_t)l * G.lvl_elems;
+    const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)(l + 1) * G.lvl_elems;
+    const T ps0 = Ps[gi], ps1 = Ps[gi + plane];
+    T pv0 = T(0), pv1 = T(0), v0 = T(0), v1 = T(0);
+    if (F.kind == FACE_INTF) {
+        pv0 = Pv[(size_t)l * lv + gv];
+        pv1 = Pv[(size_t)l * lv + gv + planev];
+        v0 = Uv[(size_t)l * lv + gv];
+        v1 = Uv[(size_t)l * lv + gv + planev];
     }
     if (F.kind != FACE_DISP) {
         // traction weight Theta_J (tau enters with -Theta_J) and the derivatives of u at the node
@@ -299,27 +310,24 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
         g[1] -= k0 * w1 + k1 * w0;
         g[2] -= k1 * w1;
     }
+    }   // levels
 #pragma unroll
     for (int k = 0; k < 7; ++k) out[k * nf + s] = g[k];
 }
 
 // ------------------------------------------------------------------ bulk part of the gradient
-// One node x: dL/dc_p(x) contracted with phi = H psi_n and u_n, for the narrow rows of both
-// directions (planes 0-2 along x1, 3-5 along x2), the mixed terms (planes 6-9), plus the SAT
-// contributions of k_grad_face at face nodes; accumulates dt^2 times that into gc and the density
-// term into grho.
+// One node x and one level n: dL/dc_p(x) contracted with phi = H psi_n and u_n, for the narrow
+// rows of both directions (planes 0-2 along x1, 3-5 along x2) and the mixed terms (planes 6-9),
+// added to acc.
 template <typename T, int O, bool INTERIOR>
-__device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, int pcur, int lvl, double dt2, int i1,
-                                          int i2) {
+__device__ __forceinline__ void grad_level(const BlockDev& B, const T* __restrict__ Ps, const T* __restrict__ U, int i1,
+                                           int i2, T* acc) {
     using PO = Ord<O>;
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const size_t plane = (size_t)n2 * P;
-    const T* __restrict__ Ps = reinterpret_cast<const T*>(B.u[pcur]);
-    const T* __restrict__ U = reinterpret_cast<const T*>(G.seg) + (size_t)lvl * G.lvl_elems;
     const T ih1 = T(B.ih1), ih2 = T(B.ih2);
     auto ps = [&](int L, int j1, int j2) { return __ldg(Ps + (size_t)L * plane + (size_t)j2 * P + j1); };
     auto uu = [&](int L, int j1, int j2) { return __ldg(U + (size_t)L * plane + (size_t)j2 * P + j1); };
-    T acc[10];
     if (INTERIOR) {
         // phi = h1 h2 psi in the interior: edge-pair form of the narrow rows,
         //   dPhi/db(x) = -sum_m sum_k e_{m,k} (phi(j+m) - phi(j)) (u(j+m) - u(j)),  j = x - k
@@ -350,12 +358,12 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
             }
         }
         const T hh = T(B.h1 * B.h2);
-        acc[0] = -hh * ih1 * ih1 * a00;
-        acc[1] = -hh * ih1 * ih1 * a01;
-        acc[2] = -hh * ih1 * ih1 * a11;
-        acc[3] = -hh * ih2 * ih2 * b00;
-        acc[4] = -hh * ih2 * ih2 * b01;
-        acc[5] = -hh * ih2 * ih2 * b11;
+        acc[0] += -hh * ih1 * ih1 * a00;
+        acc[1] += -hh * ih1 * ih1 * a01;
+        acc[2] += -hh * ih1 * ih1 * a11;
+        acc[3] += -hh * ih2 * ih2 * b00;
+        acc[4] += -hh * ih2 * ih2 * b01;
+        acc[5] += -hh * ih2 * ih2 * b11;
         // mixed: D^T = -D on interior rows
         T d1p[2], d2p[2], d1u[2], d2u[2];
 #pragma unroll
@@ -377,7 +385,7 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] = d1p[a] * d2u[b] + d2p[b] * d1u[a];
+            for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] += d1p[a] * d2u[b] + d2p[b] * d1u[a];
     } else {
         const T hh = T(B.h1 * B.h2);
         auto phi = [&](int L, int j1, int j2) {
@@ -386,14 +394,14 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
         T s00, s01, s11;
         narrow_grad_line<O, T>(n1, i1, [&](int L, int j) { return phi(L, j, i2); }, [&](int L, int j) { return uu(L, j, i2); },
                                s00, s01, s11);
-        acc[0] = s00 * ih1 * ih1;
-        acc[1] = s01 * ih1 * ih1;
-        acc[2] = s11 * ih1 * ih1;
+        acc[0] += s00 * ih1 * ih1;
+        acc[1] += s01 * ih1 * ih1;
+        acc[2] += s11 * ih1 * ih1;
         narrow_grad_line<O, T>(n2, i2, [&](int L, int j) { return phi(L, i1, j); }, [&](int L, int j) { return uu(L, i1, j); },
                                s00, s01, s11);
-        acc[3] = s00 * ih2 * ih2;
-        acc[4] = s01 * ih2 * ih2;
-        acc[5] = s11 * ih2 * ih2;
+        acc[3] += s00 * ih2 * ih2;
+        acc[4] += s01 * ih2 * ih2;
+        acc[5] += s11 * ih2 * ih2;
         T d1p[2], d2p[2], d1u[2], d2u[2];
 #pragma unroll
         for (int L = 0; L < 2; ++L) {
@@ -405,8 +413,43 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] = d1p[a] * d2u[b] + d2p[b] * d1u[a];
-        // SAT contributions at face nodes
+            for (int b = 0; b < 2; ++b) acc[6 + 2 * a + b] += d1p[a] * d2u[b] + d2p[b] * d1u[a];
+    }
+}
+
+// One node over the nl levels of a segment: the bulk terms of every level in registers, the SAT
+// terms (summed over the segment by k_grad_face) at face nodes, then gc += dt^2 acc and
+// grho -= H J sum_n psi_n . (u_{n+1} - 2 u_n + u_{n-1}).
+// levels [l0, l1) of one node: bulk terms into acc[0..9], the density sum into acc[10]
+template <typename T, int O, bool INTERIOR>
+__device__ __forceinline__ void grad_levels(const BlockDev& B, const GradDev& G, int l0, int l1, int i1, int i2, T* acc) {
+    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
+    const long long lvl = G.lvl_elems;
+    const T* __restrict__ PS = reinterpret_cast<const T*>(G.pseg);
+    const T* __restrict__ US = reinterpret_cast<const T*>(G.seg);
+    T rho = T(0);
+    T um0 = US[(size_t)l0 * lvl + gi], um1 = US[(size_t)l0 * lvl + gi + plane];              // u_{n-1}
+    T uc0 = US[(size_t)(l0 + 1) * lvl + gi], uc1 = US[(size_t)(l0 + 1) * lvl + gi + plane];  // u_n
+    for (int l = l0; l < l1; ++l) {
+        const T* Ps = PS + (size_t)l * lvl;
+        const T* U = US + (size_t)(l + 1) * lvl;
+        grad_level<T, O, INTERIOR>(B, Ps, U, i1, i2, acc);
+        const T up0 = U[lvl + gi], up1 = U[lvl + gi + plane];
+        rho += Ps[gi] * (up0 - T(2) * uc0 + um0) + Ps[gi + plane] * (up1 - T(2) * uc1 + um1);
+        um0 = uc0;
+        um1 = uc1;
+        uc0 = up0;
+        uc1 = up1;
+    }
+    acc[10] += rho;
+}
+
+// adds the SAT sums at face nodes, then gc += dt^2 acc[0..9], grho -= H J acc[10]
+template <typename T, int O, bool INTERIOR>
+__device__ __forceinline__ void grad_finish(const BlockDev& B, const GradDev& G, double dt2, int i1, int i2, T* acc) {
+    const int n1 = B.n1, n2 = B.n2;
+    const size_t plane = (size_t)n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
+    if (!INTERIOR) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const FaceDev& F = B.f[f];
@@ -424,55 +467,78 @@ __device__ __forceinline__ void grad_node(const BlockDev& B, const GradDev& G, i
             for (int k = 0; k < 4; ++k) acc[6 + k] += gs[(3 + k) * nf + s];
         }
     }
-    const size_t gi = (size_t)i2 * P + i1;
     T* __restrict__ GC = reinterpret_cast<T*>(G.gc);
     const T d2 = T(dt2);
 #pragma unroll
     for (int p = 0; p < 10; ++p) GC[(size_t)p * plane + gi] += d2 * acc[p];
-    // density: -H J psi . (u_{n+1} - 2 u_n + u_{n-1})
-    const T* Up = U + G.lvl_elems;
-    const T* Um = U - G.lvl_elems;
-    T dd = T(0);
-#pragma unroll
-    for (int L = 0; L < 2; ++L) {
-        const size_t q = (size_t)L * plane + gi;
-        dd += Ps[q] * (Up[q] - T(2) * U[q] + Um[q]);
-    }
     T* __restrict__ GR = reinterpret_cast<T*>(G.grho);
-    GR[gi] -= T(B.h1 * B.h2) * hweightT<O, T>(n1, i1) * hweightT<O, T>(n2, i2) * T(B.J[gi]) * dd;
+    GR[gi] -= T(B.h1 * B.h2) * hweightT<O, T>(n1, i1) * hweightT<O, T>(n2, i2) * T(B.J[gi]) * acc[10];
 }
 
 template <typename T, int O>
-__global__ void __launch_bounds__(256) k_grad_interior(BlockDev B, GradDev G, int pcur, int lvl, double dt2) {
+__global__ void __launch_bounds__(256) k_grad_interior(BlockDev B, GradDev G, int nl, double dt2) {
     constexpr int GS = GradCfg<O>::GS;
     const int i1 = GS + blockIdx.x * 32 + threadIdx.x;
     const int i2 = GS + blockIdx.y * 8 + threadIdx.y;
     if (i1 >= B.n1 - GS || i2 >= B.n2 - GS) return;
-    grad_node<T, O, true>(B, G, pcur, lvl, dt2, i1, i2);
+    T acc[11];
+#pragma unroll
+    for (int p = 0; p < 11; ++p) acc[p] = T(0);
+    grad_levels<T, O, true>(B, G, 0, nl, i1, i2, acc);
+    grad_finish<T, O, true>(B, G, dt2, i1, i2, acc);
 }
 
-template <typename T, int O>
-__global__ void __launch_bounds__(256) k_grad_strip(BlockDev B, GradDev G, int pcur, int lvl, double dt2) {
+// strip node t of a block (bands of width GS along every face; side bands column by column so
+// that a warp shares its distance from the face)
+template <int O>
+__device__ __forceinline__ void grad_strip_node(const BlockDev& B, long long t, int& i1, int& i2) {
     constexpr int S = GradCfg<O>::GS;       // every admissible block has n > 2 GS in both directions
     const int n1 = B.n1, n2 = B.n2;
-    const int s1 = S, s2 = S;
-    const long long inner = (long long)(n1 - 2 * s1) * (n2 - 2 * s2);
-    const long long nstrip = (long long)n1 * n2 - inner;
+    const long long top = (long long)S * n1;
+    if (t < top) { i2 = (int)(t / n1); i1 = (int)(t - (long long)i2 * n1); }
+    else if (t < 2 * top) { const long long u = t - top; i2 = n2 - S + (int)(u / n1); i1 = (int)(u - (long long)(i2 - n2 + S) * n1); }
+    else {
+        const long long u = t - 2 * top;
+        const int rows = n2 - 2 * S;
+        const int col = (int)(u / rows), row = (int)(u - (long long)col * rows);
+        i2 = S + row;
+        i1 = col < S ? col : n1 - 2 * S + col;
+    }
+}
+
+// strip nodes, phase 1: level chunk blockIdx.y of nchunk; partial sums to G.part
+template <typename T, int O>
+__global__ void __launch_bounds__(256) k_grad_strip(BlockDev B, GradDev G, int nl, int nchunk, long long nstrip) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nstrip) return;
     int i1, i2;
-    const long long top = (long long)s2 * n1;
-    if (t < top) { i2 = (int)(t / n1); i1 = (int)(t - (long long)i2 * n1); }
-    else if (t < 2 * top) { const long long u = t - top; i2 = n2 - s2 + (int)(u / n1); i1 = (int)(u - (long long)(i2 - n2 + s2) * n1); }
-    else {
-        // side bands column by column: a warp shares its distance from the face
-        const long long u = t - 2 * top;
-        const int rows = n2 - 2 * s2;
-        const int col = (int)(u / rows), row = (int)(u - (long long)col * rows);
-        i2 = s2 + row;
-        i1 = col < s1 ? col : n1 - 2 * s1 + col;
-    }
-    grad_node<T, O, false>(B, G, pcur, lvl, dt2, i1, i2);
+    grad_strip_node<O>(B, t, i1, i2);
+    const int c = blockIdx.y;
+    const int l0 = (int)((long long)nl * c / nchunk), l1 = (int)((long long)nl * (c + 1) / nchunk);
+    T acc[11];
+#pragma unroll
+    for (int p = 0; p < 11; ++p) acc[p] = T(0);
+    grad_levels<T, O, false>(B, G, l0, l1, i1, i2, acc);
+    T* part = reinterpret_cast<T*>(G.part) + (size_t)c * 11 * nstrip;
+#pragma unroll
+    for (int p = 0; p < 11; ++p) part[(size_t)p * nstrip + t] = acc[p];
+}
+
+// strip nodes, phase 2: the chunks in order, the SAT sums, and the accumulator update
+template <typename T, int O>
+__global__ void __launch_bounds__(256) k_grad_strip_sum(BlockDev B, GradDev G, int nchunk, long long nstrip, double dt2) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nstrip) return;
+    int i1, i2;
+    grad_strip_node<O>(B, t, i1, i2);
+    T acc[11];
+#pragma unroll
+    for (int p = 0; p < 11; ++p) acc[p] = T(0);
+    const T* part = reinterpret_cast<const T*>(G.part);
+    for (int c = 0; c < nchunk; ++c)
+#pragma unroll
+        for (int p = 0; p < 11; ++p) acc[p] += part[((size_t)c * 11 + p) * nstrip + t];
+    grad_finish<T, O, false>(B, G, dt2, i1, i2, acc);
 }
 
 // dPhi/dC (pair layout, 10 planes of the upper triangle of M[2I+J][2K+L]) and dPhi/drho as dense

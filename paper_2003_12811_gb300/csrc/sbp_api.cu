@@ -517,13 +517,30 @@ int record_receivers(sbp_handle* h, double* d_row, cudaStream_t st) {
     return SBP_OK;
 }
 
+// strip nodes of the gradient (bands of width gs along every face)
+long long grad_strip_nodes(const HostBlock& hb, int gs) {
+    return (long long)hb.n1 * hb.n2 - (long long)(hb.n1 - 2 * gs) * (hb.n2 - 2 * gs);
+}
+int order_gs(int o) { return o == 2 ? SBP2_GS : (o == 4 ? SBP4_GS : SBP6_GS); }
+// level chunks of the strip gradient: about 4 waves of 256-thread CTAs over the SMs, at most
+// one chunk per level and at most GRAD_MAX_CHUNKS
+constexpr int GRAD_MAX_CHUNKS = 16;
+int grad_strip_chunks(const sbp_handle* h, long long nstrip, int nl) {
+    const long long want = 4LL * h->num_sms * 2048;
+    long long c = (want + nstrip - 1) / std::max(1LL, nstrip);
+    c = std::min<long long>(c, GRAD_MAX_CHUNKS);
+    c = std::min<long long>(c, nl);
+    return (int)std::max(1LL, c);
+}
+
+// gradient contributions of the nl levels of one segment
 template <typename T, int O>
-void launch_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int pc, int lvl, double dt2,
+void launch_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int nl, double dt2,
                  cudaStream_t st) {
     const int total = h->nface_nodes;
     if (total > 0) {
         ProfScope ps(h, 6, st, 1);
-        k_grad_face<T, O><<<grid_for(total, 128), 128, 0, st>>>(h->d_blocks_adj, d_grad, h->d_refs, h->nrefs, total, pc, lvl, h->beta);
+        k_grad_face<T, O><<<grid_for(total, 128), 128, 0, st>>>(h->d_blocks_adj, d_grad, h->d_refs, h->nrefs, total, nl, h->beta);
     }
     constexpr int GS = GradCfg<O>::GS;
     for (size_t b = 0; b < h->blocks.size(); ++b) {
@@ -532,26 +549,28 @@ void launch_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev
         {
             ProfScope ps(h, 4, st, 1);
             dim3 gi((hb.n1 - 2 * GS + 31) / 32, (hb.n2 - 2 * GS + 7) / 8);
-            k_grad_interior<T, O><<<gi, dim3(32, 8), 0, st>>>(v, grads[b], pc, lvl, dt2);
+            k_grad_interior<T, O><<<gi, dim3(32, 8), 0, st>>>(v, grads[b], nl, dt2);
         }
         {
-            ProfScope ps(h, 5, st, 1);
-            const long long nstrip = (long long)hb.n1 * hb.n2 - (long long)(hb.n1 - 2 * GS) * (hb.n2 - 2 * GS);
-            k_grad_strip<T, O><<<grid_for(nstrip), 256, 0, st>>>(v, grads[b], pc, lvl, dt2);
+            ProfScope ps(h, 5, st, 2);
+            const long long nstrip = grad_strip_nodes(hb, GS);
+            const int nchunk = grad_strip_chunks(h, nstrip, nl);
+            k_grad_strip<T, O><<<dim3(grid_for(nstrip), nchunk), 256, 0, st>>>(v, grads[b], nl, nchunk, nstrip);
+            k_grad_strip_sum<T, O><<<grid_for(nstrip), 256, 0, st>>>(v, grads[b], nchunk, nstrip, dt2);
         }
     }
 }
 
-void run_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int pc, int lvl, double dt2,
+void run_grad(sbp_handle* h, const GradDev* d_grad, const std::vector<GradDev>& grads, int nl, double dt2,
               cudaStream_t st) {
     if (h->precision == SBP_FP64) {
-        if (h->order == 2) launch_grad<double, 2>(h, d_grad, grads, pc, lvl, dt2, st);
-        else if (h->order == 4) launch_grad<double, 4>(h, d_grad, grads, pc, lvl, dt2, st);
-        else launch_grad<double, 6>(h, d_grad, grads, pc, lvl, dt2, st);
+        if (h->order == 2) launch_grad<double, 2>(h, d_grad, grads, nl, dt2, st);
+        else if (h->order == 4) launch_grad<double, 4>(h, d_grad, grads, nl, dt2, st);
+        else launch_grad<double, 6>(h, d_grad, grads, nl, dt2, st);
     } else {
-        if (h->order == 2) launch_grad<float, 2>(h, d_grad, grads, pc, lvl, dt2, st);
-        else if (h->order == 4) launch_grad<float, 4>(h, d_grad, grads, pc, lvl, dt2, st);
-        else launch_grad<float, 6>(h, d_grad, grads, pc, lvl, dt2, st);
+        if (h->order == 2) launch_grad<float, 2>(h, d_grad, grads, nl, dt2, st);
+        else if (h->order == 4) launch_grad<float, 4>(h, d_grad, grads, nl, dt2, st);
+        else launch_grad<float, 6>(h, d_grad, grads, nl, dt2, st);
     }
 }
 
@@ -1372,7 +1391,7 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     const size_t per = 2 * h->recs.size();
     const int nb = (int)h->blocks.size();
     GradScratch sc(h);
-    std::vector<void*> ck(nb), seg(nb), fin(nb);
+    std::vector<void*> ck(nb), seg(nb), pseg(nb), fin(nb);
     std::vector<size_t> lvl_bytes(nb);
     std::vector<GradDev> grads(nb);
     for (int b = 0; b < nb; ++b) {
@@ -1381,14 +1400,17 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
         lvl_bytes[b] = 2 * plane * es;
         ck[b] = sc.get((size_t)nseg * 2 * lvl_bytes[b]);
         seg[b] = sc.get((size_t)(K + 2) * lvl_bytes[b]);
+        pseg[b] = sc.get((size_t)K * lvl_bytes[b]);
         fin[b] = sc.get(2 * lvl_bytes[b]);
         GradDev& G = grads[b];
         G.seg = seg[b];
+        G.pseg = pseg[b];
         G.lvl_elems = (long long)(2 * plane);
         G.gc = sc.get(10 * plane * es);
         G.grho = sc.get(plane * es);
         for (int f = 0; f < 4; ++f) G.gsat[f] = sc.get(7 * (size_t)hb.f[f].nf * es);
-        if (!ck[b] || !seg[b] || !fin[b] || !G.gc || !G.grho || !G.gsat[0] || !G.gsat[1] || !G.gsat[2] || !G.gsat[3])
+        G.part = sc.get((size_t)GRAD_MAX_CHUNKS * 11 * grad_strip_nodes(hb, order_gs(h->order)) * es);
+        if (!ck[b] || !seg[b] || !pseg[b] || !fin[b] || !G.part || !G.gc || !G.grho || !G.gsat[0] || !G.gsat[1] || !G.gsat[2] || !G.gsat[3])
             return h->fail(SBP_E_OOM, "misfit-gradient workspace (checkpoints every " + std::to_string(K) + " steps)");
     }
     GradDev* d_grad = (GradDev*)sc.get(sizeof(GradDev) * nb);
@@ -1477,8 +1499,13 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
                 else
                     k_inject<float><<<grid_for(nr, 128), 128, 0, st>>>(h->d_blocks_adj, h->d_recs, nr, pc, d_res + (size_t)q * per, dt);
             }
-            run_grad(h, d_grad, grads, pc, q - a0 + 1, dt * dt, st);
+            // keep psi_n for the segment's gradient pass
+            for (int b = 0; b < nb; ++b)
+                if (!copy(lvl_ptr(pseg, b, (size_t)(q - a0)), h->blocks[b].psi[pc], lvl_bytes[b]))
+                    return h->fail(SBP_E_CUDA, "adjoint level copy");
         }
+        // the gradient terms of the whole segment: psi level l pairs with forward level l + 1
+        run_grad(h, d_grad, grads, a1 - a0 + 1, dt * dt, st);
     }
     rc = check_cuda(h, "misfit gradient");
     if (rc != SBP_OK) return rc;

@@ -107,11 +107,14 @@ def test_gradient_fp32_close_to_oracle(order):
     assert e <= 2e-3, e
 
 
-@pytest.mark.parametrize("prec", ("fp64", "fp32"))
-def test_checkpoint_interval_invariance_and_final_state(prec):
+@pytest.mark.parametrize("prec,tol", (("fp64", 1e-12), ("fp32", 1e-5)))
+def test_checkpoint_interval_invariance_and_final_state(prec, tol):
+    """The recomputed levels are bitwise those of the forward pass, so the checkpoint interval only
+    changes how the gradient terms are grouped into per-segment sums (rounding); a repeated call is
+    bitwise identical; the state left behind is the one sbp_step leaves."""
     P, u0, dt, rec, obs = _setup(6)
     res = []
-    for K in (1, 6, 0, NSTEPS):
+    for K in (1, 6, 0, NSTEPS, 6):
         S = _solver(P, prec, u0, rec)
         res.append(S.sbp_misfit_gradient(NSTEPS, dt, obs, checkpoint_every=K))
         st = S.state()
@@ -123,9 +126,12 @@ def test_checkpoint_interval_invariance_and_final_state(prec):
         for x, y in zip(st[0] + st[1], ref[0] + ref[1]):
             assert np.array_equal(x, y)
     for phi, gr, gc in res[1:]:
-        assert phi == res[0][0]
+        assert phi == res[0][0]                      # the misfit does not depend on the segments
         for b in range(2):
-            assert np.array_equal(gr[b], res[0][1][b]) and np.array_equal(gc[b], res[0][2][b])
+            for got, want in ((gr[b], res[0][1][b]), (gc[b], res[0][2][b])):
+                assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+    for x, y in zip(res[1][1] + res[1][2], res[4][1] + res[4][2]):   # same interval twice: bitwise
+        assert np.array_equal(x, y)
 
 
 def test_gradient_rejects_displacement_data():
