@@ -291,6 +291,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true", help="print the misfit-gradient measurement alone")
+    ap.add_argument("--adjoint-steps", type=int, default=2000, help="leapfrog steps of the misfit-gradient workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -314,7 +315,7 @@ def main():
 
     prec = args.precision
     if args.adjoint_only:
-        print(json.dumps(adjoint_bench(prec=prec)), flush=True)
+        print(json.dumps(adjoint_bench(nsteps=args.adjoint_steps, prec=prec)), flush=True)
         return 0
     P = W.config3(n1=args.n1, n2=args.n2)
     S = Solver(P, prec)
@@ -401,7 +402,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_bench()
     if rank == 0 and world == 1 and not args.no_adjoint:
-        line["adjoint"] = adjoint_bench(prec=prec)
+        line["adjoint"] = adjoint_bench(nsteps=args.adjoint_steps, prec=prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

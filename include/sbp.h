@@ -170,8 +170,9 @@ int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out);
 
 /* Kernel timing for benchmarks.  sbp_profile(h, 1) resets the counters and, until
  * sbp_profile(h, 0), makes every kernel launch record CUDA events (on the launch stream)
- * around its family: [0] interior stencil, [1] boundary strips (closures + SATs), [2] face
- * traces and SAT terms, [3] point sources, [4] gradient interior, [5] gradient strips,
+ * around its family: [0] interior stencil, [1] boundary strips (closures, and the SAT terms,
+ * which the strip kernel forms itself), [2] reserved (no kernel), [3] point sources,
+ * [4] gradient interior, [5] gradient strips,
  * [6] gradient face terms, receiver recording and adjoint injection, [7] misfit reduction and
  * gradient output.  sbp_profile_read returns the accumulated milliseconds per family
  * (ms[SBP_PROF_FAMILIES], needs profiling on) and the number of kernel launches per family since
@@ -189,7 +190,7 @@ int sbp_profile_read(sbp_handle* h, double* ms, long long* launches);
  *          block in order, 2 planes (component 1, component 2) of n2 rows x pitch elements,
  *          pitch = n1 rounded up to a multiple of 32, elements in the handle's precision
  *          (double for SBP_FP64, float for SBP_FP32); blocks follow each other without gaps.
- * The per-face traces and SAT terms and the device copies of the block tables live in one
+ * The per-face SAT terms and the device copies of the block tables live in one
  * fixed 8 MiB file-scope device array shared by every call; grids needing more scratch are
  * rejected with SBP_E_INVALID_ARG before any device work.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) -- make that first call before any stream

@@ -216,7 +216,7 @@ __global__ void k_grad_face(const BlockDev* __restrict__ adj, const GradDev* __r
     const int Nm = m == 0 ? n1 : n2, Nt = m == 0 ? n2 : n1;
     const size_t plane = (size_t)n2 * P;
     const T nu = T(F.nu);
-    const T ihm = T(m == 0 ? B.ih1 : B.ih2), iht = T(m == 0 ? B.ih2 : B.ih1);
+    const T ihm = (m == 0 ? ih1T<T>(B) : ih2T<T>(B)), iht = (m == 0 ? ih2T<T>(B) : ih1T<T>(B));
     const T Ht = T(m == 0 ? B.h2 : B.h1) * hweightT<O, T>(Nt, s);
     // node at tangential index sp and depth d from the face
     auto node = [&](int sp, int d) -> size_t {
@@ -325,7 +325,7 @@ __device__ __forceinline__ void grad_level(const BlockDev& B, const T* __restric
     using PO = Ord<O>;
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const size_t plane = (size_t)n2 * P;
-    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
+    const T ih1 = ih1T<T>(B), ih2 = ih2T<T>(B);
     auto ps = [&](int L, int j1, int j2) { return __ldg(Ps + (size_t)L * plane + (size_t)j2 * P + j1); };
     auto uu = [&](int L, int j1, int j2) { return __ldg(U + (size_t)L * plane + (size_t)j2 * P + j1); };
     if (INTERIOR) {

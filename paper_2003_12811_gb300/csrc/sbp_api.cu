@@ -37,7 +37,6 @@ struct HostFace {
     double* jhat = nullptr;
     void* ju = nullptr;
     void* g = nullptr;
-    void* tr = nullptr;
     void* sat = nullptr;
 };
 
@@ -193,6 +192,8 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
     b.h2 = hb.h2;
     b.ih1 = 1.0 / hb.h1;
     b.ih2 = 1.0 / hb.h2;
+    b.ih1f = (float)b.ih1;
+    b.ih2f = (float)b.ih2;
     b.u[0] = hb.u[0];
     b.u[1] = hb.u[1];
     b.c = hb.c;
@@ -222,11 +223,11 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
         for (int d = 0; d < 12; ++d) {
             const double dq0 = d < order_ncol(h->order) ? order_dq0(h->order, d) : 0.0;
             D.fac[d] = ((f % 2) ? -dq0 : dq0) / (hm * hm * host_hweight(h->order, Nm, (f % 2) ? Nm - 1 - d : d));
+            D.facf[d] = (float)D.fac[d];
         }
         D.jhat = F.jhat;
         D.ju = F.ju;
         D.g = F.g;
-        D.tr = F.tr;
         D.sat = F.sat;
     }
     return b;
@@ -286,13 +287,7 @@ template <int O> int tma_rows() { return TmaTile<O>::SY; }
 // on the adjoint fields (the same kernels; the sources are skipped)
 template <typename T, int O>
 int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj) {
-    const int total = h->nface_nodes;
     const BlockDev* tab = adj ? h->d_blocks_adj : h->d_blocks;
-    if (total > 0) {
-        ProfScope ps(h, 2, st, 2);
-        k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(tab, h->d_refs, h->nrefs, total, a.cur);
-        k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(tab, h->d_refs, h->nrefs, total, a, h->beta);
-    }
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
     for (auto& hb : h->blocks) {
         BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
@@ -325,8 +320,8 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
             using ST = StripTile<O>;
             const int ntile = 2 * ((hb.n1 + 31) / 32) + 2 * ((hb.n2 - 2 * ST::S + 31) / 32);
             constexpr size_t ssm = (size_t)ST::ELEMS * sizeof(T);
-            if (mode == 0) k_strip_tile<T, O, 0><<<ntile, ST::THREADS, ssm, st>>>(b, a);
-            else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, st>>>(b, a);
+            if (mode == 0) k_strip_tile<T, O, 0><<<ntile, ST::THREADS, ssm, st>>>(b, tab, a, h->beta);
+            else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, st>>>(b, tab, a, h->beta);
         }
     }
     if (!adj && !h->src_nodes.empty()) {
@@ -409,7 +404,7 @@ bool all_materials(const sbp_handle* h) {
 // Fixed scratch for sbp_apply_noalloc.  Callers that cannot allocate device memory (for example
 // code running inside a memory pool it may not grow, or a real-time loop where cudaMalloc's
 // implicit synchronisation is not allowed) get the operator application with every temporary --
-// the per-face trace and SAT arrays and the device copies of the block/face tables -- placed in
+// the per-face SAT arrays and the device copies of the block/face tables -- placed in
 // this file-scope array.  Every GPU that loads the library holds it until the process exits.
 constexpr size_t NOALLOC_SCRATCH_BYTES = 8u << 20;   // 8 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -444,10 +439,7 @@ template <typename T, int O>
 void launch_noalloc(sbp_handle* h, const BlockDev* views, int nviews, BlockDev* d_views, FaceRef* d_refs,
                     const StepArgs& a, cudaStream_t st) {
     const int total = h->nface_nodes;
-    if (total > 0) {
-        k_face_trace<T, O><<<grid_for(total), 256, 0, st>>>(d_views, d_refs, h->nrefs, total, a.cur);
-        k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(d_views, d_refs, h->nrefs, total, a, h->beta);
-    }
+    if (total > 0) k_face_sat<T, O><<<grid_for(total), 256, 0, st>>>(d_views, d_refs, h->nrefs, total, a, h->beta);
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
     for (int b = 0; b < nviews; ++b) {
         const BlockDev& v = views[b];
@@ -499,6 +491,7 @@ int step_once(sbp_handle* h, double dt, cudaStream_t st) {
     StepArgs a{};
     a.with_data = 1;
     a.dt2 = dt * dt;
+    a.dt2f = (float)a.dt2;
     a.cur = h->cur;
     a.t = h->t;
     fill_basis(h, h->t, a);
@@ -689,9 +682,8 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             F.reversed = bd.faces[f].reversed ? 1 : 0;
             F.nf = f < 2 ? hb.n2 : hb.n1;
             F.jhat = (double*)h->dalloc(F.nf * sizeof(double));
-            F.tr = h->dalloc(4 * (size_t)F.nf * es);
             F.sat = h->dalloc(4 * (size_t)F.nf * es);
-            if (!F.jhat || !F.tr || !F.sat) return cleanup(SBP_E_OOM, "face buffers");
+            if (!F.jhat || !F.sat) return cleanup(SBP_E_OOM, "face buffers");
             refs.push_back(FaceRef{b, f, start, F.nf});
             start += F.nf;
         }
@@ -933,6 +925,7 @@ int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream) {
     StepArgs a{};
     a.with_data = 1;
     a.dt2 = dt * dt;
+    a.dt2f = (float)a.dt2;
     for (int n = 0; n < nsteps; ++n) {
         a.cur = h->cur;
         a.t = h->t;
@@ -1068,10 +1061,10 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
     const int nb = (int)h->blocks.size();
     if (nb > NOALLOC_MAX_BLOCKS) return h->fail(SBP_E_INVALID_ARG, "sbp_apply_noalloc supports at most 32 blocks");
     const size_t es = h->esize;
-    // scratch layout: block views | face refs | per face: trace (4 x nf) and SAT (4 x nf) arrays
+    // scratch layout: block views | face refs | per face: SAT (4 x nf) array
     size_t need = align256(sizeof(BlockDev) * nb) + align256(sizeof(FaceRef) * h->nrefs);
     for (auto& hb : h->blocks)
-        for (auto& F : hb.f) need += 2 * align256(4 * (size_t)F.nf * es);
+        for (auto& F : hb.f) need += align256(4 * (size_t)F.nf * es);
     if (need > NOALLOC_SCRATCH_BYTES)
         return h->fail(SBP_E_INVALID_ARG, "grid needs more scratch than the fixed 8 MiB of sbp_apply_noalloc");
     unsigned char* base = nullptr;
@@ -1097,8 +1090,6 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
         uoff += planes2;
         for (int f = 0; f < 4; ++f) {
             const size_t fb = align256(4 * (size_t)hb.f[f].nf * es);
-            v.f[f].tr = base + off;
-            off += fb;
             v.f[f].sat = base + off;
             off += fb;
             refs[nr++] = FaceRef{b, f, start, hb.f[f].nf};
@@ -1166,6 +1157,7 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
             StepArgs a{};
             a.with_data = 1;
             a.dt2 = dt * dt;
+    a.dt2f = (float)a.dt2;
             a.cur = (h->cur + n) & 1;
             a.tstep = n;
             a.tdev = h->d_time;
@@ -1204,7 +1196,6 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         const int nb = (int)h->blocks.size();
         h->launches[0] += (long long)nsteps * nb;
         h->launches[1] += (long long)nsteps * nb;
-        if (h->nface_nodes > 0) h->launches[2] += 2LL * nsteps;
         if (!h->src_nodes.empty()) h->launches[3] += nsteps;
     }
     h->t = tt;
@@ -1227,7 +1218,7 @@ int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out) {
         total += al(2 * plane * 8) + al(4 * plane * 8) + al(plane * 8);
         for (int f = 0; f < 4; ++f) {
             const long long nf = f < 2 ? bd.n2 : bd.n1;
-            total += al(nf * 8) + 2 * al(4 * nf * es) + al(3 * nf * es) + al(2 * 8 * nf * es);
+            total += al(nf * 8) + al(4 * nf * es) + al(3 * nf * es) + al(2 * 8 * nf * es);
         }
     }
     total += 4096;   // block views, face tables, source tables
@@ -1467,6 +1458,7 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     StepArgs aa{};
     aa.with_data = 0;
     aa.dt2 = dt * dt;
+    aa.dt2f = (float)aa.dt2;
     const int nr = (int)h->recs.size();
     for (int s = nseg - 1; s >= 0; --s) {
         const int a0 = s * K, a1 = std::min(a0 + K, nsteps) - 1;   // 0-based steps of the segment

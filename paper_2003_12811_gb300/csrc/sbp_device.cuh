@@ -194,17 +194,18 @@ struct FaceDev {
     double nu, hm0;           // outward reference normal component, H_m[0] (includes h_m)
     double inv_h0;            // 1 / H_m[0]
     double fac[12];           // D_m[face row][i_m] / H_m[i_m] / h_m at depth d = |i_m - face| < NCOL
+    float facf[12];           // the same in FP32
     const double* jhat;       // surface scale factor per face node
     const void* ju;           // robin: J^ U (3 x nf), type T
     const void* g;            // data: displacement g (2 x K x nf) or robin J^ g, type T
-    void* tr;                 // scratch: u1, u2, J^ tau1, J^ tau2 (4 x nf), type T
-    void* sat;                // scratch: face term (2 x nf), normal-spread amplitude (2 x nf), type T
+    void* sat;                // scratch of k_face_sat: face term (2 x nf), normal-spread amplitude (2 x nf), type T
 };
 
 struct BlockDev {
     int n1, n2, pitch, strip;  // strip = width of the boundary strips handled by k_boundary
     double h1, h2;
     double ih1, ih2;          // 1 / h1, 1 / h2
+    float ih1f, ih2f;         // the same in FP32 (read directly as constant operands by FP32 kernels)
     void* u[2];               // state buffers, 2 planes each
     const void* c;            // 10 planes
     const void* w;            // 1/(rho J)
@@ -226,6 +227,22 @@ struct StepArgs {
     double Tk[8];             // basis values T_k(t)
     const double* tdev;       // graph mode: device array of the times of the captured steps (else null)
     double dt;                // step size
+    float dt2f;               // dt^2 in FP32
 };
+
+// the per-block and per-face step constants in the arithmetic type T (FP32 kernels read the FP32
+// copies, which need no conversion)
+template <typename T> __device__ __forceinline__ T ih1T(const BlockDev& B) {
+    if constexpr (sizeof(T) == 4) return B.ih1f; else return B.ih1;
+}
+template <typename T> __device__ __forceinline__ T ih2T(const BlockDev& B) {
+    if constexpr (sizeof(T) == 4) return B.ih2f; else return B.ih2;
+}
+template <typename T> __device__ __forceinline__ T facT(const FaceDev& F, int d) {
+    if constexpr (sizeof(T) == 4) return F.facf[d]; else return F.fac[d];
+}
+template <typename T> __device__ __forceinline__ T dt2T(const StepArgs& a) {
+    if constexpr (sizeof(T) == 4) return a.dt2f; else return a.dt2;
+}
 
 }  // namespace sbp

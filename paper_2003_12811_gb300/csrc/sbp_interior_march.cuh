@@ -102,8 +102,8 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
 
     float ak[Q];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) ak[k] = (float)Ord<O>::a(k);
-    const float ih1 = (float)B.ih1, ih2 = (float)B.ih2;
+    for (int k = 0; k < Q; ++k) ak[k] = Ord<O>::template aT<float>(k);
+    const float ih1 = B.ih1f, ih2 = B.ih2f;
     const float ih11 = ih1 * ih1, ih22 = ih2 * ih2;
 
     // register queues, index 0 = oldest row
@@ -299,7 +299,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         }
         if (MODE == 0) {
             float* __restrict__ Un = reinterpret_cast<float*>(B.u[1 - a.cur]);
-            const float dt2 = (float)a.dt2;
+            const float dt2 = a.dt2f;
             Un[gi] = 2.f * uc0 - u0_c + dt2 * w_c * r0;
             Un[gi + plane] = 2.f * uc1 - u1_c + dt2 * w_c * r1;
         } else {

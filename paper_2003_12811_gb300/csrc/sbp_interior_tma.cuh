@@ -129,11 +129,11 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
     if (tile >= ntiles) return;
     if (threadIdx.x == 0) issue(tile, 0, true);
 
-    const float ih1 = (float)B.ih1, ih2 = (float)B.ih2;
+    const float ih1 = B.ih1f, ih2 = B.ih2f;
     const float ih11 = ih1 * ih1, ih22 = ih2 * ih2;
     float ak[Q];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) ak[k] = (float)Ord<O>::a(k);
+    for (int k = 0; k < Q; ++k) ak[k] = Ord<O>::template aT<float>(k);
 
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
         const int s = it & 1;
@@ -319,7 +319,7 @@ k_interior_tma(const __grid_constant__ TmaMaps maps, BlockDev B, StepArgs a, int
             }
             if (MODE == 0) {
                 float* __restrict__ Un = reinterpret_cast<float*>(B.u[1 - a.cur]);
-                const float dt2 = (float)a.dt2;
+                const float dt2 = a.dt2f;
                 Un[gi] = 2.f * uc0 - up0[k] + dt2 * wv[k] * r0;
                 Un[gi + plane] = 2.f * uc1 - up1[k] + dt2 * wv[k] * r1;
             } else {

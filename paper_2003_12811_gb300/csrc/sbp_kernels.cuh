@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
     for (int f = 0; f < 4; ++f) load(smx + f * SY * SX, C + (6 + f) * plane, SY, SX, y0 - Q, x0 - Q);
     __syncthreads();
 
-    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
+    const T ih1 = ih1T<T>(B), ih2 = ih2T<T>(B);
     // mixed fluxes g1_j = c_1j2l D_2 u_l on tile rows x (tile cols + x-halo)
     for (int idx = tid; idx < TY * SX; idx += ITHREADS) {
         const int r = idx / SX, c = idx - r * SX;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
         }
         if (MODE == 0) {
             T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
-            const T wv = Wp[gi], dt2 = T(a.dt2);
+            const T wv = Wp[gi], dt2 = dt2T<T>(a);
             Un[gi] = T(2) * uc0 - Un[gi] + dt2 * wv * r0;
             Un[gi + plane] = T(2) * uc1 - Un[gi + plane] + dt2 * wv * r1;
         } else {
@@ -189,6 +189,211 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
             R[gi + plane] = r1;
         }
     }
+}
+
+// ============================================================================ faces
+struct FaceRef {
+    int block, face, start, nf;
+};
+
+__device__ __forceinline__ int find_face(const FaceRef* refs, int nrefs, int t) {
+    int k = 0;
+    while (k + 1 < nrefs && t >= refs[k + 1].start) ++k;
+    return k;
+}
+
+// c planes at a face node: narrow of the normal direction m (c_mJmL) and the mixed c_mJtL
+__device__ __forceinline__ int plane_nn(int m, int J, int L) { return 3 * m + J + L; }
+__device__ __forceinline__ int plane_nt(int m, int J, int L) { return m == 0 ? 6 + 2 * J + L : 6 + 2 * L + J; }
+
+// node (j1, j2) of face F at tangential index sp and depth d
+__device__ __forceinline__ void face_at(const BlockDev& B, const FaceDev& F, int sp, int d, int& j1, int& j2) {
+    if (F.m == 0) { j1 = F.side ? B.n1 - 1 - d : d; j2 = sp; }
+    else { j2 = F.side ? B.n2 - 1 - d : d; j1 = sp; }
+}
+
+// J^ tau_J = nu_i c_iJkL D_k u_L at face node s (eq. n-C_conversion); u(L, j1, j2), c(pl, j1, j2)
+template <typename T, int O, class UA, class CA>
+__device__ __forceinline__ void face_traction(const BlockDev& B, const FaceDev& F, int s, UA u, CA c, T& t0, T& t1) {
+    const int m = F.m, Nm = m == 0 ? B.n1 : B.n2, Nt = m == 0 ? B.n2 : B.n1;
+    const T ihm = (m == 0 ? ih1T<T>(B) : ih2T<T>(B)), iht = (m == 0 ? ih2T<T>(B) : ih1T<T>(B));
+    T dn[2], dt[2];
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+        dn[L] = dsum<O, T>(Nm, F.side ? Nm - 1 : 0, [&](int j) {
+                    int j1, j2;
+                    face_at(B, F, s, F.side ? Nm - 1 - j : j, j1, j2);
+                    return u(L, j1, j2);
+                }) * ihm;
+        dt[L] = dsum<O, T>(Nt, s, [&](int j) {
+                    int j1, j2;
+                    face_at(B, F, j, 0, j1, j2);
+                    return u(L, j1, j2);
+                }) * iht;
+    }
+    int i1, i2;
+    face_at(B, F, s, 0, i1, i2);
+    const T nu = T(F.nu);
+    t0 = nu * (c(plane_nn(m, 0, 0), i1, i2) * dn[0] + c(plane_nn(m, 0, 1), i1, i2) * dn[1] +
+               c(plane_nt(m, 0, 0), i1, i2) * dt[0] + c(plane_nt(m, 0, 1), i1, i2) * dt[1]);
+    t1 = nu * (c(plane_nn(m, 1, 0), i1, i2) * dn[0] + c(plane_nn(m, 1, 1), i1, i2) * dn[1] +
+               c(plane_nt(m, 1, 0), i1, i2) * dt[0] + c(plane_nt(m, 1, 1), i1, i2) * dt[1]);
+}
+
+// SAT terms of face node s of face F of block B (Sec. 5.1 eq. sat_traction, Sec. 5.2 eq.
+// dirichlet_ansatz with Z of Theorem 3, Sec. 6 eq. scheme_interface with V = Theta = 0), using
+// J^ Z_JL = beta d / h1 * c_mJmL (boundary) and beta d / 4 (c^u_mJmL / h1^u + c^v / h1^v) (interface):
+//   Fs_J: the term added at the face node itself,
+//   As_J: the amplitude a_J = half nu c_mJmL w_L spread by D_m^T into the first NCOL nodes along
+//         the normal (times F.fac[d]).
+// u(L, j1, j2), c(pl, j1, j2) read this block's current level and coefficients; the interface
+// neighbour is read from `blocks` (its current level in the same buffer parity a.cur).
+template <typename T, int O, class UA, class CA>
+__device__ void face_sat_node(const BlockDev* __restrict__ blocks, const BlockDev& B, const FaceDev& F, int s,
+                              const StepArgs& a, double beta, UA u, CA c, T& Fs0, T& Fs1, T& As0, T& As1) {
+    const int m = F.m, nf = F.nf;
+    const T nu = T(F.nu);
+    const T inv_h0 = T(F.inv_h0);
+    int i1, i2;
+    face_at(B, F, s, 0, i1, i2);
+    const bool has_data = a.with_data && F.g;
+    const T* __restrict__ g = reinterpret_cast<const T*>(F.g);
+    if (F.kind == FACE_ROBIN) {
+        T f0, f1;
+        face_traction<T, O>(B, F, s, u, c, f0, f1);
+        const T u0 = u(0, i1, i2), u1 = u(1, i1, i2);
+        if (F.ju) {
+            const T* ju = reinterpret_cast<const T*>(F.ju);
+            const T a11 = ju[s], a12 = ju[nf + s], a22 = ju[2 * nf + s];
+            f0 += a11 * u0 + a12 * u1;
+            f1 += a12 * u0 + a22 * u1;
+        }
+        if (has_data) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k >= a.K) break;
+                f0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
+                f1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
+            }
+        }
+        Fs0 = -inv_h0 * f0;
+        Fs1 = -inv_h0 * f1;
+        As0 = As1 = T(0);
+        return;
+    }
+    const bool intf = F.kind == FACE_INTF;
+    // the neighbour across an interface: its block, face, current level and coefficients
+    const BlockDev* V = intf ? &blocks[F.nbr_block] : nullptr;
+    const FaceDev* FV = intf ? &V->f[F.nbr_face] : nullptr;
+    const T* __restrict__ Uv = intf ? reinterpret_cast<const T*>(V->u[a.cur]) : nullptr;
+    const T* __restrict__ Cv = intf ? reinterpret_cast<const T*>(V->c) : nullptr;
+    const size_t pv = intf ? (size_t)V->n2 * V->pitch : 0;
+    auto uv = [&](int L, int j1, int j2) { return Uv[(size_t)L * pv + (size_t)j2 * V->pitch + j1]; };
+    auto cv = [&](int pl, int j1, int j2) { return Cv[(size_t)pl * pv + (size_t)j2 * V->pitch + j1]; };
+    // jump w_L at face node sp (displacement: u - g(t); interface: u - v)
+    auto jump = [&](int sp, T& w0, T& w1) {
+        int j1, j2;
+        face_at(B, F, sp, 0, j1, j2);
+        w0 = u(0, j1, j2);
+        w1 = u(1, j1, j2);
+        if (intf) {
+            int v1, v2;
+            face_at(*V, *FV, F.reversed ? nf - 1 - sp : sp, 0, v1, v2);
+            w0 -= uv(0, v1, v2);
+            w1 -= uv(1, v1, v2);
+        } else if (has_data) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k >= a.K) break;
+                w0 -= T(a.Tk[k]) * g[(size_t)k * nf + sp];
+                w1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + sp];
+            }
+        }
+    };
+    const T half = intf ? T(0.5) : T(1);
+    const double dd = 2.0;   // spatial dimension d
+    T w0, w1;
+    jump(s, w0, w1);
+    const T c00 = c(plane_nn(m, 0, 0), i1, i2), c01 = c(plane_nn(m, 0, 1), i1, i2), c11 = c(plane_nn(m, 1, 1), i1, i2);
+    T z00, z01, z11;
+    if (!intf) {
+        const T k = T(beta * dd * F.inv_h0);
+        z00 = k * c00; z01 = k * c01; z11 = k * c11;
+    } else {
+        const int sv = F.reversed ? nf - 1 - s : s;
+        int v1, v2;
+        face_at(*V, *FV, sv, 0, v1, v2);
+        const int mv = FV->m;
+        const T ku = T(beta * dd / 4.0 * F.inv_h0), kv = T(beta * dd / 4.0 * FV->inv_h0);
+        z00 = ku * c00 + kv * cv(plane_nn(mv, 0, 0), v1, v2);
+        z01 = ku * c01 + kv * cv(plane_nn(mv, 0, 1), v1, v2);
+        z11 = ku * c11 + kv * cv(plane_nn(mv, 1, 1), v1, v2);
+    }
+    // normal-spread amplitude a_J = half nu c_mJmL w_L
+    As0 = half * nu * (c00 * w0 + c01 * w1);
+    As1 = half * nu * (c01 * w0 + c11 * w1);
+    // tangential transpose term (1/H_t(s)) sum_s' D_t[s'][s] H_t(s') b_J(s'),  b_J = nu c_mLtJ w_L;
+    // rows of D with a non-zero in column s: the interior band s-Q..s+Q plus, near an end, every
+    // boundary row (boundary rows span columns 0..NCOL-1, which can reach past s+Q)
+    const int Nt = nf;
+    int lo = s - Ord<O>::Q, hi = s + Ord<O>::Q;
+    if (s < Ord<O>::NCOL) { lo = 0; hi = max(hi, Ord<O>::NB - 1); }
+    if (s >= Nt - Ord<O>::NCOL) { hi = Nt - 1; lo = min(lo, Nt - Ord<O>::NB); }
+    if (lo < 0) lo = 0;
+    if (hi > Nt - 1) hi = Nt - 1;
+    T tt0 = T(0), tt1 = T(0);
+    for (int sp = lo; sp <= hi; ++sp) {
+        const T dc = dcoefT<O, T>(Nt, sp, s);
+        if (dc == T(0)) continue;
+        T v0, v1;
+        jump(sp, v0, v1);
+        int j1, j2;
+        face_at(B, F, sp, 0, j1, j2);
+        const T b0 = nu * (c(plane_nt(m, 0, 0), j1, j2) * v0 + c(plane_nt(m, 1, 0), j1, j2) * v1);
+        const T b1 = nu * (c(plane_nt(m, 0, 1), j1, j2) * v0 + c(plane_nt(m, 1, 1), j1, j2) * v1);
+        const T wgt = dc * hweightT<O, T>(Nt, sp);
+        tt0 += wgt * b0;
+        tt1 += wgt * b1;
+    }
+    const T tfac = (m == 0 ? ih2T<T>(B) : ih1T<T>(B)) / hweightT<O, T>(Nt, s);
+    T f0 = half * tt0 * tfac - (z00 * w0 + z01 * w1);
+    T f1 = half * tt1 * tfac - (z01 * w0 + z11 * w1);
+    if (intf) {
+        T tu0, tu1, tv0, tv1;
+        face_traction<T, O>(B, F, s, u, c, tu0, tu1);
+        face_traction<T, O>(*V, *FV, F.reversed ? nf - 1 - s : s, uv, cv, tv0, tv1);
+        f0 -= T(0.5) * (tu0 + tv0);
+        f1 -= T(0.5) * (tu1 + tv1);
+    }
+    Fs0 = inv_h0 * f0;
+    Fs1 = inv_h0 * f1;
+}
+
+// SAT terms of every face node from global memory into F.sat (face term 2 x nf, spread amplitude
+// 2 x nf); used with k_boundary (the strip tile kernel computes them itself)
+template <typename T, int O>
+__global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
+                           int total, StepArgs a, double beta) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const FaceRef fr = refs[find_face(refs, nrefs, t)];
+    const int s = t - fr.start;
+    const BlockDev& B = blocks[fr.block];
+    const FaceDev& F = B.f[fr.face];
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+    T f0, f1, a0, a1;
+    face_sat_node<T, O>(blocks, B, F, s, a, beta,
+                        [&](int L, int j1, int j2) { return U[(size_t)L * plane + (size_t)j2 * B.pitch + j1]; },
+                        [&](int pl, int j1, int j2) { return C[(size_t)pl * plane + (size_t)j2 * B.pitch + j1]; },
+                        f0, f1, a0, a1);
+    T* sat = reinterpret_cast<T*>(F.sat);
+    const int nf = F.nf;
+    sat[s] = f0;
+    sat[nf + s] = f1;
+    sat[2 * nf + s] = a0;
+    sat[3 * nf + s] = a1;
 }
 
 // ============================================================================ boundary strips
@@ -203,7 +408,7 @@ template <typename T, int O, int MODE, class FU0, class FU1, class FC>
 __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a, int i1, int i2, FU0 u0, FU1 u1, FC cc) {
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const size_t plane = (size_t)n2 * P;
-    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
+    const T ih1 = ih1T<T>(B), ih2 = ih2T<T>(B);
     T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0);
     dxx_vec<O, T>(n1, i1, [&](int j) { return u0(j, i2); }, [&](int j) { return u1(j, i2); },
                   [&](int k) { return cc(0, k, i2); }, [&](int k) { return cc(1, k, i2); },
@@ -251,7 +456,7 @@ __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a,
         const int s = m == 0 ? i2 : i1;
         const T* __restrict__ sat = reinterpret_cast<const T*>(F.sat);
         const int nf = F.nf;
-        const T fac = T(F.fac[d]);
+        const T fac = facT<T>(F, d);
         r0 += fac * sat[2 * nf + s];
         r1 += fac * sat[3 * nf + s];
         if (d == 0) {
@@ -271,7 +476,7 @@ __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a,
     }
     if (MODE == 0) {
         T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
-        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = T(a.dt2);
+        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
         Un[gi] = T(2) * u0(i1, i2) - Un[gi] + dt2 * wv * r0;
         Un[gi + plane] = T(2) * u1(i1, i2) - Un[gi + plane] + dt2 * wv * r1;
     } else {
@@ -313,20 +518,25 @@ __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
 // The strips are cut into tiles of 32 nodes along the face x (strip width) nodes across it:
 // bottom and top bands (tiles along x1), left and right bands (tiles along x2, between the
 // bands).  A tile and a halo of HALO nodes (>= the widest closure stencil) are staged in shared
-// memory (2 displacement + 10 coefficient planes).  The mixed fluxes g1_j = c_1j2l D_2 u_l and
-// g2_j = c_1l2j D_1 u_l are formed once per staged node (where their stencils fit), so every
-// output node needs only the narrow rows, two <= NCOL-tap sums and its SAT terms.
+// memory (2 displacement + 10 coefficient planes).  The mixed fluxes g1_j = c_1j2l D_2 u_l (on
+// the tile's rows) and g2_j = c_1l2j D_1 u_l (on its columns) are formed once per staged node, and
+// the SAT terms of the tile's face nodes (every face whose first NCOL nodes the tile touches)
+// are formed from the staged data (the interface neighbour from global memory), so every output
+// node needs only the narrow rows, two <= NCOL-tap sums and shared-memory SAT terms.
 template <int O> struct StripTile {
     static constexpr int HALO = O == 2 ? 3 : (O == 4 ? 8 : 12);
     static constexpr int S = Ord<O>::NCLOS > Ord<O>::NCOL ? Ord<O>::NCLOS : Ord<O>::NCOL;
     static constexpr int RLONG = 32 + 2 * HALO;
     static constexpr int RMAX = RLONG * (S + HALO);     // one side of the region is the face
-    static constexpr int ELEMS = 16 * RMAX;             // 12 staged planes + 4 flux planes
+    static constexpr int FLUX = 2 * (S * RLONG + (S + HALO) * 32);   // g1 on the tile rows, g2 on its columns
+    static constexpr int SATS = 4 * 32 * 4;             // per face, per face node: Fs0, Fs1, As0, As1
+    static constexpr int ELEMS = 12 * RMAX + FLUX + SATS;
     static constexpr int THREADS = 32 * S;
 };
 
 template <typename T, int O, int MODE>
-__global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B, StepArgs a) {
+__global__ void __launch_bounds__(StripTile<O>::THREADS, 3)
+k_strip_tile(BlockDev B, const BlockDev* __restrict__ blocks, StepArgs a, double beta) {
     using ST = StripTile<O>;
     constexpr int S = ST::S, H = ST::HALO, NT = ST::THREADS;
     extern __shared__ __align__(16) unsigned char strip_smem[];
@@ -375,26 +585,49 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
     asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
     __syncthreads();
     auto at = [&](int pl, int j1, int j2) -> T& { return sm[pl * ST::RMAX + (j2 - ry0) * RW + (j1 - rx0)]; };
-    const T ih1 = T(B.ih1), ih2 = T(B.ih2);
-    // fluxes at every staged node whose D stencils lie inside the staged region
-    for (int idx = threadIdx.x; idx < RN; idx += NT) {
+    // g1_J (J = 0, 1) at (j1, j2), j2 in the tile rows; g2_J at (j1, j2), j1 in the tile columns
+    T* g1s = sm + 12 * ST::RMAX;
+    T* g2s = g1s + 2 * h * RW;
+    auto g1 = [&](int J, int j1, int j2) -> T& { return g1s[(J * h + (j2 - y0)) * RW + (j1 - rx0)]; };
+    auto g2 = [&](int J, int j1, int j2) -> T& { return g2s[(J * RH + (j2 - ry0)) * w + (j1 - x0)]; };
+    const T ih1 = ih1T<T>(B), ih2 = ih2T<T>(B);
+    (void)RN;
+    // g1 on the tile's rows (all staged columns), g2 on the tile's columns (all staged rows)
+    for (int idx = threadIdx.x; idx < h * RW; idx += NT) {
         const int r = idx / RW, c = idx - r * RW;
-        const int j1 = rx0 + c, j2 = ry0 + r;
-        int lo, hi;
-        drow_range<O>(n2, j2, lo, hi);
-        if (lo >= ry0 && hi < ry1) {     // g1 needs D_2 u
-            const T d0 = dsum<O, T>(n2, j2, [&](int bb) { return at(0, j1, bb); }) * ih2;
-            const T d1 = dsum<O, T>(n2, j2, [&](int bb) { return at(1, j1, bb); }) * ih2;
-            at(12, j1, j2) = at(8, j1, j2) * d0 + at(9, j1, j2) * d1;
-            at(13, j1, j2) = at(10, j1, j2) * d0 + at(11, j1, j2) * d1;
-        }
-        drow_range<O>(n1, j1, lo, hi);
-        if (lo >= rx0 && hi < rx1) {     // g2 needs D_1 u
-            const T d0 = dsum<O, T>(n1, j1, [&](int aa) { return at(0, aa, j2); }) * ih1;
-            const T d1 = dsum<O, T>(n1, j1, [&](int aa) { return at(1, aa, j2); }) * ih1;
-            at(14, j1, j2) = at(8, j1, j2) * d0 + at(10, j1, j2) * d1;
-            at(15, j1, j2) = at(9, j1, j2) * d0 + at(11, j1, j2) * d1;
-        }
+        const int j1 = rx0 + c, j2 = y0 + r;
+        const T d0 = dsum<O, T>(n2, j2, [&](int bb) { return at(0, j1, bb); }) * ih2;
+        const T d1 = dsum<O, T>(n2, j2, [&](int bb) { return at(1, j1, bb); }) * ih2;
+        g1(0, j1, j2) = at(8, j1, j2) * d0 + at(9, j1, j2) * d1;
+        g1(1, j1, j2) = at(10, j1, j2) * d0 + at(11, j1, j2) * d1;
+    }
+    for (int idx = threadIdx.x; idx < RH * w; idx += NT) {
+        const int r = idx / w, c = idx - r * w;
+        const int j1 = x0 + c, j2 = ry0 + r;
+        const T d0 = dsum<O, T>(n1, j1, [&](int aa) { return at(0, aa, j2); }) * ih1;
+        const T d1 = dsum<O, T>(n1, j1, [&](int aa) { return at(1, aa, j2); }) * ih1;
+        g2(0, j1, j2) = at(8, j1, j2) * d0 + at(10, j1, j2) * d1;
+        g2(1, j1, j2) = at(9, j1, j2) * d0 + at(11, j1, j2) * d1;
+    }
+    // SAT terms of the face nodes whose first NCOL nodes meet the tile: face f's tangential range
+    // is the tile's y range (f = 0, 1) or x range (f = 2, 3)
+    T* sats = sm + 12 * ST::RMAX + ST::FLUX;
+    auto face_meets = [&](int f) {
+        if (f < 2) return f == 0 ? x0 < Ord<O>::NCOL : x0 + w > n1 - Ord<O>::NCOL;
+        return f == 2 ? y0 < Ord<O>::NCOL : y0 + h > n2 - Ord<O>::NCOL;
+    };
+    for (int idx = threadIdx.x; idx < 4 * 32; idx += NT) {
+        const int f = idx >> 5, k = idx & 31;
+        if (k >= (f < 2 ? h : w) || !face_meets(f)) continue;
+        const int s = (f < 2 ? y0 : x0) + k;
+        T f0, f1, a0, a1;
+        face_sat_node<T, O>(blocks, B, B.f[f], s, a, beta, [&](int L, int j1, int j2) { return at(L, j1, j2); },
+                            [&](int pl, int j1, int j2) { return at(2 + pl, j1, j2); }, f0, f1, a0, a1);
+        T* q = sats + (f * 32 + k) * 4;
+        q[0] = f0;
+        q[1] = f1;
+        q[2] = a0;
+        q[3] = a1;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -410,10 +643,10 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
                   [&](int k) { return at(7, i1, k); }, ry0v, ry1v);
     T r0 = rx0v * ih1 * ih1 + ry0v * ih2 * ih2;
     T r1 = rx1v * ih1 * ih1 + ry1v * ih2 * ih2;
-    r0 += dsum<O, T>(n1, i1, [&](int aa) { return at(12, aa, i2); }) * ih1 +
-          dsum<O, T>(n2, i2, [&](int bb) { return at(14, i1, bb); }) * ih2;
-    r1 += dsum<O, T>(n1, i1, [&](int aa) { return at(13, aa, i2); }) * ih1 +
-          dsum<O, T>(n2, i2, [&](int bb) { return at(15, i1, bb); }) * ih2;
+    r0 += dsum<O, T>(n1, i1, [&](int aa) { return g1(0, aa, i2); }) * ih1 +
+          dsum<O, T>(n2, i2, [&](int bb) { return g2(0, i1, bb); }) * ih2;
+    r1 += dsum<O, T>(n1, i1, [&](int aa) { return g1(1, aa, i2); }) * ih1 +
+          dsum<O, T>(n2, i2, [&](int bb) { return g2(1, i1, bb); }) * ih2;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const FaceDev& F = B.f[f];
@@ -421,15 +654,13 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
         const int im = m == 0 ? i1 : i2, Nm = m == 0 ? n1 : n2;
         const int d = F.side ? Nm - 1 - im : im;
         if (d >= Ord<O>::NCOL) continue;
-        const int s = m == 0 ? i2 : i1;
-        const T* __restrict__ sat = reinterpret_cast<const T*>(F.sat);
-        const int nf = F.nf;
-        const T fac = T(F.fac[d]);
-        r0 += fac * sat[2 * nf + s];
-        r1 += fac * sat[3 * nf + s];
+        const T* q = sats + (f * 32 + (m == 0 ? i2 - y0 : i1 - x0)) * 4;
+        const T fac = facT<T>(F, d);
+        r0 += fac * q[2];
+        r1 += fac * q[3];
         if (d == 0) {
-            r0 += sat[s];
-            r1 += sat[nf + s];
+            r0 += q[0];
+            r1 += q[1];
         }
     }
     const size_t gi = (size_t)i2 * P + i1;
@@ -444,7 +675,7 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
     }
     if (MODE == 0) {
         T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
-        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = T(a.dt2);
+        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
         Un[gi] = T(2) * at(0, i1, i2) - Un[gi] + dt2 * wv * r0;
         Un[gi + plane] = T(2) * at(1, i1, i2) - Un[gi + plane] + dt2 * wv * r1;
     } else {
@@ -452,210 +683,6 @@ __global__ void __launch_bounds__(StripTile<O>::THREADS) k_strip_tile(BlockDev B
         R[gi] = r0;
         R[gi + plane] = r1;
     }
-}
-
-// ============================================================================ faces
-struct FaceRef {
-    int block, face, start, nf;
-};
-
-__device__ __forceinline__ int find_face(const FaceRef* refs, int nrefs, int t) {
-    int k = 0;
-    while (k + 1 < nrefs && t >= refs[k + 1].start) ++k;
-    return k;
-}
-
-// c planes at a face node: narrow of the normal direction m (c_mJmL) and the mixed c_mJtL
-__device__ __forceinline__ int plane_nn(int m, int J, int L) { return 3 * m + J + L; }
-__device__ __forceinline__ int plane_nt(int m, int J, int L) { return m == 0 ? 6 + 2 * J + L : 6 + 2 * L + J; }
-
-// trace u_L and J^ tau_J = nu_i c_iJkL D_k u_L (eq. n-C_conversion) at every face node
-template <typename T, int O>
-__global__ void k_face_trace(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
-                             int total, int cur) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const FaceRef fr = refs[find_face(refs, nrefs, t)];
-    const int s = t - fr.start;
-    const BlockDev& B = blocks[fr.block];
-    const FaceDev& F = B.f[fr.face];
-    const int m = F.m, P = B.pitch;
-    const int n1 = B.n1, n2 = B.n2;
-    const size_t plane = (size_t)n2 * P;
-    const T* __restrict__ U0 = reinterpret_cast<const T*>(B.u[cur]);
-    const T* __restrict__ U1 = U0 + plane;
-    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
-    int i1, i2;
-    if (m == 0) { i1 = F.side ? n1 - 1 : 0; i2 = s; }
-    else { i2 = F.side ? n2 - 1 : 0; i1 = s; }
-    const size_t gi = (size_t)i2 * P + i1;
-    T dn0, dn1, dt0, dt1;
-    if (m == 0) {
-        const size_t row = (size_t)i2 * P;
-        dn0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(B.ih1);
-        dn1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(B.ih1);
-        dt0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(B.ih2);
-        dt1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(B.ih2);
-    } else {
-        const size_t row = (size_t)i2 * P;
-        dn0 = dsum<O, T>(n2, i2, [&](int j) { return U0[(size_t)j * P + i1]; }) * T(B.ih2);
-        dn1 = dsum<O, T>(n2, i2, [&](int j) { return U1[(size_t)j * P + i1]; }) * T(B.ih2);
-        dt0 = dsum<O, T>(n1, i1, [&](int j) { return U0[row + j]; }) * T(B.ih1);
-        dt1 = dsum<O, T>(n1, i1, [&](int j) { return U1[row + j]; }) * T(B.ih1);
-    }
-    const T nu = T(F.nu);
-    T tau[2];
-#pragma unroll
-    for (int J = 0; J < 2; ++J) {
-        tau[J] = nu * (C[plane_nn(m, J, 0) * plane + gi] * dn0 + C[plane_nn(m, J, 1) * plane + gi] * dn1 +
-                       C[plane_nt(m, J, 0) * plane + gi] * dt0 + C[plane_nt(m, J, 1) * plane + gi] * dt1);
-    }
-    T* tr = reinterpret_cast<T*>(F.tr);
-    const int nf = F.nf;
-    tr[s] = U0[gi];
-    tr[nf + s] = U1[gi];
-    tr[2 * nf + s] = tau[0];
-    tr[3 * nf + s] = tau[1];
-}
-
-// value of c_{plane} at tangential face index s of face F of block B
-template <typename T>
-__device__ __forceinline__ T face_c(const BlockDev& B, const FaceDev& F, int pl, int s) {
-    int i1, i2;
-    if (F.m == 0) { i1 = F.side ? B.n1 - 1 : 0; i2 = s; }
-    else { i2 = F.side ? B.n2 - 1 : 0; i1 = s; }
-    return reinterpret_cast<const T*>(B.c)[(size_t)pl * B.n2 * B.pitch + (size_t)i2 * B.pitch + i1];
-}
-
-// jump w_L at face node s (displacement: u - g(t); interface: u - v)
-template <typename T>
-__device__ __forceinline__ void face_jump(const BlockDev* blocks, const BlockDev& B, const FaceDev& F, int s,
-                                          const StepArgs& a, T& w0, T& w1) {
-    const T* tr = reinterpret_cast<const T*>(F.tr);
-    const int nf = F.nf;
-    w0 = tr[s];
-    w1 = tr[nf + s];
-    if (F.kind == FACE_DISP) {
-        if (a.with_data && F.g) {
-            const T* g = reinterpret_cast<const T*>(F.g);
-            #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (k >= a.K) break;
-                w0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
-                w1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
-            }
-        }
-    } else if (F.kind == FACE_INTF) {
-        const BlockDev& V = blocks[F.nbr_block];
-        const FaceDev& FV = V.f[F.nbr_face];
-        const int sv = F.reversed ? nf - 1 - s : s;
-        const T* trv = reinterpret_cast<const T*>(FV.tr);
-        w0 -= trv[sv];
-        w1 -= trv[nf + sv];
-    }
-}
-
-// SAT terms of every face node (Sec. 5.1 eq. sat_traction, Sec. 5.2 eq. dirichlet_ansatz with
-// Z of Theorem 3, Sec. 6 eq. scheme_interface with V = Theta = 0), using
-// J^ Z_JL = beta d / h1 * c_mJmL (boundary) and beta d / 4 (c^u_mJmL / h1^u + c^v / h1^v) (interface).
-template <typename T, int O>
-__global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
-                           int total, StepArgs a, double beta) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const FaceRef fr = refs[find_face(refs, nrefs, t)];
-    const int s = t - fr.start;
-    const BlockDev& B = blocks[fr.block];
-    const FaceDev& F = B.f[fr.face];
-    const int m = F.m, nf = F.nf;
-    const T* tr = reinterpret_cast<const T*>(F.tr);
-    T* sat = reinterpret_cast<T*>(F.sat);
-    const T inv_h0 = T(F.inv_h0);
-    const T nu = T(F.nu);
-    const double dd = 2.0;   // spatial dimension d
-    if (F.kind == FACE_ROBIN) {
-        T u0 = tr[s], u1 = tr[nf + s];
-        T f0 = tr[2 * nf + s], f1 = tr[3 * nf + s];
-        if (F.ju) {
-            const T* ju = reinterpret_cast<const T*>(F.ju);
-            const T a11 = ju[s], a12 = ju[nf + s], a22 = ju[2 * nf + s];
-            f0 += a11 * u0 + a12 * u1;
-            f1 += a12 * u0 + a22 * u1;
-        }
-        if (a.with_data && F.g) {
-            const T* g = reinterpret_cast<const T*>(F.g);
-            #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (k >= a.K) break;
-                f0 -= T(a.Tk[k]) * g[(size_t)k * nf + s];
-                f1 -= T(a.Tk[k]) * g[(size_t)(a.K + k) * nf + s];
-            }
-        }
-        sat[s] = -inv_h0 * f0;
-        sat[nf + s] = -inv_h0 * f1;
-        sat[2 * nf + s] = T(0);
-        sat[3 * nf + s] = T(0);
-        return;
-    }
-    const bool intf = F.kind == FACE_INTF;
-    const T half = intf ? T(0.5) : T(1);
-    T w0, w1;
-    face_jump<T>(blocks, B, F, s, a, w0, w1);
-    // penalty J^ Z
-    const T c00 = face_c<T>(B, F, plane_nn(m, 0, 0), s), c01 = face_c<T>(B, F, plane_nn(m, 0, 1), s),
-            c11 = face_c<T>(B, F, plane_nn(m, 1, 1), s);
-    T z00, z01, z11;
-    if (!intf) {
-        const T k = T(beta * dd / F.hm0);
-        z00 = k * c00; z01 = k * c01; z11 = k * c11;
-    } else {
-        const BlockDev& V = blocks[F.nbr_block];
-        const FaceDev& FV = V.f[F.nbr_face];
-        const int sv = F.reversed ? nf - 1 - s : s;
-        const int mv = FV.m;
-        const T ku = T(beta * dd / 4.0 / F.hm0), kv = T(beta * dd / 4.0 / FV.hm0);
-        z00 = ku * c00 + kv * face_c<T>(V, FV, plane_nn(mv, 0, 0), sv);
-        z01 = ku * c01 + kv * face_c<T>(V, FV, plane_nn(mv, 0, 1), sv);
-        z11 = ku * c11 + kv * face_c<T>(V, FV, plane_nn(mv, 1, 1), sv);
-    }
-    // normal-spread amplitude a_J = half * nu c_mJmL w_L
-    sat[2 * nf + s] = half * nu * (c00 * w0 + c01 * w1);
-    sat[3 * nf + s] = half * nu * (c01 * w0 + c11 * w1);
-    // tangential transpose term (1/H_t(s)) sum_s' D_t[s'][s] H_t(s') b_J(s'),  b_J = nu c_mLtJ w_L
-    const int Nt = nf;
-    const double ht = m == 0 ? B.h2 : B.h1;
-    // rows of D with a non-zero in column s: the interior band s-Q..s+Q plus, near an end, every
-    // boundary row (boundary rows span columns 0..NCOL-1, which can reach past s+Q)
-    int lo = s - Ord<O>::Q, hi = s + Ord<O>::Q;
-    if (s < Ord<O>::NCOL) { lo = 0; hi = max(hi, Ord<O>::NB - 1); }
-    if (s >= Nt - Ord<O>::NCOL) { hi = Nt - 1; lo = min(lo, Nt - Ord<O>::NB); }
-    if (lo < 0) lo = 0;
-    if (hi > Nt - 1) hi = Nt - 1;
-    T tt0 = T(0), tt1 = T(0);
-    for (int sp = lo; sp <= hi; ++sp) {
-        const double dc = dcoef<O>(Nt, sp, s);
-        if (dc == 0.0) continue;
-        T v0, v1;
-        face_jump<T>(blocks, B, F, sp, a, v0, v1);
-        const T b0 = nu * (face_c<T>(B, F, plane_nt(m, 0, 0), sp) * v0 + face_c<T>(B, F, plane_nt(m, 1, 0), sp) * v1);
-        const T b1 = nu * (face_c<T>(B, F, plane_nt(m, 0, 1), sp) * v0 + face_c<T>(B, F, plane_nt(m, 1, 1), sp) * v1);
-        const T wgt = T(dc * hweight<O>(Nt, sp));
-        tt0 += wgt * b0;
-        tt1 += wgt * b1;
-    }
-    const T tfac = T(1.0 / (ht * hweight<O>(Nt, s)));
-    T f0 = half * tt0 * tfac - (z00 * w0 + z01 * w1);
-    T f1 = half * tt1 * tfac - (z01 * w0 + z11 * w1);
-    if (intf) {
-        const BlockDev& V = blocks[F.nbr_block];
-        const FaceDev& FV = V.f[F.nbr_face];
-        const int sv = F.reversed ? nf - 1 - s : s;
-        const T* trv = reinterpret_cast<const T*>(FV.tr);
-        f0 -= T(0.5) * (tr[2 * nf + s] + trv[2 * nf + sv]);
-        f1 -= T(0.5) * (tr[3 * nf + s] + trv[3 * nf + sv]);
-    }
-    sat[s] = inv_h0 * f0;
-    sat[nf + s] = inv_h0 * f1;
 }
 
 // ============================================================================ point sources
@@ -835,15 +862,18 @@ __global__ void k_from_pitched(double* dst, const T* __restrict__ src, int n1, i
 }
 
 // CFL (Sec. 7): per node min(h1,h2) / v_max with v_max^2 = max_theta lambda_max(Gamma(theta)) / (rho J),
-// Gamma_jl = xi_i c_ijkl xi_k; 720 samples in [0, pi) then 40 golden-section steps around the best.
-template <typename T>
-__device__ __forceinline__ double christoffel_lmax(const double* c, double th) {
-    const double x1 = cos(th), x2 = sin(th);
-    const double g00 = x1 * x1 * c[0] + 2.0 * x1 * x2 * c[6] + x2 * x2 * c[3];
-    const double g01 = x1 * x1 * c[1] + x1 * x2 * (c[7] + c[8]) + x2 * x2 * c[4];
-    const double g11 = x1 * x1 * c[2] + 2.0 * x1 * x2 * c[9] + x2 * x2 * c[5];
-    const double hm = 0.5 * (g00 - g11);
-    return 0.5 * (g00 + g11) + sqrt(hm * hm + g01 * g01);
+// Gamma_jl = xi_i c_ijkl xi_k, xi = (cos theta, sin theta); lambda_max has period pi in theta.
+// The maximisation is done in two precisions: 720 FP32 samples of [0, pi) locate the three best
+// local maxima (cheap: GB300's FP64 rate is a small fraction of its FP32 rate), then each is
+// refined in FP64 by Newton steps on d lambda/d theta = 0 with central differences (step 1e-4:
+// the derivative error O(1e-8) leaves lambda exact to rounding), and the largest refined value wins.
+template <typename R>
+__device__ __forceinline__ R christoffel_lmax(const R* c, R x1, R x2) {
+    const R g00 = x1 * x1 * c[0] + R(2) * x1 * x2 * c[6] + x2 * x2 * c[3];
+    const R g01 = x1 * x1 * c[1] + x1 * x2 * (c[7] + c[8]) + x2 * x2 * c[4];
+    const R g11 = x1 * x1 * c[2] + R(2) * x1 * x2 * c[9] + x2 * x2 * c[5];
+    const R hm = R(0.5) * (g00 - g11);
+    return R(0.5) * (g00 + g11) + sqrt(hm * hm + g01 * g01);
 }
 
 template <typename T>
@@ -854,28 +884,60 @@ __global__ void k_cfl(BlockDev B, unsigned long long* out_bits) {
     const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
     const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
     double c[10];
+    float cf[10];
     const T* C = reinterpret_cast<const T*>(B.c);
-    for (int p = 0; p < 10; ++p) c[p] = (double)C[p * plane + gi];
+    for (int p = 0; p < 10; ++p) {
+        c[p] = (double)C[p * plane + gi];
+        cf[p] = (float)c[p];
+    }
     const double rhoJ = 1.0 / (double)reinterpret_cast<const T*>(B.w)[gi];
-    const double PI = 3.14159265358979323846;
-    double best = -1.0, bth = 0.0;
-    for (int k = 0; k < 720; ++k) {
-        const double th = k * PI / 720;
-        const double l = christoffel_lmax<T>(c, th);
-        if (l > best) { best = l; bth = th; }
+    constexpr int NS = 720;
+    // FP32 sweep: the three largest local maxima of the cyclic sample sequence
+    float best[3] = {-1.f, -1.f, -1.f};
+    int bk[3] = {0, 0, 0};
+    float s, co;
+    sincospif(-1.0f / NS, &s, &co);
+    float prev = christoffel_lmax<float>(cf, co, s);
+    sincospif(0.0f, &s, &co);
+    float cur = christoffel_lmax<float>(cf, co, s);
+    const float first = cur;
+    for (int k = 0; k < NS; ++k) {
+        float nxt;
+        if (k + 1 < NS) {
+            sincospif((float)(k + 1) / NS, &s, &co);
+            nxt = christoffel_lmax<float>(cf, co, s);
+        } else {
+            nxt = first;
+        }
+        if (cur >= prev && cur >= nxt) {
+            if (cur > best[0]) { best[2] = best[1]; bk[2] = bk[1]; best[1] = best[0]; bk[1] = bk[0]; best[0] = cur; bk[0] = k; }
+            else if (cur > best[1]) { best[2] = best[1]; bk[2] = bk[1]; best[1] = cur; bk[1] = k; }
+            else if (cur > best[2]) { best[2] = cur; bk[2] = k; }
+        }
+        prev = cur;
+        cur = nxt;
     }
-    double lo = bth - PI / 720, hi = bth + PI / 720;
-    const double gr = (sqrt(5.0) - 1.0) / 2.0;
-    double cc = hi - gr * (hi - lo), dd = lo + gr * (hi - lo);
-    double fc = christoffel_lmax<T>(c, cc), fd = christoffel_lmax<T>(c, dd);
-    for (int it = 0; it < 40; ++it) {
-        if (fc > fd) hi = dd; else lo = cc;
-        cc = hi - gr * (hi - lo);
-        dd = lo + gr * (hi - lo);
-        fc = christoffel_lmax<T>(c, cc);
-        fd = christoffel_lmax<T>(c, dd);
+    // FP64 refinement of each candidate
+    const double PI = 3.14159265358979323846, dl = 1e-4;
+    auto lam = [&](double th) { double sd, cd; sincos(th, &sd, &cd); return christoffel_lmax<double>(c, cd, sd); };
+    double lmax = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        if (best[q] < 0.f) continue;
+        double th = bk[q] * PI / NS;
+        double f0 = lam(th);
+        lmax = fmax(lmax, f0);
+        for (int it = 0; it < 3; ++it) {
+            const double fp = lam(th + dl), fm = lam(th - dl);
+            const double d1 = (fp - fm) / (2 * dl), d2 = (fp - 2 * f0 + fm) / (dl * dl);
+            lmax = fmax(lmax, fmax(fp, fm));
+            if (!(d2 < 0.0)) break;
+            double step = -d1 / d2;
+            step = fmax(-2 * PI / NS, fmin(2 * PI / NS, step));
+            th += step;
+            f0 = lam(th);
+            lmax = fmax(lmax, f0);
+        }
     }
-    const double lmax = fmax(fmax(fc, fd), best);
     const double v = sqrt(lmax / rhoJ);
     const double hmin = fmin(B.h1, B.h2);
     const double r = hmin / v;

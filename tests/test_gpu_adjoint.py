@@ -170,3 +170,45 @@ def test_misfit_gradient_workload_small():
     assert np.max(np.abs(gr[0] - ref["grad_rho"][0])) <= 1e-9 * scale
     got = np.array([gc[0][Pp, i2, i1] for (_, Pp, i1, i2) in params])
     assert np.max(np.abs(got - ref["grad_C"])) <= 1e-9 * np.max(np.abs(ref["grad_C"]))
+
+
+def test_autograd_bridge_and_gpu_central_differences():
+    """torch.autograd through sbp_misfit_gradient returns the library's gradient, and that gradient
+    agrees with central differences of the GPU misfit itself (FP64)."""
+    import torch
+    from paper_2003_12811_gb300.autograd import misfit, pair_planes
+    P, u0, dt, rec, obs = _setup(4, nsteps=30)
+    S = _solver(P, "fp64", u0, rec)
+    rho = [torch.tensor(b.rho, dtype=torch.float64, requires_grad=True) for b in P.blocks]
+    C = [pair_planes(torch.tensor(b.C, dtype=torch.float64)).clone().requires_grad_(True) for b in P.blocks]
+    phi = misfit(S, rho, C, u0, u0, 0.0, 30, dt, obs)
+    phi.backward()
+    S.set_state(u0, u0, 0.0)
+    phi2, gr, gc = S.sbp_misfit_gradient(30, dt, obs)
+    assert float(phi) == phi2
+    for b in range(2):
+        assert np.array_equal(rho[b].grad.numpy(), gr[b]) and np.array_equal(C[b].grad.numpy(), gc[b])
+
+    def phi_at(rr, cc):
+        with torch.no_grad():
+            return float(misfit(S, rr, cc, u0, u0, 0.0, 30, dt, obs))
+
+    for (b, i1, i2) in [(0, 3, 4), (1, 0, 7), (0, 20, 18)]:
+        eps = 1e-6
+        rp = [r.detach().clone() for r in rho]
+        rm = [r.detach().clone() for r in rho]
+        rp[b][i2, i1] += eps
+        rm[b][i2, i1] -= eps
+        Cd = [c.detach() for c in C]
+        fd = (phi_at(rp, Cd) - phi_at(rm, Cd)) / (2 * eps)
+        assert abs(fd - gr[b][i2, i1]) <= 1e-5 * abs(fd) + 100 * np.finfo(float).eps * phi2 / eps
+    for (b, Pp, i1, i2) in [(0, 0, 5, 5), (1, 9, 20, 3), (0, 4, 0, 0)]:
+        eps = 1e-5
+        cp = [c.detach().clone() for c in C]
+        cm = [c.detach().clone() for c in C]
+        cp[b][Pp, i2, i1] += eps
+        cm[b][Pp, i2, i1] -= eps
+        Rd = [r.detach() for r in rho]
+        fd = (phi_at(Rd, cp) - phi_at(Rd, cm)) / (2 * eps)
+        assert abs(fd - gc[b][Pp, i2, i1]) <= 1e-5 * abs(fd) + 100 * np.finfo(float).eps * phi2 / eps
+    S.close()
