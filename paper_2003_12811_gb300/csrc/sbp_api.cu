@@ -118,6 +118,11 @@ struct sbp_handle {
     int d_time_cap = 0;
     // marching-kernel rows per CTA chosen by sbp_autotune (0 = default heuristic)
     int rows_per_cta = 0;
+    // the boundary strips run on a second stream concurrently with the interior kernel (they
+    // write disjoint nodes); forked from and joined back into the launch stream every step
+    bool overlap = true;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // adjoint: block views whose state buffers are the adjoint fields; receivers
     BlockDev* d_blocks_adj = nullptr;
     std::vector<RecDev> recs;
@@ -289,6 +294,14 @@ template <typename T, int O>
 int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj) {
     const BlockDev* tab = adj ? h->d_blocks_adj : h->d_blocks;
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
+    // interior kernels on st; strip kernels on the auxiliary stream when overlapping (profiling
+    // runs serialise so that every family's events time that family alone)
+    const bool ovl = h->overlap && h->aux && !h->prof;
+    cudaStream_t sst = ovl ? h->aux : st;
+    if (ovl) {
+        cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
+    }
     for (auto& hb : h->blocks) {
         BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
         const MarchMaps& mm = adj ? hb.pmaps : hb.mmaps;
@@ -315,14 +328,19 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
                 else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
             }
         }
-        {
-            ProfScope ps(h, 1, st, 1);
-            using ST = StripTile<O>;
-            const int ntile = 2 * ((hb.n1 + 31) / 32) + 2 * ((hb.n2 - 2 * ST::S + 31) / 32);
-            constexpr size_t ssm = (size_t)ST::ELEMS * sizeof(T);
-            if (mode == 0) k_strip_tile<T, O, 0><<<ntile, ST::THREADS, ssm, st>>>(b, tab, a, h->beta);
-            else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, st>>>(b, tab, a, h->beta);
-        }
+    }
+    for (auto& hb : h->blocks) {
+        BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
+        ProfScope ps(h, 1, sst, 1);
+        using ST = StripTile<O>;
+        const int ntile = 2 * ((hb.n1 + 31) / 32) + 2 * ((hb.n2 - 2 * ST::S + 31) / 32);
+        constexpr size_t ssm = (size_t)ST::ELEMS * sizeof(T);
+        if (mode == 0) k_strip_tile<T, O, 0><<<ntile, ST::THREADS, ssm, sst>>>(b, tab, a, h->beta);
+        else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, sst>>>(b, tab, a, h->beta);
+    }
+    if (ovl) {
+        cudaEventRecord(h->ev_join, h->aux);
+        cudaStreamWaitEvent(st, h->ev_join, 0);
     }
     if (!adj && !h->src_nodes.empty()) {
         ProfScope ps(h, 3, st, 1);
@@ -652,6 +670,10 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (h->num_sms <= 0) h->num_sms = 1;
     }
+    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(SBP_E_CUDA, "auxiliary stream");
     std::vector<FaceRef> refs;
     int start = 0;
     for (int b = 0; b < desc->nblocks; ++b) {
@@ -742,6 +764,9 @@ int sbp_destroy(sbp_handle* h) {
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     delete h;
     return SBP_OK;
 }
