@@ -8,8 +8,11 @@
 //  * rows stream through a ring of NCH chunks of R rows in shared memory, each chunk filled by
 //    two cp.async.bulk.tensor.3d boxes (displacement [2][R][140], coefficients [10][R][140],
 //    x from the tile start - 8) tracked by an mbarrier per ring slot (bounded waits);
-//  * the y-direction stencils use register queues of the last 2q+1 rows of the thread's own
-//    column (displacement, the three c_2j2l fields, and the fluxes g2 = c_1l2j D_1 u_l);
+//  * the y-direction stencils use register queues of the thread's own column (displacement and
+//    the fluxes g2 = c_1l2j D_1 u_l for the last 2q+1 rows, the three c_2j2l fields for rows
+//    r-q+1..r+q); the narrow y rows are written in edge-flux form
+//      h^2 D_yy(b) u |_r = sum_m F_m(r) - F_m(r-m),  F_m(r) = E_m(r) (u_{r+m} - u_r),
+//    so every edge weight E_m is formed once and F_m waits m rows in a short delay line;
 //  * the x-direction fluxes g1 = c_1j2l D_2 u_l of the current row are exchanged through a
 //    double-buffered shared row (one barrier per row);
 //  * 1/(rho J) and u^{n-1} of the output row are loaded from global memory two rows ahead.
@@ -106,10 +109,19 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     const float ih1 = B.ih1f, ih2 = B.ih2f;
     const float ih11 = ih1 * ih1, ih22 = ih2 * ih2;
 
-    // register queues, index 0 = oldest row
-    float qu0[L], qu1[L], qb0[L], qb1[L], qb2[L], qg0[L], qg1[L], qh0[L], qh1[L];
+    // register queues, index 0 = oldest row (qb: rows r-q+1 .. r+q of the c_2j2l fields)
+    constexpr int LB = 2 * Q;
+    float qu0[L], qu1[L], qb0[LB], qb1[LB], qb2[LB], qg0[L], qg1[L], qh0[L], qh1[L];
 #pragma unroll
-    for (int k = 0; k < L; ++k) qu0[k] = qu1[k] = qb0[k] = qb1[k] = qb2[k] = qg0[k] = qg1[k] = qh0[k] = qh1[k] = 0.f;
+    for (int k = 0; k < L; ++k) qu0[k] = qu1[k] = qg0[k] = qg1[k] = qh0[k] = qh1[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < LB; ++k) qb0[k] = qb1[k] = qb2[k] = 0.f;
+    // delay lines of the y edge fluxes: fy*[m-1][0] = F_m(r-m) .. fy*[m-1][m-1] = F_m(r-1)
+    float fy0[Q][Q], fy1[Q][Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) fy0[m][k] = fy1[m][k] = 0.f;
     // threads 0..2Q-1 also follow one halo column each (x0-Q..x0-1, x0+128..x0+127+Q) for g1
     const int hc = tx < Q ? MXOFF - Q + tx : MXOFF + MTHREADS + (tx - Q);
     const bool halo = tx < 2 * Q;
@@ -159,14 +171,17 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
 #pragma unroll
             for (int k = 0; k < L - 1; ++k) {
                 qu0[k] = qu0[k + 1]; qu1[k] = qu1[k + 1];
-                qb0[k] = qb0[k + 1]; qb1[k] = qb1[k + 1]; qb2[k] = qb2[k + 1];
                 qg0[k] = qg0[k + 1]; qg1[k] = qg1[k + 1];
+            }
+#pragma unroll
+            for (int k = 0; k < LB - 1; ++k) {
+                qb0[k] = qb0[k + 1]; qb1[k] = qb1[k + 1]; qb2[k] = qb2[k + 1];
             }
             qu0[L - 1] = u0n;
             qu1[L - 1] = u1n;
-            qb0[L - 1] = pL[poff(5)];
-            qb1[L - 1] = pL[poff(6)];
-            qb2[L - 1] = pL[poff(7)];
+            qb0[LB - 1] = pL[poff(5)];
+            qb1[LB - 1] = pL[poff(6)];
+            qb2[LB - 1] = pL[poff(7)];
             qg0[L - 1] = m6 * d0 + m8 * d1;       // g2_1 = c_1121 D_1 u_1 + c_1221 D_1 u_2
             qg1[L - 1] = m7 * d0 + m9 * d1;       // g2_2 = c_1122 D_1 u_1 + c_1222 D_1 u_2
             if (halo) {
@@ -177,6 +192,31 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
                 }
                 qh0[L - 1] = at(0, Lr, hc);
                 qh1[L - 1] = at(1, Lr, hc);
+            }
+        }
+        // --- narrow y in edge-flux form: F_m(r) from the queued rows, F_m(r-m) from the delay
+        // lines (needed from the first output row on, so formed from row ys - Q on)
+        float ry0 = 0.f, ry1 = 0.f;
+        if (r >= ys - Q) {
+            const float uc0 = qu0[Q], uc1 = qu1[Q];
+#pragma unroll
+            for (int m = 1; m <= Q; ++m) {
+                auto B0p = [&](int k) { return qb0[k + Q - 1]; };
+                auto B1p = [&](int k) { return qb1[k + Q - 1]; };
+                auto B2p = [&](int k) { return qb2[k + Q - 1]; };
+                const float e0 = Edge<O>::template e<float>(m, B0p), e1 = Edge<O>::template e<float>(m, B1p),
+                            e2 = Edge<O>::template e<float>(m, B2p);
+                const float dp0 = qu0[Q + m] - uc0, dp1 = qu1[Q + m] - uc1;
+                const float f0 = e0 * dp0 + e1 * dp1, f1 = e1 * dp0 + e2 * dp1;
+                ry0 += f0 - fy0[m - 1][0];
+                ry1 += f1 - fy1[m - 1][0];
+#pragma unroll
+                for (int k = 0; k < m - 1; ++k) {
+                    fy0[m - 1][k] = fy0[m - 1][k + 1];
+                    fy1[m - 1][k] = fy1[m - 1][k + 1];
+                }
+                fy0[m - 1][m - 1] = f0;
+                fy1[m - 1][m - 1] = f1;
             }
         }
         if (r < ys) continue;                    // queue fill (prologue)
@@ -252,25 +292,6 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
             const float dm0 = pr[poff(0) - m] - uc0, dm1 = pr[poff(1) - m] - uc1;
             rx0 += e0p * dp0 + e1p * dp1 + e0m * dm0 + e1m * dm1;
             rx1 += e1p * dp0 + e2p * dp1 + e1m * dm0 + e2m * dm1;
-        }
-        // --- narrow y: edge weights from the queued c_2j2l fields of rows r-Q..r+Q
-        float ry0 = 0.f, ry1 = 0.f;
-#pragma unroll
-        for (int m = 1; m <= Q; ++m) {
-            auto B0p = [&](int k) { return qb0[Q + k]; };
-            auto B1p = [&](int k) { return qb1[Q + k]; };
-            auto B2p = [&](int k) { return qb2[Q + k]; };
-            auto B0m = [&](int k) { return qb0[Q - m + k]; };
-            auto B1m = [&](int k) { return qb1[Q - m + k]; };
-            auto B2m = [&](int k) { return qb2[Q - m + k]; };
-            const float e0p = Edge<O>::template e<float>(m, B0p), e1p = Edge<O>::template e<float>(m, B1p),
-                        e2p = Edge<O>::template e<float>(m, B2p);
-            const float e0m = Edge<O>::template e<float>(m, B0m), e1m = Edge<O>::template e<float>(m, B1m),
-                        e2m = Edge<O>::template e<float>(m, B2m);
-            const float dp0 = qu0[Q + m] - uc0, dp1 = qu1[Q + m] - uc1;
-            const float dm0 = qu0[Q - m] - uc0, dm1 = qu1[Q - m] - uc1;
-            ry0 += e0p * dp0 + e1p * dp1 + e0m * dm0 + e1m * dm1;
-            ry1 += e1p * dp0 + e2p * dp1 + e1m * dm0 + e2m * dm1;
         }
         float r0 = rx0 * ih11 + ry0 * ih22;
         float r1 = rx1 * ih11 + ry1 * ih22;
