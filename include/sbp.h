@@ -141,14 +141,18 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream);
  * footprint.  No device work. */
 int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out);
 
-/* Pick the FP32 interior kernel's rows per CTA for this grid by timing candidate shapes
- * (operator applications on the current state, which is left unchanged); the choice is kept
- * by the handle and written to *rows_out (0 = the built-in heuristic).  FP64 handles: no-op. */
-int sbp_autotune(sbp_handle* h, int* rows_out);
+/* Pick the launch tuning for this grid by timing candidates on leapfrog steps from the current
+ * state (the overwritten level is saved and restored: the state is left unchanged; device memory
+ * for one copy of the state is allocated for the call): the FP32 interior kernel's rows per CTA (written to
+ * *rows_out, 0 = the built-in heuristic; FP64 handles: 0), and whether the boundary-strip kernel
+ * runs on a second stream concurrently with the interior kernel (*overlap_out, 0 or 1; the
+ * default is 0).  The choice is kept by the handle.  Either pointer may be NULL. */
+int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out);
 
-/* Set the FP32 interior kernel's rows per CTA directly (e.g. a choice sbp_autotune made for
- * another handle with the same grid); 0 restores the heuristic. */
-int sbp_set_tuning(sbp_handle* h, int rows_per_cta);
+/* Set the tuning directly (e.g. a choice sbp_autotune made for another handle with the same
+ * grid): rows per CTA of the FP32 interior kernel (0 = heuristic) and the strip/interior overlap
+ * (0 off, 1 on, -1 unchanged). */
+int sbp_set_tuning(sbp_handle* h, int rows_per_cta, int overlap);
 
 /* Apply the spatial operator to the current level of every block (synchronous):
  * r = DD(c) u + J SAT(u) (+ J f(t) + point sources when with_data != 0, SAT data at t).

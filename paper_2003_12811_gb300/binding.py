@@ -82,8 +82,8 @@ def lib():
         L.sbp_profile.argtypes = [C.c_void_p, C.c_int]
         L.sbp_step_graph.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_grid_footprint.argtypes = [C.POINTER(GridDesc), C.POINTER(C.c_longlong)]
-        L.sbp_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
-        L.sbp_set_tuning.argtypes = [C.c_void_p, C.c_int]
+        L.sbp_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sbp_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.sbp_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -227,12 +227,13 @@ class Solver:
         self._check(self.L.sbp_step_graph(self.h, int(nsteps), float(dt), s))
 
     def sbp_autotune(self):
-        r = C.c_int()
-        self._check(self.L.sbp_autotune(self.h, C.byref(r)))
-        return r.value
+        """Returns (rows_per_cta, overlap) chosen for this grid."""
+        r, o = C.c_int(), C.c_int()
+        self._check(self.L.sbp_autotune(self.h, C.byref(r), C.byref(o)))
+        return r.value, o.value
 
-    def sbp_set_tuning(self, rows_per_cta):
-        self._check(self.L.sbp_set_tuning(self.h, int(rows_per_cta)))
+    def sbp_set_tuning(self, rows_per_cta, overlap=-1):
+        self._check(self.L.sbp_set_tuning(self.h, int(rows_per_cta), int(overlap)))
 
     def sbp_apply(self, with_data=False, t=0.0):
         self._check(self.L.sbp_apply(self.h, int(bool(with_data)), float(t)))

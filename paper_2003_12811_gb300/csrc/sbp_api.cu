@@ -118,9 +118,16 @@ struct sbp_handle {
     int d_time_cap = 0;
     // marching-kernel rows per CTA chosen by sbp_autotune (0 = default heuristic)
     int rows_per_cta = 0;
-    // the boundary strips run on a second stream concurrently with the interior kernel (they
-    // write disjoint nodes); forked from and joined back into the launch stream every step
-    bool overlap = true;
+    // optionally (sbp_autotune, sbp_set_tuning) the boundary strips run on a second stream
+    // concurrently with the interior kernel (they write disjoint nodes); both are forked from and
+    // joined back into the launch stream every step, the interior on a high-priority stream so
+    // that its CTAs are placed first
+    bool overlap = false;
+    cudaStream_t hi = nullptr;
+    cudaEvent_t ev_join_hi = nullptr;
+    // strip tiles of every block, costliest first (one k_strip_tile launch per step)
+    int2* d_tiles = nullptr;
+    int ntiles = 0;
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // adjoint: block views whose state buffers are the adjoint fields; receivers
@@ -298,8 +305,10 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
     // runs serialise so that every family's events time that family alone)
     const bool ovl = h->overlap && h->aux && !h->prof;
     cudaStream_t sst = ovl ? h->aux : st;
+    cudaStream_t ist = ovl ? h->hi : st;
     if (ovl) {
         cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(h->hi, h->ev_fork, 0);
         cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
     }
     for (auto& hb : h->blocks) {
@@ -309,7 +318,7 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         const int ni1 = hb.n1 - 2 * S, ni2 = hb.n2 - 2 * S;
         dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
         {
-            ProfScope ps(h, 0, st, 1);
+            ProfScope ps(h, 0, ist, 1);
             if constexpr (std::is_same<T, float>::value) {
                 // column-marching kernel: one wave of ~4 CTAs per SM, rows split evenly
                 const int S2 = b.strip;
@@ -321,26 +330,26 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
                 if (h->rows_per_cta > 0) rows = std::min(h->rows_per_cta, n2i);
                 ncy = (n2i + rows - 1) / rows;
                 constexpr size_t msm = MarchCfg<O>::BYTES;
-                if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, st>>>(mm, b, a, rows, h->d_err);
-                else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, st>>>(mm, b, a, rows, h->d_err);
+                if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
+                else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
             } else {
-                if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, st>>>(b, a);
-                else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, st>>>(b, a);
+                if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, ist>>>(b, a);
+                else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, ist>>>(b, a);
             }
         }
     }
-    for (auto& hb : h->blocks) {
-        BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
+    {
         ProfScope ps(h, 1, sst, 1);
         using ST = StripTile<O>;
-        const int ntile = 2 * ((hb.n1 + 31) / 32) + 2 * ((hb.n2 - 2 * ST::S + 31) / 32);
         constexpr size_t ssm = (size_t)ST::ELEMS * sizeof(T);
-        if (mode == 0) k_strip_tile<T, O, 0><<<ntile, ST::THREADS, ssm, sst>>>(b, tab, a, h->beta);
-        else k_strip_tile<T, O, 1><<<ntile, ST::THREADS, ssm, sst>>>(b, tab, a, h->beta);
+        if (mode == 0) k_strip_tile<T, O, 0><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta);
+        else k_strip_tile<T, O, 1><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta);
     }
     if (ovl) {
         cudaEventRecord(h->ev_join, h->aux);
+        cudaEventRecord(h->ev_join_hi, h->hi);
         cudaStreamWaitEvent(st, h->ev_join, 0);
+        cudaStreamWaitEvent(st, h->ev_join_hi, 0);
     }
     if (!adj && !h->src_nodes.empty()) {
         ProfScope ps(h, 3, st, 1);
@@ -670,10 +679,16 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (h->num_sms <= 0) h->num_sms = 1;
     }
-    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
-        return cleanup(SBP_E_CUDA, "auxiliary stream");
+    {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_join_hi, cudaEventDisableTiming) != cudaSuccess)
+            return cleanup(SBP_E_CUDA, "auxiliary streams");
+    }
     std::vector<FaceRef> refs;
     int start = 0;
     for (int b = 0; b < desc->nblocks; ++b) {
@@ -736,6 +751,36 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     if (!h->d_refs || !h->d_blocks) return cleanup(SBP_E_OOM, "tables");
     cudaMemcpy(h->d_refs, refs.data(), sizeof(FaceRef) * refs.size(), cudaMemcpyHostToDevice);
     if (sync_views(h) != SBP_OK) return cleanup(SBP_E_CUDA, h->err);
+    {
+        // strip tiles (the tile numbering of k_strip_tile: 2 bands of ceil(n1/32) tiles along x1,
+        // then 2 side bands of ceil((n2 - 2S)/32) tiles), ordered by a cost estimate: side tiles
+        // stage narrow rows, interface tiles read the neighbour, corner tiles carry two faces
+        const int S = std::max(order_nclos(o), order_ncol(o));
+        std::vector<std::pair<int, int2>> tl;
+        for (int b = 0; b < desc->nblocks; ++b) {
+            const HostBlock& hb = h->blocks[b];
+            const int nbx = (hb.n1 + 31) / 32, nby = (hb.n2 - 2 * S + 31) / 32;
+            for (int t = 0; t < 2 * nbx + 2 * nby; ++t) {
+                int cost;
+                if (t < 2 * nbx) {
+                    const int f = 2 + t / nbx, k = t % nbx;
+                    cost = (hb.f[f].kind == SBP_BC_INTERFACE ? 3 : 1) + ((k == 0 || k == nbx - 1) ? 2 : 0);
+                } else {
+                    const int f = (t - 2 * nbx) / nby;
+                    cost = 2 + (hb.f[f].kind == SBP_BC_INTERFACE ? 3 : 0);
+                }
+                tl.push_back({cost, make_int2(b, t)});
+            }
+        }
+        std::stable_sort(tl.begin(), tl.end(),
+                         [](const std::pair<int, int2>& x, const std::pair<int, int2>& y) { return x.first > y.first; });
+        std::vector<int2> tv;
+        for (auto& e : tl) tv.push_back(e.second);
+        h->ntiles = (int)tv.size();
+        h->d_tiles = (int2*)h->dalloc(sizeof(int2) * tv.size());
+        if (!h->d_tiles) return cleanup(SBP_E_OOM, "tile table");
+        cudaMemcpy(h->d_tiles, tv.data(), sizeof(int2) * tv.size(), cudaMemcpyHostToDevice);
+    }
     // metric
     cudaMemset(h->d_flag, 0, sizeof(int));
     for (auto& hb : h->blocks) {
@@ -767,6 +812,8 @@ int sbp_destroy(sbp_handle* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_join_hi) cudaEventDestroy(h->ev_join_hi);
+    if (h->hi) cudaStreamDestroy(h->hi);
     delete h;
     return SBP_OK;
 }
@@ -1251,69 +1298,119 @@ int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out) {
     return SBP_OK;
 }
 
-int sbp_set_tuning(sbp_handle* h, int rows_per_cta) {
+int sbp_set_tuning(sbp_handle* h, int rows_per_cta, int overlap) {
     if (!h) return SBP_E_INVALID_ARG;
     if (rows_per_cta < 0) return h->fail(SBP_E_INVALID_ARG, "rows per CTA must be >= 0");
-    if (rows_per_cta != h->rows_per_cta && h->graph_exec) {
+    if (overlap < -1 || overlap > 1) return h->fail(SBP_E_INVALID_ARG, "overlap must be -1, 0 or 1");
+    const bool ov = overlap < 0 ? h->overlap : overlap != 0;
+    if ((rows_per_cta != h->rows_per_cta || ov != h->overlap) && h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
     }
     h->rows_per_cta = rows_per_cta;
+    h->overlap = ov;
     return SBP_OK;
 }
 
-int sbp_autotune(sbp_handle* h, int* rows_out) {
+int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
     if (!h) return SBP_E_INVALID_ARG;
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
-    if (h->precision != SBP_FP32) {
-        if (rows_out) *rows_out = 0;
-        return SBP_OK;   // only the FP32 marching kernel has a tunable shape
-    }
-    // candidates for the marching kernel's rows per CTA; 0 = heuristic (one wave at 4 CTAs/SM)
-    const int cand[] = {0, 16, 32, 64, 128, 256};
+    // candidates for the marching kernel's rows per CTA (FP32 only); 0 = heuristic (one wave at
+    // 4 CTAs/SM); then whether the strips run concurrently with the interior
+    const int cand32[] = {0, 16, 32, 64, 128, 256};
+    const int cand64[] = {0};
+    const int* cand = h->precision == SBP_FP32 ? cand32 : cand64;
+    const int ncand = h->precision == SBP_FP32 ? 6 : 1;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int best = 0;
     float best_ms = 1e30f;
+    // candidates are timed on leapfrog steps (the launch pattern that matters); the state they
+    // overwrite is saved first and put back afterwards
     StepArgs a{};
     a.cur = h->cur;
     a.with_data = 0;
+    a.dt2 = 0.0;
+    a.dt2f = 0.f;
+    std::vector<void*> keep;
+    for (auto& hb : h->blocks) {
+        const size_t bytes = 2 * (size_t)hb.n2 * hb.pitch * h->esize;
+        void* p = h->dalloc(bytes);
+        if (!p) {
+            for (void* q : keep) h->dfree(q);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return h->fail(SBP_E_OOM, "autotune state copy");
+        }
+        cudaMemcpy(p, hb.u[1 - h->cur], bytes, cudaMemcpyDeviceToDevice);
+        keep.push_back(p);
+    }
+    auto put_back = [&]() {
+        for (size_t b = 0; b < h->blocks.size(); ++b) {
+            const HostBlock& hb = h->blocks[b];
+            cudaMemcpy(hb.u[1 - h->cur], keep[b], 2 * (size_t)hb.n2 * hb.pitch * h->esize, cudaMemcpyDeviceToDevice);
+            h->dfree(keep[b]);
+        }
+    };
     const int saved = h->rows_per_cta;
+    const bool saved_ov = h->overlap;
     long long saved_l[SBP_PROF_FAMILIES];
     for (int k = 0; k < SBP_PROF_FAMILIES; ++k) saved_l[k] = h->launches[k];
-    for (int c : cand) {
-        h->rows_per_cta = c;
-        float tot = 0.f;
+    auto time_it = [&](float& tot) -> int {
+        tot = 0.f;
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, 0);
-            int rc = run_operator(h, a, 1, 0);   // apply mode: the state is left untouched
+            int rc = run_operator(h, a, 0, 0);   // a step without data from the current level
             cudaEventRecord(e1, 0);
-            if (rc != SBP_OK) {
-                h->rows_per_cta = saved;
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return rc;
-            }
+            if (rc != SBP_OK) return rc;
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0) tot += ms;            // first repetition is a warm-up
         }
+        return SBP_OK;
+    };
+    auto restore = [&](int rc) {
+        cudaDeviceSynchronize();
+        put_back();
+        h->rows_per_cta = saved;
+        h->overlap = saved_ov;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    };
+    h->overlap = false;
+    for (int ci = 0; ci < ncand; ++ci) {
+        h->rows_per_cta = cand[ci];
+        float tot;
+        const int rc = time_it(tot);
+        if (rc != SBP_OK) return restore(rc);
         if (tot < best_ms) {
             best_ms = tot;
-            best = c;
+            best = cand[ci];
         }
     }
+    h->rows_per_cta = best;
+    h->overlap = true;
+    float tot_ov;
+    {
+        const int rc = time_it(tot_ov);
+        if (rc != SBP_OK) return restore(rc);
+    }
+    const bool best_ov = tot_ov < best_ms;
+    h->overlap = best_ov;
+    cudaDeviceSynchronize();
+    put_back();
     for (int k = 0; k < SBP_PROF_FAMILIES; ++k) h->launches[k] = saved_l[k];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->rows_per_cta = best;
     if (h->graph_exec) {   // the captured graph used the previous shape
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
     }
     if (rows_out) *rows_out = best;
+    if (overlap_out) *overlap_out = best_ov ? 1 : 0;
     return check_kernel_errors(h);
 }
 

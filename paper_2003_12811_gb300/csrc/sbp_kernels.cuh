@@ -534,16 +534,20 @@ template <int O> struct StripTile {
     static constexpr int THREADS = 32 * S;
 };
 
+// One launch covers the strips of every block: tiles[blockIdx.x] = (block, tile of that block),
+// ordered by the host so that the costliest tiles (interface bands, side bands) start first.
 template <typename T, int O, int MODE>
 __global__ void __launch_bounds__(StripTile<O>::THREADS, 3)
-k_strip_tile(BlockDev B, const BlockDev* __restrict__ blocks, StepArgs a, double beta) {
+k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles, StepArgs a, double beta) {
     using ST = StripTile<O>;
     constexpr int S = ST::S, H = ST::HALO, NT = ST::THREADS;
     extern __shared__ __align__(16) unsigned char strip_smem[];
     T* sm = reinterpret_cast<T*>(strip_smem);
+    const int2 tt = tiles[blockIdx.x];
+    const BlockDev& B = blocks[tt.x];
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int nbx = (n1 + 31) / 32, nby = (n2 - 2 * S + 31) / 32;
-    int t = blockIdx.x, x0, y0, w, h;
+    int t = tt.y, x0, y0, w, h;
     bool along_x;
     if (t < 2 * nbx) {
         along_x = true;

@@ -72,7 +72,7 @@ class GpuBackend:
             if key not in self._tuned:
                 self._tuned[key] = S.sbp_autotune()
             else:
-                S.sbp_set_tuning(self._tuned[key])
+                S.sbp_set_tuning(*self._tuned[key])
         return _GpuShot(S, torch.cuda.Stream(), dt, torch)
 
 

@@ -46,9 +46,9 @@ def test_autotune_choice_does_not_change_results():
     dt = A.suggest_dt(0.3)
     for S in (A, B):
         S.set_state(_zero(P), _zero(P), 0.0)
-    rows = B.sbp_autotune()
-    assert rows in (0, 16, 32, 64, 128, 256)
-    B.sbp_set_tuning(16 if rows != 16 else 32)
+    rows, ov = B.sbp_autotune()
+    assert rows in (0, 16, 32, 64, 128, 256) and ov in (0, 1)
+    B.sbp_set_tuning(16 if rows != 16 else 32, 1 - ov)   # the other shape and overlap choice
     A.step(30, dt)
     B.step(30, dt)
     for x, y in zip(A.state()[1], B.state()[1]):
