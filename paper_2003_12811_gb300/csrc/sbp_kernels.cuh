@@ -336,24 +336,35 @@ __device__ void face_sat_node(const BlockDev* __restrict__ blocks, const BlockDe
     // rows of D with a non-zero in column s: the interior band s-Q..s+Q plus, near an end, every
     // boundary row (boundary rows span columns 0..NCOL-1, which can reach past s+Q)
     const int Nt = nf;
-    int lo = s - Ord<O>::Q, hi = s + Ord<O>::Q;
-    if (s < Ord<O>::NCOL) { lo = 0; hi = max(hi, Ord<O>::NB - 1); }
-    if (s >= Nt - Ord<O>::NCOL) { hi = Nt - 1; lo = min(lo, Nt - Ord<O>::NB); }
-    if (lo < 0) lo = 0;
-    if (hi > Nt - 1) hi = Nt - 1;
     T tt0 = T(0), tt1 = T(0);
-    for (int sp = lo; sp <= hi; ++sp) {
-        const T dc = dcoefT<O, T>(Nt, sp, s);
-        if (dc == T(0)) continue;
+    auto tterm = [&](int sp, T wgt) {
         T v0, v1;
         jump(sp, v0, v1);
         int j1, j2;
         face_at(B, F, sp, 0, j1, j2);
-        const T b0 = nu * (c(plane_nt(m, 0, 0), j1, j2) * v0 + c(plane_nt(m, 1, 0), j1, j2) * v1);
-        const T b1 = nu * (c(plane_nt(m, 0, 1), j1, j2) * v0 + c(plane_nt(m, 1, 1), j1, j2) * v1);
-        const T wgt = dc * hweightT<O, T>(Nt, sp);
-        tt0 += wgt * b0;
-        tt1 += wgt * b1;
+        tt0 += wgt * nu * (c(plane_nt(m, 0, 0), j1, j2) * v0 + c(plane_nt(m, 1, 0), j1, j2) * v1);
+        tt1 += wgt * nu * (c(plane_nt(m, 0, 1), j1, j2) * v0 + c(plane_nt(m, 1, 1), j1, j2) * v1);
+    };
+    if (s >= Ord<O>::NCOL && s < Nt - Ord<O>::NCOL) {
+        // column s meets only interior rows s-Q..s+Q of D (weight 1): a fixed, unrolled sum whose
+        // loads (the neighbour's traces across an interface) can all be in flight together
+#pragma unroll
+        for (int k = 1; k <= Ord<O>::Q; ++k) {
+            const T ak = Ord<O>::template aT<T>(k - 1);
+            tterm(s - k, ak);        // row s-k has +a_k in column s
+            tterm(s + k, -ak);       // row s+k has -a_k in column s
+        }
+    } else {
+        int lo = s - Ord<O>::Q, hi = s + Ord<O>::Q;
+        if (s < Ord<O>::NCOL) { lo = 0; hi = max(hi, Ord<O>::NB - 1); }
+        if (s >= Nt - Ord<O>::NCOL) { hi = Nt - 1; lo = min(lo, Nt - Ord<O>::NB); }
+        if (lo < 0) lo = 0;
+        if (hi > Nt - 1) hi = Nt - 1;
+        for (int sp = lo; sp <= hi; ++sp) {
+            const T dc = dcoefT<O, T>(Nt, sp, s);
+            if (dc == T(0)) continue;
+            tterm(sp, dc * hweightT<O, T>(Nt, sp));
+        }
     }
     const T tfac = (m == 0 ? ih2T<T>(B) : ih1T<T>(B)) / hweightT<O, T>(Nt, s);
     T f0 = half * tt0 * tfac - (z00 * w0 + z01 * w1);
