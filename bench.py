@@ -34,6 +34,10 @@ import workloads as W  # noqa: E402
 METRIC = "grid-pt updates/s"
 UNIT = "node-updates/s"
 BYTES_PER_NODE = {"fp32": 68, "fp64": 136}     # 17 words: u^n 2, u^{n-1} 2, u^{n+1} 2, c 10, 1/(rho J) 1
+# DRAM bytes per node of one FP32 interior launch (dram__bytes_read.sum + dram__bytes_write.sum of
+# k_interior_march<6,0> at 2 x 1601x801, scaled by nodes; profiles/launches_topography_fp32.md).
+# Set to None whenever that kernel changes until it is measured again.
+TRAFFIC_BYTES_PER_NODE = {"fp32": 79136256 / 1239489, "fp64": None}
 FALLBACK_HBM_GBS = 6800.0
 N1, N2 = 4001, 2001
 # crop of the workload the oracle is timed on: a 401-column window around the source spanning
@@ -394,7 +398,9 @@ def main():
                        "tuning": {"rows_per_cta": tune_rows, "strips_concurrent": bool(tune_overlap)},
                        "l2": f"inputs larger than L2 ({bpn * nodes / 1e9:.2f} GB moved per step vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC_BYTES_PER_NODE[prec] * (interior_nodes // len(P.blocks))
+                                     if TRAFFIC_BYTES_PER_NODE[prec] else None),
                          "kernel": "k_interior", "peak_source": peak_src,
                          "bytes_per_node": bpn, "units_per_launch": interior_nodes // len(P.blocks),
                          "kernel_ms_per_step": interior_ms,
