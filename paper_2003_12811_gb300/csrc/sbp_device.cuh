@@ -67,6 +67,16 @@ template <> struct Edge<6> {
     }
 };
 
+// support [LO, HI] of the interior edge weights (offsets of b relative to the edge's left node)
+template <int O> struct EdgeRange {
+    static constexpr int LO = O == 2 ? SBP2_ELO : (O == 4 ? SBP4_ELO : SBP6_ELO);
+    static constexpr int HI = O == 2 ? SBP2_EHI : (O == 4 ? SBP4_EHI : SBP6_EHI);
+};
+// coefficient e_{m,kk} (FP32) of b_{i+kk} in E_m(i); a compile-time constant for constant m, kk
+template <int O> __device__ __forceinline__ float edge_w(int m, int kk) {
+    return Edge<O>::template e<float>(m, [&](int q) { return q == kk ? 1.f : 0.f; });
+}
+
 // lowest b offset used by E_m (E_m is evaluated at i only if i + elo(m) stays in range)
 template <int O> __host__ __device__ constexpr int edge_lo(int m) {
     return O == 2 ? 0 : (O == 4 ? (m == 1 ? -1 : 0) : (m == 1 ? -2 : (m == 2 ? -1 : 0)));

@@ -15,7 +15,9 @@
 //    so every edge weight E_m is formed once and F_m waits m rows in a short delay line;
 //  * the x-direction fluxes g1 = c_1j2l D_2 u_l of the current row are exchanged through a
 //    double-buffered shared row (one barrier per row);
-//  * 1/(rho J) and u^{n-1} of the output row are loaded from global memory two rows ahead.
+//  * 1/(rho J) and u^{n-1} of the output row are loaded from global memory two rows ahead;
+//  * the two components of the displacement and of every flux are carried as float2 and
+//    combined with packed FP32x2 instructions (one issue slot for both).
 #pragma once
 #include <cuda.h>
 #include "sbp_device.cuh"
@@ -39,6 +41,13 @@ struct MarchMaps {
     CUtensorMap u[2];   // [2][n2][pitch], box [2][MR][MBOXW]
     CUtensorMap c;      // [10][n2][pitch], box [10][MR][MBOXW]
 };
+
+// packed FP32x2 arithmetic (one instruction for both halves)
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 // tile geometry shared with the host: first column, columns per CTA, rows per CTA
 __host__ __device__ inline int march_x0(int strip) { return (strip / 4) * 4; }
@@ -109,41 +118,50 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     const float ih1 = B.ih1f, ih2 = B.ih2f;
     const float ih11 = ih1 * ih1, ih22 = ih2 * ih2;
 
-    // register queues, index 0 = oldest row (qb: rows r-q+1 .. r+q of the c_2j2l fields)
+    // the two displacement components (and the two components of every flux) travel together
+    // as float2 and are combined with packed FP32x2 arithmetic.  Register queues, index 0 =
+    // oldest row: qu displacement, qg fluxes g2, qh halo displacement (rows r-q..r+q); qb the
+    // c_2j2l fields (c_2121, c_2122) and qc (c_2222) for rows r-q+1..r+q
     constexpr int LB = 2 * Q;
-    float qu0[L], qu1[L], qb0[LB], qb1[LB], qb2[LB], qg0[L], qg1[L], qh0[L], qh1[L];
+    float2 qu[L], qg[L], qh[L], qb[LB];
+    float qc[LB];
 #pragma unroll
-    for (int k = 0; k < L; ++k) qu0[k] = qu1[k] = qg0[k] = qg1[k] = qh0[k] = qh1[k] = 0.f;
+    for (int k = 0; k < L; ++k) qu[k] = qg[k] = qh[k] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < LB; ++k) qb0[k] = qb1[k] = qb2[k] = 0.f;
-    // delay lines of the y edge fluxes: fy*[m-1][0] = F_m(r-m) .. fy*[m-1][m-1] = F_m(r-1)
-    float fy0[Q][Q], fy1[Q][Q];
+    for (int k = 0; k < LB; ++k) {
+        qb[k] = make_float2(0.f, 0.f);
+        qc[k] = 0.f;
+    }
+    // delay lines of the y edge fluxes: fy[m-1][0] = F_m(r-m) .. fy[m-1][m-1] = F_m(r-1)
+    float2 fy[Q][Q];
 #pragma unroll
     for (int m = 0; m < Q; ++m)
 #pragma unroll
-        for (int k = 0; k < Q; ++k) fy0[m][k] = fy1[m][k] = 0.f;
+        for (int k = 0; k < Q; ++k) fy[m][k] = make_float2(0.f, 0.f);
     // threads 0..2Q-1 also follow one halo column each (x0-Q..x0-1, x0+128..x0+127+Q) for g1
     const int hc = tx < Q ? MXOFF - Q + tx : MXOFF + MTHREADS + (tx - Q);
     const bool halo = tx < 2 * Q;
     // prefetched 1/(rho J) and u^{n-1}: *_c for the row being output, *_n for the next row
-    float w_c = 0.f, u0_c = 0.f, u1_c = 0.f, w_n = 0.f, u0_n = 0.f, u1_n = 0.f;
-    auto load_row = [&](int r, float& wv, float& v0, float& v1) {
+    float w_c = 0.f, w_n = 0.f;
+    float2 up_c = make_float2(0.f, 0.f), up_n = make_float2(0.f, 0.f);
+    auto load_row = [&](int r, float& wv, float2& v) {
         if (MODE == 0 && col_ok && r >= ys && r < ye) {
             const size_t gi = (size_t)r * P + gx;
             wv = __ldg(reinterpret_cast<const float*>(B.w) + gi);
             const float* Un = reinterpret_cast<const float*>(B.u[1 - a.cur]);
-            v0 = Un[gi];
-            v1 = Un[gi + plane];
+            v = make_float2(Un[gi], Un[gi + plane]);
         }
     };
-    load_row(ys, w_c, u0_c, u1_c);
-    load_row(ys + 1, w_n, u0_n, u1_n);
+    load_row(ys, w_c, up_c);
+    load_row(ys + 1, w_n, up_n);
     auto rotate = [&](int r) {   // after row r: current <- next, next <- row r + 2
         w_c = w_n;
-        u0_c = u0_n;
-        u1_c = u1_n;
-        load_row(r + 2, w_n, u0_n, u1_n);
+        up_c = up_n;
+        load_row(r + 2, w_n, up_n);
     };
+    // displacement pair / field pairs at ring offset o of a row pointer
+    auto U2 = [&](const float* p, int o) { return make_float2(p[poff(0) + o], p[poff(1) + o]); };
+    auto X2 = [&](const float* p, int o) { return make_float2(p[poff(2) + o], p[poff(3) + o]); };
 
     bool ok = true;
     int waited = 0;                               // chunks whose completion every thread has seen
@@ -158,97 +176,79 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         // --- lookahead row: own-column values into the queues, g2 at (x, Lr)
         {
             const float* pL = rowp(Lr) + cc;
-            const float u0n = pL[poff(0)], u1n = pL[poff(1)];
-            float d0 = 0.f, d1 = 0.f;
+            float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 1; k <= Q; ++k) {
-                d0 += ak[k - 1] * (pL[poff(0) + k] - pL[poff(0) - k]);
-                d1 += ak[k - 1] * (pL[poff(1) + k] - pL[poff(1) - k]);
-            }
-            d0 *= ih1;
-            d1 *= ih1;
+            for (int k = 1; k <= Q; ++k) d = ffma2(bc2(ak[k - 1]), fsub2(U2(pL, k), U2(pL, -k)), d);
+            d = fmul2(d, bc2(ih1));
             const float m6 = pL[poff(8)], m7 = pL[poff(9)], m8 = pL[poff(10)], m9 = pL[poff(11)];
 #pragma unroll
             for (int k = 0; k < L - 1; ++k) {
-                qu0[k] = qu0[k + 1]; qu1[k] = qu1[k + 1];
-                qg0[k] = qg0[k + 1]; qg1[k] = qg1[k + 1];
+                qu[k] = qu[k + 1];
+                qg[k] = qg[k + 1];
             }
 #pragma unroll
             for (int k = 0; k < LB - 1; ++k) {
-                qb0[k] = qb0[k + 1]; qb1[k] = qb1[k + 1]; qb2[k] = qb2[k + 1];
+                qb[k] = qb[k + 1];
+                qc[k] = qc[k + 1];
             }
-            qu0[L - 1] = u0n;
-            qu1[L - 1] = u1n;
-            qb0[LB - 1] = pL[poff(5)];
-            qb1[LB - 1] = pL[poff(6)];
-            qb2[LB - 1] = pL[poff(7)];
-            qg0[L - 1] = m6 * d0 + m8 * d1;       // g2_1 = c_1121 D_1 u_1 + c_1221 D_1 u_2
-            qg1[L - 1] = m7 * d0 + m9 * d1;       // g2_2 = c_1122 D_1 u_1 + c_1222 D_1 u_2
+            qu[L - 1] = U2(pL, 0);
+            qb[LB - 1] = make_float2(pL[poff(5)], pL[poff(6)]);
+            qc[LB - 1] = pL[poff(7)];
+            // g2_1 = c_1121 D_1 u_1 + c_1221 D_1 u_2,  g2_2 = c_1122 D_1 u_1 + c_1222 D_1 u_2
+            qg[L - 1] = ffma2(make_float2(m6, m7), bc2(d.x), fmul2(make_float2(m8, m9), bc2(d.y)));
             if (halo) {
 #pragma unroll
-                for (int k = 0; k < L - 1; ++k) {
-                    qh0[k] = qh0[k + 1];
-                    qh1[k] = qh1[k + 1];
-                }
-                qh0[L - 1] = at(0, Lr, hc);
-                qh1[L - 1] = at(1, Lr, hc);
+                for (int k = 0; k < L - 1; ++k) qh[k] = qh[k + 1];
+                qh[L - 1] = make_float2(at(0, Lr, hc), at(1, Lr, hc));
             }
         }
         // --- narrow y in edge-flux form: F_m(r) from the queued rows, F_m(r-m) from the delay
         // lines (needed from the first output row on, so formed from row ys - Q on)
-        float ry0 = 0.f, ry1 = 0.f;
+        float2 ry = make_float2(0.f, 0.f);
         if (r >= ys - Q) {
-            const float uc0 = qu0[Q], uc1 = qu1[Q];
 #pragma unroll
             for (int m = 1; m <= Q; ++m) {
-                auto B0p = [&](int k) { return qb0[k + Q - 1]; };
-                auto B1p = [&](int k) { return qb1[k + Q - 1]; };
-                auto B2p = [&](int k) { return qb2[k + Q - 1]; };
-                const float e0 = Edge<O>::template e<float>(m, B0p), e1 = Edge<O>::template e<float>(m, B1p),
-                            e2 = Edge<O>::template e<float>(m, B2p);
-                const float dp0 = qu0[Q + m] - uc0, dp1 = qu1[Q + m] - uc1;
-                const float f0 = e0 * dp0 + e1 * dp1, f1 = e1 * dp0 + e2 * dp1;
-                ry0 += f0 - fy0[m - 1][0];
-                ry1 += f1 - fy1[m - 1][0];
+                float2 e01 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < m - 1; ++k) {
-                    fy0[m - 1][k] = fy0[m - 1][k + 1];
-                    fy1[m - 1][k] = fy1[m - 1][k + 1];
+                for (int k = EdgeRange<O>::LO; k <= EdgeRange<O>::HI; ++k) {
+                    const float c = edge_w<O>(m, k);
+                    if (c != 0.f) e01 = ffma2(bc2(c), qb[k + Q - 1], e01);
                 }
-                fy0[m - 1][m - 1] = f0;
-                fy1[m - 1][m - 1] = f1;
+                const float e2 = Edge<O>::template e<float>(m, [&](int k) { return qc[k + Q - 1]; });
+                const float2 dp = fsub2(qu[Q + m], qu[Q]);
+                // (F0, F1) = (e0, e1) dp_1 + (e1, e2) dp_2
+                const float2 f = ffma2(e01, bc2(dp.x), fmul2(make_float2(e01.y, e2), bc2(dp.y)));
+                ry = fadd2(ry, fsub2(f, fy[m - 1][0]));
+#pragma unroll
+                for (int k = 0; k < m - 1; ++k) fy[m - 1][k] = fy[m - 1][k + 1];
+                fy[m - 1][m - 1] = f;
             }
         }
         if (r < ys) continue;                    // queue fill (prologue)
         // --- g1 at (x, r) into the shared row
         const int par = r & 1;
         {
-            float d0 = 0.f, d1 = 0.f;
+            float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 1; k <= Q; ++k) {
-                d0 += ak[k - 1] * (qu0[Q + k] - qu0[Q - k]);
-                d1 += ak[k - 1] * (qu1[Q + k] - qu1[Q - k]);
-            }
-            d0 *= ih2;
-            d1 *= ih2;
+            for (int k = 1; k <= Q; ++k) d = ffma2(bc2(ak[k - 1]), fsub2(qu[Q + k], qu[Q - k]), d);
+            d = fmul2(d, bc2(ih2));
             const float* pr0 = rowp(r) + cc;
             const float m6 = pr0[poff(8)], m7 = pr0[poff(9)], m8 = pr0[poff(10)], m9 = pr0[poff(11)];
-            g1s[(par * 2 + 0) * W + cc] = m6 * d0 + m7 * d1;
-            g1s[(par * 2 + 1) * W + cc] = m8 * d0 + m9 * d1;
+            // g1_1 = c_1121 D_2 u_1 + c_1122 D_2 u_2,  g1_2 = c_1221 D_2 u_1 + c_1222 D_2 u_2
+            const float2 g = ffma2(make_float2(m6, m8), bc2(d.x), fmul2(make_float2(m7, m9), bc2(d.y)));
+            g1s[(par * 2 + 0) * W + cc] = g.x;
+            g1s[(par * 2 + 1) * W + cc] = g.y;
         }
         // halo columns of g1 (x0-Q .. x0-1 and x0+128 .. x0+127+Q), from the halo queues
         if (halo) {
-            float d0 = 0.f, d1 = 0.f;
+            float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 1; k <= Q; ++k) {
-                d0 += ak[k - 1] * (qh0[Q + k] - qh0[Q - k]);
-                d1 += ak[k - 1] * (qh1[Q + k] - qh1[Q - k]);
-            }
-            d0 *= ih2;
-            d1 *= ih2;
+            for (int k = 1; k <= Q; ++k) d = ffma2(bc2(ak[k - 1]), fsub2(qh[Q + k], qh[Q - k]), d);
+            d = fmul2(d, bc2(ih2));
             const float m6 = at(8, r, hc), m7 = at(9, r, hc), m8 = at(10, r, hc), m9 = at(11, r, hc);
-            g1s[(par * 2 + 0) * W + hc] = m6 * d0 + m7 * d1;
-            g1s[(par * 2 + 1) * W + hc] = m8 * d0 + m9 * d1;
+            const float2 g = ffma2(make_float2(m6, m8), bc2(d.x), fmul2(make_float2(m7, m9), bc2(d.y)));
+            g1s[(par * 2 + 0) * W + hc] = g.x;
+            g1s[(par * 2 + 1) * W + hc] = g.y;
         }
         if (__syncthreads_or(!ok)) {
             // a bounded wait ran out: record it, drain this CTA's issued copies (bounded), stop
@@ -274,40 +274,40 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         if (!col_ok) { rotate(r); continue; }
         // --- narrow x: edge weights from the x fields of row r (columns x-Q-2 .. x+Q)
         const float* pr = rowp(r) + cc;
-        const float uc0 = pr[poff(0)], uc1 = pr[poff(1)];
-        float rx0 = 0.f, rx1 = 0.f;
+        const float2 uc = U2(pr, 0);
+        float2 rx = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 1; m <= Q; ++m) {
-            auto B0p = [&](int k) { return pr[poff(2) + k]; };
-            auto B1p = [&](int k) { return pr[poff(3) + k]; };
-            auto B2p = [&](int k) { return pr[poff(4) + k]; };
-            auto B0m = [&](int k) { return pr[poff(2) - m + k]; };
-            auto B1m = [&](int k) { return pr[poff(3) - m + k]; };
-            auto B2m = [&](int k) { return pr[poff(4) - m + k]; };
-            const float e0p = Edge<O>::template e<float>(m, B0p), e1p = Edge<O>::template e<float>(m, B1p),
-                        e2p = Edge<O>::template e<float>(m, B2p);
-            const float e0m = Edge<O>::template e<float>(m, B0m), e1m = Edge<O>::template e<float>(m, B1m),
-                        e2m = Edge<O>::template e<float>(m, B2m);
-            const float dp0 = pr[poff(0) + m] - uc0, dp1 = pr[poff(1) + m] - uc1;
-            const float dm0 = pr[poff(0) - m] - uc0, dm1 = pr[poff(1) - m] - uc1;
-            rx0 += e0p * dp0 + e1p * dp1 + e0m * dm0 + e1m * dm1;
-            rx1 += e1p * dp0 + e2p * dp1 + e1m * dm0 + e2m * dm1;
+            float2 e01p = make_float2(0.f, 0.f), e01m = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = EdgeRange<O>::LO; k <= EdgeRange<O>::HI; ++k) {
+                const float c = edge_w<O>(m, k);
+                if (c != 0.f) {
+                    e01p = ffma2(bc2(c), X2(pr, k), e01p);
+                    e01m = ffma2(bc2(c), X2(pr, k - m), e01m);
+                }
+            }
+            const float e2p = Edge<O>::template e<float>(m, [&](int k) { return pr[poff(4) + k]; });
+            const float e2m = Edge<O>::template e<float>(m, [&](int k) { return pr[poff(4) - m + k]; });
+            const float2 dp = fsub2(U2(pr, m), uc), dm = fsub2(U2(pr, -m), uc);
+            rx = ffma2(e01p, bc2(dp.x), rx);
+            rx = ffma2(make_float2(e01p.y, e2p), bc2(dp.y), rx);
+            rx = ffma2(e01m, bc2(dm.x), rx);
+            rx = ffma2(make_float2(e01m.y, e2m), bc2(dm.y), rx);
         }
-        float r0 = rx0 * ih11 + ry0 * ih22;
-        float r1 = rx1 * ih11 + ry1 * ih22;
+        float2 rr = ffma2(rx, bc2(ih11), fmul2(ry, bc2(ih22)));
         // --- mixed: D_1 g1 from the shared row, D_2 g2 from the queue
-        float m10 = 0.f, m11 = 0.f, m20 = 0.f, m21 = 0.f;
+        float2 m1 = make_float2(0.f, 0.f), m2 = make_float2(0.f, 0.f);
         const float* g10 = g1s + (par * 2 + 0) * W + cc;
         const float* g11 = g1s + (par * 2 + 1) * W + cc;
 #pragma unroll
         for (int k = 1; k <= Q; ++k) {
-            m10 += ak[k - 1] * (g10[k] - g10[-k]);
-            m11 += ak[k - 1] * (g11[k] - g11[-k]);
-            m20 += ak[k - 1] * (qg0[Q + k] - qg0[Q - k]);
-            m21 += ak[k - 1] * (qg1[Q + k] - qg1[Q - k]);
+            m1 = ffma2(bc2(ak[k - 1]), fsub2(make_float2(g10[k], g11[k]), make_float2(g10[-k], g11[-k])), m1);
+            m2 = ffma2(bc2(ak[k - 1]), fsub2(qg[Q + k], qg[Q - k]), m2);
         }
-        r0 += m10 * ih1 + m20 * ih2;
-        r1 += m11 * ih1 + m21 * ih2;
+        rr = ffma2(m1, bc2(ih1), rr);
+        rr = ffma2(m2, bc2(ih2), rr);
+        float r0 = rr.x, r1 = rr.y;
         const size_t gi = (size_t)r * P + gx;
         if (a.with_data && B.jf) {
             const float* __restrict__ JF = reinterpret_cast<const float*>(B.jf);
@@ -320,9 +320,9 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         }
         if (MODE == 0) {
             float* __restrict__ Un = reinterpret_cast<float*>(B.u[1 - a.cur]);
-            const float dt2 = a.dt2f;
-            Un[gi] = 2.f * uc0 - u0_c + dt2 * w_c * r0;
-            Un[gi + plane] = 2.f * uc1 - u1_c + dt2 * w_c * r1;
+            const float2 nu = ffma2(bc2(a.dt2f * w_c), make_float2(r0, r1), fsub2(fadd2(uc, uc), up_c));
+            Un[gi] = nu.x;
+            Un[gi + plane] = nu.y;
         } else {
             float* __restrict__ R = reinterpret_cast<float*>(B.r);
             R[gi] = r0;
