@@ -166,8 +166,9 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     bool ok = true;
     int waited = 0;                               // chunks whose completion every thread has seen
     int next_issue = MNCH < nchunks ? MNCH : nchunks;   // meaningful in thread 0 only
-    // the march: step r consumes lookahead row Lr = r + Q; outputs row r when r >= ys
-    for (int r = rb - Q; r < ye; ++r) {
+    // the march: step r consumes lookahead row Lr = r + Q and outputs row r when r >= ys.
+    // look(r) pushes row Lr into the queues; yflux() forms the y edge fluxes of the queue centre
+    auto look = [&](int r) {
         const int Lr = r + Q;
         if (((Lr - rb) % MR) == 0) {
             ok = wait_row(Lr) && ok;
@@ -202,10 +203,12 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
                 qh[L - 1] = make_float2(at(0, Lr, hc), at(1, Lr, hc));
             }
         }
+    };
+    auto yflux = [&]() -> float2 {
         // --- narrow y in edge-flux form: F_m(r) from the queued rows, F_m(r-m) from the delay
         // lines (needed from the first output row on, so formed from row ys - Q on)
         float2 ry = make_float2(0.f, 0.f);
-        if (r >= ys - Q) {
+        {
 #pragma unroll
             for (int m = 1; m <= Q; ++m) {
                 float2 e01 = make_float2(0.f, 0.f);
@@ -224,7 +227,19 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
                 fy[m - 1][m - 1] = f;
             }
         }
-        if (r < ys) continue;                    // queue fill (prologue)
+        return ry;
+    };
+    // prologue: fill the queues, then the delay lines; the output rows follow in a loop of its
+    // own, unrolled so that the queue shifts become register renames
+    for (int r = rb - Q; r < ys - Q; ++r) look(r);
+    for (int r = ys - Q; r < ys; ++r) {
+        look(r);
+        (void)yflux();
+    }
+#pragma unroll 4
+    for (int r = ys; r < ye; ++r) {
+        look(r);
+        const float2 ry = yflux();
         // --- g1 at (x, r) into the shared row
         const int par = r & 1;
         {
