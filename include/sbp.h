@@ -175,7 +175,8 @@ int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out);
 /* Kernel timing for benchmarks.  sbp_profile(h, 1) resets the counters and, until
  * sbp_profile(h, 0), makes every kernel launch record CUDA events (on the launch stream)
  * around its family: [0] interior stencil, [1] boundary strips (closures, and the SAT terms,
- * which the strip kernel forms itself), [2] reserved (no kernel), [3] point sources,
+ * which the strip kernel forms itself), [2] interface traces (k_face_trace: each interface
+ * side's displacement, traction and penalty share, read by the other side's SAT terms), [3] point sources,
  * [4] gradient interior, [5] gradient strips,
  * [6] gradient face terms, receiver recording and adjoint injection, [7] misfit reduction and
  * gradient output.  sbp_profile_read returns the accumulated milliseconds per family

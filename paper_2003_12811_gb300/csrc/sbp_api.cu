@@ -38,6 +38,7 @@ struct HostFace {
     void* ju = nullptr;
     void* g = nullptr;
     void* sat = nullptr;
+    void* tr = nullptr;       // interface faces: trace of this side (k_face_trace), 7 x nf
 };
 
 struct HostBlock {
@@ -57,6 +58,7 @@ struct HostBlock {
     MarchMaps mmaps;          // FP32 column-marching interior kernel tensor maps
     void* psi[2] = {nullptr, nullptr};   // adjoint fields (sbp_misfit_gradient), allocated on first use
     MarchMaps pmaps;          // marching-kernel maps over the adjoint fields
+    CUtensorMap* d_smaps = nullptr;   // strip-tile band-box maps on the device: [0..2] state u0, u1, c; [3..5] adjoint
 };
 
 int order_nb(int o) { return o == 2 ? SBP2_NB : (o == 4 ? SBP4_NB : SBP6_NB); }
@@ -87,6 +89,8 @@ struct sbp_handle {
     BlockDev* d_blocks = nullptr;
     FaceRef* d_refs = nullptr;
     int nrefs = 0, nface_nodes = 0;
+    FaceRef* d_trefs = nullptr;   // interface faces (k_face_trace), numbered like d_refs
+    int ntrefs = 0, ntrace_nodes = 0;
     int cur = 0;
     double t = 0.0;
     int nbasis = 0;
@@ -241,7 +245,9 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
         D.ju = F.ju;
         D.g = F.g;
         D.sat = F.sat;
+        D.tr = F.tr;
     }
+    b.smaps = hb.d_smaps;
     return b;
 }
 
@@ -250,6 +256,7 @@ BlockDev make_view_adj(const sbp_handle* h, const HostBlock& hb) {
     BlockDev b = make_view(h, hb);
     b.u[0] = hb.psi[0];
     b.u[1] = hb.psi[1];
+    b.smaps = hb.d_smaps ? hb.d_smaps + 3 : nullptr;
     return b;
 }
 
@@ -282,15 +289,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 3-D map over `planes` consecutive float planes of n2 x pitch, box [planes][rows][width]
-bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows, int width = TBOXW) {
+bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows, int width = TBOXW, int esize = 4) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)n2, (cuuint64_t)planes};
-    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * n2 * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)pitch * n2 * esize};
     cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// strip-tile band box of the block's order (tiles along x1)
+template <int O> void strip_box(int& bw, int& bh) {
+    bw = StripTile<O>::BWB;
+    bh = StripTile<O>::BHB;
+}
+
+// the strip-tile band-box maps of two displacement buffers and the coefficients, written to dst[0..2]
+bool make_strip_maps(const sbp_handle* h, const HostBlock& hb, void* u0, void* u1, CUtensorMap* dst) {
+    int bw, bh;
+    if (h->order == 2) strip_box<2>(bw, bh);
+    else if (h->order == 4) strip_box<4>(bw, bh);
+    else strip_box<6>(bw, bh);
+    const int es = (int)h->esize;
+    return make_map(&dst[0], u0, hb.pitch, hb.n2, 2, bh, bw, es) &&
+           make_map(&dst[1], u1, hb.pitch, hb.n2, 2, bh, bw, es) &&
+           make_map(&dst[2], hb.c, hb.pitch, hb.n2, 10, bh, bw, es);
 }
 
 template <int O> int tma_rows() { return TmaTile<O>::SY; }
@@ -338,12 +364,17 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
             }
         }
     }
+    if (h->ntrefs > 0) {
+        ProfScope ps(h, 2, sst, 1);
+        k_face_trace<T, O><<<grid_for(h->ntrace_nodes, 128), 128, 0, sst>>>(tab, h->d_trefs, h->ntrefs,
+                                                                           h->ntrace_nodes, a, h->beta);
+    }
     {
         ProfScope ps(h, 1, sst, 1);
         using ST = StripTile<O>;
-        constexpr size_t ssm = (size_t)ST::ELEMS * sizeof(T);
-        if (mode == 0) k_strip_tile<T, O, 0><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta);
-        else k_strip_tile<T, O, 1><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta);
+        constexpr size_t ssm = ST::template bytes<T>();
+        if (mode == 0) k_strip_tile<T, O, 0><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err);
+        else k_strip_tile<T, O, 1><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err);
     }
     if (ovl) {
         cudaEventRecord(h->ev_join, h->aux);
@@ -376,7 +407,7 @@ int run_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bo
 
 template <typename T, int O> void set_smem_attr() {
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
-    constexpr size_t ssm = (size_t)StripTile<O>::ELEMS * sizeof(T);
+    constexpr size_t ssm = StripTile<O>::template bytes<T>();
     cudaFuncSetAttribute(k_strip_tile<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     cudaFuncSetAttribute(k_strip_tile<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     cudaFuncSetAttribute(k_interior<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -389,7 +420,7 @@ template <typename T, int O> void set_smem_attr() {
     }
 }
 
-// kernel error flags: bits 2 (tile kernel) and 4 (marching kernel) = a bounded wait ran out
+// kernel error flags: bits 2 (tile kernel), 4 (marching kernel), 8 (strip tiles) = a bounded wait ran out
 int check_kernel_errors(sbp_handle* h) {
     int e = 0;
     if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -503,6 +534,10 @@ int ensure_adjoint_buffers(sbp_handle* h) {
                 return h->fail(SBP_E_CUDA, "tensor map encoding failed (adjoint fields)");
             hb.pmaps.c = hb.mmaps.c;
         }
+        CUtensorMap sm[3];
+        if (!make_strip_maps(h, hb, hb.psi[0], hb.psi[1], sm) ||
+            cudaMemcpy(hb.d_smaps + 3, sm, sizeof(sm), cudaMemcpyHostToDevice) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "tensor map encoding failed (adjoint strip maps)");
         fresh = true;
     }
     if (!h->d_blocks_adj) {
@@ -689,8 +724,8 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             cudaEventCreateWithFlags(&h->ev_join_hi, cudaEventDisableTiming) != cudaSuccess)
             return cleanup(SBP_E_CUDA, "auxiliary streams");
     }
-    std::vector<FaceRef> refs;
-    int start = 0;
+    std::vector<FaceRef> refs, trefs;
+    int start = 0, tstart = 0;
     for (int b = 0; b < desc->nblocks; ++b) {
         const sbp_block_desc& bd = desc->blocks[b];
         HostBlock& hb = h->blocks[b];
@@ -723,6 +758,12 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             if (!F.jhat || !F.sat) return cleanup(SBP_E_OOM, "face buffers");
             refs.push_back(FaceRef{b, f, start, F.nf});
             start += F.nf;
+            if (F.kind == FACE_INTF) {
+                F.tr = h->dalloc(7 * (size_t)F.nf * es);
+                if (!F.tr) return cleanup(SBP_E_OOM, "interface trace buffers");
+                trefs.push_back(FaceRef{b, f, tstart, F.nf});
+                tstart += F.nf;
+            }
         }
         if (h->precision == SBP_FP32) {
             const int rows = o == 2 ? tma_rows<2>() : (o == 4 ? tma_rows<4>() : tma_rows<6>());
@@ -733,6 +774,14 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
                 !make_map(&hb.mmaps.u[1], hb.u[1], hb.pitch, hb.n2, 2, MR, MBOXW) ||
                 !make_map(&hb.mmaps.c, hb.c, hb.pitch, hb.n2, 10, MR, MBOXW))
                 return cleanup(SBP_E_CUDA, "tensor map encoding failed");
+        }
+        {
+            hb.d_smaps = (CUtensorMap*)h->dalloc(6 * sizeof(CUtensorMap));
+            CUtensorMap sm[3];
+            if (!hb.d_smaps) return cleanup(SBP_E_OOM, "strip tensor maps");
+            if (!make_strip_maps(h, hb, hb.u[0], hb.u[1], sm) ||
+                cudaMemcpy(hb.d_smaps, sm, sizeof(sm), cudaMemcpyHostToDevice) != cudaSuccess)
+                return cleanup(SBP_E_CUDA, "tensor map encoding failed (strip tiles)");
         }
         // coordinates -> pitched device planes
         double* tmp = (double*)h->dalloc(2 * (size_t)bd.n1 * bd.n2 * sizeof(double));
@@ -750,6 +799,13 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     h->d_blocks = (BlockDev*)h->dalloc(sizeof(BlockDev) * h->blocks.size());
     if (!h->d_refs || !h->d_blocks) return cleanup(SBP_E_OOM, "tables");
     cudaMemcpy(h->d_refs, refs.data(), sizeof(FaceRef) * refs.size(), cudaMemcpyHostToDevice);
+    h->ntrefs = (int)trefs.size();
+    h->ntrace_nodes = tstart;
+    if (!trefs.empty()) {
+        h->d_trefs = (FaceRef*)h->dalloc(sizeof(FaceRef) * trefs.size());
+        if (!h->d_trefs) return cleanup(SBP_E_OOM, "tables");
+        cudaMemcpy(h->d_trefs, trefs.data(), sizeof(FaceRef) * trefs.size(), cudaMemcpyHostToDevice);
+    }
     if (sync_views(h) != SBP_OK) return cleanup(SBP_E_CUDA, h->err);
     {
         // strip tiles (the tile numbering of k_strip_tile: 2 bands of ceil(n1/32) tiles along x1,
@@ -1163,6 +1219,7 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
         for (int f = 0; f < 4; ++f) {
             const size_t fb = align256(4 * (size_t)hb.f[f].nf * es);
             v.f[f].sat = base + off;
+            v.f[f].tr = nullptr;       // the face SATs read the neighbour directly
             off += fb;
             refs[nr++] = FaceRef{b, f, start, hb.f[f].nf};
             start += hb.f[f].nf;

@@ -209,6 +209,9 @@ struct FaceDev {
     const void* ju;           // robin: J^ U (3 x nf), type T
     const void* g;            // data: displacement g (2 x K x nf) or robin J^ g, type T
     void* sat;                // scratch of k_face_sat: face term (2 x nf), normal-spread amplitude (2 x nf), type T
+    void* tr;                 // interface faces: this side's trace per face node (7 x nf, type T) written by
+                              // k_face_trace: u_0, u_1, traction J^ tau_0, J^ tau_1, and k c_mJmL for
+                              // JL = 00, 01, 11 with k = beta d / 4 / H_m[0]; null where not kept
 };
 
 struct BlockDev {
@@ -224,6 +227,7 @@ struct BlockDev {
     const double* X;          // coordinates (2 planes)
     double* G;                // metric dX_I/dx_i (4 planes, [2 i + I])
     double* J;                // Jacobian
+    const void* smaps;        // strip-tile band-box tensor maps (CUtensorMap[3]: u[0], u[1], c)
     FaceDev f[4];
 };
 

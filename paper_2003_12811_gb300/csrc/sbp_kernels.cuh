@@ -3,6 +3,7 @@
 // point sources), the FP64 energy reduction, and the setup kernels (metric, material, CFL).
 #pragma once
 #include "sbp_device.cuh"
+#include "sbp_interior_tma.cuh"
 
 namespace sbp {
 
@@ -290,6 +291,10 @@ __device__ void face_sat_node(const BlockDev* __restrict__ blocks, const BlockDe
     const size_t pv = intf ? (size_t)V->n2 * V->pitch : 0;
     auto uv = [&](int L, int j1, int j2) { return Uv[(size_t)L * pv + (size_t)j2 * V->pitch + j1]; };
     auto cv = [&](int pl, int j1, int j2) { return Cv[(size_t)pl * pv + (size_t)j2 * V->pitch + j1]; };
+    // traces of both sides (k_face_trace, same level): replace the neighbour's reads and both tractions
+    const T* __restrict__ trU = intf ? reinterpret_cast<const T*>(F.tr) : nullptr;
+    const T* __restrict__ trV = intf ? reinterpret_cast<const T*>(FV->tr) : nullptr;
+    const bool traced = trU != nullptr && trV != nullptr;
     // jump w_L at face node sp (displacement: u - g(t); interface: u - v)
     auto jump = [&](int sp, T& w0, T& w1) {
         int j1, j2;
@@ -297,10 +302,16 @@ __device__ void face_sat_node(const BlockDev* __restrict__ blocks, const BlockDe
         w0 = u(0, j1, j2);
         w1 = u(1, j1, j2);
         if (intf) {
-            int v1, v2;
-            face_at(*V, *FV, F.reversed ? nf - 1 - sp : sp, 0, v1, v2);
-            w0 -= uv(0, v1, v2);
-            w1 -= uv(1, v1, v2);
+            const int svp = F.reversed ? nf - 1 - sp : sp;
+            if (traced) {
+                w0 -= trV[svp];
+                w1 -= trV[nf + svp];
+            } else {
+                int v1, v2;
+                face_at(*V, *FV, svp, 0, v1, v2);
+                w0 -= uv(0, v1, v2);
+                w1 -= uv(1, v1, v2);
+            }
         } else if (has_data) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -319,15 +330,23 @@ __device__ void face_sat_node(const BlockDev* __restrict__ blocks, const BlockDe
     if (!intf) {
         const T k = T(beta * dd * F.inv_h0);
         z00 = k * c00; z01 = k * c01; z11 = k * c11;
+    } else if (traced) {
+        const int sv = F.reversed ? nf - 1 - s : s;
+        z00 = trU[4 * nf + s] + trV[4 * nf + sv];
+        z01 = trU[5 * nf + s] + trV[5 * nf + sv];
+        z11 = trU[6 * nf + s] + trV[6 * nf + sv];
     } else {
         const int sv = F.reversed ? nf - 1 - s : s;
         int v1, v2;
         face_at(*V, *FV, sv, 0, v1, v2);
         const int mv = FV->m;
         const T ku = T(beta * dd / 4.0 * F.inv_h0), kv = T(beta * dd / 4.0 * FV->inv_h0);
-        z00 = ku * c00 + kv * cv(plane_nn(mv, 0, 0), v1, v2);
-        z01 = ku * c01 + kv * cv(plane_nn(mv, 0, 1), v1, v2);
-        z11 = ku * c11 + kv * cv(plane_nn(mv, 1, 1), v1, v2);
+        const T zu00 = ku * c00, zu01 = ku * c01, zu11 = ku * c11;
+        const T zv00 = kv * cv(plane_nn(mv, 0, 0), v1, v2), zv01 = kv * cv(plane_nn(mv, 0, 1), v1, v2),
+                zv11 = kv * cv(plane_nn(mv, 1, 1), v1, v2);
+        z00 = zu00 + zv00;
+        z01 = zu01 + zv01;
+        z11 = zu11 + zv11;
     }
     // normal-spread amplitude a_J = half nu c_mJmL w_L
     As0 = half * nu * (c00 * w0 + c01 * w1);
@@ -371,8 +390,16 @@ __device__ void face_sat_node(const BlockDev* __restrict__ blocks, const BlockDe
     T f1 = half * tt1 * tfac - (z01 * w0 + z11 * w1);
     if (intf) {
         T tu0, tu1, tv0, tv1;
-        face_traction<T, O>(B, F, s, u, c, tu0, tu1);
-        face_traction<T, O>(*V, *FV, F.reversed ? nf - 1 - s : s, uv, cv, tv0, tv1);
+        const int sv = F.reversed ? nf - 1 - s : s;
+        if (traced) {
+            tu0 = trU[2 * nf + s];
+            tu1 = trU[3 * nf + s];
+            tv0 = trV[2 * nf + sv];
+            tv1 = trV[3 * nf + sv];
+        } else {
+            face_traction<T, O>(B, F, s, u, c, tu0, tu1);
+            face_traction<T, O>(*V, *FV, sv, uv, cv, tv0, tv1);
+        }
         f0 -= T(0.5) * (tu0 + tv0);
         f1 -= T(0.5) * (tu1 + tv1);
     }
@@ -405,6 +432,40 @@ __global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* _
     sat[nf + s] = f1;
     sat[2 * nf + s] = a0;
     sat[3 * nf + s] = a1;
+}
+
+// One side's trace at every node of the interface faces listed in refs (FaceRef.face of an
+// interface face): u_L, the traction J^ tau_J = nu c_mJkL D_k u_L (eq. n-C_conversion) and this
+// side's share k c_mJmL of the interface penalty Z (Sec. 6, k = beta d / 4 / H_m[0]); the SAT
+// terms of both sides then read the neighbour from these short arrays (face_sat_node).
+template <typename T, int O>
+__global__ void k_face_trace(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
+                             int total, StepArgs a, double beta) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const FaceRef fr = refs[find_face(refs, nrefs, t)];
+    const int s = t - fr.start;
+    const BlockDev& B = blocks[fr.block];
+    const FaceDev& F = B.f[fr.face];
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+    auto u = [&](int L, int j1, int j2) { return U[(size_t)L * plane + (size_t)j2 * B.pitch + j1]; };
+    auto c = [&](int pl, int j1, int j2) { return C[(size_t)pl * plane + (size_t)j2 * B.pitch + j1]; };
+    T t0, t1;
+    face_traction<T, O>(B, F, s, u, c, t0, t1);
+    int i1, i2;
+    face_at(B, F, s, 0, i1, i2);
+    const int m = F.m, nf = F.nf;
+    const T k = T(beta * 2.0 / 4.0 * F.inv_h0);
+    T* tr = reinterpret_cast<T*>(F.tr);
+    tr[s] = u(0, i1, i2);
+    tr[nf + s] = u(1, i1, i2);
+    tr[2 * nf + s] = t0;
+    tr[3 * nf + s] = t1;
+    tr[4 * nf + s] = k * c(plane_nn(m, 0, 0), i1, i2);
+    tr[5 * nf + s] = k * c(plane_nn(m, 0, 1), i1, i2);
+    tr[6 * nf + s] = k * c(plane_nn(m, 1, 1), i1, i2);
 }
 
 // ============================================================================ boundary strips
@@ -528,37 +589,57 @@ __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
 // ============================================================================ boundary strips, tiled
 // The strips are cut into tiles of 32 nodes along the face x (strip width) nodes across it:
 // bottom and top bands (tiles along x1), left and right bands (tiles along x2, between the
-// bands).  A tile and a halo of HALO nodes (>= the widest closure stencil) are staged in shared
-// memory (2 displacement + 10 coefficient planes).  The mixed fluxes g1_j = c_1j2l D_2 u_l (on
-// the tile's rows) and g2_j = c_1l2j D_1 u_l (on its columns) are formed once per staged node, and
-// the SAT terms of the tile's face nodes (every face whose first NCOL nodes the tile touches)
-// are formed from the staged data (the interface neighbour from global memory), so every output
-// node needs only the narrow rows, two <= NCOL-tap sums and shared-memory SAT terms.
+// bands).  The tile's region of the 2 displacement and 10 coefficient planes is staged in shared
+// memory: for band tiles one elected thread issues two cp.async.bulk.tensor loads (a bounded
+// mbarrier wait; on timeout the CTA sets bit 8 of the error flag, waits once more for its copies
+// and returns); side tiles copy their narrow rows element-wise (cp.async) into rows of odd
+// stride, since their warps walk columns.  Region extents:
+//   across the face: the strip plus HN = Q nodes (the farthest reach past the strip of a closure
+//     triple of D_xx^FC, of an interior edge weight and of the mixed terms);
+//   along the face:  the tile plus HT nodes each side (the backward reach Q - LO of the edge
+//     weights, rounded up to 4 so that the box starts on a 16-byte boundary).  Band tiles stage
+//     the window of the 32 columns [xc, xc + 32), xc = min(x0, n1 - 32), so that the narrow last
+//     tile still holds the whole closure of the block corner.
+// The mixed fluxes g1_j = c_1j2l D_2 u_l (on the tile's rows) and g2_j = c_1l2j D_1 u_l (on its
+// columns) are formed once per staged node, and the SAT terms of the tile's face nodes (every
+// face whose first NCOL nodes the tile touches) are formed from the staged data (interfaces read
+// the traces of k_face_trace), so every output node needs only the narrow rows, two <= NCOL-tap
+// sums and shared-memory SAT terms.
 template <int O> struct StripTile {
-    static constexpr int HALO = O == 2 ? 3 : (O == 4 ? 8 : 12);
+    static constexpr int Q = Ord<O>::Q;
     static constexpr int S = Ord<O>::NCLOS > Ord<O>::NCOL ? Ord<O>::NCLOS : Ord<O>::NCOL;
-    static constexpr int RLONG = 32 + 2 * HALO;
-    static constexpr int RMAX = RLONG * (S + HALO);     // one side of the region is the face
-    static constexpr int FLUX = 2 * (S * RLONG + (S + HALO) * 32);   // g1 on the tile rows, g2 on its columns
+    static constexpr int HN = Q;
+    static constexpr int HT = (Q - EdgeRange<O>::LO + 3) / 4 * 4;
+    static constexpr int BWB = 32 + 2 * HT + 4, BHB = S + HN;            // band box (tiles along x1)
+    static constexpr int CWS = S + HN, BWS = CWS | 1, BHS = 32 + 2 * HT; // side region: CWS columns, odd stride
+    static constexpr int RMAX = BWB * BHB > BWS * BHS ? BWB * BHB : BWS * BHS;
+    static constexpr int FLUXB = 2 * (S * BWB + BHB * 32), FLUXS = 2 * (32 * BWS + BHS * S);
+    static constexpr int FLUX = FLUXB > FLUXS ? FLUXB : FLUXS;   // g1 on the tile rows, g2 on its columns
     static constexpr int SATS = 4 * 32 * 4;             // per face, per face node: Fs0, Fs1, As0, As1
-    static constexpr int ELEMS = 12 * RMAX + FLUX + SATS;
     static constexpr int THREADS = 32 * S;
+    // element offset of the coefficient box (128-byte aligned TMA destination), of the fluxes, and bytes
+    template <typename T> static constexpr int coff() { return (int)((2 * RMAX * sizeof(T) + 127) / 128 * 128 / sizeof(T)); }
+    template <typename T> static constexpr int foff() { return coff<T>() + 10 * RMAX; }
+    template <typename T> static constexpr size_t bar_off() { return ((foff<T>() + FLUX + SATS) * sizeof(T) + 15) / 16 * 16; }
+    template <typename T> static constexpr size_t bytes() { return bar_off<T>() + 16; }
 };
 
 // One launch covers the strips of every block: tiles[blockIdx.x] = (block, tile of that block),
 // ordered by the host so that the costliest tiles (interface bands, side bands) start first.
+// B.smaps holds the block's band-box tensor maps: u[0], u[1], c.
 template <typename T, int O, int MODE>
 __global__ void __launch_bounds__(StripTile<O>::THREADS, 3)
-k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles, StepArgs a, double beta) {
+k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles, StepArgs a, double beta, int* err) {
     using ST = StripTile<O>;
-    constexpr int S = ST::S, H = ST::HALO, NT = ST::THREADS;
-    extern __shared__ __align__(16) unsigned char strip_smem[];
+    constexpr int S = ST::S, NT = ST::THREADS;
+    extern __shared__ __align__(128) unsigned char strip_smem[];
     T* sm = reinterpret_cast<T*>(strip_smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(strip_smem + ST::template bar_off<T>());
     const int2 tt = tiles[blockIdx.x];
     const BlockDev& B = blocks[tt.x];
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int nbx = (n1 + 31) / 32, nby = (n2 - 2 * S + 31) / 32;
-    int t = tt.y, x0, y0, w, h;
+    int t = tt.y, x0, y0, w, h, xs, ys, BW, BH, VW;   // VW: staged columns (BW: row stride)
     bool along_x;
     if (t < 2 * nbx) {
         along_x = true;
@@ -567,6 +648,11 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
         w = min(32, n1 - x0);
         y0 = band ? n2 - S : 0;
         h = S;
+        const int xc = min(x0, max(0, n1 - 32));
+        xs = (xc & ~3) - ST::HT;
+        ys = band ? n2 - S - ST::HN : 0;
+        BW = VW = ST::BWB;
+        BH = ST::BHB;
     } else {
         t -= 2 * nbx;
         along_x = false;
@@ -575,50 +661,80 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
         h = min(32, n2 - S - y0);
         x0 = side ? n1 - S : 0;
         w = S;
+        xs = side ? n1 - ST::CWS : 0;
+        ys = y0 - ST::HT;
+        BW = ST::BWS;
+        VW = ST::CWS;
+        BH = ST::BHS;
     }
-    const int rx0 = max(0, x0 - H), rx1 = min(n1, x0 + w + H);
-    const int ry0 = max(0, y0 - H), ry1 = min(n2, y0 + h + H);
-    const int RW = rx1 - rx0, RH = ry1 - ry0, RN = RW * RH;
+    const int PS = BW * BH;                     // plane stride of the staged boxes
     const size_t plane = (size_t)n2 * P;
-    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
-    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
-    // stage: asynchronous element copies (cp.async), all in flight before the single wait
-    for (int pl = 0; pl < 12; ++pl) {
-        const T* src = pl < 2 ? U + pl * plane : C + (pl - 2) * plane;
-        T* dst = sm + pl * ST::RMAX;
-        for (int r = threadIdx.x / 32; r < RH; r += NT / 32) {
-            const T* srow = src + (size_t)(ry0 + r) * P + rx0;
-            for (int c = threadIdx.x & 31; c < RW; c += 32) {
-                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + r * RW + c);
+    // stage the tile's region (2 displacement planes at sm, 10 coefficient planes at sm + coff)
+    if (along_x) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(B.smaps);
+            mbar_expect_tx(bar, (uint32_t)(12 * PS * sizeof(T)));
+            tma_load_3d(sm, &maps[a.cur], xs, ys, 0, bar);
+            tma_load_3d(sm + ST::template coff<T>(), &maps[2], xs, ys, 0, bar);
+        }
+        const bool staged = mbar_wait_bounded(bar, 0);
+        if (__syncthreads_or(!staged)) {
+            if (threadIdx.x == 0) {
+                atomicOr(err, 8);
+                mbar_wait_bounded(bar, 0);
+            }
+            return;
+        }
+    } else {
+        const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
+        const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+        const int r0 = max(0, ys), r1 = min(n2, ys + BH), nel = (r1 - r0) * ST::CWS;
+        for (int pl = 0; pl < 12; ++pl) {
+            const T* src = pl < 2 ? U + pl * plane : C + (pl - 2) * plane;
+            T* dst = pl < 2 ? sm + pl * PS : sm + ST::template coff<T>() + (pl - 2) * PS;
+            for (int e = threadIdx.x; e < nel; e += NT) {
+                const int r = e / ST::CWS, c = e - r * ST::CWS;
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + (r0 + r - ys) * BW + c);
+                const T* gp = src + (size_t)(r0 + r) * P + xs + c;
                 if (sizeof(T) == 8)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(srow + c) : "memory");
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gp) : "memory");
                 else
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(srow + c) : "memory");
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gp) : "memory");
             }
         }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+        __syncthreads();
     }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    auto at = [&](int pl, int j1, int j2) -> T& { return sm[pl * ST::RMAX + (j2 - ry0) * RW + (j1 - rx0)]; };
+    auto at = [&](int pl, int j1, int j2) -> T& {
+        T* base = pl < 2 ? sm + pl * PS : sm + ST::template coff<T>() + (pl - 2) * PS;
+        return base[(j2 - ys) * BW + (j1 - xs)];
+    };
     // g1_J (J = 0, 1) at (j1, j2), j2 in the tile rows; g2_J at (j1, j2), j1 in the tile columns
-    T* g1s = sm + 12 * ST::RMAX;
-    T* g2s = g1s + 2 * h * RW;
-    auto g1 = [&](int J, int j1, int j2) -> T& { return g1s[(J * h + (j2 - y0)) * RW + (j1 - rx0)]; };
-    auto g2 = [&](int J, int j1, int j2) -> T& { return g2s[(J * RH + (j2 - ry0)) * w + (j1 - x0)]; };
+    T* g1s = sm + ST::template foff<T>();
+    T* g2s = g1s + 2 * h * BW;
+    auto g1 = [&](int J, int j1, int j2) -> T& { return g1s[(J * h + (j2 - y0)) * BW + (j1 - xs)]; };
+    auto g2 = [&](int J, int j1, int j2) -> T& { return g2s[(J * BH + (j2 - ys)) * w + (j1 - x0)]; };
     const T ih1 = ih1T<T>(B), ih2 = ih2T<T>(B);
-    (void)RN;
-    // g1 on the tile's rows (all staged columns), g2 on the tile's columns (all staged rows)
-    for (int idx = threadIdx.x; idx < h * RW; idx += NT) {
-        const int r = idx / RW, c = idx - r * RW;
-        const int j1 = rx0 + c, j2 = y0 + r;
+    // g1 on the tile's rows (the staged columns inside the block), g2 on the tile's columns (the
+    // staged rows inside the block)
+    const int cx0 = max(0, xs), cx1 = min(n1, xs + VW), RWc = cx1 - cx0;
+    const int cy0 = max(0, ys), cy1 = min(n2, ys + BH), RHc = cy1 - cy0;
+    for (int idx = threadIdx.x; idx < h * RWc; idx += NT) {
+        const int r = idx / RWc, c = idx - r * RWc;
+        const int j1 = cx0 + c, j2 = y0 + r;
         const T d0 = dsum<O, T>(n2, j2, [&](int bb) { return at(0, j1, bb); }) * ih2;
         const T d1 = dsum<O, T>(n2, j2, [&](int bb) { return at(1, j1, bb); }) * ih2;
         g1(0, j1, j2) = at(8, j1, j2) * d0 + at(9, j1, j2) * d1;
         g1(1, j1, j2) = at(10, j1, j2) * d0 + at(11, j1, j2) * d1;
     }
-    for (int idx = threadIdx.x; idx < RH * w; idx += NT) {
+    for (int idx = threadIdx.x; idx < RHc * w; idx += NT) {
         const int r = idx / w, c = idx - r * w;
-        const int j1 = x0 + c, j2 = ry0 + r;
+        const int j1 = x0 + c, j2 = cy0 + r;
         const T d0 = dsum<O, T>(n1, j1, [&](int aa) { return at(0, aa, j2); }) * ih1;
         const T d1 = dsum<O, T>(n1, j1, [&](int aa) { return at(1, aa, j2); }) * ih1;
         g2(0, j1, j2) = at(8, j1, j2) * d0 + at(10, j1, j2) * d1;
@@ -626,7 +742,7 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
     }
     // SAT terms of the face nodes whose first NCOL nodes meet the tile: face f's tangential range
     // is the tile's y range (f = 0, 1) or x range (f = 2, 3)
-    T* sats = sm + 12 * ST::RMAX + ST::FLUX;
+    T* sats = sm + ST::template foff<T>() + ST::FLUX;
     auto face_meets = [&](int f) {
         if (f < 2) return f == 0 ? x0 < Ord<O>::NCOL : x0 + w > n1 - Ord<O>::NCOL;
         return f == 2 ? y0 < Ord<O>::NCOL : y0 + h > n2 - Ord<O>::NCOL;
@@ -645,6 +761,9 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
         q[3] = a1;
     }
     __syncthreads();
+    // output node of this thread: a warp per row of a band tile (lanes along the row), a warp per
+    // column of a side tile (lanes along the column: one closure row per warp, and the odd row
+    // stride of the side staging keeps the column accesses free of bank conflicts)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i1 = along_x ? x0 + lane : x0 + wid;
     const int i2 = along_x ? y0 + wid : y0 + lane;
