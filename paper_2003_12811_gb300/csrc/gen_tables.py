@@ -247,6 +247,8 @@ def emit():
         out.append("SBP_TABLE int %s_CLOS_J[%d] = {%s};" % (P.lower(), len(js), ", ".join(map(str, js))))
         out.append("SBP_TABLE int %s_CLOS_K[%d] = {%s};" % (P.lower(), len(ks), ", ".join(map(str, ks))))
         table(out, "double", "%s_CLOS_C" % P.lower(), cs, [len(cs)])
+        # columns 0 .. NCLOSJ-1 hold every j and k of the closure triples
+        out.append("#define %s_NCLOSJ %d" % (P, max(max(js), max(ks)) + 1))
         # edge weights as an inline device function
         out.append("// interior edge weights E_m(i) = sum_k e_{m,k} b_{i+k}; B(k) reads b_{i+k}")
         for m, e in enumerate(t["edges"], start=1):

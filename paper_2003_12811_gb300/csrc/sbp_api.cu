@@ -59,11 +59,16 @@ struct HostBlock {
     void* psi[2] = {nullptr, nullptr};   // adjoint fields (sbp_misfit_gradient), allocated on first use
     MarchMaps pmaps;          // marching-kernel maps over the adjoint fields
     CUtensorMap* d_smaps = nullptr;   // strip-tile band-box maps on the device: [0..2] state u0, u1, c; [3..5] adjoint
+    void* mx = nullptr;       // closure matrices of D_xx^FC along x1 / x2 (k_closure_mats, type T)
+    void* my = nullptr;
 };
 
 int order_nb(int o) { return o == 2 ? SBP2_NB : (o == 4 ? SBP4_NB : SBP6_NB); }
 int order_ncol(int o) { return o == 2 ? SBP2_NCOL : (o == 4 ? SBP4_NCOL : SBP6_NCOL); }
 int order_nclos(int o) { return o == 2 ? SBP2_NCLOS : (o == 4 ? SBP4_NCLOS : SBP6_NCLOS); }
+int order_nclosj(int o) { return o == 2 ? SBP2_NCLOSJ : (o == 4 ? SBP4_NCLOSJ : SBP6_NCLOSJ); }
+// elements of the closure matrices of one direction with `lines` lines (layout of dxx_closure_mat)
+size_t closure_elems(int o, int lines) { return 2 * (size_t)order_nclos(o) * order_nclosj(o) * 3 * lines; }
 int order_q(int o) { return o / 2; }
 int order_min_n(int o) { return o == 2 ? 5 : (o == 4 ? 18 : 27); }
 double order_hw(int o, int i) {
@@ -89,8 +94,7 @@ struct sbp_handle {
     BlockDev* d_blocks = nullptr;
     FaceRef* d_refs = nullptr;
     int nrefs = 0, nface_nodes = 0;
-    FaceRef* d_trefs = nullptr;   // interface faces (k_face_trace), numbered like d_refs
-    int ntrefs = 0, ntrace_nodes = 0;
+    int ntrefs = 0;               // interface faces (their traces: k_face_trace)
     int cur = 0;
     double t = 0.0;
     int nbasis = 0;
@@ -248,6 +252,8 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
         D.tr = F.tr;
     }
     b.smaps = hb.d_smaps;
+    b.mx = hb.mx;
+    b.my = hb.my;
     return b;
 }
 
@@ -365,9 +371,40 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         }
     }
     if (h->ntrefs > 0) {
-        ProfScope ps(h, 2, sst, 1);
-        k_face_trace<T, O><<<grid_for(h->ntrace_nodes, 128), 128, 0, sst>>>(tab, h->d_trefs, h->ntrefs,
-                                                                           h->ntrace_nodes, a, h->beta);
+        // interface traces of the level being read, TRACE_MAX faces per launch
+        TraceArgs ta{};
+        auto flush = [&]() {
+            if (ta.nfaces == 0) return;
+            ProfScope ps(h, 2, sst, 1);
+            k_face_trace<T, O><<<grid_for(ta.total, 128), 128, 0, sst>>>(ta);
+            ta = TraceArgs{};
+        };
+        for (size_t b = 0; b < h->blocks.size(); ++b) {
+            const HostBlock& hb = h->blocks[b];
+            for (int f = 0; f < 4; ++f) {
+                const HostFace& HF = hb.f[f];
+                if (HF.kind != FACE_INTF) continue;
+                TraceFace& F = ta.f[ta.nfaces++];
+                F.u = adj ? hb.psi[a.cur] : hb.u[a.cur];
+                F.c = hb.c;
+                F.tr = HF.tr;
+                F.plane = (long long)hb.n2 * hb.pitch;
+                F.nf = HF.nf;
+                F.start = ta.total;
+                F.m = f / 2;
+                F.side = f % 2;
+                F.pitch = hb.pitch;
+                F.nm = F.m == 0 ? hb.n1 : hb.n2;
+                F.nu = (f % 2 == 0) ? -1.0 : 1.0;
+                const double hm = F.m == 0 ? hb.h1 : hb.h2, ht = F.m == 0 ? hb.h2 : hb.h1;
+                F.ihm = 1.0 / hm;
+                F.iht = 1.0 / ht;
+                F.k = h->beta * 2.0 / 4.0 * (1.0 / (hm * host_hweight(h->order, F.nm, 0)));
+                ta.total += HF.nf;
+                if (ta.nfaces == TRACE_MAX) flush();
+            }
+        }
+        flush();
     }
     {
         ProfScope ps(h, 1, sst, 1);
@@ -724,8 +761,8 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             cudaEventCreateWithFlags(&h->ev_join_hi, cudaEventDisableTiming) != cudaSuccess)
             return cleanup(SBP_E_CUDA, "auxiliary streams");
     }
-    std::vector<FaceRef> refs, trefs;
-    int start = 0, tstart = 0;
+    std::vector<FaceRef> refs;
+    int start = 0, nintf = 0;
     for (int b = 0; b < desc->nblocks; ++b) {
         const sbp_block_desc& bd = desc->blocks[b];
         HostBlock& hb = h->blocks[b];
@@ -742,6 +779,9 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         hb.w = h->dalloc(plane * es);
         hb.r = h->dalloc(2 * plane * es);
         hb.X = (double*)h->dalloc(2 * plane * sizeof(double));
+        hb.mx = h->dalloc(closure_elems(o, hb.n2) * es);
+        hb.my = h->dalloc(closure_elems(o, hb.n1) * es);
+        if (!hb.mx || !hb.my) return cleanup(SBP_E_OOM, "closure matrices");
         hb.G = (double*)h->dalloc(4 * plane * sizeof(double));
         hb.J = (double*)h->dalloc(plane * sizeof(double));
         if (!hb.u[0] || !hb.u[1] || !hb.c || !hb.w || !hb.r || !hb.X || !hb.G || !hb.J)
@@ -761,8 +801,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             if (F.kind == FACE_INTF) {
                 F.tr = h->dalloc(7 * (size_t)F.nf * es);
                 if (!F.tr) return cleanup(SBP_E_OOM, "interface trace buffers");
-                trefs.push_back(FaceRef{b, f, tstart, F.nf});
-                tstart += F.nf;
+                ++nintf;
             }
         }
         if (h->precision == SBP_FP32) {
@@ -799,13 +838,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     h->d_blocks = (BlockDev*)h->dalloc(sizeof(BlockDev) * h->blocks.size());
     if (!h->d_refs || !h->d_blocks) return cleanup(SBP_E_OOM, "tables");
     cudaMemcpy(h->d_refs, refs.data(), sizeof(FaceRef) * refs.size(), cudaMemcpyHostToDevice);
-    h->ntrefs = (int)trefs.size();
-    h->ntrace_nodes = tstart;
-    if (!trefs.empty()) {
-        h->d_trefs = (FaceRef*)h->dalloc(sizeof(FaceRef) * trefs.size());
-        if (!h->d_trefs) return cleanup(SBP_E_OOM, "tables");
-        cudaMemcpy(h->d_trefs, trefs.data(), sizeof(FaceRef) * trefs.size(), cudaMemcpyHostToDevice);
-    }
+    h->ntrefs = nintf;
     if (sync_views(h) != SBP_OK) return cleanup(SBP_E_CUDA, h->err);
     {
         // strip tiles (the tile numbering of k_strip_tile: 2 bands of ceil(n1/32) tiles along x1,
@@ -894,6 +927,17 @@ int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* 
     BlockDev b = make_view(h, hb);
     if (h->precision == SBP_FP64) k_material<double><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
     else k_material<float><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
+    // the closure rows of D_xx^FC for the new coefficients
+    const long long nx = (long long)closure_elems(h->order, hb.n2) / 3, ny = (long long)closure_elems(h->order, hb.n1) / 3;
+    if (h->precision == SBP_FP64) {
+        if (h->order == 2) { k_closure_mats<double, 2><<<grid_for(nx), 256>>>(b, 0, (double*)hb.mx); k_closure_mats<double, 2><<<grid_for(ny), 256>>>(b, 1, (double*)hb.my); }
+        else if (h->order == 4) { k_closure_mats<double, 4><<<grid_for(nx), 256>>>(b, 0, (double*)hb.mx); k_closure_mats<double, 4><<<grid_for(ny), 256>>>(b, 1, (double*)hb.my); }
+        else { k_closure_mats<double, 6><<<grid_for(nx), 256>>>(b, 0, (double*)hb.mx); k_closure_mats<double, 6><<<grid_for(ny), 256>>>(b, 1, (double*)hb.my); }
+    } else {
+        if (h->order == 2) { k_closure_mats<float, 2><<<grid_for(nx), 256>>>(b, 0, (float*)hb.mx); k_closure_mats<float, 2><<<grid_for(ny), 256>>>(b, 1, (float*)hb.my); }
+        else if (h->order == 4) { k_closure_mats<float, 4><<<grid_for(nx), 256>>>(b, 0, (float*)hb.mx); k_closure_mats<float, 4><<<grid_for(ny), 256>>>(b, 1, (float*)hb.my); }
+        else { k_closure_mats<float, 6><<<grid_for(nx), 256>>>(b, 0, (float*)hb.mx); k_closure_mats<float, 6><<<grid_for(ny), 256>>>(b, 1, (float*)hb.my); }
+    }
     cudaError_t e = cudaDeviceSynchronize();
     h->dfree(d_rho);
     h->dfree(d_C);

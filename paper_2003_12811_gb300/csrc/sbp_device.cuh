@@ -24,7 +24,7 @@ template <int O> struct Ord;
 #define SBP_ORD(O)                                                                                     \
     template <> struct Ord<O> {                                                                        \
         static constexpr int Q = SBP##O##_Q, NB = SBP##O##_NB, NCOL = SBP##O##_NCOL,                   \
-                             NCLOS = SBP##O##_NCLOS, GS = SBP##O##_GS;                                 \
+                             NCLOS = SBP##O##_NCLOS, NCLOSJ = SBP##O##_NCLOSJ, GS = SBP##O##_GS;       \
         static __device__ __forceinline__ double hw(int i) { return sbpdev::sbp##O##_HW[i]; }          \
         static __device__ __forceinline__ double dq(int r, int c) { return sbpdev::sbp##O##_DQ[r][c]; } \
         static __device__ __forceinline__ double a(int k) { return sbpdev::sbp##O##_A[k]; }            \
@@ -156,22 +156,23 @@ template <int O, typename T, class F> __device__ __forceinline__ T dsum(int N, i
 // (b0 = c_d1d1, b1 = c_d1d2 = c_d2d1, b2 = c_d2d2):
 //   r0 += D_xx(b0) u0 + D_xx(b1) u1,   r1 += D_xx(b1) u0 + D_xx(b2) u1
 template <int O, typename T, class FU0, class FU1, class FB0, class FB1, class FB2>
-__device__ __forceinline__ void dxx_vec(int N, int i, FU0 u0, FU1 u1, FB0 b0, FB1 b1, FB2 b2, T& r0, T& r1) {
+__device__ __forceinline__ void dxx_closure(int N, int i, FU0 u0, FU1 u1, FB0 b0, FB1 b1, FB2 b2, T& r0, T& r1) {
     using P = Ord<O>;
-    if (i < P::NCLOS || i >= N - P::NCLOS) {
-        const bool right = i >= N - P::NCLOS;
-        const int row = right ? N - 1 - i : i;
-        for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
-            int j = P::cj(t), k = P::ck(t);
-            if (right) { j = N - 1 - j; k = N - 1 - k; }
-            const T c = P::template ccT<T>(t);
-            const T bb0 = b0(k), bb1 = b1(k), bb2 = b2(k);
-            const T uu0 = u0(j), uu1 = u1(j);
-            r0 += c * (bb0 * uu0 + bb1 * uu1);
-            r1 += c * (bb1 * uu0 + bb2 * uu1);
-        }
-        return;
+    const bool right = i >= N - P::NCLOS;
+    const int row = right ? N - 1 - i : i;
+    for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
+        int j = P::cj(t), k = P::ck(t);
+        if (right) { j = N - 1 - j; k = N - 1 - k; }
+        const T c = P::template ccT<T>(t);
+        const T bb0 = b0(k), bb1 = b1(k), bb2 = b2(k);
+        const T uu0 = u0(j), uu1 = u1(j);
+        r0 += c * (bb0 * uu0 + bb1 * uu1);
+        r1 += c * (bb1 * uu0 + bb2 * uu1);
     }
+}
+template <int O, typename T, class FU0, class FU1, class FB0, class FB1, class FB2>
+__device__ __forceinline__ void dxx_interior(int i, FU0 u0, FU1 u1, FB0 b0, FB1 b1, FB2 b2, T& r0, T& r1) {
+    using P = Ord<O>;
     const T uc0 = u0(i), uc1 = u1(i);
 #pragma unroll
     for (int m = 1; m <= P::Q; ++m) {
@@ -190,6 +191,43 @@ __device__ __forceinline__ void dxx_vec(int N, int i, FU0 u0, FU1 u1, FB0 b0, FB
         r0 += e0p * dp0 + e1p * dp1 + e0m * dm0 + e1m * dm1;
         r1 += e1p * dp0 + e2p * dp1 + e1m * dm0 + e2m * dm1;
     }
+}
+template <int O, typename T, class FU0, class FU1, class FB0, class FB1, class FB2>
+__device__ __forceinline__ void dxx_vec(int N, int i, FU0 u0, FU1 u1, FB0 b0, FB1 b1, FB2 b2, T& r0, T& r1) {
+    using P = Ord<O>;
+    if (i < P::NCLOS || i >= N - P::NCLOS) dxx_closure<O, T>(N, i, u0, u1, b0, b1, b2, r0, r1);
+    else dxx_interior<O, T>(i, u0, u1, b0, b1, b2, r0, r1);
+}
+
+// Closure rows of h^2 D_xx^FC(b) as matrices: row r (0 .. NCLOS-1) from the low (side 0) or high
+// (side 1, mirrored) end of a line is sum_j M_b[side][r][j] u(j) with M_b[side][r][j] = sum over
+// the closure triples (r, j, k) of c_rjk b(k); j, k count from that end.  b is time-independent,
+// so M is formed once per material (k_closure_mats); layout [side][r][j][b0 b1 b2][line] with
+// the line index (the transverse node index) fastest.
+template <int O> __host__ __device__ constexpr long long closure_mat_elems(int lines) {
+    return 2LL * Ord<O>::NCLOS * Ord<O>::NCLOSJ * 3 * lines;
+}
+// node i of a line of N nodes, through the matrices M of its direction (returns false for
+// interior rows, which use the edge-weight form)
+template <int O, typename T, class FU0, class FU1>
+__device__ __forceinline__ bool dxx_closure_mat(int N, int i, int line, int lines, const T* __restrict__ M, FU0 u0,
+                                                FU1 u1, T& r0, T& r1) {
+    using P = Ord<O>;
+    constexpr int NC = P::NCLOS, NJ = P::NCLOSJ;
+    if (i >= NC && i < N - NC) return false;
+    const int side = i >= N - NC ? 1 : 0;
+    const int r = side ? N - 1 - i : i;
+    const T* Mr = M + (long long)(side * NC + r) * NJ * 3 * lines + line;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int jj = side ? N - 1 - j : j;
+        const T uu0 = u0(jj), uu1 = u1(jj);
+        const T m0 = Mr[(long long)(3 * j) * lines], m1 = Mr[(long long)(3 * j + 1) * lines],
+                m2 = Mr[(long long)(3 * j + 2) * lines];
+        r0 += m0 * uu0 + m1 * uu1;
+        r1 += m1 * uu0 + m2 * uu1;
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ views
@@ -228,6 +266,8 @@ struct BlockDev {
     double* G;                // metric dX_I/dx_i (4 planes, [2 i + I])
     double* J;                // Jacobian
     const void* smaps;        // strip-tile band-box tensor maps (CUtensorMap[3]: u[0], u[1], c)
+    const void* mx;           // closure rows of D_xx^FC along x1 as matrices, type T (k_closure_mats)
+    const void* my;           // the same along x2
     FaceDev f[4];
 };
 

@@ -49,6 +49,19 @@ __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
+// interior edge weight E_m of one field as an explicit FMA chain in a fixed order: every copy of
+// the row loop (prologue, unrolled output rows) rounds it the same way, so the result at a node
+// does not depend on how the rows are split between CTAs
+template <int O, class F> __device__ __forceinline__ float edge1(int m, F B) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = EdgeRange<O>::LO; k <= EdgeRange<O>::HI; ++k) {
+        const float c = edge_w<O>(m, k);
+        if (c != 0.f) acc = __fmaf_rn(c, B(k), acc);
+    }
+    return acc;
+}
+
 // tile geometry shared with the host: first column, columns per CTA, rows per CTA
 __host__ __device__ inline int march_x0(int strip) { return (strip / 4) * 4; }
 
@@ -217,7 +230,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
                     const float c = edge_w<O>(m, k);
                     if (c != 0.f) e01 = ffma2(bc2(c), qb[k + Q - 1], e01);
                 }
-                const float e2 = Edge<O>::template e<float>(m, [&](int k) { return qc[k + Q - 1]; });
+                const float e2 = edge1<O>(m, [&](int k) { return qc[k + Q - 1]; });
                 const float2 dp = fsub2(qu[Q + m], qu[Q]);
                 // (F0, F1) = (e0, e1) dp_1 + (e1, e2) dp_2
                 const float2 f = ffma2(e01, bc2(dp.x), fmul2(make_float2(e01.y, e2), bc2(dp.y)));
@@ -302,8 +315,8 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
                     e01m = ffma2(bc2(c), X2(pr, k - m), e01m);
                 }
             }
-            const float e2p = Edge<O>::template e<float>(m, [&](int k) { return pr[poff(4) + k]; });
-            const float e2m = Edge<O>::template e<float>(m, [&](int k) { return pr[poff(4) - m + k]; });
+            const float e2p = edge1<O>(m, [&](int k) { return pr[poff(4) + k]; });
+            const float e2m = edge1<O>(m, [&](int k) { return pr[poff(4) - m + k]; });
             const float2 dp = fsub2(U2(pr, m), uc), dm = fsub2(U2(pr, -m), uc);
             rx = ffma2(e01p, bc2(dp.x), rx);
             rx = ffma2(make_float2(e01p.y, e2p), bc2(dp.y), rx);
@@ -329,8 +342,8 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
             #pragma unroll
                 for (int kb = 0; kb < 8; ++kb) {
                     if (kb >= a.K) break;
-                r0 += (float)a.Tk[kb] * JF[(size_t)kb * plane + gi];
-                r1 += (float)a.Tk[kb] * JF[(size_t)(a.K + kb) * plane + gi];
+                r0 = __fmaf_rn((float)a.Tk[kb], JF[(size_t)kb * plane + gi], r0);
+                r1 = __fmaf_rn((float)a.Tk[kb], JF[(size_t)(a.K + kb) * plane + gi], r1);
             }
         }
         if (MODE == 0) {

@@ -434,38 +434,109 @@ __global__ void k_face_sat(const BlockDev* __restrict__ blocks, const FaceRef* _
     sat[3 * nf + s] = a1;
 }
 
-// One side's trace at every node of the interface faces listed in refs (FaceRef.face of an
-// interface face): u_L, the traction J^ tau_J = nu c_mJkL D_k u_L (eq. n-C_conversion) and this
-// side's share k c_mJmL of the interface penalty Z (Sec. 6, k = beta d / 4 / H_m[0]); the SAT
-// terms of both sides then read the neighbour from these short arrays (face_sat_node).
+// One side's trace at every node of up to TRACE_MAX interface faces: u_L, the traction
+// J^ tau_J = nu c_mJkL D_k u_L (eq. n-C_conversion) and this side's share k c_mJmL of the
+// interface penalty Z (Sec. 6, k = beta d / 4 / H_m[0]); the SAT terms of both sides then read
+// the neighbour from these short arrays (face_sat_node).  The face geometry travels in the
+// kernel parameters, so every load of a thread (NCOL nodes along the normal, the tangential
+// stencil, 7 coefficient planes) is independent of the others.
+constexpr int TRACE_MAX = 8;
+struct TraceFace {
+    const void* u;            // current level of the block (2 planes), type T
+    const void* c;            // coefficient planes
+    void* tr;                 // FaceDev::tr of this face (7 x nf)
+    long long plane;          // plane stride (elements)
+    int nf, start;            // face nodes, first thread index of this face
+    int m, side, pitch, nm;   // normal direction, high side, row pitch, nodes along the normal
+    double nu, ihm, iht, k;   // outward normal component, 1/h_m, 1/h_t, penalty share factor
+};
+struct TraceArgs {
+    TraceFace f[TRACE_MAX];
+    int nfaces, total;
+};
+
 template <typename T, int O>
-__global__ void k_face_trace(const BlockDev* __restrict__ blocks, const FaceRef* __restrict__ refs, int nrefs,
-                             int total, StepArgs a, double beta) {
+__global__ void k_face_trace(const __grid_constant__ TraceArgs ta) {
+    using P = Ord<O>;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const FaceRef fr = refs[find_face(refs, nrefs, t)];
-    const int s = t - fr.start;
-    const BlockDev& B = blocks[fr.block];
-    const FaceDev& F = B.f[fr.face];
-    const size_t plane = (size_t)B.n2 * B.pitch;
-    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
-    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
-    auto u = [&](int L, int j1, int j2) { return U[(size_t)L * plane + (size_t)j2 * B.pitch + j1]; };
-    auto c = [&](int pl, int j1, int j2) { return C[(size_t)pl * plane + (size_t)j2 * B.pitch + j1]; };
-    T t0, t1;
-    face_traction<T, O>(B, F, s, u, c, t0, t1);
-    int i1, i2;
-    face_at(B, F, s, 0, i1, i2);
-    const int m = F.m, nf = F.nf;
-    const T k = T(beta * 2.0 / 4.0 * F.inv_h0);
+    if (t >= ta.total) return;
+    int fi = 0;
+    while (fi + 1 < ta.nfaces && t >= ta.f[fi + 1].start) ++fi;
+    const TraceFace& F = ta.f[fi];
+    const int s = t - F.start, m = F.m, nf = F.nf;
+    const T* __restrict__ U = reinterpret_cast<const T*>(F.u);
+    const T* __restrict__ C = reinterpret_cast<const T*>(F.c);
+    // face node offset, step into the block along the normal, step along the face
+    long long o0, sn, st;
+    if (m == 0) {
+        o0 = (long long)s * F.pitch + (F.side ? F.nm - 1 : 0);
+        sn = F.side ? -1 : 1;
+        st = F.pitch;
+    } else {
+        o0 = (long long)(F.side ? F.nm - 1 : 0) * F.pitch + s;
+        sn = F.side ? -(long long)F.pitch : (long long)F.pitch;
+        st = 1;
+    }
+    T dn[2], dt[2];
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+        const T* UL = U + L * F.plane;
+        // boundary row of D along the normal (mirrored, with the opposite sign, on the high side)
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < P::NCOL; ++j) acc += P::template dqT<T>(0, j) * UL[o0 + j * sn];
+        dn[L] = (F.side ? -acc : acc) * T(F.ihm);
+        dt[L] = dsum<O, T>(nf, s, [&](int j) { return UL[o0 + (long long)(j - s) * st]; }) * T(F.iht);
+    }
+    const T nu = T(F.nu);
+    auto cc = [&](int pl) { return C[pl * F.plane + o0]; };
+    const T t0 = nu * (cc(plane_nn(m, 0, 0)) * dn[0] + cc(plane_nn(m, 0, 1)) * dn[1] + cc(plane_nt(m, 0, 0)) * dt[0] +
+                       cc(plane_nt(m, 0, 1)) * dt[1]);
+    const T t1 = nu * (cc(plane_nn(m, 1, 0)) * dn[0] + cc(plane_nn(m, 1, 1)) * dn[1] + cc(plane_nt(m, 1, 0)) * dt[0] +
+                       cc(plane_nt(m, 1, 1)) * dt[1]);
+    const T k = T(F.k);
     T* tr = reinterpret_cast<T*>(F.tr);
-    tr[s] = u(0, i1, i2);
-    tr[nf + s] = u(1, i1, i2);
+    tr[s] = U[o0];
+    tr[nf + s] = U[F.plane + o0];
     tr[2 * nf + s] = t0;
     tr[3 * nf + s] = t1;
-    tr[4 * nf + s] = k * c(plane_nn(m, 0, 0), i1, i2);
-    tr[5 * nf + s] = k * c(plane_nn(m, 0, 1), i1, i2);
-    tr[6 * nf + s] = k * c(plane_nn(m, 1, 1), i1, i2);
+    tr[4 * nf + s] = k * cc(plane_nn(m, 0, 0));
+    tr[5 * nf + s] = k * cc(plane_nn(m, 0, 1));
+    tr[6 * nf + s] = k * cc(plane_nn(m, 1, 1));
+}
+
+// Closure matrices of one direction of a block (dir 0: along x1, lines = rows i2; dir 1: along
+// x2, lines = columns i1) from the coefficient planes (b0, b1, b2 = planes 0..2 or 3..5),
+// accumulated in FP64 and stored in T (layout of dxx_closure_mat).
+template <typename T, int O>
+__global__ void k_closure_mats(BlockDev B, int dir, T* __restrict__ M) {
+    using P = Ord<O>;
+    constexpr int NC = P::NCLOS, NJ = P::NCLOSJ;
+    const int N = dir == 0 ? B.n1 : B.n2, lines = dir == 0 ? B.n2 : B.n1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2LL * NC * NJ * lines) return;
+    const int line = (int)(t % lines);
+    long long q = t / lines;
+    const int j = (int)(q % NJ);
+    q /= NJ;
+    const int r = (int)(q % NC), side = (int)(q / NC);
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
+    const int p0 = dir == 0 ? 0 : 3;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int tt = P::cstart(r); tt < P::cstart(r + 1); ++tt) {
+        if (P::cj(tt) != j) continue;
+        const int k = side ? N - 1 - P::ck(tt) : P::ck(tt);
+        const size_t gi = dir == 0 ? (size_t)line * B.pitch + k : (size_t)k * B.pitch + line;
+        const double c = P::cc(tt);
+        m0 += c * (double)C[(size_t)p0 * plane + gi];
+        m1 += c * (double)C[(size_t)(p0 + 1) * plane + gi];
+        m2 += c * (double)C[(size_t)(p0 + 2) * plane + gi];
+    }
+    T* Mo = M + ((long long)((side * NC + r) * NJ + j) * 3) * lines + line;
+    Mo[0] = T(m0);
+    Mo[lines] = T(m1);
+    Mo[2LL * lines] = T(m2);
 }
 
 // ============================================================================ boundary strips
@@ -768,13 +839,18 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
     const int i1 = along_x ? x0 + lane : x0 + wid;
     const int i2 = along_x ? y0 + wid : y0 + lane;
     if (i1 >= x0 + w || i2 >= y0 + h) return;
+    // narrow rows: closure rows through the precomputed matrices, interior rows by edge weights
     T rx0v = T(0), rx1v = T(0), ry0v = T(0), ry1v = T(0);
-    dxx_vec<O, T>(n1, i1, [&](int j) { return at(0, j, i2); }, [&](int j) { return at(1, j, i2); },
-                  [&](int k) { return at(2, k, i2); }, [&](int k) { return at(3, k, i2); },
-                  [&](int k) { return at(4, k, i2); }, rx0v, rx1v);
-    dxx_vec<O, T>(n2, i2, [&](int j) { return at(0, i1, j); }, [&](int j) { return at(1, i1, j); },
-                  [&](int k) { return at(5, i1, k); }, [&](int k) { return at(6, i1, k); },
-                  [&](int k) { return at(7, i1, k); }, ry0v, ry1v);
+    if (!dxx_closure_mat<O, T>(n1, i1, i2, n2, reinterpret_cast<const T*>(B.mx), [&](int j) { return at(0, j, i2); },
+                               [&](int j) { return at(1, j, i2); }, rx0v, rx1v))
+        dxx_interior<O, T>(i1, [&](int j) { return at(0, j, i2); }, [&](int j) { return at(1, j, i2); },
+                           [&](int k) { return at(2, k, i2); }, [&](int k) { return at(3, k, i2); },
+                           [&](int k) { return at(4, k, i2); }, rx0v, rx1v);
+    if (!dxx_closure_mat<O, T>(n2, i2, i1, n1, reinterpret_cast<const T*>(B.my), [&](int j) { return at(0, i1, j); },
+                               [&](int j) { return at(1, i1, j); }, ry0v, ry1v))
+        dxx_interior<O, T>(i2, [&](int j) { return at(0, i1, j); }, [&](int j) { return at(1, i1, j); },
+                           [&](int k) { return at(5, i1, k); }, [&](int k) { return at(6, i1, k); },
+                           [&](int k) { return at(7, i1, k); }, ry0v, ry1v);
     T r0 = rx0v * ih1 * ih1 + ry0v * ih2 * ih2;
     T r1 = rx1v * ih1 * ih1 + ry1v * ih2 * ih2;
     r0 += dsum<O, T>(n1, i1, [&](int aa) { return g1(0, aa, i2); }) * ih1 +
