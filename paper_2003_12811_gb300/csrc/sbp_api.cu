@@ -336,12 +336,16 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
     // interior kernels on st; strip kernels on the auxiliary stream when overlapping (profiling
     // runs serialise so that every family's events time that family alone)
     const bool ovl = h->overlap && h->aux && !h->prof;
+    // the interface traces run on the auxiliary stream beside the interior kernel (in its tail
+    // or its free slots); the strips that read them follow on that stream or wait for it
+    const bool tr_async = h->aux && !h->prof && h->ntrefs > 0;
     cudaStream_t sst = ovl ? h->aux : st;
     cudaStream_t ist = ovl ? h->hi : st;
-    if (ovl) {
+    cudaStream_t tst = (ovl || tr_async) ? h->aux : st;
+    if (ovl || tr_async) {
         cudaEventRecord(h->ev_fork, st);
-        cudaStreamWaitEvent(h->hi, h->ev_fork, 0);
         cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
+        if (ovl) cudaStreamWaitEvent(h->hi, h->ev_fork, 0);
     }
     for (auto& hb : h->blocks) {
         BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
@@ -371,12 +375,13 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         }
     }
     if (h->ntrefs > 0) {
-        // interface traces of the level being read, TRACE_MAX faces per launch
+        // interface traces of the level being read, TRACE_MAX faces per launch (enqueued after the
+        // interior kernels, so that their CTAs are placed first and the traces fill the tail)
         TraceArgs ta{};
         auto flush = [&]() {
             if (ta.nfaces == 0) return;
-            ProfScope ps(h, 2, sst, 1);
-            k_face_trace<T, O><<<grid_for(ta.total, 128), 128, 0, sst>>>(ta);
+            ProfScope ps(h, 2, tst, 1);
+            k_face_trace<T, O><<<grid_for(ta.total, 128), 128, 0, tst>>>(ta);
             ta = TraceArgs{};
         };
         for (size_t b = 0; b < h->blocks.size(); ++b) {
@@ -405,6 +410,10 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
             }
         }
         flush();
+    }
+    if (tr_async && !ovl) {    // the strips wait for the traces formed beside the interior
+        cudaEventRecord(h->ev_join, h->aux);
+        cudaStreamWaitEvent(st, h->ev_join, 0);
     }
     {
         ProfScope ps(h, 1, sst, 1);
