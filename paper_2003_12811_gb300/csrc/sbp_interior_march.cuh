@@ -33,7 +33,7 @@ template <int O> struct MarchCfg {
     // coefficient box [10][MR][W]; the slot itself is padded to 128 bytes (TMA destinations)
     static constexpr int UPAD = ((2 * MR * MBOXW * 4 + 127) / 128) * 128 / 4;
     static constexpr int CHUNK = ((UPAD + 10 * MR * MBOXW) * 4 + 127) / 128 * 128 / 4;
-    static constexpr int G1 = 2 * 2 * MBOXW;                 // [row parity][component][col]
+    static constexpr int G1 = 2 * 2 * MBOXW;                 // [row parity][col][component] (float2)
     static constexpr size_t BYTES = (size_t)(MNCH * CHUNK + G1) * 4 + 64;
 };
 
@@ -264,8 +264,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
             const float m6 = pr0[poff(8)], m7 = pr0[poff(9)], m8 = pr0[poff(10)], m9 = pr0[poff(11)];
             // g1_1 = c_1121 D_2 u_1 + c_1122 D_2 u_2,  g1_2 = c_1221 D_2 u_1 + c_1222 D_2 u_2
             const float2 g = ffma2(make_float2(m6, m8), bc2(d.x), fmul2(make_float2(m7, m9), bc2(d.y)));
-            g1s[(par * 2 + 0) * W + cc] = g.x;
-            g1s[(par * 2 + 1) * W + cc] = g.y;
+            reinterpret_cast<float2*>(g1s)[par * W + cc] = g;
         }
         // halo columns of g1 (x0-Q .. x0-1 and x0+128 .. x0+127+Q), from the halo queues
         if (halo) {
@@ -275,8 +274,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
             d = fmul2(d, bc2(ih2));
             const float m6 = at(8, r, hc), m7 = at(9, r, hc), m8 = at(10, r, hc), m9 = at(11, r, hc);
             const float2 g = ffma2(make_float2(m6, m8), bc2(d.x), fmul2(make_float2(m7, m9), bc2(d.y)));
-            g1s[(par * 2 + 0) * W + hc] = g.x;
-            g1s[(par * 2 + 1) * W + hc] = g.y;
+            reinterpret_cast<float2*>(g1s)[par * W + hc] = g;
         }
         if (__syncthreads_or(!ok)) {
             // a bounded wait ran out: record it, drain this CTA's issued copies (bounded), stop
@@ -302,7 +300,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         if (!col_ok) { rotate(r); continue; }
         // --- narrow x: edge weights from the x fields of row r (columns x-Q-2 .. x+Q)
         const float* pr = rowp(r) + cc;
-        const float2 uc = U2(pr, 0);
+        const float2 uc = qu[Q];                  // row r of this column (queue centre)
         float2 rx = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 1; m <= Q; ++m) {
@@ -326,11 +324,10 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         float2 rr = ffma2(rx, bc2(ih11), fmul2(ry, bc2(ih22)));
         // --- mixed: D_1 g1 from the shared row, D_2 g2 from the queue
         float2 m1 = make_float2(0.f, 0.f), m2 = make_float2(0.f, 0.f);
-        const float* g10 = g1s + (par * 2 + 0) * W + cc;
-        const float* g11 = g1s + (par * 2 + 1) * W + cc;
+        const float2* g1r = reinterpret_cast<const float2*>(g1s) + par * W + cc;
 #pragma unroll
         for (int k = 1; k <= Q; ++k) {
-            m1 = ffma2(bc2(ak[k - 1]), fsub2(make_float2(g10[k], g11[k]), make_float2(g10[-k], g11[-k])), m1);
+            m1 = ffma2(bc2(ak[k - 1]), fsub2(g1r[k], g1r[-k]), m1);
             m2 = ffma2(bc2(ak[k - 1]), fsub2(qg[Q + k], qg[Q - k]), m2);
         }
         rr = ffma2(m1, bc2(ih1), rr);
