@@ -37,7 +37,7 @@ BYTES_PER_NODE = {"fp32": 68, "fp64": 136}     # 17 words: u^n 2, u^{n-1} 2, u^{
 # DRAM bytes per node of one FP32 interior launch (dram__bytes_read.sum + dram__bytes_write.sum of
 # k_interior_march<6,0> at 2 x 1601x801, scaled by nodes; profiles/launches_topography_fp32.md).
 # Set to None whenever that kernel changes until it is measured again.
-TRAFFIC_BYTES_PER_NODE = {"fp32": None, "fp64": None}
+TRAFFIC_BYTES_PER_NODE = {"fp32": 79155456 / 1239489, "fp64": None}
 FALLBACK_HBM_GBS = 6800.0
 N1, N2 = 4001, 2001
 # crop of the workload the oracle is timed on: a 401-column window around the source spanning
