@@ -699,7 +699,7 @@ template <int O> struct StripTile {
 // ordered by the host so that the costliest tiles (interface bands, side bands) start first.
 // B.smaps holds the block's band-box tensor maps: u[0], u[1], c.
 template <typename T, int O, int MODE>
-__global__ void __launch_bounds__(StripTile<O>::THREADS, 3)
+__global__ void __launch_bounds__(StripTile<O>::THREADS, sizeof(T) == 4 ? 4 : 2)
 k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles, StepArgs a, double beta, int* err) {
     using ST = StripTile<O>;
     constexpr int S = ST::S, NT = ST::THREADS;
