@@ -137,8 +137,8 @@ int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream);
 int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream);
 
 /* Device bytes a handle for `desc` holds after sbp_grid_create, sbp_set_material and
- * sbp_set_state (fields, coefficients, metric, face buffers), used to admit solves by HBM
- * footprint.  No device work. */
+ * sbp_set_state (fields, coefficients, metric, closure matrices of D_xx^FC, face buffers and
+ * interface traces, tensor maps), used to admit solves by HBM footprint.  No device work. */
 int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out);
 
 /* Pick the launch tuning for this grid by timing candidates on leapfrog steps from the current

@@ -37,7 +37,7 @@ struct HostFace {
     double* jhat = nullptr;
     void* ju = nullptr;
     void* g = nullptr;
-    void* sat = nullptr;
+    void* sat = nullptr;      // unused by the handle (sbp_apply_noalloc points its views at its own scratch)
     void* tr = nullptr;       // interface faces: trace of this side (k_face_trace), 7 x nf
 };
 
@@ -803,8 +803,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             F.reversed = bd.faces[f].reversed ? 1 : 0;
             F.nf = f < 2 ? hb.n2 : hb.n1;
             F.jhat = (double*)h->dalloc(F.nf * sizeof(double));
-            F.sat = h->dalloc(4 * (size_t)F.nf * es);
-            if (!F.jhat || !F.sat) return cleanup(SBP_E_OOM, "face buffers");
+            if (!F.jhat) return cleanup(SBP_E_OOM, "face buffers");
             refs.push_back(FaceRef{b, f, start, F.nf});
             start += F.nf;
             if (F.kind == FACE_INTF) {
@@ -1398,9 +1397,15 @@ int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out) {
         // u (2 x 2), c (10), w (1), r (2) in the field precision; X (2), G (4), J (1) in FP64
         total += al(2 * plane * es) * 2 + al(10 * plane * es) + al(plane * es) + al(2 * plane * es);
         total += al(2 * plane * 8) + al(4 * plane * 8) + al(plane * 8);
+        // closure matrices of D_xx^FC along x1 and x2, strip-tile tensor maps
+        if (desc->order == 2 || desc->order == 4 || desc->order == 6)
+            total += al((long long)closure_elems(desc->order, bd.n2) * es) + al((long long)closure_elems(desc->order, bd.n1) * es);
+        total += al(6 * (long long)sizeof(CUtensorMap));
         for (int f = 0; f < 4; ++f) {
             const long long nf = f < 2 ? bd.n2 : bd.n1;
-            total += al(nf * 8) + al(4 * nf * es) + al(3 * nf * es) + al(2 * 8 * nf * es);
+            // J^, Robin J^U, boundary data (2 x up to 8 basis functions), interface trace (7)
+            total += al(nf * 8) + al(3 * nf * es) + al(2 * 8 * nf * es);
+            if (bd.faces[f].kind == SBP_BC_INTERFACE) total += al(7 * nf * es);
         }
     }
     total += 4096;   // block views, face tables, source tables
