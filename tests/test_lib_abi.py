@@ -60,3 +60,29 @@ def test_null_handle_calls_are_rejected(L):
     assert L.sbp_destroy(None) == 0
     E = C.c_double()
     assert L.sbp_energy(None, 0.1, C.byref(E)) == -1
+
+
+@pytest.mark.parametrize("prec", ("fp32", "fp64"))
+def test_footprint_covers_every_device_buffer(L, prec):
+    """sbp_grid_footprint (host arithmetic only) is at least the sum of the buffers the handle
+    allocates: per block 17 field planes in the working precision (u 2 x 2, c 10, 1/(rho J), r 2),
+    7 FP64 metric planes, the closure matrices of D_xx^FC along both directions
+    (2 x NCLOS x NCLOSJ x 3 words per boundary line) and, per interface face, a 7-word trace per
+    face node; an interface adds exactly its two traces."""
+    import re
+    import os
+    from paper_2003_12811_gb300.binding import footprint_bytes
+    import workloads as W
+    es = 4 if prec == "fp32" else 8
+    tab = open(os.path.join(os.path.dirname(__file__), "..", "paper_2003_12811_gb300", "csrc", "sbp_tables.inc")).read()
+    d = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define SBP6_(\w+) (-?\d+)", tab)}
+    P = W.config3(n1=401, n2=201, order=6)
+    need = 0
+    for blk in P.blocks:
+        pitch = (blk.N1 + 31) // 32 * 32
+        plane = blk.N2 * pitch
+        need += 17 * plane * es + 7 * plane * 8
+        need += 2 * d["NCLOS"] * d["NCLOSJ"] * 3 * (blk.N1 + blk.N2) * es
+        need += sum(7 * (blk.N2 if f < 2 else blk.N1) * es for f, face in enumerate(blk.faces) if face.kind == "interface")
+    fp = footprint_bytes(P, prec)
+    assert need <= fp <= 1.05 * need + (1 << 20), (need, fp)
