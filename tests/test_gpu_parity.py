@@ -120,6 +120,17 @@ def test_config2_reduced(prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", (("fp64", FP64_TOL), ("fp32", 1e-4)))
+def test_config2_three_by_two_blocks(prec, tol):
+    """Config 2 geometry on 3 x 2 blocks of 28^2 (order 6): 7 interfaces, 14 interface sides,
+    more than one launch of interface traces per step; MMS, 60 steps."""
+    P = W.config2(n=28, order=6, nbx=3, nby=2)
+    assert sum(f.kind == "interface" for b in P.blocks for f in b.faces) == 14
+    gc, rc, _, _ = _run_both(P, 60, 0.25, prec)
+    err = relmax(gc, rc) if prec == "fp64" else rell2(gc, rc)
+    assert err < tol
+
+
+@pytest.mark.parametrize("prec,tol", (("fp64", FP64_TOL), ("fp32", 1e-4)))
 def test_config3_reduced_with_source(prec, tol):
     """Config 3 topography, tilted VTI, Robin + traction-free top, interface, Ricker point
     source, order 6, on 2 blocks of 101 x 51, 150 steps from rest."""

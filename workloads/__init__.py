@@ -298,17 +298,17 @@ def c2_rho(X1, X2):
     return 2 + np.sin(2 * np.pi * (X1 + X2)) * np.cos(np.pi * X1)
 
 
-def config2(n: int = 801, order: int = 6, window=None) -> Problem:
-    """2x2 curvilinear blocks of n x n nodes on [0,1]^2 with X = x + 0.05 sin(2 pi x) sin(2 pi y) (1,1);
+def config2(n: int = 801, order: int = 6, window=None, nbx: int = 2, nby: int = 2) -> Problem:
+    """2x2 (nbx x nby) curvilinear blocks of n x n nodes on [0,1]^2 with X = x + 0.05 sin(2 pi x) sin(2 pi y) (1,1);
     C(X) = rotation by theta(X) = (pi/6) sin(2 pi X1) sin(2 pi X2) of diag Voigt (4, 3, 1);
     rho = 2 + sin(2 pi (X1+X2)) cos(pi X1) in [1, 3]; welded interfaces, traction on the outer
     faces with manufactured data; manufactured forcing.
 
     window: optional {block: (i1_lo, i1_hi, i2_lo, i2_hi)} crop (oracle sampling)."""
     blocks = []
-    idx = lambda bx, by: by * 2 + bx
-    for by in range(2):
-        for bx in range(2):
+    idx = lambda bx, by: by * nbx + bx
+    for by in range(nby):
+        for bx in range(nbx):
             b = idx(bx, by)
             i1 = np.arange(n)
             i2 = np.arange(n)
@@ -318,7 +318,7 @@ def config2(n: int = 801, order: int = 6, window=None) -> Problem:
                 lo1, hi1, lo2, hi2 = window[b]
                 i1, i2 = np.arange(lo1, hi1), np.arange(lo2, hi2)
             xi1, xi2 = ref_grid(n, n, i1, i2)
-            x, y = (bx + xi1) / 2, (by + xi2) / 2
+            x, y = (bx + xi1) / nbx, (by + xi2) / nby
             X1, X2 = _c2_map(x, y)
             X = np.stack([X1, X2])
             rho = c2_rho(X1, X2)
@@ -327,7 +327,7 @@ def config2(n: int = 801, order: int = 6, window=None) -> Problem:
             for f in range(4):
                 sl = face_slice(f)
                 on_real = _window_touches(window, b, f, n, n)
-                outer = (f == 0 and bx == 0) or (f == 1 and bx == 1) or (f == 2 and by == 0) or (f == 3 and by == 1)
+                outer = (f == 0 and bx == 0) or (f == 1 and bx == nbx - 1) or (f == 2 and by == 0) or (f == 3 and by == nby - 1)
                 if not on_real:
                     faces.append(Face("open"))
                 elif outer:
