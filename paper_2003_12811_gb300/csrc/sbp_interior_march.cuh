@@ -336,9 +336,9 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         const size_t gi = (size_t)r * P + gx;
         if (a.with_data && B.jf) {
             const float* __restrict__ JF = reinterpret_cast<const float*>(B.jf);
-            #pragma unroll
-                for (int kb = 0; kb < 8; ++kb) {
-                    if (kb >= a.K) break;
+#pragma unroll
+            for (int kb = 0; kb < 8; ++kb) {
+                if (kb >= a.K) break;
                 r0 = __fmaf_rn((float)a.Tk[kb], JF[(size_t)kb * plane + gi], r0);
                 r1 = __fmaf_rn((float)a.Tk[kb], JF[(size_t)(a.K + kb) * plane + gi], r1);
             }

@@ -172,9 +172,9 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
         const size_t gi = (size_t)gy * P + gx;
         if (a.with_data && B.jf) {
             const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
-            #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (k >= a.K) break;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k >= a.K) break;
                 r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
                 r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
             }
@@ -610,9 +610,9 @@ __device__ __forceinline__ void strip_node(const BlockDev& B, const StepArgs& a,
     const size_t gi = (size_t)i2 * P + i1;
     if (a.with_data && B.jf) {
         const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
-        #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (k >= a.K) break;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k >= a.K) break;
             r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
             r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
         }
@@ -876,9 +876,9 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
     const size_t gi = (size_t)i2 * P + i1;
     if (a.with_data && B.jf) {
         const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
-        #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (k >= a.K) break;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k >= a.K) break;
             r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
             r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
         }
