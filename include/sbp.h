@@ -37,7 +37,10 @@ extern "C" {
 #define SBP_E_NONCONFORMING_INTERFACE (-3)   /* interface sides differ in node count or pairing */
 #define SBP_E_OOM (-4)
 #define SBP_E_CUDA (-5)
-#define SBP_E_TIMEOUT (-6)
+#define SBP_E_TIMEOUT (-6)                   /* a bounded wait of a kernel ran out (a TMA copy into shared
+                                                memory of the interior or strip kernels did not arrive);
+                                                reported by the next call that checks the kernels' error
+                                                word; the results of the steps since are invalid */
 #define SBP_E_UNSTABLE (-7)                  /* non-finite energy */
 #define SBP_E_STATE (-8)                     /* call out of order (e.g. step before material) */
 
