@@ -262,6 +262,25 @@ def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
                          "frac": achieved / peak, "peak_source": src, "traffic": None}}
 
 
+def replica_times(times, world):
+    """Job times of `world` independent replicas (one process per GPU, no data exchange): each
+    entry is the slowest rank's (MAX over ranks).  torch.distributed must be initialised when
+    world > 1; the reduction runs on the current CUDA device under NCCL, on the CPU under gloo."""
+    if world <= 1:
+        return [float(x) for x in times]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_value(nodes, steps, seconds, world):
+    """Whole-job node updates per second: every replica advances `nodes` by `steps` steps."""
+    return world * nodes * steps / seconds
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -356,12 +375,9 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     _, launches = S.sbp_profile_read()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_times([ms], world)[0]
     ms_per_step = ms / args.steps
-    value = world * nodes * args.steps / (ms / 1e3)
+    value = replica_value(nodes, args.steps, ms / 1e3, world)
 
     # ---- per-kernel timing (roofline of the dominant kernel): same K steps with events per family
     S.sbp_profile(True)
@@ -382,10 +398,10 @@ def main():
     S.sbp_step(args.steps, dt, sh)
     out = S.sbp_get_field(1)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = replica_times([time.perf_counter() - t0], world)[0]
     h2d = sum(2 * u.nbytes for u in up_h)
     d2h = sum(o.nbytes for o in out)
-    e2e = {"value": world * nodes * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": replica_value(nodes, args.steps, e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "one request: host->device upload of (u^{n-1}, u^n) as FP64 host arrays, K steps, "
                    "device->host read of u^n; bytes amortised over the K steps"}
