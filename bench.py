@@ -35,8 +35,8 @@ METRIC = "grid-pt updates/s"
 UNIT = "node-updates/s"
 BYTES_PER_NODE = {"fp32": 68, "fp64": 136}     # 17 words: u^n 2, u^{n-1} 2, u^{n+1} 2, c 10, 1/(rho J) 1
 # DRAM bytes per node of one FP32 interior launch (dram__bytes_read.sum + dram__bytes_write.sum of
-# k_interior_march<6,0> at 2 x 1601x801, scaled by nodes; profiles/launches_topography_fp32.md).
-# Set to None whenever that kernel changes until it is measured again.
+# k_interior_march<6,0> captured at 2 x 1601x801, scaled by nodes).  Set to None whenever that
+# kernel changes until it is measured again.
 TRAFFIC_BYTES_PER_NODE = {"fp32": 79155456 / 1239489, "fp64": None}
 FALLBACK_HBM_GBS = 6800.0
 N1, N2 = 4001, 2001
@@ -65,7 +65,8 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons around and during the timed region.  Samples every
+    10 ms (a short timed region still gets samples), plus one query on entry and one on exit."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -76,11 +77,20 @@ class ClockSampler:
         self.proc = None
         self.f = None
 
+    def _once(self):
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            return out.stdout.strip().splitlines()
+        except Exception:
+            return []
+
     def __enter__(self):
+        self.edges = self._once()
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -93,16 +103,14 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        self.edges += self._once()
 
-    def summary(self):
-        if self.proc is None or self.f is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.f.flush()
-        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+    @staticmethod
+    def _parse(lines):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [x.strip() for x in r]
+        for line in lines:
+            r = [x.strip() for x in line.split(",")]
             try:
                 sm.append(float(r[1]))
                 mx.append(float(r[2]))
@@ -111,9 +119,24 @@ class ClockSampler:
             for n, v in zip(names, r[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        return sm, mx, reasons
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        loop = [x for x in open(self.f.name).read().strip().splitlines() if x.strip()]
         os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sm, mx, reasons = self._parse(loop)
+        esm, emx, ereasons = self._parse(self.edges)
+        # the median comes from the samples taken while the timed region ran; the queries on entry
+        # and exit (right before and after it) stand in only when a very short region got none
+        src = "during" if sm else "edges"
+        med = statistics.median(sm) if sm else (statistics.median(esm) if esm else None)
+        allmx = mx + emx
+        return {"sm_mhz": med, "sm_max_mhz": max(allmx) if allmx else None,
+                "reasons": sorted(reasons | ereasons), "samples": len(sm), "edge_samples": len(esm),
+                "source": src}
 
 
 def run_oracle_steps(prec_unused, steps, warmup):
@@ -141,7 +164,7 @@ def cpu_baseline(target_seconds=12.0):
     per = d["seconds"] / d["steps"]
     n = max(3, min(60, int(target_seconds / max(per, 1e-6))))
     rate, d = run_oracle_steps(None, n, 0)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": rate, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{d['steps']} leapfrog steps of the FP64 oracle on a crop of the workload: 2 blocks "
                       f"of 401x161 nodes ({d['nodes']} nodes) around the source and interface; "
                       f"{time.perf_counter() - t0:.1f} s incl. assembly"}
@@ -296,7 +319,7 @@ def reference_arm(args):
             "steps": K, "warmup": Wm, "ms_per_step": 1e3 * d["seconds"] / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name("fp64") + " -- oracle on a bounded crop", "nodes": d["nodes"]},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{K} steps on a crop of {d['nodes']} nodes (2 blocks of 401x161)"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

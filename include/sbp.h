@@ -53,6 +53,10 @@ extern "C" {
 #define SBP_BC_ROBIN 1           /* T u + U u = g, SAT of eq. sat_traction (traction when U = 0) */
 #define SBP_BC_INTERFACE 2       /* welded interface, SATs of eq. scheme_interface (V = Theta = 0) */
 
+/* stiffness layouts of sbp_set_material and sbp_misfit_gradient */
+#define SBP_C_PAIR10 0           /* 10 planes: upper triangle of the 4x4 pair matrix (any major-symmetric C) */
+#define SBP_C_VOIGT6 1           /* 6 planes: Voigt C11 C12 C13 C22 C23 C33 (1 = xx, 2 = yy, 3 = xy; needs minor symmetry) */
+
 /* fields for sbp_get_field */
 #define SBP_FIELD_PREV 0         /* u^{n-1} (after a step: the previous level) */
 #define SBP_FIELD_CUR 1          /* u^n (current level) */
@@ -95,12 +99,18 @@ int sbp_destroy(sbp_handle* h);
 /* Message of the last failing call on h (h may be NULL: last sbp_grid_create failure). */
 const char* sbp_last_error(const sbp_handle* h);
 
-/* Density and stiffness of one block (Sec. 3, eq. transf_density_stiffness).
- * rho: n1*n2 values.  C: 10 planes of n1*n2 values, the upper triangle of the symmetric 4x4
- * pair matrix M[p][q] = C_IJKL, p = 2I+J, q = 2K+L (I,J,K,L in {0,1}) in the order
- * (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3).  Major symmetry is implied;
- * minor symmetry is not assumed (Cosserat).  Forms c_ijkl and 1/(rho J) on the device. */
-int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* C);
+/* Density and stiffness of one block (Sec. 3, eq. transf_density_stiffness; the stiffness
+ * symmetries of Sec. 3: major symmetry always, minor symmetry not assumed).
+ * rho: n1*n2 values.  C in the layout c_layout, planes of n1*n2 values:
+ *   SBP_C_PAIR10: 10 planes, the upper triangle of the symmetric 4x4 pair matrix M[p][q] = C_IJKL,
+ *     p = 2I+J, q = 2K+L (I,J,K,L in {0,1}), in the order (0,0) (0,1) (0,2) (0,3) (1,1) (1,2)
+ *     (1,3) (2,2) (2,3) (3,3) -- any major-symmetric (Cosserat) stiffness;
+ *   SBP_C_VOIGT6: 6 planes C11 C12 C13 C22 C23 C33 of the symmetric 3x3 Voigt matrix (Voigt
+ *     index 1 = (1,1), 2 = (2,2), 3 = (1,2) = (2,1)) -- stiffness with minor symmetry; it is
+ *     expanded to the pair layout (C_IJKL = Voigt entry of (IJ), (KL)).
+ * Forms c_ijkl and 1/(rho J) on the device.  Errors: SBP_E_INVALID_ARG (bad block, layout,
+ * non-positive or non-finite density). */
+int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* C, int c_layout);
 
 /* Robin matrix U (Sec. 5.1) of a ROBIN face: 3 planes of nf values (U11, U12, U22), physical. */
 int sbp_set_robin(sbp_handle* h, int block, int face, const double* U);
@@ -126,6 +136,21 @@ int sbp_add_point_source(sbp_handle* h, int block, double x1, double x2, double 
 /* Initial state of one block: u_prev = u^{-1}, u_cur = u^0, each 2 planes (u_1, u_2) of
  * n1*n2 values (host).  t is the time of u_cur (same for all blocks; the last call wins). */
 int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* u_cur, double t);
+
+/* State through caller-owned device buffers (borrowed: read or written by work enqueued on `stream`,
+ * so they must stay alive until that work has finished; the caller, e.g. PyTorch, owns them).
+ * Layout: 2 planes (u_1, u_2) of n2 rows x `pitch` elements, x1 fastest, elements in the handle's
+ * precision (double for SBP_FP64, float for SBP_FP32); plane 1 starts n2*pitch elements after
+ * plane 0.  The pointer must be 16-byte aligned and pitch*sizeof(element) a multiple of 16 bytes
+ * with pitch >= n1; buffers must live on the handle's device.
+ * sbp_set_state_device: u_prev = u^{-1}, u_cur = u^0 of one block, t the time of u_cur (as
+ *   sbp_set_state, without the FP64 host round trip).
+ * sbp_get_field_device: copy SBP_FIELD_PREV / CUR / APPLY of one block into dst.
+ * Both are stream-ordered (asynchronous).  Errors: SBP_E_INVALID_ARG (pointer, alignment, pitch,
+ * device), SBP_E_CUDA. */
+int sbp_set_state_device(sbp_handle* h, int block, const void* u_prev, const void* u_cur, long long pitch, double t,
+                         void* stream);
+int sbp_get_field_device(sbp_handle* h, int block, int which, void* dst, long long pitch, void* stream);
 
 /* Advance all blocks by nsteps leapfrog steps of size dt, asynchronously on `stream`
  * (a cudaStream_t; NULL = default stream). */
@@ -201,11 +226,24 @@ int sbp_profile_read(sbp_handle* h, double* ms, long long* launches);
  * The per-face SAT terms and the device copies of the block tables live in one
  * fixed 8 MiB file-scope device array shared by every call; grids needing more scratch are
  * rejected with SBP_E_INVALID_ARG before any device work.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) -- make that first call before any stream
- * capture.  Calls that overlap on the GPU (concurrent streams, several handles) race on the
- * shared array: serialise them.  The call is stream-ordered on `stream` and returns after the
- * stream has drained.  No cudaMalloc/cudaFree or allocating library routine is called. */
+ * that array's device address (cudaGetSymbolAddress, once per device).  Calls that overlap on the
+ * GPU (concurrent streams, several handles) race on the shared array: serialise them.  The call
+ * is stream-ordered on `stream` and returns after the stream has drained (it synchronises the
+ * stream), so it cannot be called while that stream is being captured into a CUDA graph.  The
+ * current device must be the one that was current at sbp_grid_create (else SBP_E_STATE).
+ * No cudaMalloc/cudaFree or allocating library routine is called. */
 int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_data, double t, void* stream);
+
+/* Synchronise the device and report any error the kernels recorded since the last check
+ * (SBP_E_TIMEOUT when a bounded wait ran out; the error word is cleared by the report). */
+int sbp_check(sbp_handle* h);
+
+/* Diagnostic of the timeout path (no counterpart in the paper): enqueues, on the default stream,
+ * one thread that waits with the kernels' bounded mbarrier wait on a barrier that nothing arrives
+ * at, giving up after `polls` polls (1 .. 2^20); no copy is issued, so nothing is left in flight.
+ * The next call that checks the error word (sbp_check, sbp_apply, sbp_get_field, sbp_energy, ...)
+ * returns SBP_E_TIMEOUT and clears it.  Errors: SBP_E_INVALID_ARG for polls out of range. */
+int sbp_debug_wait_probe(sbp_handle* h, int polls);
 
 /* Current simulation time and number of resident nodes. */
 int sbp_get_time(const sbp_handle* h, double* t_out);
@@ -228,9 +266,11 @@ int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces);
  * leapfrog steps from the current state (the levels sbp_record would record), and its exact
  * discrete gradient with respect to the density and the stiffness of every node:
  *   grad_rho[b]: n1*n2 doubles (x1 fastest), dPhi/drho;
- *   grad_C[b]:   10 planes of n1*n2 doubles, dPhi/dC in the pair layout of sbp_set_material
- *                (plane P = entry P of the upper triangle of M[2I+J][2K+L] = C_IJKL, which stands
- *                for both M[p][q] and M[q][p]).
+ *   grad_C[b]:   dPhi/dC in the layout c_layout of sbp_set_material: SBP_C_PAIR10, 10 planes of
+ *                n1*n2 doubles (plane P = entry P of the upper triangle of M[2I+J][2K+L] =
+ *                C_IJKL, which stands for both M[p][q] and M[q][p]); SBP_C_VOIGT6, 6 planes, the
+ *                derivative with respect to each Voigt entry C11 C12 C13 C22 C23 C33 (the sum of
+ *                the pair entries it sets).
  * Either array pointer (or an entry) may be null to skip that output; `observed` is host FP64
  * [nsteps][nrec][2]; *misfit receives Phi.  Method: a forward pass that stores the state every
  * `checkpoint_every` steps (0: ceil(sqrt(nsteps))), then, segment by segment from the last, a
@@ -245,7 +285,7 @@ int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces);
  * Errors: SBP_E_STATE without receivers or when a displacement face carries boundary data (the
  * data would then depend on C); SBP_E_OOM when the workspace does not fit. */
 int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* observed, int checkpoint_every,
-                        double* misfit, double* const* grad_rho, double* const* grad_C);
+                        double* misfit, double* const* grad_rho, double* const* grad_C, int c_layout);
 
 #ifdef __cplusplus
 }

@@ -134,16 +134,42 @@ def pair_unit(P: int) -> np.ndarray:
     return m
 
 
+# Voigt parametrisation (stiffness with minor symmetry): index 0 = (1,1), 1 = (2,2), 2 = (1,2) = (2,1)
+# of a pair of tensor indices, entries in the order 11 12 13 22 23 33 of the symmetric 3x3 matrix
+VOIGT_OF_PAIR = (0, 2, 2, 1)          # pair p = 2I+J -> Voigt index of (I, J)
+VOIGT_ENTRIES = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+
+
+def voigt_unit(V: int) -> np.ndarray:
+    """4x4 pair matrix of the tensor whose Voigt matrix has a one at entry V (and its mirror):
+    C_IJKL = 1 where the Voigt indices of (I,J) and (K,L) are the two indices of entry V."""
+    a, b = VOIGT_ENTRIES[V]
+    m = np.zeros((4, 4))
+    for p in range(4):
+        for q in range(4):
+            if sorted((VOIGT_OF_PAIR[p], VOIGT_OF_PAIR[q])) == [a, b]:
+                m[p, q] = 1.0
+    return m
+
+
 def _with_stiffness(problem: W.Problem, stiff: List[np.ndarray]) -> W.Problem:
     blocks = [dataclasses.replace(b, C=C) for b, C in zip(problem.blocks, stiff)]
     return dataclasses.replace(problem, blocks=blocks, sources=[], time_basis=[])
 
 
-def stiffness_derivative(problem: W.Problem, block: int, P: int, i1: int, i2: int, A0=None):
-    """dA_glob/dC_P(x) = A(E) - A(0) (A_glob is affine in C); A0 = A(0) may be passed in."""
+def _unit_matrix(P) -> np.ndarray:
+    """Pair matrix of a stiffness parameter: P an int (pair entry) or ("voigt", V) (Voigt entry)."""
+    if isinstance(P, tuple) and P[0] == "voigt":
+        return voigt_unit(int(P[1]))
+    return pair_unit(int(P))
+
+
+def stiffness_derivative(problem: W.Problem, block: int, P, i1: int, i2: int, A0=None):
+    """dA_glob/dC_P(x) = A(E) - A(0) (A_glob is affine in C); A0 = A(0) may be passed in.
+    P: pair entry (int) or ("voigt", V)."""
     zero = [np.zeros_like(b.C) for b in problem.blocks]
     unit = [z.copy() for z in zero]
-    unit[block][..., i2, i1] = W.pair10_to_tensor(pair_unit(P)[:, :, None, None])[..., 0, 0]
+    unit[block][..., i2, i1] = W.pair10_to_tensor(_unit_matrix(P)[:, :, None, None])[..., 0, 0]
     A1 = Oracle(_with_stiffness(problem, unit)).A
     if A0 is None:
         A0 = Oracle(_with_stiffness(problem, zero)).A
@@ -151,7 +177,7 @@ def stiffness_derivative(problem: W.Problem, block: int, P: int, i1: int, i2: in
 
 
 def grad_stiffness(oracle: Oracle, levels, lams, dt: float, params):
-    """dPhi/dC_P(x) for params given as (block, P, i1, i2)."""
+    """dPhi/dC_P(x) for params given as (block, P, i1, i2), P a pair entry or ("voigt", V)."""
     U = np.stack(levels[1:len(lams) + 1], axis=1)              # u_1 .. u_N as columns
     WL = np.stack(lams, axis=1) * oracle.wvec[:, None]          # diag(w) lambda_n
     A0 = Oracle(_with_stiffness(oracle.problem, [np.zeros_like(b.C) for b in oracle.problem.blocks])).A
@@ -183,7 +209,8 @@ def misfit_of(problem: W.Problem, u_prev, u_cur, t0, dt, nsteps, receivers, obse
 
 
 def perturbed(problem: W.Problem, block: int, kind, i1: int, i2: int, eps: float) -> W.Problem:
-    """Copy of problem with rho (kind == 'rho') or pair entry P (kind == P) at one node moved by eps."""
+    """Copy of problem with rho (kind == 'rho'), pair entry P (kind == P) or Voigt entry V
+    (kind == ("voigt", V)) at one node moved by eps."""
     blocks = list(problem.blocks)
     b = blocks[block]
     if kind == "rho":
@@ -192,6 +219,6 @@ def perturbed(problem: W.Problem, block: int, kind, i1: int, i2: int, eps: float
         blocks[block] = dataclasses.replace(b, rho=rho)
     else:
         C = b.C.copy()
-        C[..., i2, i1] += eps * W.pair10_to_tensor(pair_unit(int(kind))[:, :, None, None])[..., 0, 0]
+        C[..., i2, i1] += eps * W.pair10_to_tensor(_unit_matrix(kind)[:, :, None, None])[..., 0, 0]
         blocks[block] = dataclasses.replace(b, C=C)
     return dataclasses.replace(problem, blocks=blocks)

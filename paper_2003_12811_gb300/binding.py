@@ -23,6 +23,7 @@ STATUS = {0: "SBP_OK", -1: "SBP_E_INVALID_ARG", -2: "SBP_E_JACOBIAN_NONPOSITIVE"
 FP64, FP32 = 0, 1
 BC = {"displacement": 0, "robin": 1, "interface": 2}
 FIELD_PREV, FIELD_CUR, FIELD_APPLY = 0, 1, 2
+C_PAIR10, C_VOIGT6 = 0, 1
 PROF_FAMILIES = 8      # SBP_PROF_FAMILIES
 
 
@@ -66,13 +67,16 @@ def lib():
         L.sbp_destroy.argtypes = [C.c_void_p]
         L.sbp_last_error.argtypes = [C.c_void_p]
         L.sbp_last_error.restype = C.c_char_p
-        L.sbp_set_material.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
+        L.sbp_set_material.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_int]
         L.sbp_set_robin.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.sbp_set_time_basis.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), _DP]
         L.sbp_set_boundary_data.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.sbp_set_forcing.argtypes = [C.c_void_p, C.c_int, _DP]
         L.sbp_add_point_source.argtypes = [C.c_void_p, C.c_int] + [C.c_double] * 7
         L.sbp_set_state.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_double]
+        L.sbp_set_state_device.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_double,
+                                           C.c_void_p]
+        L.sbp_get_field_device.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p]
         L.sbp_step.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_apply.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.sbp_get_field.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
@@ -87,10 +91,12 @@ def lib():
         L.sbp_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sbp_check.argtypes = [C.c_void_p]
+        L.sbp_debug_wait_probe.argtypes = [C.c_void_p, C.c_int]
         L.sbp_set_receivers.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
         L.sbp_record.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP]
         L.sbp_misfit_gradient.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP, C.c_int, _DP,
-                                          C.POINTER(_DP), C.POINTER(_DP)]
+                                          C.POINTER(_DP), C.POINTER(_DP), C.c_int]
         _lib = L
     return _lib
 
@@ -154,25 +160,7 @@ class Solver:
         self.L = lib()
         self.problem = problem
         self.precision = FP64 if precision == "fp64" else FP32
-        self._keep = []
-        blocks = (BlockDesc * len(problem.blocks))()
-        for b, blk in enumerate(problem.blocks):
-            x1, x2 = _f64(blk.X[0]), _f64(blk.X[1])
-            self._keep += [x1, x2]
-            bd = blocks[b]
-            bd.n1, bd.n2 = blk.N1, blk.N2
-            bd.x1, bd.x2 = _ptr(x1), _ptr(x2)
-            bd.h1, bd.h2 = blk.spacing
-            for f, face in enumerate(blk.faces):
-                if face.kind not in BC:
-                    raise ValueError(f"face kind {face.kind!r} is not supported by libsbp")
-                fd = bd.faces[f]
-                fd.kind = BC[face.kind]
-                if face.kind == "interface":
-                    fd.nbr_block, fd.nbr_face, fd.reversed = face.nbr[0], face.nbr[1], int(bool(face.nbr[2]))
-                else:
-                    fd.nbr_block, fd.nbr_face, fd.reversed = -1, -1, 0
-        desc = GridDesc(problem.order, self.precision, len(problem.blocks), blocks, problem.beta)
+        desc, self._keep = grid_desc(problem, precision)
         h = C.c_void_p()
         rc = self.L.sbp_grid_create(C.byref(desc), C.byref(h))
         if rc != SBP_OK:
@@ -195,9 +183,7 @@ class Solver:
             om = _f64([w for _, w in P.time_basis])
             self._check(self.L.sbp_set_time_basis(self.h, len(P.time_basis), kinds, _ptr(om)))
         for b, blk in enumerate(P.blocks):
-            rho = _f64(blk.rho)
-            Cp = _f64(pair10(blk.C))
-            self._check(self.L.sbp_set_material(self.h, b, _ptr(rho), _ptr(Cp)))
+            self.sbp_set_material(b, blk.rho, pair10(blk.C), C_PAIR10)
             for f, face in enumerate(blk.faces):
                 if face.kind == "robin" and face.U is not None:
                     U = _f64(face.U)
@@ -213,6 +199,21 @@ class Solver:
                                                     s.direction[1], s.amplitude, s.alpha_p, s.t0))
 
     # ---------------------------------------------------------------- C entry points
+    def sbp_set_material(self, block, rho, Cplanes, layout=C_PAIR10):
+        """rho (N2, N1); Cplanes (10, N2, N1) pair layout or (6, N2, N1) Voigt layout."""
+        r, c = _f64(rho), _f64(Cplanes)
+        self._check(self.L.sbp_set_material(self.h, int(block), _ptr(r), _ptr(c), int(layout)))
+
+    def sbp_set_state_device(self, block, u_prev_ptr, u_cur_ptr, pitch, t, stream=None):
+        """Device addresses of caller buffers: 2 planes of N2 rows x pitch elements each."""
+        s = None if stream is None else C.c_void_p(stream)
+        self._check(self.L.sbp_set_state_device(self.h, int(block), C.c_void_p(u_prev_ptr), C.c_void_p(u_cur_ptr),
+                                                int(pitch), float(t), s))
+
+    def sbp_get_field_device(self, block, which, dst_ptr, pitch, stream=None):
+        s = None if stream is None else C.c_void_p(stream)
+        self._check(self.L.sbp_get_field_device(self.h, int(block), int(which), C.c_void_p(dst_ptr), int(pitch), s))
+
     def sbp_set_state(self, u_prev, u_cur, t):
         for b, (up, uc) in enumerate(zip(u_prev, u_cur)):
             a, c = _f64(up), _f64(uc)
@@ -279,18 +280,25 @@ class Solver:
         self._check(self.L.sbp_record(self.h, int(nsteps), float(dt), _ptr(out)))
         return out
 
-    def sbp_misfit_gradient(self, nsteps, dt, observed, checkpoint_every=0, rho=True, stiffness=True):
-        """Returns (misfit, [dPhi/drho (N2, N1)] or None, [dPhi/dC (10, N2, N1) pair layout] or None)."""
+    def sbp_misfit_gradient(self, nsteps, dt, observed, checkpoint_every=0, rho=True, stiffness=True, layout=C_PAIR10):
+        """Returns (misfit, [dPhi/drho (N2, N1)] or None, [dPhi/dC (10 or 6, N2, N1) in `layout`] or None)."""
         obs = _f64(observed)
         nb = len(self.problem.blocks)
+        ncp = 6 if layout == C_VOIGT6 else 10
         gr = [np.empty((b.N2, b.N1)) for b in self.problem.blocks] if rho else None
-        gc = [np.empty((10, b.N2, b.N1)) for b in self.problem.blocks] if stiffness else None
+        gc = [np.empty((ncp, b.N2, b.N1)) for b in self.problem.blocks] if stiffness else None
         pr = (_DP * nb)(*[_ptr(a) for a in gr]) if rho else None
         pc = (_DP * nb)(*[_ptr(a) for a in gc]) if stiffness else None
         phi = C.c_double()
         self._check(self.L.sbp_misfit_gradient(self.h, int(nsteps), float(dt), _ptr(obs), int(checkpoint_every),
-                                               C.byref(phi), pr, pc))
+                                               C.byref(phi), pr, pc, int(layout)))
         return phi.value, gr, gc
+
+    def sbp_check(self):
+        self._check(self.L.sbp_check(self.h))
+
+    def sbp_debug_wait_probe(self, polls):
+        self._check(self.L.sbp_debug_wait_probe(self.h, int(polls)))
 
     def sbp_profile(self, enable):
         self._check(self.L.sbp_profile(self.h, int(bool(enable))))

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(256) k_grad_strip_sum(BlockDev B, GradDev G, i
 // FP64 arrays: g_C[P] = sum_p g_c[p] dc_p/dC_P with c_ijkl = J F_Ii C_IjKl F_Kk.
 template <typename T>
 __global__ void k_grad_to_C(BlockDev B, const T* __restrict__ gc, const T* __restrict__ grho, double* __restrict__ outC,
-                            double* __restrict__ outR) {
+                            double* __restrict__ outR, int voigt) {
     const long long n = (long long)B.n1 * B.n2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -562,6 +562,12 @@ __global__ void k_grad_to_C(BlockDev B, const T* __restrict__ gc, const T* __res
     for (int p = 0; p < 10; ++p) g[p] = (double)gc[(size_t)p * plane + gi];
     const int ijkl[10][4] = {{0, 0, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}, {1, 0, 1, 0}, {1, 0, 1, 1},
                              {1, 1, 1, 1}, {0, 0, 1, 0}, {0, 0, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
+    // Voigt output (minor symmetry): the Voigt entry of pair entry idx (the Voigt index of a pair
+    // p = 2I+J is 0 for (0,0), 1 for (1,1), 2 for (0,1)/(1,0); upper triangle in the order
+    // 11 12 13 22 23 33); a Voigt entry moves every pair entry that maps to it, so its derivative
+    // is the sum of theirs
+    const int to_voigt[10] = {0, 2, 2, 1, 5, 5, 4, 5, 4, 3};
+    double gv[6] = {0, 0, 0, 0, 0, 0};
     int idx = 0;
     for (int p = 0; p < 4; ++p)
         for (int q = p; q < 4; ++q) {
@@ -577,9 +583,12 @@ __global__ void k_grad_to_C(BlockDev B, const T* __restrict__ gc, const T* __res
                     }
                 s += g[pl] * J * c;
             }
-            outC[(size_t)idx * n + t] = s;
+            if (voigt) gv[to_voigt[idx]] += s;
+            else outC[(size_t)idx * n + t] = s;
             ++idx;
         }
+    if (voigt)
+        for (int v = 0; v < 6; ++v) outC[(size_t)v * n + t] = gv[v];
     outR[t] = (double)grho[gi];
 }
 

@@ -14,7 +14,6 @@
 #include <cudaTypedefs.h>
 
 #include "../../include/sbp.h"
-#include "sbp_interior_tma.cuh"
 #include "sbp_interior_march.cuh"
 #include "sbp_kernels.cuh"
 #include "sbp_adjoint.cuh"
@@ -54,7 +53,6 @@ struct HostBlock {
     double* J = nullptr;
     bool material = false;
     HostFace f[4];
-    TmaMaps maps;             // FP32 tile interior kernel tensor maps
     MarchMaps mmaps;          // FP32 column-marching interior kernel tensor maps
     void* psi[2] = {nullptr, nullptr};   // adjoint fields (sbp_misfit_gradient), allocated on first use
     MarchMaps pmaps;          // marching-kernel maps over the adjoint fields
@@ -109,6 +107,7 @@ struct sbp_handle {
     int* d_flag = nullptr;
     int* d_err = nullptr;       // kernel error flags (bounded waits that ran out)
     int num_sms = 0;
+    int device = 0;             // CUDA device current at sbp_grid_create (holds every buffer)
     std::string err;
     std::vector<void*> allocs;
     // kernel timing (benchmarks): the families of sbp_profile in include/sbp.h
@@ -295,7 +294,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 3-D map over `planes` consecutive float planes of n2 x pitch, box [planes][rows][width]
-bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows, int width = TBOXW, int esize = 4) {
+bool make_map(CUtensorMap* m, void* base, int pitch, int n2, int planes, int rows, int width, int esize = 4) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)n2, (cuuint64_t)planes};
@@ -324,8 +323,6 @@ bool make_strip_maps(const sbp_handle* h, const HostBlock& hb, void* u0, void* u
            make_map(&dst[1], u1, hb.pitch, hb.n2, 2, bh, bw, es) &&
            make_map(&dst[2], hb.c, hb.pitch, hb.n2, 10, bh, bw, es);
 }
-
-template <int O> int tma_rows() { return TmaTile<O>::SY; }
 
 // one operator application (mode 1) or leapfrog step (mode 0) on the state fields, or, with adj,
 // on the adjoint fields (the same kernels; the sources are skipped)
@@ -461,12 +458,10 @@ template <typename T, int O> void set_smem_attr() {
     if (std::is_same<T, float>::value) {
         cudaFuncSetAttribute(k_interior_march<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
-        cudaFuncSetAttribute(k_interior_tma<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaTile<O>::BYTES);
-        cudaFuncSetAttribute(k_interior_tma<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaTile<O>::BYTES);
     }
 }
 
-// kernel error flags: bits 2 (tile kernel), 4 (marching kernel), 8 (strip tiles) = a bounded wait ran out
+// kernel error word: ERR_* bits (sbp_device.cuh) set by kernels whose bounded wait ran out
 int check_kernel_errors(sbp_handle* h) {
     int e = 0;
     if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -490,8 +485,9 @@ int upload_sources(sbp_handle* h) {
     h->d_src_nodes = (SrcNode*)h->dalloc(sizeof(SrcNode) * h->src_nodes.size());
     h->d_src_params = (SrcParam*)h->dalloc(sizeof(SrcParam) * h->src_params.size());
     if (!h->d_src_nodes || !h->d_src_params) return h->fail(SBP_E_OOM, "source tables");
-    cudaMemcpy(h->d_src_nodes, h->src_nodes.data(), sizeof(SrcNode) * h->src_nodes.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(h->d_src_params, h->src_params.data(), sizeof(SrcParam) * h->src_params.size(), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(h->d_src_nodes, h->src_nodes.data(), sizeof(SrcNode) * h->src_nodes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_src_params, h->src_params.data(), sizeof(SrcParam) * h->src_params.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "source table upload failed");
     h->src_dirty = false;
     return check_cuda(h, "source upload");
 }
@@ -757,6 +753,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     {
         int dev = 0;
         cudaGetDevice(&dev);
+        h->device = dev;
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (h->num_sms <= 0) h->num_sms = 1;
     }
@@ -813,11 +810,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             }
         }
         if (h->precision == SBP_FP32) {
-            const int rows = o == 2 ? tma_rows<2>() : (o == 4 ? tma_rows<4>() : tma_rows<6>());
-            if (!make_map(&hb.maps.u[0], hb.u[0], hb.pitch, hb.n2, 2, rows) ||
-                !make_map(&hb.maps.u[1], hb.u[1], hb.pitch, hb.n2, 2, rows) ||
-                !make_map(&hb.maps.c, hb.c, hb.pitch, hb.n2, 10, rows) ||
-                !make_map(&hb.mmaps.u[0], hb.u[0], hb.pitch, hb.n2, 2, MR, MBOXW) ||
+            if (!make_map(&hb.mmaps.u[0], hb.u[0], hb.pitch, hb.n2, 2, MR, MBOXW) ||
                 !make_map(&hb.mmaps.u[1], hb.u[1], hb.pitch, hb.n2, 2, MR, MBOXW) ||
                 !make_map(&hb.mmaps.c, hb.c, hb.pitch, hb.n2, 10, MR, MBOXW))
                 return cleanup(SBP_E_CUDA, "tensor map encoding failed");
@@ -834,18 +827,21 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         double* tmp = (double*)h->dalloc(2 * (size_t)bd.n1 * bd.n2 * sizeof(double));
         if (!tmp) return cleanup(SBP_E_OOM, "staging buffer");
         const size_t n = (size_t)bd.n1 * bd.n2;
-        cudaMemcpy(tmp, bd.x1, n * sizeof(double), cudaMemcpyHostToDevice);
-        cudaMemcpy(tmp + n, bd.x2, n * sizeof(double), cudaMemcpyHostToDevice);
+        if (cudaMemcpy(tmp, bd.x1, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(tmp + n, bd.x2, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(SBP_E_CUDA, "coordinate upload failed");
         k_to_pitched<double><<<grid_for(2 * (long long)n), 256>>>(hb.X, tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
-        cudaDeviceSynchronize();
+        const cudaError_t ce = cudaDeviceSynchronize();
         h->dfree(tmp);
+        if (ce != cudaSuccess) return cleanup(SBP_E_CUDA, std::string("coordinate conversion failed: ") + cudaGetErrorString(ce));
     }
     h->nrefs = (int)refs.size();
     h->nface_nodes = start;
     h->d_refs = (FaceRef*)h->dalloc(sizeof(FaceRef) * refs.size());
     h->d_blocks = (BlockDev*)h->dalloc(sizeof(BlockDev) * h->blocks.size());
     if (!h->d_refs || !h->d_blocks) return cleanup(SBP_E_OOM, "tables");
-    cudaMemcpy(h->d_refs, refs.data(), sizeof(FaceRef) * refs.size(), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(h->d_refs, refs.data(), sizeof(FaceRef) * refs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(SBP_E_CUDA, "face table upload failed");
     h->ntrefs = nintf;
     if (sync_views(h) != SBP_OK) return cleanup(SBP_E_CUDA, h->err);
     {
@@ -876,7 +872,8 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         h->ntiles = (int)tv.size();
         h->d_tiles = (int2*)h->dalloc(sizeof(int2) * tv.size());
         if (!h->d_tiles) return cleanup(SBP_E_OOM, "tile table");
-        cudaMemcpy(h->d_tiles, tv.data(), sizeof(int2) * tv.size(), cudaMemcpyHostToDevice);
+        if (cudaMemcpy(h->d_tiles, tv.data(), sizeof(int2) * tv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(SBP_E_CUDA, "tile table upload failed");
     }
     // metric
     cudaMemset(h->d_flag, 0, sizeof(int));
@@ -889,8 +886,9 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         for (int f = 0; f < 4; ++f) k_face_jhat<<<grid_for(hb.f[f].nf), 256>>>(b, f, hb.f[f].jhat);
     }
     int flag = 0;
-    cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost);
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return cleanup(SBP_E_CUDA, "metric setup failed");
+    if (cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return cleanup(SBP_E_CUDA, "metric setup failed");
     if (flag) return cleanup(SBP_E_JACOBIAN_NONPOSITIVE, "non-positive Jacobian determinant");
     *out = h;
     return SBP_OK;
@@ -915,14 +913,25 @@ int sbp_destroy(sbp_handle* h) {
     return SBP_OK;
 }
 
-int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* C) {
+int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* C, int c_layout) {
     if (!h) return SBP_E_INVALID_ARG;
     if (block < 0 || block >= h->nblocks) return h->fail(SBP_E_INVALID_ARG, "bad block index");
     if (!rho || !C) return h->fail(SBP_E_INVALID_ARG, "null material arrays");
+    if (c_layout != SBP_C_PAIR10 && c_layout != SBP_C_VOIGT6) return h->fail(SBP_E_INVALID_ARG, "c_layout must be SBP_C_PAIR10 or SBP_C_VOIGT6");
     HostBlock& hb = h->blocks[block];
     const size_t n = (size_t)hb.n1 * hb.n2;
     for (size_t i = 0; i < n; ++i)
         if (!(rho[i] > 0.0) || !std::isfinite(rho[i])) return h->fail(SBP_E_INVALID_ARG, "density must be positive and finite");
+    // Voigt input (minor symmetry): every pair entry M[2I+J][2K+L] = C_IJKL is the Voigt entry of
+    // its two pair indices (Voigt index 0 for (0,0), 1 for (1,1), 2 for (0,1) and (1,0)); the
+    // planes are permuted into the pair layout the material kernel reads
+    std::vector<double> expanded;
+    if (c_layout == SBP_C_VOIGT6) {
+        const int from_voigt[10] = {0, 2, 2, 1, 5, 5, 4, 5, 4, 3};
+        expanded.resize(10 * n);
+        for (int p = 0; p < 10; ++p) std::memcpy(expanded.data() + p * n, C + from_voigt[p] * n, n * sizeof(double));
+        C = expanded.data();
+    }
     double* d_rho = (double*)h->dalloc(n * sizeof(double));
     double* d_C = (double*)h->dalloc(10 * n * sizeof(double));
     if (!d_rho || !d_C) {
@@ -930,8 +939,12 @@ int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* 
         h->dfree(d_C);
         return h->fail(SBP_E_OOM, "material staging");
     }
-    cudaMemcpy(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(d_C, C, 10 * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_C, C, 10 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        h->dfree(d_rho);
+        h->dfree(d_C);
+        return h->fail(SBP_E_CUDA, "material upload failed");
+    }
     BlockDev b = make_view(h, hb);
     if (h->precision == SBP_FP64) k_material<double><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
     else k_material<float><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
@@ -966,7 +979,10 @@ int sbp_set_robin(sbp_handle* h, int block, int face, const double* U) {
     if (!F.ju) F.ju = h->dalloc(3 * (size_t)F.nf * h->esize);
     double* tmp = (double*)h->dalloc(3 * (size_t)F.nf * sizeof(double));
     if (!F.ju || !tmp) return h->fail(SBP_E_OOM, "robin buffers");
-    cudaMemcpy(tmp, U, 3 * (size_t)F.nf * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(tmp, U, 3 * (size_t)F.nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        h->dfree(tmp);
+        return h->fail(SBP_E_CUDA, "robin upload failed");
+    }
     if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for(3LL * F.nf), 256>>>((double*)F.ju, tmp, F.jhat, F.nf, 3);
     else k_scale_copy<float><<<grid_for(3LL * F.nf), 256>>>((float*)F.ju, tmp, F.jhat, F.nf, 3);
     cudaError_t e = cudaDeviceSynchronize();
@@ -1005,7 +1021,10 @@ int sbp_set_boundary_data(sbp_handle* h, int block, int face, const double* g) {
     if (!F.g) F.g = h->dalloc(cnt * h->esize);
     double* tmp = (double*)h->dalloc(cnt * sizeof(double));
     if (!F.g || !tmp) return h->fail(SBP_E_OOM, "boundary data");
-    cudaMemcpy(tmp, g, cnt * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(tmp, g, cnt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        h->dfree(tmp);
+        return h->fail(SBP_E_CUDA, "boundary data upload failed");
+    }
     const double* scale = F.kind == SBP_BC_ROBIN ? F.jhat : nullptr;
     if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for((long long)cnt), 256>>>((double*)F.g, tmp, scale, F.nf, 2 * h->nbasis);
     else k_scale_copy<float><<<grid_for((long long)cnt), 256>>>((float*)F.g, tmp, scale, F.nf, 2 * h->nbasis);
@@ -1025,7 +1044,10 @@ int sbp_set_forcing(sbp_handle* h, int block, const double* f) {
     if (!hb.jf) hb.jf = h->dalloc(planes * plane * h->esize);
     double* tmp = (double*)h->dalloc(planes * n * sizeof(double));
     if (!hb.jf || !tmp) return h->fail(SBP_E_OOM, "forcing");
-    cudaMemcpy(tmp, f, planes * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(tmp, f, planes * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        h->dfree(tmp);
+        return h->fail(SBP_E_CUDA, "forcing upload failed");
+    }
     if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for((long long)(planes * n)), 256>>>((double*)hb.jf, tmp, hb.n1, hb.n2, hb.pitch, (int)planes, hb.J);
     else k_to_pitched<float><<<grid_for((long long)(planes * n)), 256>>>((float*)hb.jf, tmp, hb.n1, hb.n2, hb.pitch, (int)planes, hb.J);
     cudaError_t e = cudaDeviceSynchronize();
@@ -1086,7 +1108,10 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
     const double* src[2] = {u_prev, u_cur};
     const int dst_idx[2] = {1 - h->cur, h->cur};
     for (int k = 0; k < 2; ++k) {
-        cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice);
+        if (cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            h->dfree(tmp);
+            return h->fail(SBP_E_CUDA, "state upload failed");
+        }
         if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
         else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
     }
@@ -1094,6 +1119,60 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
     h->dfree(tmp);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
     h->t = t;
+    return SBP_OK;
+}
+
+namespace {
+// checks of a caller-owned device buffer in the library layout (2 planes of n2 rows x pitch)
+int check_device_buffer(sbp_handle* h, const void* p, long long pitch, const HostBlock& hb, const char* what) {
+    if (!p) return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": null device pointer");
+    if (((uintptr_t)p & 15) != 0) return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": device pointer not 16-byte aligned");
+    if (pitch < hb.n1) return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": pitch smaller than n1");
+    if ((pitch * (long long)h->esize) % 16 != 0)
+        return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": row pitch is not a multiple of 16 bytes");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": not a device pointer");
+    }
+    if (at.type == cudaMemoryTypeDevice && at.device != h->device)
+        return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": buffer on another device");
+    return SBP_OK;
+}
+}  // namespace
+
+int sbp_set_state_device(sbp_handle* h, int block, const void* u_prev, const void* u_cur, long long pitch, double t,
+                         void* stream) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks) return h->fail(SBP_E_INVALID_ARG, "bad block index");
+    HostBlock& hb = h->blocks[block];
+    int rc = check_device_buffer(h, u_prev, pitch, hb, "u_prev");
+    if (rc == SBP_OK) rc = check_device_buffer(h, u_cur, pitch, hb, "u_cur");
+    if (rc != SBP_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = h->esize;
+    // both planes in one pitched copy: plane 1 follows plane 0 after n2 rows on both sides
+    const void* src[2] = {u_prev, u_cur};
+    void* dst[2] = {hb.u[1 - h->cur], hb.u[h->cur]};
+    for (int k = 0; k < 2; ++k)
+        if (cudaMemcpy2DAsync(dst[k], hb.pitch * es, src[k], (size_t)pitch * es, hb.n1 * es, 2 * (size_t)hb.n2,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "device state copy failed");
+    h->t = t;
+    return SBP_OK;
+}
+
+int sbp_get_field_device(sbp_handle* h, int block, int which, void* dst, long long pitch, void* stream) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || which < 0 || which > 2) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostBlock& hb = h->blocks[block];
+    int rc = check_device_buffer(h, dst, pitch, hb, "dst");
+    if (rc != SBP_OK) return rc;
+    const void* src = which == SBP_FIELD_APPLY ? hb.r : hb.u[which == SBP_FIELD_CUR ? h->cur : 1 - h->cur];
+    const size_t es = h->esize;
+    if (cudaMemcpy2DAsync(dst, (size_t)pitch * es, src, hb.pitch * es, hb.n1 * es, 2 * (size_t)hb.n2,
+                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "device field copy failed");
     return SBP_OK;
 }
 
@@ -1187,7 +1266,8 @@ int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out) {
     if (!dt_out || !(cfl > 0)) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
     unsigned long long init = 0x7FF0000000000000ULL;   // +inf
-    cudaMemcpy(h->d_scalar, &init, sizeof(init), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(h->d_scalar, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "cfl initialisation failed");
     for (auto& hb : h->blocks) {
         BlockDev b = make_view(h, hb);
         const long long n = (long long)hb.n1 * hb.n2;
@@ -1238,6 +1318,11 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
     if (!h) return SBP_E_INVALID_ARG;
     if (!u_dev || !r_dev) return h->fail(SBP_E_INVALID_ARG, "null device buffer");
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    {
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+            return h->fail(SBP_E_STATE, "sbp_apply_noalloc: the current device is not the device of the handle");
+    }
     const int nb = (int)h->blocks.size();
     if (nb > NOALLOC_MAX_BLOCKS) return h->fail(SBP_E_INVALID_ARG, "sbp_apply_noalloc supports at most 32 blocks");
     const size_t es = h->esize;
@@ -1458,13 +1543,20 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
             cudaEventDestroy(e1);
             return h->fail(SBP_E_OOM, "autotune state copy");
         }
-        cudaMemcpy(p, hb.u[1 - h->cur], bytes, cudaMemcpyDeviceToDevice);
         keep.push_back(p);
+        if (cudaMemcpy(p, hb.u[1 - h->cur], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+            for (void* q : keep) h->dfree(q);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return h->fail(SBP_E_CUDA, "autotune state copy failed");
+        }
     }
+    bool restored = true;
     auto put_back = [&]() {
         for (size_t b = 0; b < h->blocks.size(); ++b) {
             const HostBlock& hb = h->blocks[b];
-            cudaMemcpy(hb.u[1 - h->cur], keep[b], 2 * (size_t)hb.n2 * hb.pitch * h->esize, cudaMemcpyDeviceToDevice);
+            if (cudaMemcpy(hb.u[1 - h->cur], keep[b], 2 * (size_t)hb.n2 * hb.pitch * h->esize, cudaMemcpyDeviceToDevice) != cudaSuccess)
+                restored = false;
             h->dfree(keep[b]);
         }
     };
@@ -1524,8 +1616,22 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
     }
+    if (!restored) return h->fail(SBP_E_CUDA, "autotune could not restore the state");
     if (rows_out) *rows_out = best;
     if (overlap_out) *overlap_out = best_ov ? 1 : 0;
+    return check_kernel_errors(h);
+}
+
+int sbp_debug_wait_probe(sbp_handle* h, int polls) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (polls < 1 || polls > (1 << 20)) return h->fail(SBP_E_INVALID_ARG, "polls must be in [1, 2^20]");
+    k_wait_probe<<<1, 32>>>(polls, h->d_err);
+    return check_cuda(h, "wait probe launch");
+}
+
+int sbp_check(sbp_handle* h) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return h->fail(SBP_E_CUDA, "device error");
     return check_kernel_errors(h);
 }
 
@@ -1600,10 +1706,12 @@ int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces) {
 }
 
 int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* observed, int checkpoint_every,
-                        double* misfit, double* const* grad_rho, double* const* grad_C) {
+                        double* misfit, double* const* grad_rho, double* const* grad_C, int c_layout) {
     if (!h) return SBP_E_INVALID_ARG;
     if (nsteps < 1 || !(dt > 0) || !std::isfinite(dt) || !observed || !misfit || checkpoint_every < 0)
         return h->fail(SBP_E_INVALID_ARG, "bad misfit-gradient arguments");
+    if (c_layout != SBP_C_PAIR10 && c_layout != SBP_C_VOIGT6) return h->fail(SBP_E_INVALID_ARG, "c_layout must be SBP_C_PAIR10 or SBP_C_VOIGT6");
+    const int ncp = c_layout == SBP_C_VOIGT6 ? 6 : 10;
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
     if (h->recs.empty()) return h->fail(SBP_E_STATE, "set the receivers first");
     for (auto& hb : h->blocks)
@@ -1648,8 +1756,9 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     double* d_part = (double*)sc.get(sizeof(double) * nsteps);
     double* d_phi = (double*)sc.get(sizeof(double));
     if (!d_grad || !d_tr || !d_obs || !d_res || !d_part || !d_phi) return h->fail(SBP_E_OOM, "misfit-gradient tables");
-    cudaMemcpy(d_grad, grads.data(), sizeof(GradDev) * nb, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_obs, observed, sizeof(double) * per * nsteps, cudaMemcpyHostToDevice);
+    if (cudaMemcpy(d_grad, grads.data(), sizeof(GradDev) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_obs, observed, sizeof(double) * per * nsteps, cudaMemcpyHostToDevice) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "misfit-gradient table upload failed");
     cudaStream_t st = 0;
     auto copy = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
@@ -1742,16 +1851,16 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     for (int b = 0; b < nb; ++b) {
         HostBlock& hb = h->blocks[b];
         const size_t n = (size_t)hb.n1 * hb.n2;
-        double* dC = (double*)sc.get(10 * n * sizeof(double));
+        double* dC = (double*)sc.get((size_t)ncp * n * sizeof(double));
         double* dR = (double*)sc.get(n * sizeof(double));
         if (!dC || !dR) return h->fail(SBP_E_OOM, "gradient download staging");
         const BlockDev v = make_view(h, hb);
         ProfScope ps(h, 7, st, 1);
         if (h->precision == SBP_FP64)
-            k_grad_to_C<double><<<grid_for((long long)n), 256, 0, st>>>(v, (const double*)grads[b].gc, (const double*)grads[b].grho, dC, dR);
+            k_grad_to_C<double><<<grid_for((long long)n), 256, 0, st>>>(v, (const double*)grads[b].gc, (const double*)grads[b].grho, dC, dR, ncp == 6);
         else
-            k_grad_to_C<float><<<grid_for((long long)n), 256, 0, st>>>(v, (const float*)grads[b].gc, (const float*)grads[b].grho, dC, dR);
-        if (grad_C && grad_C[b] && cudaMemcpy(grad_C[b], dC, 10 * n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            k_grad_to_C<float><<<grid_for((long long)n), 256, 0, st>>>(v, (const float*)grads[b].gc, (const float*)grads[b].grho, dC, dR, ncp == 6);
+        if (grad_C && grad_C[b] && cudaMemcpy(grad_C[b], dC, (size_t)ncp * n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
             return h->fail(SBP_E_CUDA, "gradient download");
         if (grad_rho && grad_rho[b] && cudaMemcpy(grad_rho[b], dR, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
             return h->fail(SBP_E_CUDA, "gradient download");

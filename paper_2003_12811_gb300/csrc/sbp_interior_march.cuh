@@ -21,7 +21,6 @@
 #pragma once
 #include <cuda.h>
 #include "sbp_device.cuh"
-#include "sbp_interior_tma.cuh"
 
 namespace sbp {
 
@@ -279,7 +278,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         if (__syncthreads_or(!ok)) {
             // a bounded wait ran out: record it, drain this CTA's issued copies (bounded), stop
             if (tx == 0) {
-                atomicOr(err, 4);
+                atomicOr(err, ERR_MARCH_WAIT);
                 for (int ch = waited; ch < next_issue; ++ch) mbar_wait_bounded(&bars[ch % MNCH], (ch / MNCH) & 1);
             }
             __syncthreads();

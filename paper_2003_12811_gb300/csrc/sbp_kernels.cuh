@@ -3,7 +3,6 @@
 // point sources), the FP64 energy reduction, and the setup kernels (metric, material, CFL).
 #pragma once
 #include "sbp_device.cuh"
-#include "sbp_interior_tma.cuh"
 
 namespace sbp {
 
@@ -756,7 +755,7 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
         const bool staged = mbar_wait_bounded(bar, 0);
         if (__syncthreads_or(!staged)) {
             if (threadIdx.x == 0) {
-                atomicOr(err, 8);
+                atomicOr(err, ERR_STRIP_WAIT);
                 mbar_wait_bounded(bar, 0);
             }
             return;
@@ -927,6 +926,20 @@ __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __
         atomicAdd(R + nd.gi, T(Wt * nd.wt0));
         atomicAdd(R + plane + nd.gi, T(Wt * nd.wt1));
     }
+}
+
+// ============================================================================ wait probe
+// Diagnostic for the kernels' timeout path: one thread waits, with the bounded wait the step
+// kernels use, on an mbarrier that nothing ever arrives at (no copy is issued, so nothing is in
+// flight); when its `polls` polls run out it sets ERR_SELFTEST_WAIT in the error word.
+__global__ void k_wait_probe(int polls, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, polls)) atomicOr(err, ERR_SELFTEST_WAIT);
 }
 
 // ============================================================================ energy

@@ -212,3 +212,23 @@ def test_autograd_bridge_and_gpu_central_differences():
         fd = (phi_at(Rd, cp) - phi_at(Rd, cm)) / (2 * eps)
         assert abs(fd - gc[b][Pp, i2, i1]) <= 1e-5 * abs(fd) + 100 * np.finfo(float).eps * phi2 / eps
     S.close()
+
+
+def test_voigt_gradient_matches_oracle_fp64():
+    """sbp_misfit_gradient with the Voigt layout: dPhi/dC for the six Voigt entries at sampled
+    nodes against the oracle's Voigt gradient (the derivative along the Voigt unit tensors)."""
+    from paper_2003_12811_gb300.binding import C_VOIGT6
+    order = 4
+    P, u0, dt, rec, obs = _setup(order)
+    n1, n2 = SIZES[order]
+    nodes = [(0, 0, 0), (1, n1 - 1, n2 - 1), (0, n1 - 1, 3), (1, 0, 5), (0, 2, 1), (1, n1 // 2, n2 // 2)]
+    params = [(b, ("voigt", V), i1, i2) for (b, i1, i2) in nodes for V in range(6)]
+    ref = AD.gradient(P, u0, u0, 0.0, dt, NSTEPS, rec, obs, params)
+    S = _solver(P, "fp64", u0, rec)
+    phi, gr, gc = S.sbp_misfit_gradient(NSTEPS, dt, obs, checkpoint_every=9, layout=C_VOIGT6)
+    S.close()
+    assert phi == pytest.approx(ref["misfit"], rel=1e-12)
+    assert gc[0].shape == (6, n2, n1)
+    got = np.array([gc[b][V, i2, i1] for (b, (_, V), i1, i2) in params])
+    scale = np.max(np.abs(ref["grad_C"]))
+    assert np.all(np.abs(got - ref["grad_C"]) <= 1e-9 * scale)

@@ -96,3 +96,40 @@ def test_gradient_rejects_displacement_data():
     P = W.mms_problem(20, 4)
     with pytest.raises(ValueError):
         AD.check_gradient_problem(P)
+
+
+def test_voigt_unit_reproduces_the_voigt_tensor():
+    """Sum_V c_V voigt_unit(V) is the tensor that workloads.voigt_to_tensor builds from the same
+    symmetric Voigt matrix (an independent construction of C_IJKL from Voigt entries)."""
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((3, 3))
+    cv = a + a.T
+    m = sum(cv[AD.VOIGT_ENTRIES[V]] * AD.voigt_unit(V) for V in range(6))
+    T1 = W.pair10_to_tensor(m[:, :, None, None])[..., 0, 0]
+    T2 = W.voigt_to_tensor(cv.reshape(3, 3, 1, 1))[..., 0, 0]
+    assert np.array_equal(T1, T2)
+
+
+def test_voigt_gradient_matches_central_differences_and_pair_sum():
+    """dPhi/dC_V for the six Voigt entries at a few nodes: central differences of the misfit under
+    Voigt perturbations, and the sum of the pair-entry gradients each Voigt entry sets."""
+    order = 4
+    P, u0, dt, rec, obs = _setup(order)
+    n1, n2 = SIZES[order]
+    nodes = [(0, 0, 0), (1, 0, 5), (0, 5, 2), (1, 7, 5)]
+    vparams = [(b, ("voigt", V), i1, i2) for (b, i1, i2) in nodes for V in range(6)]
+    pparams = [(b, Pp, i1, i2) for (b, i1, i2) in nodes for Pp in range(10)]
+    G = AD.gradient(P, u0, u0, 0.0, dt, NSTEPS, rec, obs, vparams + pparams)
+    gv, gp = G["grad_C"][:len(vparams)], G["grad_C"][len(vparams):].reshape(len(nodes), 10)
+    phi = G["misfit"]
+    to_voigt = (0, 2, 2, 1, 5, 5, 4, 5, 4, 3)
+    for k, (b, (_, V), i1, i2) in enumerate(vparams):
+        eps = 1e-5
+        fp = AD.misfit_of(AD.perturbed(P, b, ("voigt", V), i1, i2, eps), u0, u0, 0.0, dt, NSTEPS, rec, obs)
+        fm = AD.misfit_of(AD.perturbed(P, b, ("voigt", V), i1, i2, -eps), u0, u0, 0.0, dt, NSTEPS, rec, obs)
+        f = (fp - fm) / (2 * eps)
+        floor = 100 * np.finfo(float).eps * phi / eps
+        assert abs(gv[k] - f) <= 1e-5 * abs(f) + floor, (b, V, i1, i2, gv[k], f)
+        node = k // 6
+        s = sum(gp[node, e] for e in range(10) if to_voigt[e] == V)
+        assert abs(gv[k] - s) <= 1e-10 * max(1e-300, np.abs(gp[node]).max()), (V, gv[k], s)
