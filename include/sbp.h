@@ -61,6 +61,7 @@ extern "C" {
 #define SBP_FIELD_PREV 0         /* u^{n-1} (after a step: the previous level) */
 #define SBP_FIELD_CUR 1          /* u^n (current level) */
 #define SBP_FIELD_APPLY 2        /* result of the last sbp_apply */
+#define SBP_FIELD_VELOCITY 3     /* v of the RK4 state (sbp_set_state_rk4 / sbp_step_rk4) */
 
 typedef struct sbp_handle sbp_handle;
 
@@ -145,7 +146,7 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
  * with pitch >= n1; buffers must live on the handle's device.
  * sbp_set_state_device: u_prev = u^{-1}, u_cur = u^0 of one block, t the time of u_cur (as
  *   sbp_set_state, without the FP64 host round trip).
- * sbp_get_field_device: copy SBP_FIELD_PREV / CUR / APPLY of one block into dst.
+ * sbp_get_field_device: copy SBP_FIELD_PREV / CUR / APPLY / VELOCITY of one block into dst.
  * Both are stream-ordered (asynchronous).  Errors: SBP_E_INVALID_ARG (pointer, alignment, pitch,
  * device), SBP_E_CUDA. */
 int sbp_set_state_device(sbp_handle* h, int block, const void* u_prev, const void* u_cur, long long pitch, double t,
@@ -155,6 +156,19 @@ int sbp_get_field_device(sbp_handle* h, int block, int which, void* dst, long lo
 /* Advance all blocks by nsteps leapfrog steps of size dt, asynchronously on `stream`
  * (a cudaStream_t; NULL = default stream). */
 int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream);
+
+/* Classical fourth-order Runge-Kutta time stepping (the paper's integrator, Sec. 7.1 and 7.4) of
+ * the first-order form u' = v, v' = (rho J)^-1 [DD(c) u + J SAT(u, t) + J f(t)], as an alternative
+ * to leapfrog.  The RK4 state of a block is (u, v) (host, 2 planes of n1*n2 values each); t the
+ * time.  sbp_set_state_rk4 allocates the block's RK4 buffers (10 planes) on first use.
+ * sbp_step_rk4 advances nsteps steps of size dt asynchronously on `stream`: four operator passes
+ * per step, each fused with its stage combination (stage input U_{s+1} = u + c h V_s, stage
+ * velocity V_{s+1} = v + c h a_s and the running sums of b_s V_s and b_s a_s are formed in the
+ * same kernels that apply the operator; c = 1/2, 1/2, 1, b = 1/6, 1/3, 1/3, 1/6).  After the
+ * steps, SBP_FIELD_CUR holds u and SBP_FIELD_VELOCITY holds v; the leapfrog level
+ * SBP_FIELD_PREV is then meaningless.  Errors: SBP_E_STATE without materials or RK4 state. */
+int sbp_set_state_rk4(sbp_handle* h, int block, const double* u, const double* v, double t);
+int sbp_step_rk4(sbp_handle* h, int nsteps, double dt, void* stream);
 
 /* The same leapfrog steps as sbp_step, replayed from a CUDA graph: the first call (and any call
  * with a different nsteps or dt) captures nsteps launches of the step kernels into a graph,

@@ -22,7 +22,7 @@ STATUS = {0: "SBP_OK", -1: "SBP_E_INVALID_ARG", -2: "SBP_E_JACOBIAN_NONPOSITIVE"
           -7: "SBP_E_UNSTABLE", -8: "SBP_E_STATE"}
 FP64, FP32 = 0, 1
 BC = {"displacement": 0, "robin": 1, "interface": 2}
-FIELD_PREV, FIELD_CUR, FIELD_APPLY = 0, 1, 2
+FIELD_PREV, FIELD_CUR, FIELD_APPLY, FIELD_VELOCITY = 0, 1, 2, 3
 C_PAIR10, C_VOIGT6 = 0, 1
 PROF_FAMILIES = 8      # SBP_PROF_FAMILIES
 
@@ -78,6 +78,8 @@ def lib():
                                            C.c_void_p]
         L.sbp_get_field_device.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p]
         L.sbp_step.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+        L.sbp_set_state_rk4.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_double]
+        L.sbp_step_rk4.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp_apply.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.sbp_get_field.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.sbp_energy.argtypes = [C.c_void_p, C.c_double, _DP]
@@ -222,6 +224,19 @@ class Solver:
     def sbp_step(self, nsteps, dt, stream=None):
         s = None if stream is None else C.c_void_p(stream)
         self._check(self.L.sbp_step(self.h, int(nsteps), float(dt), s))
+
+    def sbp_set_state_rk4(self, u, v, t):
+        for b, (ub, vb) in enumerate(zip(u, v)):
+            a, c = _f64(ub), _f64(vb)
+            self._check(self.L.sbp_set_state_rk4(self.h, b, _ptr(a), _ptr(c), float(t)))
+
+    def sbp_step_rk4(self, nsteps, dt, stream=None):
+        s = None if stream is None else C.c_void_p(stream)
+        self._check(self.L.sbp_step_rk4(self.h, int(nsteps), float(dt), s))
+
+    def state_rk4(self):
+        """(u, v) of the RK4 state."""
+        return self.sbp_get_field(FIELD_CUR), self.sbp_get_field(FIELD_VELOCITY)
 
     def sbp_step_graph(self, nsteps, dt, stream=None):
         s = None if stream is None else C.c_void_p(stream)

@@ -57,6 +57,7 @@ struct HostBlock {
     void* psi[2] = {nullptr, nullptr};   // adjoint fields (sbp_misfit_gradient), allocated on first use
     MarchMaps pmaps;          // marching-kernel maps over the adjoint fields
     CUtensorMap* d_smaps = nullptr;   // strip-tile band-box maps on the device: [0..2] state u0, u1, c; [3..5] adjoint
+    void* rk = nullptr;       // RK4 state (u, v, V, S_u, S_v; sbp_set_state_rk4), allocated on first use
     void* mx = nullptr;       // closure matrices of D_xx^FC along x1 / x2 (k_closure_mats, type T)
     void* my = nullptr;
 };
@@ -100,7 +101,10 @@ struct sbp_handle {
     double basis_omega[8] = {0};
     std::vector<SrcNode> src_nodes;
     std::vector<SrcParam> src_params;
-    SrcNode* d_src_nodes = nullptr;
+    SrcNode* d_src_nodes = nullptr;     // every source node (sbp_apply_noalloc)
+    SrcNode* d_src_int = nullptr;       // source nodes off the boundary strips (k_sources)
+    int n_src_int = 0;
+    SrcNode* d_src_strip = nullptr;     // source nodes on the strips, grouped by strip tile (k_strip_tile)
     SrcParam* d_src_params = nullptr;
     bool src_dirty = false;
     double* d_scalar = nullptr;
@@ -133,8 +137,10 @@ struct sbp_handle {
     cudaStream_t hi = nullptr;
     cudaEvent_t ev_join_hi = nullptr;
     // strip tiles of every block, costliest first (one k_strip_tile launch per step)
-    int2* d_tiles = nullptr;
+    int4* d_tiles = nullptr;            // (block, tile, first, end source node of the tile) in launch order
     int ntiles = 0;
+    std::vector<int4> tiles_host;
+    std::vector<std::vector<int>> tile_pos;   // [block][tile of the block] -> position in the launch order
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // adjoint: block views whose state buffers are the adjoint fields; receivers
@@ -251,6 +257,7 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
         D.tr = F.tr;
     }
     b.smaps = hb.d_smaps;
+    b.rk = hb.rk;
     b.mx = hb.mx;
     b.my = hb.my;
     return b;
@@ -364,9 +371,11 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
                 ncy = (n2i + rows - 1) / rows;
                 constexpr size_t msm = MarchCfg<O>::BYTES;
                 if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
+                else if (mode == 2) k_interior_march<O, 2><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
                 else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
             } else {
                 if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, ist>>>(b, a);
+                else if (mode == 2) k_interior<T, O, 2><<<grid, dim3(32, 8), smem, ist>>>(b, a);
                 else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, ist>>>(b, a);
             }
         }
@@ -416,8 +425,13 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         ProfScope ps(h, 1, sst, 1);
         using ST = StripTile<O>;
         constexpr size_t ssm = ST::template bytes<T>();
-        if (mode == 0) k_strip_tile<T, O, 0><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err);
-        else k_strip_tile<T, O, 1><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err);
+        const SrcNode* ss = adj ? nullptr : h->d_src_strip;
+        if (mode == 0)
+            k_strip_tile<T, O, 0><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err, ss, h->d_src_params);
+        else if (mode == 2)
+            k_strip_tile<T, O, 2><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err, ss, h->d_src_params);
+        else
+            k_strip_tile<T, O, 1><<<h->ntiles, ST::THREADS, ssm, sst>>>(tab, h->d_tiles, a, h->beta, h->d_err, ss, h->d_src_params);
     }
     if (ovl) {
         cudaEventRecord(h->ev_join, h->aux);
@@ -425,11 +439,12 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         cudaStreamWaitEvent(st, h->ev_join, 0);
         cudaStreamWaitEvent(st, h->ev_join_hi, 0);
     }
-    if (!adj && !h->src_nodes.empty()) {
+    if (!adj && h->n_src_int > 0) {   // source nodes off the strips (the strip kernel adds the others)
         ProfScope ps(h, 3, st, 1);
-        const int ns = (int)h->src_nodes.size();
-        if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
-        else k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
+        const int ns = h->n_src_int;
+        if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_int, ns, h->d_src_params, a);
+        else if (mode == 2) k_sources<T, 2><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_int, ns, h->d_src_params, a);
+        else k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_int, ns, h->d_src_params, a);
     }
     return check_cuda(h, "operator launch");
 }
@@ -453,11 +468,14 @@ template <typename T, int O> void set_smem_attr() {
     constexpr size_t ssm = StripTile<O>::template bytes<T>();
     cudaFuncSetAttribute(k_strip_tile<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     cudaFuncSetAttribute(k_strip_tile<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    cudaFuncSetAttribute(k_strip_tile<T, O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     cudaFuncSetAttribute(k_interior<T, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_interior<T, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_interior<T, O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (std::is_same<T, float>::value) {
         cudaFuncSetAttribute(k_interior_march<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_march<O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
     }
 }
 
@@ -478,16 +496,71 @@ void fill_basis(const sbp_handle* h, double t, StepArgs& a) {
     for (int k = 0; k < h->nbasis; ++k) a.Tk[k] = h->basis_kind[k] == 0 ? sin(h->basis_omega[k] * t) : cos(h->basis_omega[k] * t);
 }
 
+// strip tile of node (i1, i2) of a block in the numbering of k_strip_tile (bands of width S along
+// x2 = 0 and x2 = 1, then the side bands between them), or -1 for a node off the strips
+int strip_tile_of(const sbp_handle* h, const HostBlock& hb, int i1, int i2) {
+    const int S = std::max(order_nclos(h->order), order_ncol(h->order));
+    const int nbx = (hb.n1 + 31) / 32, nby = (hb.n2 - 2 * S + 31) / 32;
+    if (i2 < S) return i1 / 32;
+    if (i2 >= hb.n2 - S) return nbx + i1 / 32;
+    if (i1 < S) return 2 * nbx + (i2 - S) / 32;
+    if (i1 >= hb.n1 - S) return 2 * nbx + nby + (i2 - S) / 32;
+    return -1;
+}
+
 int upload_sources(sbp_handle* h) {
     if (!h->src_dirty) return SBP_OK;
     h->dfree(h->d_src_nodes);
     h->dfree(h->d_src_params);
+    h->dfree(h->d_src_int);
+    h->dfree(h->d_src_strip);
+    h->d_src_int = h->d_src_strip = nullptr;
+    h->n_src_int = 0;
     h->d_src_nodes = (SrcNode*)h->dalloc(sizeof(SrcNode) * h->src_nodes.size());
     h->d_src_params = (SrcParam*)h->dalloc(sizeof(SrcParam) * h->src_params.size());
     if (!h->d_src_nodes || !h->d_src_params) return h->fail(SBP_E_OOM, "source tables");
     if (cudaMemcpy(h->d_src_nodes, h->src_nodes.data(), sizeof(SrcNode) * h->src_nodes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_src_params, h->src_params.data(), sizeof(SrcParam) * h->src_params.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return h->fail(SBP_E_CUDA, "source table upload failed");
+    // split: nodes on the boundary strips go with their strip tile, the rest to k_sources
+    std::vector<std::pair<int, SrcNode>> strip;
+    std::vector<SrcNode> inner;
+    for (const SrcNode& nd : h->src_nodes) {
+        const HostBlock& hb = h->blocks[nd.block];
+        const int i2 = (int)(nd.gi / hb.pitch), i1 = (int)(nd.gi - (long long)i2 * hb.pitch);
+        const int t = strip_tile_of(h, hb, i1, i2);
+        if (t < 0) inner.push_back(nd);
+        else strip.push_back({h->tile_pos[nd.block][t], nd});
+    }
+    std::stable_sort(strip.begin(), strip.end(),
+                     [](const std::pair<int, SrcNode>& x, const std::pair<int, SrcNode>& y) { return x.first < y.first; });
+    for (int4& tl : h->tiles_host) tl.z = tl.w = 0;
+    std::vector<SrcNode> sv;
+    for (size_t k = 0; k < strip.size(); ++k) {
+        int4& tl = h->tiles_host[strip[k].first];
+        if (tl.z == tl.w) tl.z = tl.w = (int)k;
+        tl.w = (int)k + 1;
+        sv.push_back(strip[k].second);
+    }
+    if (!sv.empty()) {
+        h->d_src_strip = (SrcNode*)h->dalloc(sizeof(SrcNode) * sv.size());
+        if (!h->d_src_strip) return h->fail(SBP_E_OOM, "source tables");
+        if (cudaMemcpy(h->d_src_strip, sv.data(), sizeof(SrcNode) * sv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "source table upload failed");
+    }
+    if (!inner.empty()) {
+        h->d_src_int = (SrcNode*)h->dalloc(sizeof(SrcNode) * inner.size());
+        if (!h->d_src_int) return h->fail(SBP_E_OOM, "source tables");
+        if (cudaMemcpy(h->d_src_int, inner.data(), sizeof(SrcNode) * inner.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "source table upload failed");
+        h->n_src_int = (int)inner.size();
+    }
+    if (cudaMemcpy(h->d_tiles, h->tiles_host.data(), sizeof(int4) * h->tiles_host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return h->fail(SBP_E_CUDA, "tile table upload failed");
+    if (h->graph_exec) {   // captured launches hold the old tables and launch counts
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
     h->src_dirty = false;
     return check_cuda(h, "source upload");
 }
@@ -867,12 +940,20 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         }
         std::stable_sort(tl.begin(), tl.end(),
                          [](const std::pair<int, int2>& x, const std::pair<int, int2>& y) { return x.first > y.first; });
-        std::vector<int2> tv;
-        for (auto& e : tl) tv.push_back(e.second);
-        h->ntiles = (int)tv.size();
-        h->d_tiles = (int2*)h->dalloc(sizeof(int2) * tv.size());
+        h->tile_pos.assign(desc->nblocks, {});
+        for (int b = 0; b < desc->nblocks; ++b) {
+            const HostBlock& hb = h->blocks[b];
+            h->tile_pos[b].assign(2 * ((hb.n1 + 31) / 32) + 2 * ((hb.n2 - 2 * S + 31) / 32), -1);
+        }
+        h->tiles_host.clear();
+        for (auto& e : tl) {
+            h->tile_pos[e.second.x][e.second.y] = (int)h->tiles_host.size();
+            h->tiles_host.push_back(make_int4(e.second.x, e.second.y, 0, 0));
+        }
+        h->ntiles = (int)h->tiles_host.size();
+        h->d_tiles = (int4*)h->dalloc(sizeof(int4) * h->tiles_host.size());
         if (!h->d_tiles) return cleanup(SBP_E_OOM, "tile table");
-        if (cudaMemcpy(h->d_tiles, tv.data(), sizeof(int2) * tv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpy(h->d_tiles, h->tiles_host.data(), sizeof(int4) * h->tiles_host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(SBP_E_CUDA, "tile table upload failed");
     }
     // metric
@@ -1123,6 +1204,13 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
 }
 
 namespace {
+// device planes of a field of a block (SBP_FIELD_*)
+void* field_ptr(const sbp_handle* h, const HostBlock& hb, int which) {
+    if (which == SBP_FIELD_APPLY) return hb.r;
+    if (which == SBP_FIELD_VELOCITY) return (unsigned char*)hb.rk + 2 * (size_t)hb.n2 * hb.pitch * h->esize;
+    return hb.u[which == SBP_FIELD_CUR ? h->cur : 1 - h->cur];
+}
+
 // checks of a caller-owned device buffer in the library layout (2 planes of n2 rows x pitch)
 int check_device_buffer(sbp_handle* h, const void* p, long long pitch, const HostBlock& hb, const char* what) {
     if (!p) return h->fail(SBP_E_INVALID_ARG, std::string(what) + ": null device pointer");
@@ -1164,11 +1252,12 @@ int sbp_set_state_device(sbp_handle* h, int block, const void* u_prev, const voi
 
 int sbp_get_field_device(sbp_handle* h, int block, int which, void* dst, long long pitch, void* stream) {
     if (!h) return SBP_E_INVALID_ARG;
-    if (block < 0 || block >= h->nblocks || which < 0 || which > 2) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    if (block < 0 || block >= h->nblocks || which < 0 || which > 3) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
     HostBlock& hb = h->blocks[block];
+    if (which == SBP_FIELD_VELOCITY && !hb.rk) return h->fail(SBP_E_STATE, "no RK4 state on this block");
     int rc = check_device_buffer(h, dst, pitch, hb, "dst");
     if (rc != SBP_OK) return rc;
-    const void* src = which == SBP_FIELD_APPLY ? hb.r : hb.u[which == SBP_FIELD_CUR ? h->cur : 1 - h->cur];
+    const void* src = field_ptr(h, hb, which);
     const size_t es = h->esize;
     if (cudaMemcpy2DAsync(dst, (size_t)pitch * es, src, hb.pitch * es, hb.n1 * es, 2 * (size_t)hb.n2,
                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
@@ -1197,6 +1286,64 @@ int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream) {
     return SBP_OK;
 }
 
+int sbp_set_state_rk4(sbp_handle* h, int block, const double* u, const double* v, double t) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || !u || !v) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostBlock& hb = h->blocks[block];
+    const size_t n = (size_t)hb.n1 * hb.n2, plane = (size_t)hb.n2 * hb.pitch;
+    if (!hb.rk) {
+        hb.rk = h->dalloc(10 * plane * h->esize);
+        if (!hb.rk) return h->fail(SBP_E_OOM, "RK4 state");
+        int rc = sync_views(h);
+        if (rc != SBP_OK) return rc;
+    }
+    double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
+    if (!tmp) return h->fail(SBP_E_OOM, "state staging");
+    // u -> RK planes 0-1 and the current state buffer (the first stage input); v -> RK planes 2-3
+    void* dst[3] = {hb.rk, hb.u[h->cur], (unsigned char*)hb.rk + 2 * plane * h->esize};
+    const double* src[3] = {u, u, v};
+    for (int k = 0; k < 3; ++k) {
+        if (cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            h->dfree(tmp);
+            return h->fail(SBP_E_CUDA, "state upload failed");
+        }
+        if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)dst[k], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+        else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)dst[k], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    h->dfree(tmp);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
+    h->t = t;
+    return SBP_OK;
+}
+
+int sbp_step_rk4(sbp_handle* h, int nsteps, double dt, void* stream) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return h->fail(SBP_E_INVALID_ARG, "bad step arguments");
+    if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    for (auto& hb : h->blocks)
+        if (!hb.rk) return h->fail(SBP_E_STATE, "set the RK4 state (sbp_set_state_rk4) of every block first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int n = 0; n < nsteps; ++n) {
+        for (int s = 1; s <= 4; ++s) {
+            StepArgs a{};
+            a.with_data = 1;
+            a.cur = h->cur;
+            a.stage = s;
+            a.rkh = dt;
+            a.rkhf = (float)dt;
+            a.t = h->t + cs[s - 1] * dt;
+            fill_basis(h, a.t, a);
+            const int rc = run_operator(h, a, 2, st);
+            if (rc != SBP_OK) return rc;
+            h->cur = 1 - h->cur;
+        }
+        h->t += dt;
+    }
+    return SBP_OK;
+}
+
 int sbp_apply(sbp_handle* h, int with_data, double t) {
     if (!h) return SBP_E_INVALID_ARG;
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
@@ -1213,10 +1360,11 @@ int sbp_apply(sbp_handle* h, int with_data, double t) {
 
 int sbp_get_field(sbp_handle* h, int block, int which, double* dst) {
     if (!h) return SBP_E_INVALID_ARG;
-    if (block < 0 || block >= h->nblocks || !dst || which < 0 || which > 2) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    if (block < 0 || block >= h->nblocks || !dst || which < 0 || which > 3) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
     HostBlock& hb = h->blocks[block];
     const size_t n = (size_t)hb.n1 * hb.n2;
-    void* src = which == SBP_FIELD_APPLY ? hb.r : hb.u[which == SBP_FIELD_CUR ? h->cur : 1 - h->cur];
+    if (which == SBP_FIELD_VELOCITY && !hb.rk) return h->fail(SBP_E_STATE, "no RK4 state on this block");
+    void* src = field_ptr(h, hb, which);
     double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
     if (!tmp) return h->fail(SBP_E_OOM, "download staging");
     cudaDeviceSynchronize();
@@ -1462,7 +1610,7 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         const int nb = (int)h->blocks.size();
         h->launches[0] += (long long)nsteps * nb;
         h->launches[1] += (long long)nsteps * nb;
-        if (!h->src_nodes.empty()) h->launches[3] += nsteps;
+        if (h->n_src_int > 0) h->launches[3] += nsteps;
     }
     h->t = tt;
     return SBP_OK;

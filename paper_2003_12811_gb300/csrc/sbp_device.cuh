@@ -265,6 +265,7 @@ struct BlockDev {
     const double* X;          // coordinates (2 planes)
     double* G;                // metric dX_I/dx_i (4 planes, [2 i + I])
     double* J;                // Jacobian
+    void* rk;                 // RK4 state (10 planes): u, v, stage velocity V, sums S_u, S_v (2 planes each)
     const void* smaps;        // strip-tile band-box tensor maps (CUtensorMap[3]: u[0], u[1], c)
     const void* mx;           // closure rows of D_xx^FC along x1 as matrices, type T (k_closure_mats)
     const void* my;           // the same along x2
@@ -282,7 +283,52 @@ struct StepArgs {
     const double* tdev;       // graph mode: device array of the times of the captured steps (else null)
     double dt;                // step size
     float dt2f;               // dt^2 in FP32
+    int stage;                // RK4 mode: stage s = 1..4 of the step
+    double rkh;               // RK4 mode: step size h
+    float rkhf;               // the same in FP32
 };
+
+// RK4 stage epilogue (mode 2) of one node.  The classical RK4 of Sec. 7.1 on y = (u, v),
+// y' = (v, a(u, t)), a = (rho J)^-1 [DD(c) u + J SAT + J f], organised by stage inputs
+// Y_s = (U_s, V_s): U_1 = u, V_1 = v, U_{s+1} = u + c_{s+1} h V_s, V_{s+1} = v + c_{s+1} h a_s with
+// a_s = a(U_s, t + c_s h), c = (0, 1/2, 1/2, 1), and u_new = u + h sum_s b_s V_s,
+// v_new = v + h sum_s b_s a_s, b = (1, 2, 2, 1)/6.  The kernel of stage s has read U_s (state
+// buffer u[cur]) and formed r = DD(c) U_s + J SAT + J f at node gi; this writes U_{s+1} (or u_new)
+// into u[1 - cur] and keeps V, S_u = sum b V, S_v = sum b a and, after stage 4, (u, v) in B.rk.
+template <typename T>
+__device__ __forceinline__ void rk4_store(const BlockDev& B, const StepArgs& a, size_t gi, size_t plane, T w, T r0,
+                                          T r1) {
+    T* __restrict__ R = reinterpret_cast<T*>(B.rk);
+    T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+    const int s = a.stage;
+    T h;
+    if constexpr (sizeof(T) == 4) h = a.rkhf; else h = a.rkh;
+    const T a0 = w * r0, a1 = w * r1;
+    const T u0 = R[gi], u1 = R[plane + gi], v0 = R[2 * plane + gi], v1 = R[3 * plane + gi];
+    const T V0 = s == 1 ? v0 : R[4 * plane + gi], V1 = s == 1 ? v1 : R[5 * plane + gi];
+    const T su0 = s == 1 ? T(0) : R[6 * plane + gi], su1 = s == 1 ? T(0) : R[7 * plane + gi];
+    const T sv0 = s == 1 ? T(0) : R[8 * plane + gi], sv1 = s == 1 ? T(0) : R[9 * plane + gi];
+    const T b = (s == 1 || s == 4) ? T(1) / T(6) : T(1) / T(3);
+    if (s < 4) {
+        const T ch = s == 3 ? h : T(0.5) * h;
+        Un[gi] = u0 + ch * V0;
+        Un[plane + gi] = u1 + ch * V1;
+        R[4 * plane + gi] = v0 + ch * a0;
+        R[5 * plane + gi] = v1 + ch * a1;
+        R[6 * plane + gi] = su0 + b * V0;
+        R[7 * plane + gi] = su1 + b * V1;
+        R[8 * plane + gi] = sv0 + b * a0;
+        R[9 * plane + gi] = sv1 + b * a1;
+    } else {
+        const T un0 = u0 + h * (su0 + b * V0), un1 = u1 + h * (su1 + b * V1);
+        Un[gi] = un0;
+        Un[plane + gi] = un1;
+        R[gi] = un0;
+        R[plane + gi] = un1;
+        R[2 * plane + gi] = v0 + h * (sv0 + b * a0);
+        R[3 * plane + gi] = v1 + h * (sv1 + b * a1);
+    }
+}
 
 // the per-block and per-face step constants in the arithmetic type T (FP32 kernels read the FP32
 // copies, which need no conversion)

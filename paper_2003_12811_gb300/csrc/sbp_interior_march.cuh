@@ -16,6 +16,7 @@
 //  * the x-direction fluxes g1 = c_1j2l D_2 u_l of the current row are exchanged through a
 //    double-buffered shared row (one barrier per row);
 //  * 1/(rho J) and u^{n-1} of the output row are loaded from global memory two rows ahead;
+//  * MODE 0: leapfrog update; 1: operator output r; 2: RK4 stage (rk4_store);
 //  * the two components of the displacement and of every flux are carried as float2 and
 //    combined with packed FP32x2 instructions (one issue slot for both).
 #pragma once
@@ -157,11 +158,13 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     float w_c = 0.f, w_n = 0.f;
     float2 up_c = make_float2(0.f, 0.f), up_n = make_float2(0.f, 0.f);
     auto load_row = [&](int r, float& wv, float2& v) {
-        if (MODE == 0 && col_ok && r >= ys && r < ye) {
+        if (MODE != 1 && col_ok && r >= ys && r < ye) {
             const size_t gi = (size_t)r * P + gx;
             wv = __ldg(reinterpret_cast<const float*>(B.w) + gi);
-            const float* Un = reinterpret_cast<const float*>(B.u[1 - a.cur]);
-            v = make_float2(Un[gi], Un[gi + plane]);
+            if (MODE == 0) {
+                const float* Un = reinterpret_cast<const float*>(B.u[1 - a.cur]);
+                v = make_float2(Un[gi], Un[gi + plane]);
+            }
         }
     };
     load_row(ys, w_c, up_c);
@@ -347,6 +350,8 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
             const float2 nu = ffma2(bc2(a.dt2f * w_c), make_float2(r0, r1), fsub2(fadd2(uc, uc), up_c));
             Un[gi] = nu.x;
             Un[gi + plane] = nu.y;
+        } else if (MODE == 2) {
+            rk4_store<float>(B, a, gi, plane, w_c, r0, r1);
         } else {
             float* __restrict__ R = reinterpret_cast<float*>(B.r);
             R[gi] = r0;

@@ -183,6 +183,8 @@ __global__ void __launch_bounds__(ITHREADS) k_interior(BlockDev B, StepArgs a) {
             const T wv = Wp[gi], dt2 = dt2T<T>(a);
             Un[gi] = T(2) * uc0 - Un[gi] + dt2 * wv * r0;
             Un[gi + plane] = T(2) * uc1 - Un[gi + plane] + dt2 * wv * r1;
+        } else if (MODE == 2) {
+            rk4_store<T>(B, a, gi, plane, Wp[gi], r0, r1);
         } else {
             T* __restrict__ R = reinterpret_cast<T*>(B.r);
             R[gi] = r0;
@@ -656,6 +658,23 @@ __global__ void __launch_bounds__(256) k_boundary(BlockDev B, StepArgs a) {
         [&](int pl, int j1, int j2) { return __ldg(C + pl * plane + (size_t)j2 * P + j1); });
 }
 
+// ============================================================================ point-source tables
+struct SrcNode {
+    int block, src;
+    long long gi;             // node offset in the planes
+    double wt0, wt1;          // dir_J * amplitude * w1 w2 / H
+};
+struct SrcParam {
+    double alpha_p, t0;
+};
+// Ricker wavelet W(t) of a point source at the step's time (Sec. 7.4); graph mode reads the time of
+// the captured step from the device array the host uploads
+__device__ __forceinline__ double ricker_at(const SrcParam& p, const StepArgs& a) {
+    const double tnow = a.tdev ? a.tdev[a.tstep] : a.t;
+    const double x = 3.14159265358979323846 * p.alpha_p * (tnow - p.t0);
+    return (1.0 - 2.0 * x * x) * exp(-x * x);
+}
+
 // ============================================================================ boundary strips, tiled
 // The strips are cut into tiles of 32 nodes along the face x (strip width) nodes across it:
 // bottom and top bands (tiles along x1), left and right bands (tiles along x2, between the
@@ -694,18 +713,21 @@ template <int O> struct StripTile {
     template <typename T> static constexpr size_t bytes() { return bar_off<T>() + 16; }
 };
 
-// One launch covers the strips of every block: tiles[blockIdx.x] = (block, tile of that block),
-// ordered by the host so that the costliest tiles (interface bands, side bands) start first.
-// B.smaps holds the block's band-box tensor maps: u[0], u[1], c.
+// One launch covers the strips of every block: tiles[blockIdx.x] = (block, tile of that block,
+// first and end index of the tile's point-source nodes in ssrc), ordered by the host so that the
+// costliest tiles (interface bands, side bands) start first.  B.smaps holds the block's band-box
+// tensor maps: u[0], u[1], c.  Point-source nodes inside the strips are added here (ssrc null:
+// none, e.g. on the adjoint fields); the host launches k_sources only for interior source nodes.
 template <typename T, int O, int MODE>
 __global__ void __launch_bounds__(StripTile<O>::THREADS, sizeof(T) == 4 ? 4 : 2)
-k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles, StepArgs a, double beta, int* err) {
+k_strip_tile(const BlockDev* __restrict__ blocks, const int4* __restrict__ tiles, StepArgs a, double beta, int* err,
+             const SrcNode* __restrict__ ssrc, const SrcParam* __restrict__ spar) {
     using ST = StripTile<O>;
     constexpr int S = ST::S, NT = ST::THREADS;
     extern __shared__ __align__(128) unsigned char strip_smem[];
     T* sm = reinterpret_cast<T*>(strip_smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(strip_smem + ST::template bar_off<T>());
-    const int2 tt = tiles[blockIdx.x];
+    const int4 tt = tiles[blockIdx.x];
     const BlockDev& B = blocks[tt.x];
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int nbx = (n1 + 31) / 32, nby = (n2 - 2 * S + 31) / 32;
@@ -882,11 +904,23 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
             r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
         }
     }
+    // point-source nodes of this tile: J f_J = dir_J amp W(t) w1 w2 / H (Sec. 7.4, discrete delta)
+    if (ssrc && a.with_data) {
+        for (int k = tt.z; k < tt.w; ++k) {
+            const SrcNode nd = ssrc[k];
+            if (nd.gi != (long long)gi) continue;
+            const double Wt = ricker_at(spar[nd.src], a);
+            r0 += T(Wt * nd.wt0);
+            r1 += T(Wt * nd.wt1);
+        }
+    }
     if (MODE == 0) {
         T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
         const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
         Un[gi] = T(2) * at(0, i1, i2) - Un[gi] + dt2 * wv * r0;
         Un[gi + plane] = T(2) * at(1, i1, i2) - Un[gi + plane] + dt2 * wv * r1;
+    } else if (MODE == 2) {
+        rk4_store<T>(B, a, gi, plane, reinterpret_cast<const T*>(B.w)[gi], r0, r1);
     } else {
         T* __restrict__ R = reinterpret_cast<T*>(B.r);
         R[gi] = r0;
@@ -895,14 +929,6 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int2* __restrict__ tiles
 }
 
 // ============================================================================ point sources
-struct SrcNode {
-    int block, src;
-    long long gi;             // node offset in the planes
-    double wt0, wt1;          // dir_J * amplitude * w1 w2 / H
-};
-struct SrcParam {
-    double alpha_p, t0;
-};
 
 template <typename T, int MODE>
 __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __restrict__ nodes, int nnodes,
@@ -910,10 +936,7 @@ __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= nnodes || !a.with_data) return;
     const SrcNode nd = nodes[tid];
-    const SrcParam p = par[nd.src];
-    const double tnow = a.tdev ? a.tdev[a.tstep] : a.t;   // graph mode: per-step times uploaded by the host
-    const double x = 3.14159265358979323846 * p.alpha_p * (tnow - p.t0);
-    const double Wt = (1.0 - 2.0 * x * x) * exp(-x * x);        // Ricker wavelet (Sec. 7.4)
+    const double Wt = ricker_at(par[nd.src], a);
     const BlockDev& B = blocks[nd.block];
     const size_t plane = (size_t)B.n2 * B.pitch;
     if (MODE == 0) {
@@ -921,6 +944,23 @@ __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __
         const double fac = a.dt2 * (double)reinterpret_cast<const T*>(B.w)[nd.gi] * Wt;
         atomicAdd(Un + nd.gi, T(fac * nd.wt0));
         atomicAdd(Un + plane + nd.gi, T(fac * nd.wt1));
+    } else if (MODE == 2) {
+        // the stage acceleration gains da = w W(t) wt after rk4_store ran: V_{s+1} += c_{s+1} h da,
+        // S_v += b_s da (stages 1-3); v_new += h b_4 da (stage 4)
+        T* R = reinterpret_cast<T*>(B.rk);
+        const double da = (double)reinterpret_cast<const T*>(B.w)[nd.gi] * Wt, h = a.rkh;
+        const int s = a.stage;
+        const double b = (s == 1 || s == 4) ? 1.0 / 6.0 : 1.0 / 3.0;
+        if (s < 4) {
+            const double ch = s == 3 ? h : 0.5 * h;
+            atomicAdd(R + 4 * plane + nd.gi, T(ch * da * nd.wt0));
+            atomicAdd(R + 5 * plane + nd.gi, T(ch * da * nd.wt1));
+            atomicAdd(R + 8 * plane + nd.gi, T(b * da * nd.wt0));
+            atomicAdd(R + 9 * plane + nd.gi, T(b * da * nd.wt1));
+        } else {
+            atomicAdd(R + 2 * plane + nd.gi, T(h * b * da * nd.wt0));
+            atomicAdd(R + 3 * plane + nd.gi, T(h * b * da * nd.wt1));
+        }
     } else {
         T* R = reinterpret_cast<T*>(B.r);
         atomicAdd(R + nd.gi, T(Wt * nd.wt0));
