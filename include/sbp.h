@@ -166,7 +166,8 @@ int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream);
  * velocity V_{s+1} = v + c h a_s and the running sums of b_s V_s and b_s a_s are formed in the
  * same kernels that apply the operator; c = 1/2, 1/2, 1, b = 1/6, 1/3, 1/3, 1/6).  After the
  * steps, SBP_FIELD_CUR holds u and SBP_FIELD_VELOCITY holds v; the leapfrog level
- * SBP_FIELD_PREV is then meaningless.  Errors: SBP_E_STATE without materials or RK4 state. */
+ * SBP_FIELD_PREV and the operator output SBP_FIELD_APPLY (used as scratch for the point sources)
+ * are then meaningless.  Errors: SBP_E_STATE without materials or RK4 state. */
 int sbp_set_state_rk4(sbp_handle* h, int block, const double* u, const double* v, double t);
 int sbp_step_rk4(sbp_handle* h, int nsteps, double dt, void* stream);
 
@@ -262,6 +263,59 @@ int sbp_debug_wait_probe(sbp_handle* h, int polls);
 /* Current simulation time and number of resident nodes. */
 int sbp_get_time(const sbp_handle* h, double* t_out);
 int sbp_get_info(const sbp_handle* h, long long* nodes_out, int* precision_out, int* order_out);
+
+/* ---- batch of resident shots: the persistent tile-queue step ---------------------------------
+ * Serving layer (no counterpart in the paper): many independent forward solves ("shots") kept
+ * resident on the device and advanced together.  One step of the batch is ONE launch of a
+ * persistent kernel whose CTAs (as many as fit on the GPU at once) pull work items from a single
+ * device queue covering every active shot -- interior tiles of the column-marching stencil (128
+ * columns x `rows` rows) and boundary-strip tiles (closures, SAT terms, point sources on the
+ * strips) -- so small and large shots fill the GPU together; the last CTA to finish adds the
+ * point sources off the strips and advances every shot.  sbp_batch_step replays a CUDA graph of
+ * K such launches.  Shots are admitted (sbp_batch_add) and retired (sbp_batch_remove) between
+ * sbp_batch_step calls; each shot advances by its own step count and stops when it is reached.
+ * The arithmetic per node is that of sbp_step, so a shot's result does not depend on the batch
+ * it ran in.
+ * Shots: single-block FP32 handles of the batch's order without interfaces or time-basis data,
+ * with their material and state set.  A handle in a batch must not be stepped or modified by any
+ * other call until it is removed; sbp_batch_remove hands the state (level parity, time) back to
+ * the handle, after which sbp_get_field and every other call apply to it as usual. */
+typedef struct sbp_batch sbp_batch;
+
+/* Create an empty batch for `max_shots` shots (1 .. 4096) of interior order `order`, on the current
+ * device.  Errors: SBP_E_INVALID_ARG, SBP_E_OOM, SBP_E_CUDA. */
+int sbp_batch_create(int order, int max_shots, sbp_batch** out);
+int sbp_batch_destroy(sbp_batch* b);
+const char* sbp_batch_last_error(const sbp_batch* b);
+
+/* Admit handle h for nsteps leapfrog steps of size dt from its current state; *slot_out receives
+ * its slot.  Takes effect at the next sbp_batch_step.  Errors: SBP_E_INVALID_ARG (not a
+ * single-block FP32 handle of the batch's order, interfaces), SBP_E_STATE (batch full, handle
+ * already admitted, time-basis data, material missing). */
+int sbp_batch_add(sbp_batch* b, sbp_handle* h, int nsteps, double dt, int* slot_out);
+
+/* Enqueue ksteps batch steps on `stream` (asynchronous; a CUDA graph of ksteps persistent
+ * launches, captured on the first call with this ksteps).  Admissions and removals since the last
+ * call are uploaded first, stream-ordered. */
+int sbp_batch_step(sbp_batch* b, int ksteps, void* stream);
+
+/* Synchronise `stream` and write the steps each slot still has to run into remaining[max_shots]
+ * (-1 for a free slot).  Returns SBP_E_TIMEOUT (and clears it) if a bounded wait of the batch
+ * kernel ran out since the last poll. */
+int sbp_batch_poll(sbp_batch* b, int* remaining, void* stream);
+
+/* Retire the shot in `slot` (finished or not): synchronises `stream`, hands its level parity and
+ * time back to its handle and frees the slot. */
+int sbp_batch_remove(sbp_batch* b, int slot, void* stream);
+
+/* Rows of an interior work item (the tile shape; 0 = default 64).  Only while the batch is empty. */
+int sbp_batch_set_rows(sbp_batch* b, int rows);
+
+/* Pick the tile shape (rows of an interior work item: 32, 64, 128 or 256) by timing batch steps of
+ * a representative shot h alone; h's levels, parity and time are restored afterwards (one copy of
+ * its state is allocated for the call).  The batch must be empty; the choice is kept by the batch
+ * and written to *rows_out (may be NULL). */
+int sbp_batch_autotune(sbp_batch* b, sbp_handle* h, int* rows_out);
 
 /* ---- misfit gradient (adjoint) --------------------------------------------------------------
  * Sec. 5.2 remarks that self-adjointness (Theorems 3 and 5) lets an adjoint solver reuse the

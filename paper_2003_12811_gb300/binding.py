@@ -95,6 +95,16 @@ def lib():
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sbp_check.argtypes = [C.c_void_p]
         L.sbp_debug_wait_probe.argtypes = [C.c_void_p, C.c_int]
+        L.sbp_batch_create.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+        L.sbp_batch_destroy.argtypes = [C.c_void_p]
+        L.sbp_batch_last_error.argtypes = [C.c_void_p]
+        L.sbp_batch_last_error.restype = C.c_char_p
+        L.sbp_batch_add.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_int)]
+        L.sbp_batch_step.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.sbp_batch_poll.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.c_void_p]
+        L.sbp_batch_remove.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.sbp_batch_set_rows.argtypes = [C.c_void_p, C.c_int]
+        L.sbp_batch_autotune.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
         L.sbp_set_receivers.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
         L.sbp_record.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP]
         L.sbp_misfit_gradient.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP, C.c_int, _DP,
@@ -341,6 +351,63 @@ class Solver:
         if getattr(self, "h", None):
             self.L.sbp_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batch of resident shots advanced by the persistent tile-queue kernel (sbp_batch_*)."""
+
+    def __init__(self, order, max_shots):
+        self.L = lib()
+        self.max_shots = int(max_shots)
+        b = C.c_void_p()
+        rc = self.L.sbp_batch_create(int(order), self.max_shots, C.byref(b))
+        if rc != SBP_OK:
+            raise SbpError(rc, "sbp_batch_create failed")
+        self.b = b
+        self._rem = (C.c_int * self.max_shots)()
+
+    def _check(self, rc):
+        if rc != SBP_OK:
+            raise SbpError(rc, self.L.sbp_batch_last_error(self.b).decode())
+
+    @staticmethod
+    def _s(stream):
+        return None if stream is None else C.c_void_p(stream)
+
+    def sbp_batch_add(self, solver, nsteps, dt):
+        slot = C.c_int()
+        self._check(self.L.sbp_batch_add(self.b, solver.h, int(nsteps), float(dt), C.byref(slot)))
+        return slot.value
+
+    def sbp_batch_step(self, ksteps, stream=None):
+        self._check(self.L.sbp_batch_step(self.b, int(ksteps), self._s(stream)))
+
+    def sbp_batch_poll(self, stream=None):
+        """Steps left per slot (-1: free slot); synchronises the stream."""
+        self._check(self.L.sbp_batch_poll(self.b, self._rem, self._s(stream)))
+        return list(self._rem)
+
+    def sbp_batch_remove(self, slot, stream=None):
+        self._check(self.L.sbp_batch_remove(self.b, int(slot), self._s(stream)))
+
+    def sbp_batch_set_rows(self, rows):
+        self._check(self.L.sbp_batch_set_rows(self.b, int(rows)))
+
+    def sbp_batch_autotune(self, solver):
+        rows = C.c_int()
+        self._check(self.L.sbp_batch_autotune(self.b, solver.h, C.byref(rows)))
+        return rows.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.L.sbp_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -17,6 +17,7 @@
 #include "sbp_interior_march.cuh"
 #include "sbp_kernels.cuh"
 #include "sbp_adjoint.cuh"
+#include "sbp_batch.cuh"
 
 namespace sbphost {
 #define SBP_TABLE static const
@@ -339,6 +340,10 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
     constexpr size_t smem = interior_smem_elems<T, O>() * sizeof(T);
     // interior kernels on st; strip kernels on the auxiliary stream when overlapping (profiling
     // runs serialise so that every family's events time that family alone)
+    if (mode == 2 && !adj && h->n_src_int > 0) {   // RK4 stage: interior sources first (into r)
+        ProfScope ps(h, 3, st, 1);
+        k_sources<T, 2><<<grid_for(h->n_src_int), 256, 0, st>>>(h->d_blocks, h->d_src_int, h->n_src_int, h->d_src_params, a);
+    }
     const bool ovl = h->overlap && h->aux && !h->prof;
     // the interface traces run on the auxiliary stream beside the interior kernel (in its tail
     // or its free slots); the strips that read them follow on that stream or wait for it
@@ -351,29 +356,48 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
         if (ovl) cudaStreamWaitEvent(h->hi, h->ev_fork, 0);
     }
-    for (auto& hb : h->blocks) {
+    if constexpr (std::is_same<T, float>::value) {
+        // column-marching kernel: the interior tiles of up to MARCH_MAX_BLOCKS blocks per launch,
+        // rows per tile chosen for one wave of ~4 CTAs per SM per block
+        MarchMulti mmul{};
+        int tiles = 0;
+        auto flush = [&]() {
+            if (mmul.nb == 0) return;
+            mmul.start[mmul.nb] = tiles;
+            ProfScope ps(h, 0, ist, 1);
+            constexpr size_t msm = MarchCfg<O>::BYTES;
+            if (mode == 0) k_interior_march_multi<O, 0><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
+            else if (mode == 2) k_interior_march_multi<O, 2><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
+            else k_interior_march_multi<O, 1><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
+            mmul = MarchMulti{};
+            tiles = 0;
+        };
+        for (auto& hb : h->blocks) {
+            const int S2 = std::max(order_nclos(h->order), order_ncol(h->order));
+            const int ncx = march_ncx(hb.n1, S2);
+            const int n2i = hb.n2 - 2 * S2;
+            int ncy = std::max(1, (4 * h->num_sms + ncx / 2) / ncx);
+            int rows = (n2i + ncy - 1) / ncy;
+            if (rows < 16) rows = std::min(16, n2i);
+            if (h->rows_per_cta > 0) rows = std::min(h->rows_per_cta, n2i);
+            ncy = (n2i + rows - 1) / rows;
+            const int k = mmul.nb++;
+            mmul.maps[k] = adj ? hb.pmaps : hb.mmaps;
+            mmul.b[k] = adj ? make_view_adj(h, hb) : make_view(h, hb);
+            mmul.start[k] = tiles;
+            mmul.rows[k] = rows;
+            tiles += ncx * ncy;
+            if (mmul.nb == MARCH_MAX_BLOCKS) flush();
+        }
+        flush();
+    } else for (auto& hb : h->blocks) {
         BlockDev b = adj ? make_view_adj(h, hb) : make_view(h, hb);
-        const MarchMaps& mm = adj ? hb.pmaps : hb.mmaps;
         const int S = b.strip;
         const int ni1 = hb.n1 - 2 * S, ni2 = hb.n2 - 2 * S;
         dim3 grid((ni1 + ITX - 1) / ITX, (ni2 + ITY - 1) / ITY);
         {
             ProfScope ps(h, 0, ist, 1);
-            if constexpr (std::is_same<T, float>::value) {
-                // column-marching kernel: one wave of ~4 CTAs per SM, rows split evenly
-                const int S2 = b.strip;
-                const int ncx = (hb.n1 - S2 - march_x0(S2) + MTHREADS - 1) / MTHREADS;
-                const int n2i = hb.n2 - 2 * S2;
-                int ncy = std::max(1, (4 * h->num_sms + ncx / 2) / ncx);
-                int rows = (n2i + ncy - 1) / ncy;
-                if (rows < 16) rows = std::min(16, n2i);
-                if (h->rows_per_cta > 0) rows = std::min(h->rows_per_cta, n2i);
-                ncy = (n2i + rows - 1) / rows;
-                constexpr size_t msm = MarchCfg<O>::BYTES;
-                if (mode == 0) k_interior_march<O, 0><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
-                else if (mode == 2) k_interior_march<O, 2><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
-                else k_interior_march<O, 1><<<ncx * ncy, MTHREADS, msm, ist>>>(mm, b, a, rows, h->d_err);
-            } else {
+            {
                 if (mode == 0) k_interior<T, O, 0><<<grid, dim3(32, 8), smem, ist>>>(b, a);
                 else if (mode == 2) k_interior<T, O, 2><<<grid, dim3(32, 8), smem, ist>>>(b, a);
                 else k_interior<T, O, 1><<<grid, dim3(32, 8), smem, ist>>>(b, a);
@@ -439,11 +463,10 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
         cudaStreamWaitEvent(st, h->ev_join, 0);
         cudaStreamWaitEvent(st, h->ev_join_hi, 0);
     }
-    if (!adj && h->n_src_int > 0) {   // source nodes off the strips (the strip kernel adds the others)
+    if (!adj && h->n_src_int > 0 && mode != 2) {   // source nodes off the strips (the strip kernel adds the others)
         ProfScope ps(h, 3, st, 1);
         const int ns = h->n_src_int;
         if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_int, ns, h->d_src_params, a);
-        else if (mode == 2) k_sources<T, 2><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_int, ns, h->d_src_params, a);
         else k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_int, ns, h->d_src_params, a);
     }
     return check_cuda(h, "operator launch");
@@ -476,6 +499,9 @@ template <typename T, int O> void set_smem_attr() {
         cudaFuncSetAttribute(k_interior_march<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march<O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_march_multi<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_march_multi<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_march_multi<O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
     }
 }
 
@@ -1324,6 +1350,10 @@ int sbp_step_rk4(sbp_handle* h, int nsteps, double dt, void* stream) {
     for (auto& hb : h->blocks)
         if (!hb.rk) return h->fail(SBP_E_STATE, "set the RK4 state (sbp_set_state_rk4) of every block first");
     cudaStream_t st = (cudaStream_t)stream;
+    // the operator-output planes carry the interior point sources of each stage (zero elsewhere)
+    for (auto& hb : h->blocks)
+        if (cudaMemsetAsync(hb.r, 0, 2 * (size_t)hb.n2 * hb.pitch * h->esize, st) != cudaSuccess)
+            return h->fail(SBP_E_CUDA, "RK4 scratch clear failed");
     const double cs[4] = {0.0, 0.5, 0.5, 1.0};
     for (int n = 0; n < nsteps; ++n) {
         for (int s = 1; s <= 4; ++s) {
@@ -1413,15 +1443,27 @@ int sbp_suggest_dt(sbp_handle* h, double cfl, double* dt_out) {
     if (!h) return SBP_E_INVALID_ARG;
     if (!dt_out || !(cfl > 0)) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    // two passes over every block (the operator-output planes serve as scratch for the per-node
+    // FP32 estimates): the FP32 sweep and its minimum, then FP64 refinement near that minimum
     unsigned long long init = 0x7FF0000000000000ULL;   // +inf
-    if (cudaMemcpy(h->d_scalar, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess)
+    unsigned initf = 0x7F800000u;                       // +inf (FP32)
+    unsigned* minf = reinterpret_cast<unsigned*>(h->d_scalar + 1);
+    if (cudaMemcpy(h->d_scalar, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(minf, &initf, sizeof(initf), cudaMemcpyHostToDevice) != cudaSuccess)
         return h->fail(SBP_E_CUDA, "cfl initialisation failed");
-    for (auto& hb : h->blocks) {
-        BlockDev b = make_view(h, hb);
-        const long long n = (long long)hb.n1 * hb.n2;
-        if (h->precision == SBP_FP64) k_cfl<double><<<grid_for(n), 256>>>(b, (unsigned long long*)h->d_scalar);
-        else k_cfl<float><<<grid_for(n), 256>>>(b, (unsigned long long*)h->d_scalar);
-    }
+    for (int pass = 0; pass < 2; ++pass)
+        for (auto& hb : h->blocks) {
+            BlockDev b = make_view(h, hb);
+            const long long n = (long long)hb.n1 * hb.n2;
+            float* rf = reinterpret_cast<float*>(hb.r);
+            if (pass == 0) {
+                if (h->precision == SBP_FP64) k_cfl_sweep<double><<<grid_for(n), 256>>>(b, rf, minf);
+                else k_cfl_sweep<float><<<grid_for(n), 256>>>(b, rf, minf);
+            } else {
+                if (h->precision == SBP_FP64) k_cfl_refine<double><<<grid_for(n), 256>>>(b, rf, minf, 1e-3f, (unsigned long long*)h->d_scalar);
+                else k_cfl_refine<float><<<grid_for(n), 256>>>(b, rf, minf, 1e-3f, (unsigned long long*)h->d_scalar);
+            }
+        }
     double r = 0;
     if (cudaMemcpy(&r, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return h->fail(SBP_E_CUDA, "cfl");
     *dt_out = cfl * r;
@@ -1608,7 +1650,8 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
     // launches in the graph, per family (counted as if launched one by one)
     {
         const int nb = (int)h->blocks.size();
-        h->launches[0] += (long long)nsteps * nb;
+        const int nint = h->precision == SBP_FP32 ? (nb + MARCH_MAX_BLOCKS - 1) / MARCH_MAX_BLOCKS : nb;
+        h->launches[0] += (long long)nsteps * nint;
         h->launches[1] += (long long)nsteps * nb;
         if (h->n_src_int > 0) h->launches[3] += nsteps;
     }
@@ -2024,6 +2067,343 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
         return h->fail(SBP_E_CUDA, "misfit download");
     rc = check_cuda(h, "misfit gradient");
     return rc != SBP_OK ? rc : check_kernel_errors(h);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batch of resident shots stepped by the persistent tile-queue kernel (k_batch_step).
+
+}  // extern "C"
+
+struct sbp_batch {
+    int order = 0, max_shots = 0, rows = 0;
+    int num_sms = 1, ctas = 0;
+    sbp::BatchHead* d_head = nullptr;
+    sbp::BatchShot* d_shots = nullptr;
+    sbp::BatchState* d_state = nullptr;
+    int4* d_items = nullptr;
+    int items_cap = 0;
+    int* d_err = nullptr;
+    std::vector<sbp_handle*> shot;          // null: free slot
+    std::vector<sbp::BatchShot> mirror;     // host copies of the immutable descriptions
+    std::vector<sbp::BatchState> pending;   // state of slots admitted since the last launch
+    std::vector<char> pending_set;
+    std::vector<int> nint, nstrip;          // work items per slot
+    bool dirty = false;
+    int graph_k = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::string err;
+    int fail(int code, const std::string& m) {
+        err = m;
+        return code;
+    }
+};
+
+namespace {
+
+template <int O> void batch_smem_attr() {
+    cudaFuncSetAttribute(k_batch_step<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<O>());
+}
+template <int O> size_t batch_smem() { return batch_smem_bytes<O>(); }
+
+void batch_launch(sbp_batch* b, cudaStream_t st) {
+    if (b->order == 2) k_batch_step<2><<<b->ctas, MTHREADS, batch_smem<2>(), st>>>(b->d_head, b->d_err);
+    else if (b->order == 4) k_batch_step<4><<<b->ctas, MTHREADS, batch_smem<4>(), st>>>(b->d_head, b->d_err);
+    else k_batch_step<6><<<b->ctas, MTHREADS, batch_smem<6>(), st>>>(b->d_head, b->d_err);
+}
+
+int batch_rows_for(const sbp_batch* b, const HostBlock& hb) {
+    if (b->rows > 0) return b->rows;
+    return 64;
+}
+
+// rebuild and upload the work list: interior tiles of every active shot first (the long items),
+// then the strip tiles; uploads the state of newly admitted slots; stream-ordered
+int batch_sync(sbp_batch* b, cudaStream_t st) {
+    if (!b->dirty) return SBP_OK;
+    std::vector<int4> items;
+    for (int s = 0; s < b->max_shots; ++s)
+        if (b->shot[s])
+            for (int k = 0; k < b->nint[s]; ++k) items.push_back(make_int4(s, 0, k, 0));
+    for (int s = 0; s < b->max_shots; ++s)
+        if (b->shot[s])
+            for (int k = 0; k < b->nstrip[s]; ++k) items.push_back(make_int4(s, 1, k, 0));
+    if ((int)items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = 0;
+        const int cap = (int)items.size() * 2;
+        if (cudaMalloc(&b->d_items, sizeof(int4) * cap) != cudaSuccess) return b->fail(SBP_E_OOM, "batch work list");
+        b->items_cap = cap;
+    }
+    if (!items.empty() &&
+        cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return b->fail(SBP_E_CUDA, "batch work list upload");
+    for (int s = 0; s < b->max_shots; ++s) {
+        if (!b->pending_set[s]) continue;
+        if (cudaMemcpyAsync(b->d_shots + s, &b->mirror[s], sizeof(BatchShot), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(b->d_state + s, &b->pending[s], sizeof(BatchState), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return b->fail(SBP_E_CUDA, "batch shot upload");
+        b->pending_set[s] = 0;
+    }
+    BatchHead hd{};
+    hd.items = b->d_items;
+    hd.nitems = (int)items.size();
+    hd.nshots = b->max_shots;
+    hd.shots = b->d_shots;
+    hd.state = b->d_state;
+    hd.next = 0;
+    hd.done = 0;
+    if (cudaMemcpyAsync(b->d_head, &hd, sizeof(hd), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return b->fail(SBP_E_CUDA, "batch head upload");
+    // the host sources above are staged by the copies at call time (pageable memory) except the
+    // members of b, which live until the batch is destroyed
+    b->dirty = false;
+    return SBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbp_batch_create(int order, int max_shots, sbp_batch** out) {
+    if (!out) return SBP_E_INVALID_ARG;
+    *out = nullptr;
+    if ((order != 2 && order != 4 && order != 6) || max_shots < 1 || max_shots > 4096) return SBP_E_INVALID_ARG;
+    sbp_batch* b = new sbp_batch();
+    b->order = order;
+    b->max_shots = max_shots;
+    b->shot.assign(max_shots, nullptr);
+    b->mirror.assign(max_shots, BatchShot{});
+    b->pending.assign(max_shots, BatchState{});
+    b->pending_set.assign(max_shots, 0);
+    b->nint.assign(max_shots, 0);
+    b->nstrip.assign(max_shots, 0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (b->num_sms <= 0) b->num_sms = 1;
+    if (order == 2) batch_smem_attr<2>();
+    else if (order == 4) batch_smem_attr<4>();
+    else batch_smem_attr<6>();
+    int per_sm = 0;
+    if (order == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<2>, MTHREADS, batch_smem<2>());
+    else if (order == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<4>, MTHREADS, batch_smem<4>());
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<6>, MTHREADS, batch_smem<6>());
+    b->ctas = std::max(1, per_sm) * b->num_sms;      // persistent: every CTA resident at once
+    if (cudaMalloc(&b->d_head, sizeof(BatchHead)) != cudaSuccess || cudaMalloc(&b->d_shots, sizeof(BatchShot) * max_shots) != cudaSuccess ||
+        cudaMalloc(&b->d_state, sizeof(BatchState) * max_shots) != cudaSuccess || cudaMalloc(&b->d_err, 64) != cudaSuccess) {
+        sbp_batch_destroy(b);
+        return SBP_E_OOM;
+    }
+    cudaMemset(b->d_state, 0, sizeof(BatchState) * max_shots);
+    cudaMemset(b->d_err, 0, 64);
+    BatchHead hd{};
+    hd.nshots = max_shots;
+    hd.shots = b->d_shots;
+    hd.state = b->d_state;
+    if (cudaMemcpy(b->d_head, &hd, sizeof(hd), cudaMemcpyHostToDevice) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        sbp_batch_destroy(b);
+        return SBP_E_CUDA;
+    }
+    *out = b;
+    return SBP_OK;
+}
+
+int sbp_batch_destroy(sbp_batch* b) {
+    if (!b) return SBP_OK;
+    cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_head) cudaFree(b->d_head);
+    if (b->d_shots) cudaFree(b->d_shots);
+    if (b->d_state) cudaFree(b->d_state);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_err) cudaFree(b->d_err);
+    delete b;
+    return SBP_OK;
+}
+
+const char* sbp_batch_last_error(const sbp_batch* b) { return b ? b->err.c_str() : ""; }
+
+int sbp_batch_add(sbp_batch* b, sbp_handle* h, int nsteps, double dt, int* slot_out) {
+    if (!b || !h || !slot_out) return SBP_E_INVALID_ARG;
+    *slot_out = -1;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return b->fail(SBP_E_INVALID_ARG, "bad step arguments");
+    if (h->precision != SBP_FP32 || h->order != b->order || h->nblocks != 1)
+        return b->fail(SBP_E_INVALID_ARG, "batch shots are single-block FP32 handles of the batch's order");
+    const HostBlock& hb = h->blocks[0];
+    for (auto& F : hb.f)
+        if (F.kind == SBP_BC_INTERFACE) return b->fail(SBP_E_INVALID_ARG, "batch shots have no interfaces");
+    if (h->nbasis != 0) return b->fail(SBP_E_STATE, "batch shots take point sources only (no time-basis data)");
+    if (!hb.material) return b->fail(SBP_E_STATE, "set the material first");
+    for (int s = 0; s < b->max_shots; ++s) if (b->shot[s] == h) return b->fail(SBP_E_STATE, "handle already in the batch");
+    int slot = -1;
+    for (int s = 0; s < b->max_shots && slot < 0; ++s)
+        if (!b->shot[s]) slot = s;
+    if (slot < 0) return b->fail(SBP_E_STATE, "batch full");
+    if (upload_sources(h) != SBP_OK) return b->fail(SBP_E_CUDA, h->err);
+    BatchShot& sh = b->mirror[slot];
+    sh = BatchShot{};
+    sh.maps = hb.mmaps;
+    sh.view = make_view(h, hb);
+    sh.tiles = h->d_tiles;
+    sh.ssrc = h->d_src_strip;
+    sh.isrc = h->d_src_int;
+    sh.spar = h->d_src_params;
+    sh.nisrc = h->n_src_int;
+    sh.rows = batch_rows_for(b, hb);
+    sh.dt = dt;
+    sh.dt2 = dt * dt;
+    sh.dt2f = (float)sh.dt2;
+    sh.beta = h->beta;
+    const int S = sh.view.strip;
+    const int n2i = hb.n2 - 2 * S;
+    b->nint[slot] = march_ncx(hb.n1, S) * ((n2i + sh.rows - 1) / sh.rows);
+    b->nstrip[slot] = h->ntiles;
+    b->pending[slot] = BatchState{nsteps, h->cur, h->t};
+    b->pending_set[slot] = 1;
+    b->shot[slot] = h;
+    b->dirty = true;
+    *slot_out = slot;
+    return SBP_OK;
+}
+
+int sbp_batch_step(sbp_batch* b, int ksteps, void* stream) {
+    if (!b) return SBP_E_INVALID_ARG;
+    if (ksteps < 1) return b->fail(SBP_E_INVALID_ARG, "ksteps must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = batch_sync(b, st);
+    if (rc != SBP_OK) return rc;
+    if (!b->graph || b->graph_k != ksteps) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return b->fail(SBP_E_CUDA, "stream");
+        cudaGraph_t g = nullptr;
+        bool okc = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        for (int k = 0; okc && k < ksteps; ++k) batch_launch(b, cs);
+        okc = cudaStreamEndCapture(cs, &g) == cudaSuccess && okc && g;
+        cudaStreamDestroy(cs);
+        if (!okc || cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            b->graph = nullptr;
+            return b->fail(SBP_E_CUDA, "batch graph capture failed");
+        }
+        cudaGraphDestroy(g);
+        b->graph_k = ksteps;
+    }
+    if (cudaGraphLaunch(b->graph, st) != cudaSuccess) return b->fail(SBP_E_CUDA, "batch graph launch failed");
+    return SBP_OK;
+}
+
+int sbp_batch_poll(sbp_batch* b, int* remaining, void* stream) {
+    if (!b || !remaining) return SBP_E_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<BatchState> v(b->max_shots);
+    int e = 0;
+    if (cudaMemcpyAsync(v.data(), b->d_state, sizeof(BatchState) * b->max_shots, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return b->fail(SBP_E_CUDA, std::string("batch poll: ") + cudaGetErrorString(cudaGetLastError()));
+    for (int s = 0; s < b->max_shots; ++s) {
+        if (!b->shot[s]) remaining[s] = -1;
+        else remaining[s] = b->pending_set[s] ? b->pending[s].remaining : v[s].remaining;
+    }
+    if (e) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return b->fail(SBP_E_TIMEOUT, "a bounded wait in the batch kernel ran out; results of the last steps are invalid");
+    }
+    return SBP_OK;
+}
+
+int sbp_batch_remove(sbp_batch* b, int slot, void* stream) {
+    if (!b) return SBP_E_INVALID_ARG;
+    if (slot < 0 || slot >= b->max_shots || !b->shot[slot]) return b->fail(SBP_E_INVALID_ARG, "bad slot");
+    cudaStream_t st = (cudaStream_t)stream;
+    sbp_handle* h = b->shot[slot];
+    BatchState cur{};
+    if (b->pending_set[slot]) {
+        cur = b->pending[slot];
+    } else if (cudaMemcpyAsync(&cur, b->d_state + slot, sizeof(cur), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess) {
+        return b->fail(SBP_E_CUDA, "batch state read");
+    }
+    // hand the state back to the handle: its levels sit in its own buffers with parity cur
+    h->cur = cur.cur;
+    h->t = cur.t;
+    b->shot[slot] = nullptr;
+    b->pending[slot] = BatchState{0, 0, 0.0};
+    b->pending_set[slot] = 1;               // the slot's device state is cleared at the next launch
+    b->mirror[slot] = BatchShot{};
+    b->nint[slot] = b->nstrip[slot] = 0;
+    b->dirty = true;
+    return SBP_OK;
+}
+
+int sbp_batch_autotune(sbp_batch* b, sbp_handle* h, int* rows_out) {
+    if (!b || !h) return SBP_E_INVALID_ARG;
+    for (int s = 0; s < b->max_shots; ++s)
+        if (b->shot[s]) return b->fail(SBP_E_STATE, "autotune an empty batch");
+    // the candidates advance h; its two levels, parity and time are restored afterwards
+    const HostBlock& hb = h->blocks[0];
+    const size_t bytes = 2 * (size_t)hb.n2 * hb.pitch * h->esize;
+    void* keep[2] = {nullptr, nullptr};
+    if (cudaMalloc(&keep[0], bytes) != cudaSuccess || cudaMalloc(&keep[1], bytes) != cudaSuccess) {
+        if (keep[0]) cudaFree(keep[0]);
+        return b->fail(SBP_E_OOM, "autotune state copy");
+    }
+    const int cur0 = h->cur;
+    const double t0 = h->t;
+    int rc = SBP_OK;
+    if (cudaMemcpy(keep[0], hb.u[0], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(keep[1], hb.u[1], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess)
+        rc = b->fail(SBP_E_CUDA, "autotune state copy");
+    const int cand[] = {32, 64, 128, 256};
+    int best = 64;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> rem(b->max_shots);
+    for (int c = 0; c < 4 && rc == SBP_OK; ++c) {
+        b->rows = cand[c];
+        int slot = -1;
+        rc = sbp_batch_add(b, h, 10, 1e-9, &slot);
+        if (rc == SBP_OK) rc = sbp_batch_step(b, 2, nullptr);     // warm-up (and the graph capture)
+        if (rc == SBP_OK) {
+            cudaEventRecord(e0, 0);
+            rc = sbp_batch_step(b, 8, nullptr);
+            cudaEventRecord(e1, 0);
+        }
+        if (rc == SBP_OK) rc = sbp_batch_poll(b, rem.data(), nullptr);
+        float ms = 0.f;
+        if (rc == SBP_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+        if (slot >= 0) sbp_batch_remove(b, slot, nullptr);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaDeviceSynchronize();
+    if (cudaMemcpy(hb.u[0], keep[0], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(hb.u[1], keep[1], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess)
+        rc = rc != SBP_OK ? rc : b->fail(SBP_E_CUDA, "autotune state restore");
+    cudaFree(keep[0]);
+    cudaFree(keep[1]);
+    h->cur = cur0;
+    h->t = t0;
+    b->rows = best;
+    if (rows_out) *rows_out = best;
+    return rc;
+}
+
+int sbp_batch_set_rows(sbp_batch* b, int rows) {
+    if (!b) return SBP_E_INVALID_ARG;
+    if (rows < 0) return b->fail(SBP_E_INVALID_ARG, "rows must be >= 0");
+    for (int s = 0; s < b->max_shots; ++s)
+        if (b->shot[s]) return b->fail(SBP_E_STATE, "set the tile shape while the batch is empty");
+    b->rows = rows;
+    return SBP_OK;
 }
 
 }  // extern "C"

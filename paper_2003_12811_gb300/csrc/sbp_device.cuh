@@ -295,6 +295,7 @@ struct StepArgs {
 // v_new = v + h sum_s b_s a_s, b = (1, 2, 2, 1)/6.  The kernel of stage s has read U_s (state
 // buffer u[cur]) and formed r = DD(c) U_s + J SAT + J f at node gi; this writes U_{s+1} (or u_new)
 // into u[1 - cur] and keeps V, S_u = sum b V, S_v = sum b a and, after stage 4, (u, v) in B.rk.
+// B.r holds zeros except at point-source nodes off the strips (their J f, added before the stage).
 template <typename T>
 __device__ __forceinline__ void rk4_store(const BlockDev& B, const StepArgs& a, size_t gi, size_t plane, T w, T r0,
                                           T r1) {
@@ -303,6 +304,16 @@ __device__ __forceinline__ void rk4_store(const BlockDev& B, const StepArgs& a, 
     const int s = a.stage;
     T h;
     if constexpr (sizeof(T) == 4) h = a.rkhf; else h = a.rkh;
+    // point sources off the strips were added into B.r (zero elsewhere) before this kernel ran:
+    // take them into the operator sum, then clear them for the next stage
+    T* __restrict__ Rs = reinterpret_cast<T*>(B.r);
+    const T rs0 = Rs[gi], rs1 = Rs[plane + gi];
+    if (rs0 != T(0) || rs1 != T(0)) {
+        r0 += rs0;
+        r1 += rs1;
+        Rs[gi] = T(0);
+        Rs[plane + gi] = T(0);
+    }
     const T a0 = w * r0, a1 = w * r1;
     const T u0 = R[gi], u1 = R[plane + gi], v0 = R[2 * plane + gi], v1 = R[3 * plane + gi];
     const T V0 = s == 1 ? v0 : R[4 * plane + gi], V1 = s == 1 ? v1 : R[5 * plane + gi];
@@ -353,6 +364,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -365,10 +379,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: returns false after `polls` unsuccessful polls (default 2^22)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int polls = 1 << 22) {
-    for (int i = 0; i < polls; ++i)
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: returns false after `polls` unsuccessful polls or after about 2 s, whichever
+// comes first (a poll may suspend the thread for a while, so the poll count alone does not bound
+// the time); the clock is read only once the first poll has failed
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int polls = 1 << 30) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (int i = 1; i < polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && globaltimer_ns() - t0 > 2000000000ull) return false;
+    }
     return false;
 }
 // tiled bulk tensor copy global -> shared of a 3-D box at (x, y, z); completion on `bar`

@@ -65,12 +65,20 @@ template <int O, class F> __device__ __forceinline__ float edge1(int m, F B) {
 // tile geometry shared with the host: first column, columns per CTA, rows per CTA
 __host__ __device__ inline int march_x0(int strip) { return (strip / 4) * 4; }
 
+// columns-of-128 tiles across the interior of a block (the host sizes grids and work lists with it)
+__host__ __device__ inline int march_ncx(int n1, int strip) { return (n1 - strip - march_x0(strip) + MTHREADS - 1) / MTHREADS; }
+
+// One interior tile: the 128 columns of column tile `tile % ncx` and the rows_per_cta rows of row
+// band `tile / ncx`, by the 128 threads of the calling CTA, with `smem` (MarchCfg<O>::BYTES, 128-byte
+// aligned) as its ring, flux row and mbarriers.  Returns false when a bounded wait ran out (the
+// error word is set; the tile's copies have been drained).  The mbarriers are invalidated before
+// the return, so a persistent caller can reuse the shared memory for its next tile after a
+// CTA barrier.
 template <int O, int MODE>
-__global__ void __launch_bounds__(MTHREADS, 4)
-k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a, int rows_per_cta, int* err) {
+__device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BlockDev& B, const StepArgs& a, int rows_per_cta,
+                                           int tile, int* err, unsigned char* march_smem) {
     using MC = MarchCfg<O>;
     constexpr int Q = MC::Q, W = MBOXW, L = 2 * Q + 1;
-    extern __shared__ __align__(128) unsigned char march_smem[];
     float* ring = reinterpret_cast<float*>(march_smem);
     float* g1s = ring + MNCH * MC::CHUNK;
     uint64_t* bars = reinterpret_cast<uint64_t*>(g1s + MC::G1);
@@ -78,11 +86,11 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     const int S = B.strip, n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int lim1 = n1 - S, lim2 = n2 - S;
     const int X0 = march_x0(S);
-    const int ncx = (lim1 - X0 + MTHREADS - 1) / MTHREADS;
-    const int cx = blockIdx.x % ncx, cy = blockIdx.x / ncx;
+    const int ncx = march_ncx(n1, S);
+    const int cx = tile % ncx, cy = tile / ncx;
     const int x0 = X0 + cx * MTHREADS;
     const int ys = S + cy * rows_per_cta;
-    if (ys >= lim2) return;
+    if (ys >= lim2) return true;
     const int ye = min(lim2, ys + rows_per_cta);
     const int rb = ys - Q;                       // first row streamed into the ring
     const int tx = threadIdx.x;
@@ -114,14 +122,14 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
 
     // ring access: rowp(r) points at (plane 0, row r, column 0) of row r's slot; plane p
     // (0,1 displacement; 2..11 coefficient planes 0..9) is at the compile-time offset poff(p)
-    auto rowp = [&](int r) -> const float* {
-        const int rr = r - rb;
+    auto rowp = [&](int r) -> const float* {     // r >= rb: unsigned division is a shift
+        const unsigned rr = (unsigned)(r - rb);
         return ring + ((rr / MR) % MNCH) * MC::CHUNK + (rr % MR) * W;
     };
     auto poff = [](int p) { return p < 2 ? p * MR * W : MC::UPAD + (p - 2) * MR * W; };
     auto at = [&](int p, int r, int col) -> float { return rowp(r)[poff(p) + col]; };
     auto wait_row = [&](int r) -> bool {        // called when row r is the first row of a chunk
-        const int ch = (r - rb) / MR;
+        const unsigned ch = (unsigned)(r - rb) / MR;
         return mbar_wait_bounded(&bars[ch % MNCH], (ch / MNCH) & 1);
     };
 
@@ -185,7 +193,7 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
     // look(r) pushes row Lr into the queues; yflux() forms the y edge fluxes of the queue centre
     auto look = [&](int r) {
         const int Lr = r + Q;
-        if (((Lr - rb) % MR) == 0) {
+        if (((unsigned)(Lr - rb) % MR) == 0) {
             ok = wait_row(Lr) && ok;
             ++waited;
         }
@@ -285,11 +293,11 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
                 for (int ch = waited; ch < next_issue; ++ch) mbar_wait_bounded(&bars[ch % MNCH], (ch / MNCH) & 1);
             }
             __syncthreads();
-            return;
+            return false;
         }
         // every thread is past row r-1: ring slots holding only rows below r can be refilled
         if (tx == 0) {
-            const int below = (r - rb) / MR;      // chunks entirely below row r
+            const int below = (int)((unsigned)(r - rb) / MR);   // chunks entirely below row r
             bool fenced = false;
             while (next_issue < nchunks && next_issue < below + MNCH) {
                 if (!fenced) {
@@ -360,7 +368,41 @@ k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a,
         rotate(r);
     }
     // every issued chunk has been waited for inside the march (the last lookahead rows cover
-    // the last chunk), so no bulk copy is still in flight when the CTA exits
+    // the last chunk), so no bulk copy is still in flight when the CTA exits; the barriers are
+    // invalidated once every thread is past its last wait
+    __syncthreads();
+    if (tx == 0)
+        for (int k = 0; k < MNCH; ++k) mbar_inval(&bars[k]);
+    return true;
+}
+
+template <int O, int MODE>
+__global__ void __launch_bounds__(MTHREADS, 4)
+k_interior_march(const __grid_constant__ MarchMaps maps, BlockDev B, StepArgs a, int rows_per_cta, int* err) {
+    extern __shared__ __align__(128) unsigned char march_smem[];
+    (void)march_tile<O, MODE>(maps, B, a, rows_per_cta, blockIdx.x, err, march_smem);
+}
+
+// The interior tiles of several blocks in one launch: CTA k takes tile k - start[b] of the block b
+// with start[b] <= k < start[b + 1], so the CTAs of the next block fill the tail of the previous
+// one instead of waiting for a launch boundary.
+constexpr int MARCH_MAX_BLOCKS = 8;
+struct MarchMulti {
+    MarchMaps maps[MARCH_MAX_BLOCKS];
+    BlockDev b[MARCH_MAX_BLOCKS];
+    int start[MARCH_MAX_BLOCKS + 1];
+    int rows[MARCH_MAX_BLOCKS];
+    int nb;
+};
+
+template <int O, int MODE>
+__global__ void __launch_bounds__(MTHREADS, 4)
+k_interior_march_multi(const __grid_constant__ MarchMulti mm, StepArgs a, int* err) {
+    extern __shared__ __align__(128) unsigned char march_smem[];
+    const int k = blockIdx.x;
+    int b = 0;
+    while (b + 1 < mm.nb && k >= mm.start[b + 1]) ++b;
+    (void)march_tile<O, MODE>(mm.maps[b], mm.b[b], a, mm.rows[b], k - mm.start[b], err, march_smem);
 }
 
 }  // namespace sbp

@@ -718,16 +718,19 @@ template <int O> struct StripTile {
 // costliest tiles (interface bands, side bands) start first.  B.smaps holds the block's band-box
 // tensor maps: u[0], u[1], c.  Point-source nodes inside the strips are added here (ssrc null:
 // none, e.g. on the adjoint fields); the host launches k_sources only for interior source nodes.
-template <typename T, int O, int MODE>
-__global__ void __launch_bounds__(StripTile<O>::THREADS, sizeof(T) == 4 ? 4 : 2)
-k_strip_tile(const BlockDev* __restrict__ blocks, const int4* __restrict__ tiles, StepArgs a, double beta, int* err,
-             const SrcNode* __restrict__ ssrc, const SrcParam* __restrict__ spar) {
+// The body of one strip tile, by the NT threads of the calling CTA (NT a multiple of 32; with fewer
+// than 32 S threads a warp takes several output rows).  Returns false when the bounded wait for
+// the tile's staging copies ran out (the error word is set).  The staging mbarrier is
+// invalidated before the return, so a persistent caller can reuse the shared memory for its next
+// tile after a CTA barrier.
+template <typename T, int O, int MODE, int NT>
+__device__ __forceinline__ bool strip_tile_body(const BlockDev* __restrict__ blocks, const int4 tt, const StepArgs& a,
+                                                double beta, int* err, const SrcNode* __restrict__ ssrc,
+                                                const SrcParam* __restrict__ spar, unsigned char* strip_smem) {
     using ST = StripTile<O>;
-    constexpr int S = ST::S, NT = ST::THREADS;
-    extern __shared__ __align__(128) unsigned char strip_smem[];
+    constexpr int S = ST::S;
     T* sm = reinterpret_cast<T*>(strip_smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(strip_smem + ST::template bar_off<T>());
-    const int4 tt = tiles[blockIdx.x];
     const BlockDev& B = blocks[tt.x];
     const int n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int nbx = (n1 + 31) / 32, nby = (n2 - 2 * S + 31) / 32;
@@ -769,6 +772,9 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int4* __restrict__ tiles
         }
         __syncthreads();
         if (threadIdx.x == 0) {
+            // the region may have been read and written by this CTA's threads for an earlier tile
+            // (persistent callers): order those accesses before the bulk copies overwrite it
+            fence_proxy_async();
             const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(B.smaps);
             mbar_expect_tx(bar, (uint32_t)(12 * PS * sizeof(T)));
             tma_load_3d(sm, &maps[a.cur], xs, ys, 0, bar);
@@ -780,8 +786,9 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int4* __restrict__ tiles
                 atomicOr(err, ERR_STRIP_WAIT);
                 mbar_wait_bounded(bar, 0);
             }
-            return;
+            return false;
         }
+        if (threadIdx.x == 0) mbar_inval(bar);   // every thread has seen the phase complete
     } else {
         const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
         const T* __restrict__ C = reinterpret_cast<const T*>(B.c);
@@ -856,76 +863,88 @@ k_strip_tile(const BlockDev* __restrict__ blocks, const int4* __restrict__ tiles
     // output node of this thread: a warp per row of a band tile (lanes along the row), a warp per
     // column of a side tile (lanes along the column: one closure row per warp, and the odd row
     // stride of the side staging keeps the column accesses free of bank conflicts)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int i1 = along_x ? x0 + lane : x0 + wid;
-    const int i2 = along_x ? y0 + wid : y0 + lane;
-    if (i1 >= x0 + w || i2 >= y0 + h) return;
-    // narrow rows: closure rows through the precomputed matrices, interior rows by edge weights
-    T rx0v = T(0), rx1v = T(0), ry0v = T(0), ry1v = T(0);
-    if (!dxx_closure_mat<O, T>(n1, i1, i2, n2, reinterpret_cast<const T*>(B.mx), [&](int j) { return at(0, j, i2); },
-                               [&](int j) { return at(1, j, i2); }, rx0v, rx1v))
-        dxx_interior<O, T>(i1, [&](int j) { return at(0, j, i2); }, [&](int j) { return at(1, j, i2); },
-                           [&](int k) { return at(2, k, i2); }, [&](int k) { return at(3, k, i2); },
-                           [&](int k) { return at(4, k, i2); }, rx0v, rx1v);
-    if (!dxx_closure_mat<O, T>(n2, i2, i1, n1, reinterpret_cast<const T*>(B.my), [&](int j) { return at(0, i1, j); },
-                               [&](int j) { return at(1, i1, j); }, ry0v, ry1v))
-        dxx_interior<O, T>(i2, [&](int j) { return at(0, i1, j); }, [&](int j) { return at(1, i1, j); },
-                           [&](int k) { return at(5, i1, k); }, [&](int k) { return at(6, i1, k); },
-                           [&](int k) { return at(7, i1, k); }, ry0v, ry1v);
-    T r0 = rx0v * ih1 * ih1 + ry0v * ih2 * ih2;
-    T r1 = rx1v * ih1 * ih1 + ry1v * ih2 * ih2;
-    r0 += dsum<O, T>(n1, i1, [&](int aa) { return g1(0, aa, i2); }) * ih1 +
-          dsum<O, T>(n2, i2, [&](int bb) { return g2(0, i1, bb); }) * ih2;
-    r1 += dsum<O, T>(n1, i1, [&](int aa) { return g1(1, aa, i2); }) * ih1 +
-          dsum<O, T>(n2, i2, [&](int bb) { return g2(1, i1, bb); }) * ih2;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const FaceDev& F = B.f[f];
-        const int m = F.m;
-        const int im = m == 0 ? i1 : i2, Nm = m == 0 ? n1 : n2;
-        const int d = F.side ? Nm - 1 - im : im;
-        if (d >= Ord<O>::NCOL) continue;
-        const T* q = sats + (f * 32 + (m == 0 ? i2 - y0 : i1 - x0)) * 4;
-        const T fac = facT<T>(F, d);
-        r0 += fac * q[2];
-        r1 += fac * q[3];
-        if (d == 0) {
-            r0 += q[0];
-            r1 += q[1];
+    const int lane = threadIdx.x & 31;
+    for (int wid = threadIdx.x >> 5; wid < S; wid += NT / 32) {
+        const int i1 = along_x ? x0 + lane : x0 + wid;
+        const int i2 = along_x ? y0 + wid : y0 + lane;
+        if (i1 >= x0 + w || i2 >= y0 + h) continue;
+        // narrow rows: closure rows through the precomputed matrices, interior rows by edge weights
+        T rx0v = T(0), rx1v = T(0), ry0v = T(0), ry1v = T(0);
+        if (!dxx_closure_mat<O, T>(n1, i1, i2, n2, reinterpret_cast<const T*>(B.mx), [&](int j) { return at(0, j, i2); },
+                                   [&](int j) { return at(1, j, i2); }, rx0v, rx1v))
+            dxx_interior<O, T>(i1, [&](int j) { return at(0, j, i2); }, [&](int j) { return at(1, j, i2); },
+                               [&](int k) { return at(2, k, i2); }, [&](int k) { return at(3, k, i2); },
+                               [&](int k) { return at(4, k, i2); }, rx0v, rx1v);
+        if (!dxx_closure_mat<O, T>(n2, i2, i1, n1, reinterpret_cast<const T*>(B.my), [&](int j) { return at(0, i1, j); },
+                                   [&](int j) { return at(1, i1, j); }, ry0v, ry1v))
+            dxx_interior<O, T>(i2, [&](int j) { return at(0, i1, j); }, [&](int j) { return at(1, i1, j); },
+                               [&](int k) { return at(5, i1, k); }, [&](int k) { return at(6, i1, k); },
+                               [&](int k) { return at(7, i1, k); }, ry0v, ry1v);
+        T r0 = rx0v * ih1 * ih1 + ry0v * ih2 * ih2;
+        T r1 = rx1v * ih1 * ih1 + ry1v * ih2 * ih2;
+        r0 += dsum<O, T>(n1, i1, [&](int aa) { return g1(0, aa, i2); }) * ih1 +
+              dsum<O, T>(n2, i2, [&](int bb) { return g2(0, i1, bb); }) * ih2;
+        r1 += dsum<O, T>(n1, i1, [&](int aa) { return g1(1, aa, i2); }) * ih1 +
+              dsum<O, T>(n2, i2, [&](int bb) { return g2(1, i1, bb); }) * ih2;
+    #pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const FaceDev& F = B.f[f];
+            const int m = F.m;
+            const int im = m == 0 ? i1 : i2, Nm = m == 0 ? n1 : n2;
+            const int d = F.side ? Nm - 1 - im : im;
+            if (d >= Ord<O>::NCOL) continue;
+            const T* q = sats + (f * 32 + (m == 0 ? i2 - y0 : i1 - x0)) * 4;
+            const T fac = facT<T>(F, d);
+            r0 += fac * q[2];
+            r1 += fac * q[3];
+            if (d == 0) {
+                r0 += q[0];
+                r1 += q[1];
+            }
+        }
+        const size_t gi = (size_t)i2 * P + i1;
+        if (a.with_data && B.jf) {
+            const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
+    #pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k >= a.K) break;
+                r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
+                r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
+            }
+        }
+        // point-source nodes of this tile: J f_J = dir_J amp W(t) w1 w2 / H (Sec. 7.4, discrete delta)
+        if (ssrc && a.with_data) {
+            for (int k = tt.z; k < tt.w; ++k) {
+                const SrcNode nd = ssrc[k];
+                if (nd.gi != (long long)gi) continue;
+                const double Wt = ricker_at(spar[nd.src], a);
+                r0 += T(Wt * nd.wt0);
+                r1 += T(Wt * nd.wt1);
+            }
+        }
+        if (MODE == 0) {
+            T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+            const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
+            Un[gi] = T(2) * at(0, i1, i2) - Un[gi] + dt2 * wv * r0;
+            Un[gi + plane] = T(2) * at(1, i1, i2) - Un[gi + plane] + dt2 * wv * r1;
+        } else if (MODE == 2) {
+            rk4_store<T>(B, a, gi, plane, reinterpret_cast<const T*>(B.w)[gi], r0, r1);
+        } else {
+            T* __restrict__ R = reinterpret_cast<T*>(B.r);
+            R[gi] = r0;
+            R[gi + plane] = r1;
         }
     }
-    const size_t gi = (size_t)i2 * P + i1;
-    if (a.with_data && B.jf) {
-        const T* __restrict__ JF = reinterpret_cast<const T*>(B.jf);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (k >= a.K) break;
-            r0 += T(a.Tk[k]) * JF[(size_t)k * plane + gi];
-            r1 += T(a.Tk[k]) * JF[(size_t)(a.K + k) * plane + gi];
-        }
-    }
-    // point-source nodes of this tile: J f_J = dir_J amp W(t) w1 w2 / H (Sec. 7.4, discrete delta)
-    if (ssrc && a.with_data) {
-        for (int k = tt.z; k < tt.w; ++k) {
-            const SrcNode nd = ssrc[k];
-            if (nd.gi != (long long)gi) continue;
-            const double Wt = ricker_at(spar[nd.src], a);
-            r0 += T(Wt * nd.wt0);
-            r1 += T(Wt * nd.wt1);
-        }
-    }
-    if (MODE == 0) {
-        T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
-        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
-        Un[gi] = T(2) * at(0, i1, i2) - Un[gi] + dt2 * wv * r0;
-        Un[gi + plane] = T(2) * at(1, i1, i2) - Un[gi + plane] + dt2 * wv * r1;
-    } else if (MODE == 2) {
-        rk4_store<T>(B, a, gi, plane, reinterpret_cast<const T*>(B.w)[gi], r0, r1);
-    } else {
-        T* __restrict__ R = reinterpret_cast<T*>(B.r);
-        R[gi] = r0;
-        R[gi + plane] = r1;
-    }
+    return true;
+}
+
+template <typename T, int O, int MODE>
+__global__ void __launch_bounds__(StripTile<O>::THREADS, sizeof(T) == 4 ? 4 : 2)
+k_strip_tile(const BlockDev* __restrict__ blocks, const int4* __restrict__ tiles, StepArgs a, double beta, int* err,
+             const SrcNode* __restrict__ ssrc, const SrcParam* __restrict__ spar) {
+    extern __shared__ __align__(128) unsigned char strip_smem[];
+    (void)strip_tile_body<T, O, MODE, StripTile<O>::THREADS>(blocks, tiles[blockIdx.x], a, beta, err, ssrc, spar,
+                                                             strip_smem);
 }
 
 // ============================================================================ point sources
@@ -945,22 +964,11 @@ __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __
         atomicAdd(Un + nd.gi, T(fac * nd.wt0));
         atomicAdd(Un + plane + nd.gi, T(fac * nd.wt1));
     } else if (MODE == 2) {
-        // the stage acceleration gains da = w W(t) wt after rk4_store ran: V_{s+1} += c_{s+1} h da,
-        // S_v += b_s da (stages 1-3); v_new += h b_4 da (stage 4)
-        T* R = reinterpret_cast<T*>(B.rk);
-        const double da = (double)reinterpret_cast<const T*>(B.w)[nd.gi] * Wt, h = a.rkh;
-        const int s = a.stage;
-        const double b = (s == 1 || s == 4) ? 1.0 / 6.0 : 1.0 / 3.0;
-        if (s < 4) {
-            const double ch = s == 3 ? h : 0.5 * h;
-            atomicAdd(R + 4 * plane + nd.gi, T(ch * da * nd.wt0));
-            atomicAdd(R + 5 * plane + nd.gi, T(ch * da * nd.wt1));
-            atomicAdd(R + 8 * plane + nd.gi, T(b * da * nd.wt0));
-            atomicAdd(R + 9 * plane + nd.gi, T(b * da * nd.wt1));
-        } else {
-            atomicAdd(R + 2 * plane + nd.gi, T(h * b * da * nd.wt0));
-            atomicAdd(R + 3 * plane + nd.gi, T(h * b * da * nd.wt1));
-        }
+        // RK4 stage: J f at the node into the (otherwise zero) operator-output planes, which the
+        // stage's kernels add to the operator sum before forming the acceleration (rk4_store)
+        T* R = reinterpret_cast<T*>(B.r);
+        atomicAdd(R + nd.gi, T(Wt * nd.wt0));
+        atomicAdd(R + plane + nd.gi, T(Wt * nd.wt1));
     } else {
         T* R = reinterpret_cast<T*>(B.r);
         atomicAdd(R + nd.gi, T(Wt * nd.wt0));
@@ -1139,54 +1147,90 @@ __device__ __forceinline__ R christoffel_lmax(const R* c, R x1, R x2) {
     return R(0.5) * (g00 + g11) + sqrt(hm * hm + g01 * g01);
 }
 
-template <typename T>
-__global__ void k_cfl(BlockDev B, unsigned long long* out_bits) {
-    const long long n = (long long)B.n1 * B.n2;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
-    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
-    double c[10];
-    float cf[10];
-    const T* C = reinterpret_cast<const T*>(B.c);
-    for (int p = 0; p < 10; ++p) {
-        c[p] = (double)C[p * plane + gi];
-        cf[p] = (float)c[p];
-    }
-    const double rhoJ = 1.0 / (double)reinterpret_cast<const T*>(B.w)[gi];
-    constexpr int NS = 720;
-    // FP32 sweep: the three largest local maxima of the cyclic sample sequence
-    float best[3] = {-1.f, -1.f, -1.f};
-    int bk[3] = {0, 0, 0};
+// CFL (Sec. 7, eq. christoffel; reading: the direction maximisation is a sampled sweep refined
+// by Newton steps).  Pass 1 (every node): an FP32 sweep over NS directions gives the node's
+// estimate r_f = min(h1, h2) / v_max; their minimum goes to *minf_bits.  Pass 2: only nodes with
+// r_f within `margin` of that minimum (the FP32 sweep is accurate to ~1e-5, so the minimising
+// node is always among them) refine their three best sampled maxima with FP64 Newton steps and
+// take the exact minimum into *out_bits.
+constexpr int CFL_NS = 720;
+
+struct CflSweep {
+    float best[3];
+    int bk[3];
+};
+
+__device__ __forceinline__ CflSweep cfl_sweep(const float* cf) {
+    CflSweep w{{-1.f, -1.f, -1.f}, {0, 0, 0}};
     float s, co;
-    sincospif(-1.0f / NS, &s, &co);
+    sincospif(-1.0f / CFL_NS, &s, &co);
     float prev = christoffel_lmax<float>(cf, co, s);
     sincospif(0.0f, &s, &co);
     float cur = christoffel_lmax<float>(cf, co, s);
     const float first = cur;
-    for (int k = 0; k < NS; ++k) {
+    for (int k = 0; k < CFL_NS; ++k) {
         float nxt;
-        if (k + 1 < NS) {
-            sincospif((float)(k + 1) / NS, &s, &co);
+        if (k + 1 < CFL_NS) {
+            sincospif((float)(k + 1) / CFL_NS, &s, &co);
             nxt = christoffel_lmax<float>(cf, co, s);
         } else {
             nxt = first;
         }
         if (cur >= prev && cur >= nxt) {
-            if (cur > best[0]) { best[2] = best[1]; bk[2] = bk[1]; best[1] = best[0]; bk[1] = bk[0]; best[0] = cur; bk[0] = k; }
-            else if (cur > best[1]) { best[2] = best[1]; bk[2] = bk[1]; best[1] = cur; bk[1] = k; }
-            else if (cur > best[2]) { best[2] = cur; bk[2] = k; }
+            if (cur > w.best[0]) { w.best[2] = w.best[1]; w.bk[2] = w.bk[1]; w.best[1] = w.best[0]; w.bk[1] = w.bk[0]; w.best[0] = cur; w.bk[0] = k; }
+            else if (cur > w.best[1]) { w.best[2] = w.best[1]; w.bk[2] = w.bk[1]; w.best[1] = cur; w.bk[1] = k; }
+            else if (cur > w.best[2]) { w.best[2] = cur; w.bk[2] = k; }
         }
         prev = cur;
         cur = nxt;
     }
-    // FP64 refinement of each candidate
+    return w;
+}
+
+template <typename T>
+__device__ __forceinline__ void cfl_node(const BlockDev& B, long long t, double c[10], float cf[10], double& rhoJ) {
+    const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
+    const T* C = reinterpret_cast<const T*>(B.c);
+    for (int p = 0; p < 10; ++p) {
+        c[p] = (double)C[p * plane + gi];
+        cf[p] = (float)c[p];
+    }
+    rhoJ = 1.0 / (double)reinterpret_cast<const T*>(B.w)[gi];
+}
+
+template <typename T>
+__global__ void k_cfl_sweep(BlockDev B, float* __restrict__ rf, unsigned* minf_bits) {
+    const long long n = (long long)B.n1 * B.n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double c[10], rhoJ;
+    float cf[10];
+    cfl_node<T>(B, t, c, cf, rhoJ);
+    const CflSweep w = cfl_sweep(cf);
+    const float v = sqrtf(fmaxf(w.best[0], 0.f) / (float)rhoJ);
+    const float r = (float)fmin(B.h1, B.h2) / v;
+    rf[t] = r;
+    atomicMin(minf_bits, __float_as_uint(r));    // positive floats order as their bit patterns
+}
+
+template <typename T>
+__global__ void k_cfl_refine(BlockDev B, const float* __restrict__ rf, const unsigned* minf_bits, float margin,
+                             unsigned long long* out_bits) {
+    const long long n = (long long)B.n1 * B.n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    if (!(rf[t] <= __uint_as_float(*minf_bits) * (1.f + margin))) return;
+    double c[10], rhoJ;
+    float cf[10];
+    cfl_node<T>(B, t, c, cf, rhoJ);
+    const CflSweep w = cfl_sweep(cf);
     const double PI = 3.14159265358979323846, dl = 1e-4;
     auto lam = [&](double th) { double sd, cd; sincos(th, &sd, &cd); return christoffel_lmax<double>(c, cd, sd); };
     double lmax = 0.0;
     for (int q = 0; q < 3; ++q) {
-        if (best[q] < 0.f) continue;
-        double th = bk[q] * PI / NS;
+        if (w.best[q] < 0.f) continue;
+        double th = w.bk[q] * PI / CFL_NS;
         double f0 = lam(th);
         lmax = fmax(lmax, f0);
         for (int it = 0; it < 3; ++it) {
@@ -1195,15 +1239,14 @@ __global__ void k_cfl(BlockDev B, unsigned long long* out_bits) {
             lmax = fmax(lmax, fmax(fp, fm));
             if (!(d2 < 0.0)) break;
             double step = -d1 / d2;
-            step = fmax(-2 * PI / NS, fmin(2 * PI / NS, step));
+            step = fmax(-2 * PI / CFL_NS, fmin(2 * PI / CFL_NS, step));
             th += step;
             f0 = lam(th);
             lmax = fmax(lmax, f0);
         }
     }
     const double v = sqrt(lmax / rhoJ);
-    const double hmin = fmin(B.h1, B.h2);
-    const double r = hmin / v;
+    const double r = fmin(B.h1, B.h2) / v;
     atomicMin(out_bits, (unsigned long long)__double_as_longlong(r));
 }
 

@@ -1,15 +1,20 @@
 """Continuous batching of independent forward solves ("shots") on one GPU.
 
-Requests arrive over time (each with its own grid, material, sources and step count).  The
+Requests arrive over time (each with its own grid, material, sources and step count).  An
 engine admits a waiting request as soon as a slot is free and its device footprint
 (``sbp_grid_footprint``) fits under the HBM cap, keeps every admitted shot's wavefield resident,
-and advances all active shots in ticks of ``tick_steps`` leapfrog steps.  Each shot runs on its
-own CUDA stream and its ticks are replayed from a CUDA graph (``sbp_step_graph``), so the
-kernels of different shots overlap on the device; when a shot finishes, its result is read
-back, its memory is released and the next request is admitted -- while the others keep running.
+and advances the active shots in ticks of ``tick_steps`` leapfrog steps; when a shot finishes,
+its result is read back, its memory is released and the next request is admitted -- while the
+others keep running.  Two engines:
+
+* ``BatchServingEngine`` (the serving path): every active shot lives in one ``sbp_batch``; a
+  tick is one CUDA-graph replay of ``tick_steps`` launches of the persistent tile-queue kernel,
+  whose CTAs pull interior and boundary tiles of all resident shots from one device queue.
+* ``ServingEngine``: each shot on its own CUDA stream, ticks replayed from a per-shot CUDA graph
+  (``sbp_step_graph``); the kernels of different shots overlap through the streams.
 
 All arithmetic is in libsbp; this module only schedules.  The scheduling logic is written
-against a small backend interface so that it can be exercised without a GPU.
+against small backend interfaces so that it can be exercised without a GPU.
 """
 from __future__ import annotations
 
@@ -23,7 +28,7 @@ from typing import Any, Callable, List, Optional
 class Request:
     rid: int
     arrival: float                 # seconds after the engine starts
-    problem: Any                   # workloads.Problem
+    problem: Any                   # workloads.Problem, or a callable returning it (made on admission)
     nsteps: int
     dt: Optional[float] = None     # None: dt = suggest_dt(cfl) of the shot
 
@@ -138,13 +143,14 @@ class ServingEngine:
             # admission: first come, first served, by device footprint
             while waiting and len(active) < self.max_active:
                 req = waiting[0]
-                fp = self.backend.footprint(req.problem)
+                prob = _problem_of(req)
+                fp = self.backend.footprint(prob)
                 if fp > self.cap:
                     raise ValueError(f"request {req.rid} needs {fp} bytes, more than the cap {self.cap}")
                 if used + fp > self.cap:
                     break
                 waiting.popleft()
-                shot = self.backend.create(req.problem, self.cfl, req.dt)
+                shot = self.backend.create(prob, self.cfl, req.dt)
                 used += fp
                 self.peak_bytes = max(self.peak_bytes, used)
                 active.append(dict(req=req, shot=shot, fp=fp, done=0, admitted=self.clock() - t0))
@@ -181,6 +187,133 @@ class ServingEngine:
                         self.sleep(min(wait, 0.05))
                 else:
                     self.sleep(self.idle_sleep)
+        return sorted(results, key=lambda r: r.rid)
+
+
+def _problem_of(req):
+    return req.problem() if callable(req.problem) else req.problem
+
+
+class GpuBatchBackend:
+    """Shots in one libsbp batch (persistent tile-queue kernel), stepped on one CUDA stream."""
+
+    def __init__(self, order=6, max_shots=256, rows=0, precision="fp32"):
+        import torch
+        from .binding import Batch, Solver, footprint_bytes
+        if precision != "fp32":
+            raise ValueError("the batch kernel steps FP32 shots")
+        self.torch = torch
+        self.Solver = Solver
+        self.footprint_bytes = footprint_bytes
+        self.batch = Batch(order, max_shots)
+        if rows:
+            self.batch.sbp_batch_set_rows(rows)
+        self.stream = torch.cuda.Stream()
+        self.max_shots = max_shots
+        self.shots = {}
+
+    def footprint(self, problem) -> int:
+        return self.footprint_bytes(problem, "fp32")
+
+    def admit(self, problem, nsteps, cfl, dt=None):
+        import numpy as np
+        S = self.Solver(problem, "fp32")
+        if dt is None:
+            dt = S.suggest_dt(cfl)
+        z = [np.zeros((2, b.N2, b.N1)) for b in problem.blocks]
+        S.set_state(z, z, 0.0)
+        slot = self.batch.sbp_batch_add(S, nsteps, dt)
+        self.shots[slot] = S
+        return slot, dt
+
+    def step(self, k):
+        self.batch.sbp_batch_step(k, self.stream.cuda_stream)
+
+    def poll(self):
+        return self.batch.sbp_batch_poll(self.stream.cuda_stream)
+
+    def retire(self, slot):
+        self.batch.sbp_batch_remove(slot, self.stream.cuda_stream)
+        S = self.shots.pop(slot)
+        _, u = S.state()
+        S.close()
+        return u
+
+    def close(self):
+        for S in self.shots.values():
+            S.close()
+        self.shots = {}
+        self.batch.close()
+
+
+class BatchServingEngine:
+    """Continuous batching on the persistent tile-queue kernel (see the module docstring).
+
+    Between ticks the engine retires finished shots (reading their results), admits waiting
+    requests first come first served while slots and the HBM cap allow, and launches the next
+    tick for every resident shot; each shot advances by its own step count."""
+
+    def __init__(self, hbm_cap_bytes: int, backend=None, tick_steps: int = 32, max_active: int = 256,
+                 cfl: float = 0.3, clock: Callable[[], float] = time.perf_counter,
+                 sleep: Callable[[float], None] = time.sleep):
+        if tick_steps < 1:
+            raise ValueError("tick_steps must be >= 1")
+        self.cap = int(hbm_cap_bytes)
+        self.backend = backend if backend is not None else GpuBatchBackend(max_shots=max_active)
+        self.tick = tick_steps
+        self.max_active = max_active
+        self.cfl = cfl
+        self.clock = clock
+        self.sleep = sleep
+        self.peak_bytes = 0
+        self.peak_active = 0
+        self.ticks = 0
+        self.trace: List[tuple] = []
+
+    def run(self, requests: List[Request]) -> List[Result]:
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        waiting: collections.deque = collections.deque()
+        active = {}                       # slot -> dict(req, fp, admitted, dt)
+        used = 0
+        results = []
+        t0 = self.clock()
+        while pending or waiting or active:
+            now = self.clock() - t0
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            while waiting and len(active) < self.max_active:
+                req = waiting[0]
+                prob = _problem_of(req)
+                fp = self.backend.footprint(prob)
+                if fp > self.cap:
+                    raise ValueError(f"request {req.rid} needs {fp} bytes, more than the cap {self.cap}")
+                if used + fp > self.cap:
+                    break
+                waiting.popleft()
+                slot, dt = self.backend.admit(prob, req.nsteps, self.cfl, req.dt)
+                used += fp
+                self.peak_bytes = max(self.peak_bytes, used)
+                active[slot] = dict(req=req, fp=fp, admitted=self.clock() - t0, dt=dt)
+                self.peak_active = max(self.peak_active, len(active))
+                self.trace.append((self.clock() - t0, "admit", req.rid))
+            if not active:
+                if pending:
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(min(wait, 0.05))
+                continue
+            self.backend.step(self.tick)
+            self.ticks += 1
+            rem = self.backend.poll()
+            for slot in sorted(active):
+                if rem[slot] == 0:
+                    info = active.pop(slot)
+                    fields = self.backend.retire(slot)
+                    used -= info["fp"]
+                    t = self.clock() - t0
+                    req = info["req"]
+                    results.append(Result(req.rid, req.arrival, info["admitted"], t, req.nsteps, info["dt"], fields))
+                    self.trace.append((t, "finish", req.rid))
         return sorted(results, key=lambda r: r.rid)
 
 

@@ -103,3 +103,81 @@ def test_odd_remainders_and_ticks():
 def test_percentile():
     assert percentile([1, 2, 3, 4], 50) == 2.5
     assert percentile([5], 99) == 5
+
+
+# ------------------------------------------------------------------ the batch engine (persistent kernel)
+class FakeBatchBackend:
+    """A batch of slots on a virtual clock: a tick of k steps costs `cost` per step of the resident
+    shots together (one launch serves all of them); each slot advances by its own remaining count."""
+
+    def __init__(self, clock, sizes, max_shots=4, cost=1e-3):
+        self.clock, self.sizes, self.cost = clock, sizes, cost
+        self.rem = [-1] * max_shots
+        self.steps = [0] * max_shots
+        self.rid = [None] * max_shots
+        self.log = []
+
+    def footprint(self, problem):
+        return self.sizes[problem]
+
+    def admit(self, problem, nsteps, cfl, dt=None):
+        slot = self.rem.index(-1)
+        self.rem[slot], self.steps[slot], self.rid[slot] = nsteps, 0, problem
+        self.log.append(("admit", problem, slot))
+        return slot, 0.01
+
+    def step(self, k):
+        self.clock.t += k * self.cost
+        for s in range(len(self.rem)):
+            if self.rem[s] > 0:
+                n = min(k, self.rem[s])
+                self.rem[s] -= n
+                self.steps[s] += n
+        self.log.append(("step", k, tuple(r for r in self.rem)))
+
+    def poll(self):
+        return list(self.rem)
+
+    def retire(self, slot):
+        self.log.append(("retire", self.rid[slot], slot))
+        out = self.steps[slot]
+        self.rem[slot] = -1
+        return out
+
+
+def _run_batch(sizes, arrivals, nsteps, cap, max_active=4, tick=4):
+    from paper_2003_12811_gb300.serve import BatchServingEngine
+    clk = VClock()
+    be = FakeBatchBackend(clk, sizes, max_shots=max_active)
+    eng = BatchServingEngine(cap, backend=be, tick_steps=tick, max_active=max_active, clock=clk, sleep=clk.sleep)
+    reqs = [Request(rid=i, arrival=a, problem=i, nsteps=n) for i, (a, n) in enumerate(zip(arrivals, nsteps))]
+    return eng, be, eng.run(reqs)
+
+
+def test_batch_engine_completes_every_request_with_its_steps():
+    eng, be, res = _run_batch({i: 10 for i in range(7)}, [0.0, 0.0, 0.001, 0.002, 0.01, 0.05, 0.5],
+                              [8, 13, 6, 4, 10, 2, 5], cap=100)
+    assert [r.rid for r in res] == list(range(7))
+    assert [r.fields for r in res] == [8, 13, 6, 4, 10, 2, 5]
+    assert all(r.finished >= r.admitted >= r.arrival for r in res)
+
+
+def test_batch_engine_shares_ticks_and_respects_slots_and_cap():
+    sizes = {0: 40, 1: 40, 2: 40, 3: 10, 4: 10}
+    eng, be, res = _run_batch(sizes, [0.0] * 5, [40, 40, 8, 8, 8], cap=90, max_active=4)
+    assert eng.peak_bytes <= 90 and eng.peak_active <= 4
+    # 0 and 1 are resident together (one tick advances both); 2 waits for memory (FIFO: 3 and 4
+    # are not admitted ahead of it)
+    admits = [e[1] for e in be.log if e[0] == "admit"]
+    assert admits == [0, 1, 2, 3, 4]
+    r = {x.rid: x for x in res}
+    assert r[2].admitted >= r[0].finished - 1e-12
+    first_step = next(e for e in be.log if e[0] == "step")
+    assert sum(1 for x in first_step[2] if x >= 0) == 2
+
+
+def test_batch_engine_admits_between_ticks_while_others_run():
+    eng, be, res = _run_batch({0: 10, 1: 10}, [0.0, 0.0105], [40, 4], cap=100, tick=4)
+    r = {x.rid: x for x in res}
+    # request 1 joins while request 0 is still running and finishes first
+    assert r[1].admitted < r[0].finished and r[1].finished < r[0].finished

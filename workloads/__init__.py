@@ -591,21 +591,46 @@ def _smooth_field(X1, X2, rng, nmodes=3, kmax=3.0):
     return 0.5 + 0.5 * f / nmodes
 
 
+def _smooth_field_sep(g1, g2, rng, nmodes=3, kmax=3.0, out=None):
+    """Seeded smooth field in [0, 1] on the tensor grid g1 (x1, along the row) x g2 (x2): the
+    normalised sum 1/2 + 1/(2 nmodes) sum_j sin(k1_j x1 + k2_j x2 + phi_j) of low Fourier modes,
+    each split as sin(k1 x1 + phi) cos(k2 x2) + cos(k1 x1 + phi) sin(k2 x2), so the field is one
+    rank-(2 nmodes + 1) product of O(n) factors."""
+    A = np.empty((g2.size, 2 * nmodes + 1))
+    Bm = np.empty((2 * nmodes + 1, g1.size))
+    for j in range(nmodes):
+        k1, k2 = rng.uniform(-kmax, kmax, 2) * np.pi
+        ph = rng.uniform(0, 2 * np.pi)
+        A[:, 2 * j] = np.cos(k2 * g2) * (0.5 / nmodes)
+        A[:, 2 * j + 1] = np.sin(k2 * g2) * (0.5 / nmodes)
+        Bm[2 * j] = np.sin(k1 * g1 + ph)
+        Bm[2 * j + 1] = np.cos(k1 * g1 + ph)
+    A[:, -1] = 0.5
+    Bm[-1] = 1.0
+    if out is None:
+        return A @ Bm
+    np.matmul(A, Bm, out=out)
+    return out
+
+
 def shot_problem(side: int, seed: int, order: int = 6, f_peak: float = 4.0) -> Problem:
     """One served shot: a single curvilinear block side x side on a unit square perturbed by a
     seeded smooth mapping; smooth random material after the Sec. 7.2 recipe (rho = 1 + r,
-    the 10 independent pair entries of C~ smooth in [0,1], +4 on I=K, J=L); traction-free top,
-    displacement elsewhere; a vertical Ricker point force at a seeded interior point."""
+    the 10 independent pair entries of C~ smooth in [0,1], +4 on I=K, J=L; the smooth fields are
+    sums of low Fourier modes of the reference coordinates); traction-free top, displacement
+    elsewhere; a vertical Ricker point force at a seeded interior point."""
     rng = np.random.default_rng(seed)
-    x1, x2 = ref_grid(side, side)
+    g = np.linspace(0.0, 1.0, side)
     a1, a2 = rng.uniform(0.02, 0.05, 2)
-    X1 = x1 + a1 * np.sin(np.pi * x1) * np.sin(2 * np.pi * x2)
-    X2 = x2 + a2 * np.sin(2 * np.pi * x1) * np.sin(np.pi * x2)
-    rho = 1 + _smooth_field(X1, X2, rng)
-    m = np.zeros((4, 4) + X1.shape)
+    X1 = g[None, :] + a1 * np.multiply.outer(np.sin(2 * np.pi * g), np.sin(np.pi * g))
+    X2 = g[:, None] + a2 * np.multiply.outer(np.sin(np.pi * g), np.sin(2 * np.pi * g))
+    rho = 1 + _smooth_field_sep(g, g, rng)
+    m = np.zeros((4, 4, side, side))
     for a in range(4):
         for b in range(a, 4):
-            m[a, b] = m[b, a] = _smooth_field(X1, X2, rng)
+            _smooth_field_sep(g, g, rng, out=m[a, b])
+            if b != a:
+                m[b, a] = m[a, b]
     for a in range(4):
         m[a, a] += 4
     C = pair10_to_tensor(m)
