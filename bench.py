@@ -37,7 +37,7 @@ BYTES_PER_NODE = {"fp32": 68, "fp64": 136}     # 17 words: u^n 2, u^{n-1} 2, u^{
 # DRAM bytes per node of one FP32 interior launch (dram__bytes_read.sum + dram__bytes_write.sum of
 # k_interior_march<6,0> captured at 2 x 1601x801, scaled by nodes).  Set to None whenever that
 # kernel changes until it is measured again.
-TRAFFIC_BYTES_PER_NODE = {"fp32": 79155456 / 1239489, "fp64": None}
+TRAFFIC_BYTES_PER_NODE = {"fp32": None, "fp64": None}
 FALLBACK_HBM_GBS = 6800.0
 N1, N2 = 4001, 2001
 # crop of the workload the oracle is timed on: a 401-column window around the source spanning
@@ -333,6 +333,129 @@ def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
                          "frac": achieved / peak, "peak_source": src, "traffic": None}}
 
 
+# algorithmic bytes per node: an RK4 stage reads U_s (2), c (10), 1/(rho J) (1), u, v, V, S_u, S_v
+# (10) and writes U_{s+1}, V, S_u, S_v (8): 31 words; four stages per step
+RK4_WORDS_PER_STAGE = 31
+# the wide operator's two passes move: fluxes u (2) + c (10) -> G (4); divergence G (4), 1/(rho J) (1),
+# u^n (2), u^{n-1} (2) -> u^{n+1} (2): 27 words, against the 17 of a fused step
+WIDE_WORDS_IMPLEMENTED = 27
+
+
+def variant_bench(P, prec, nsteps=100):
+    """The time integrator and operator variants on the bench workload: RK4 steps (the paper's
+    integrator; four fused stage passes per step) and leapfrog steps of the wide-stencil operator,
+    node-updates/s with the bandwidth their traffic implies (CUDA events on the launch stream)."""
+    import dataclasses
+    import torch
+    from paper_2003_12811_gb300 import Solver
+    es = 4 if prec == "fp32" else 8
+    nodes = P.n_nodes
+    peak, src = peaks()
+    out = {}
+    zero = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    # RK4
+    S = Solver(P, prec)
+    dt = S.suggest_dt(0.5)
+    S.sbp_set_state_rk4(zero, zero, 0.0)
+    S.sbp_step_rk4(3, dt, sh)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.sbp_step_rk4(nsteps, dt, sh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    S.close()
+    gbs = 4 * RK4_WORDS_PER_STAGE * es * nodes / (ms / 1e3) / 1e9
+    out["rk4"] = {"node_updates_per_s": nodes / (ms / 1e3), "ms_per_step": ms, "cfl": 0.5,
+                  "bytes_per_node_per_step": 4 * RK4_WORDS_PER_STAGE * es, "achieved_GBs": gbs,
+                  "frac_of_peak": gbs / peak, "peak_source": src, "steps": nsteps}
+    # wide stencil, leapfrog
+    S = Solver(dataclasses.replace(P, stencil="wide"), prec)
+    dtw = S.suggest_dt(0.3)
+    S.set_state(zero, zero, 0.0)
+    S.sbp_step(3, dtw, sh)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    S.sbp_step(nsteps, dtw, sh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    S.close()
+    bpn = BYTES_PER_NODE[prec]
+    out["wide"] = {"node_updates_per_s": nodes / (ms / 1e3), "ms_per_step": ms,
+                   "algorithmic_GBs": bpn * nodes / (ms / 1e3) / 1e9,
+                   "frac_of_peak_algorithmic": bpn * nodes / (ms / 1e3) / 1e9 / peak,
+                   "implemented_words_per_node": WIDE_WORDS_IMPLEMENTED,
+                   "implemented_GBs": WIDE_WORDS_IMPLEMENTED * es * nodes / (ms / 1e3) / 1e9,
+                   "peak_source": src, "steps": nsteps}
+    return out
+
+
+def accuracy_table():
+    """FP32 against FP64 after each configuration's own step count (configs 1-3 at their stated
+    sizes; the FP64 GPU path is the reference: the parity tests hold it to the oracle at 1e-12,
+    at full size included), and the l2 error against the manufactured solution where one exists
+    (configs 1 and 2).  Norms: the scheme's J H-weighted l2 (sbp_l2_diff, FP64 on the device)."""
+    import torch
+    from paper_2003_12811_gb300 import Solver
+    from paper_2003_12811_gb300.binding import FIELD_CUR
+
+    def run(P, prec, nsteps, dt, up, uc):
+        S = Solver(P, prec)
+        S.set_state(up, uc, 0.0)
+        out = {}
+        done = 0
+        for mark in sorted(nsteps):
+            S.sbp_step(mark - done, dt)
+            done = mark
+            _, u = S.state()
+            t = S.sbp_get_time()
+            err_exact = None
+            if P.exact is not None:
+                e2, _ = S.sbp_l2_diff(FIELD_CUR, [P.exact(b, t) for b in P.blocks])
+                err_exact = math.sqrt(e2)
+            out[mark] = (u, err_exact)
+        return S, out
+
+    table = {}
+    cases = [("config 1: 101^2 Cartesian, order 4, manufactured solution", lambda: W.config1(), [200], 0.25, True),
+             ("config 2: 4 x 801^2 curvilinear, order 6, manufactured solution", lambda: W.config2(n=801), [1000], 0.25, True),
+             ("config 3: 2 x 4001x2001 topography, order 6, Ricker source", lambda: W.config3(), [1000, 5000], 0.3, False)]
+    for name, make, marks, cfl, mms in cases:
+        P = make()
+        S64 = Solver(P, "fp64")
+        dt = S64.suggest_dt(cfl)
+        S64.close()
+        if mms:
+            up = [P.exact(b, -dt) for b in P.blocks]
+            uc = [P.exact(b, 0.0) for b in P.blocks]
+        else:
+            up = uc = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+        t0 = time.perf_counter()
+        S64, r64 = run(P, "fp64", marks, dt, up, uc)
+        S32, r32 = run(P, "fp32", marks, dt, up, uc)
+        rows = {}
+        for m in marks:
+            u64, e64 = r64[m]
+            u32, e32 = r32[m]
+            # relative l2 in the scheme's norm: the FP32 field against the FP64 field
+            Sref = Solver(P, "fp32")
+            Sref.set_state(u32, u32, 0.0)
+            e2, r2 = Sref.sbp_l2_diff(FIELD_CUR, u64)
+            Sref.close()
+            relmax = max(np.abs(a - b).max() for a, b in zip(u32, u64)) / max(np.abs(b).max() for b in u64)
+            rows[str(m)] = {"fp32_rel_l2_vs_fp64": math.sqrt(e2 / r2), "fp32_rel_max_vs_fp64": relmax,
+                            "l2_error_exact_fp64": e64, "l2_error_exact_fp32": e32}
+        S64.close()
+        S32.close()
+        table[name] = {"dt": dt, "steps": rows, "seconds": time.perf_counter() - t0}
+        torch.cuda.synchronize()
+    return table
+
+
 def replica_times(times, world):
     """Job times of `world` independent replicas (one process per GPU, no data exchange): each
     entry is the slowest rank's (MAX over ranks).  torch.distributed must be initialised when
@@ -386,6 +509,9 @@ def main():
     ap.add_argument("--n2", type=int, default=N2)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the RK4 and wide-stencil measurements")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="print the FP32-against-FP64 accuracy table of configs 1-3 and exit")
     ap.add_argument("--adjoint-only", action="store_true", help="print the misfit-gradient measurement alone")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="leapfrog steps of the misfit-gradient workload")
     args = ap.parse_args()
@@ -410,6 +536,9 @@ def main():
     from paper_2003_12811_gb300 import Solver
 
     prec = args.precision
+    if args.accuracy:
+        print(json.dumps({"accuracy": accuracy_table()}), flush=True)
+        return 0
     if args.adjoint_only:
         print(json.dumps(adjoint_bench(nsteps=args.adjoint_steps, prec=prec)), flush=True)
         return 0
@@ -456,7 +585,9 @@ def main():
     torch.cuda.synchronize()
     fam_ms, _ = S.sbp_profile_read()
     S.sbp_profile(False)
-    interior_ms = fam_ms[0] / args.steps         # both blocks' interior launches per step
+    interior_ms = fam_ms[0] / args.steps         # the interior launches of a step (both blocks)
+    # FP32: one launch covers the interior of both blocks; FP64: one launch per block
+    units_per_launch = interior_nodes if prec == "fp32" else interior_nodes // len(P.blocks)
     bpn = BYTES_PER_NODE[prec]
     achieved = bpn * interior_nodes / (interior_ms / 1e3) / 1e9
     peak, peak_src = peaks()
@@ -486,10 +617,11 @@ def main():
                        "l2": f"inputs larger than L2 ({bpn * nodes / 1e9:.2f} GB moved per step vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (TRAFFIC_BYTES_PER_NODE[prec] * (interior_nodes // len(P.blocks))
+                         "traffic": (TRAFFIC_BYTES_PER_NODE[prec] * units_per_launch
                                      if TRAFFIC_BYTES_PER_NODE[prec] else None),
-                         "kernel": "k_interior", "peak_source": peak_src,
-                         "bytes_per_node": bpn, "units_per_launch": interior_nodes // len(P.blocks),
+                         "kernel": "k_interior_march_multi" if prec == "fp32" else "k_interior",
+                         "peak_source": peak_src,
+                         "bytes_per_node": bpn, "units_per_launch": units_per_launch,
                          "kernel_ms_per_step": interior_ms,
                          "family_ms_per_step": {"interior": fam_ms[0] / args.steps, "boundary": fam_ms[1] / args.steps,
                                                 "faces": fam_ms[2] / args.steps, "sources": fam_ms[3] / args.steps}},
@@ -497,6 +629,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e}
     S.close()
+    if rank == 0 and world == 1 and not args.no_variants:
+        line["variants"] = variant_bench(P, prec)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_bench(value)
     if rank == 0 and world == 1 and not args.no_adjoint:

@@ -48,6 +48,11 @@ extern "C" {
 #define SBP_FP64 0
 #define SBP_FP32 1
 
+/* spatial operator (sbp_grid_desc.stencil) */
+#define SBP_STENCIL_NARROW 0     /* fully compatible narrow second derivatives D_xx^FC(c) (Sec. 4.4-4.6) */
+#define SBP_STENCIL_WIDE 1       /* every term D_i c D_k (first derivatives applied twice), same SATs
+                                    (the narrow/wide comparison of Sec. 7.1) */
+
 /* face kinds */
 #define SBP_BC_DISPLACEMENT 0    /* u = g, SAT of eq. dirichlet_ansatz with Z of Theorem 3 */
 #define SBP_BC_ROBIN 1           /* T u + U u = g, SAT of eq. sat_traction (traction when U = 0) */
@@ -86,6 +91,9 @@ typedef struct {
     int nblocks;
     const sbp_block_desc* blocks;
     double beta;                 /* SAT penalty factor beta >= 1 (Sec. 5.2, 6); 0 selects 1 */
+    int stencil;                 /* SBP_STENCIL_NARROW (0, the paper's scheme) or SBP_STENCIL_WIDE; the wide
+                                    operator is applied in two passes (fluxes, divergence) by generic kernels;
+                                    the misfit gradient, the batch and sbp_apply_noalloc take narrow handles */
 } sbp_grid_desc;
 
 /* Create a solver for a multiblock curvilinear grid.  Computes the numerical metric on the
@@ -115,6 +123,27 @@ int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* 
 
 /* Robin matrix U (Sec. 5.1) of a ROBIN face: 3 planes of nf values (U11, U12, U22), physical. */
 int sbp_set_robin(sbp_handle* h, int block, int face, const double* U);
+
+/* Dissipative Robin condition (the remark of Sec. 5.1): T u + U u + V du/dt = g on a ROBIN face, V
+ * symmetric positive semidefinite: 3 planes of nf values (V11, V12, V22), physical.  The SAT of
+ * eq. sat_traction gains -(JH)^-1 e_f J^ H_f V e_f^T du/dt.  Leapfrog takes the centred velocity
+ * (u^{n+1} - u^{n-1}) / (2 dt), a 2 x 2 solve per face node, so the leapfrog energy decreases by
+ * exactly |u^{n+1} - u^{n-1}|^2 / (4 dt) in the damping's norm each step; RK4 takes the stage
+ * velocity.  sbp_apply and sbp_energy leave the term out (it needs a velocity).
+ * Errors: SBP_E_INVALID_ARG (not a Robin face, V not PSD or not finite). */
+int sbp_set_robin_damping(sbp_handle* h, int block, int face, const double* V);
+
+/* Super-grid layer dissipation (Sec. 7.3: a term E du/dt that is zero outside the absorbing layers
+ * and makes H E symmetric negative semidefinite inside; the stretched layer grid itself is part of
+ * the block's mapping).  Reading: J E = -H^-1 sum_i Dt_i^T diag(s) Dt_i for each component, Dt_i
+ * the undivided second difference along x_i at the nodes 1 .. N-2 of every grid line, s >= 0 the
+ * coefficient of the node at the difference's centre (n1*n2 values, host; zero outside the
+ * layers; s = eta rho J c h1 h2 / (32 h) damps the grid-scale checkerboard at the rate eta c / h).
+ * Leapfrog takes the backward velocity (u^n - u^{n-1}) / dt (explicit; stable while the layer
+ * damping rate times dt stays well below one), RK4 the stage velocity; only the nodes the layer
+ * reaches are visited (two small kernels around each leapfrog step, one before each RK4 stage).
+ * Errors: SBP_E_INVALID_ARG (negative or non-finite s). */
+int sbp_set_layer_dissipation(sbp_handle* h, int block, const double* s);
 
 /* Time basis of separable data: T_k(t) = sin(omega_k t) (kind 0) or cos(omega_k t) (kind 1);
  * nbasis <= 8. */
@@ -209,6 +238,13 @@ int sbp_get_field(sbp_handle* h, int block, int which, double* dst);
  * with u^n = PREV, u^{n+1} = CUR and A the homogeneous operator (Sec. 5-6 energies); FP64
  * reductions.  Returns SBP_E_UNSTABLE if the result is not finite. */
 int sbp_energy(sbp_handle* h, double dt, double* E_out);
+
+/* Discrete l2 distance of a field (SBP_FIELD_*) from reference arrays, with the norm of the
+ * scheme: err2 = sum_blocks sum_J (u_J - ref_J)^T (J H) (u_J - ref_J) and ref2 = sum ref_J^T (J H)
+ * ref_J, FP64 reductions on the device (the l2 error of Table 1 is sqrt(err2) with the exact
+ * solution as reference; sqrt(err2 / ref2) is the relative l2 distance).  ref[b]: 2 planes of
+ * n1*n2 doubles per block (host, x1 fastest).  Synchronous.  Either output may be NULL. */
+int sbp_l2_diff(sbp_handle* h, int which, const double* const* ref, double* err2_out, double* ref2_out);
 
 /* dt = cfl * min over nodes of min(h1,h2) / v_max, v_max the largest quasi-P speed from the
  * Christoffel equation in the reference domain (Sec. 7, eq. christoffel), maximised over

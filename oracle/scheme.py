@@ -18,6 +18,7 @@ from typing import List
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import workloads as W
 from .sbp1d import SBP1D
@@ -32,8 +33,9 @@ def _diag(v):
 class BlockOps:
     """Operators, metric and transformed material of one block."""
 
-    def __init__(self, blk: W.Block, order: int):
+    def __init__(self, blk: W.Block, order: int, stencil: str = "narrow"):
         self.blk = blk
+        self.stencil = stencil
         self.N1, self.N2 = blk.N1, blk.N2
         self.N = self.N1 * self.N2
         h1, h2 = blk.spacing
@@ -107,8 +109,9 @@ class BlockOps:
         return Hinv @ (-Dk.T @ Hk @ Bm @ Dk - R + Bd @ Bm @ Dk)
 
     def DD(self, i, k, b):
-        """DD_ik(b) of eq. def_cd: narrow when i == k, D_i b D_k otherwise."""
-        if i == k:
+        """DD_ik(b) of eq. def_cd: narrow when i == k, D_i b D_k otherwise.  The wide-stencil variant
+        (the comparison of Sec. 7.1) uses D_i b D_k for i == k as well."""
+        if i == k and self.stencil == "narrow":
             return self.narrow(i, b)
         return self.Dr[i] @ _diag(b) @ self.Dr[k]
 
@@ -185,7 +188,7 @@ class Oracle:
         self.problem = problem
         self.order = problem.order
         self.beta = problem.beta
-        self.bops: List[BlockOps] = [BlockOps(b, problem.order) for b in problem.blocks]
+        self.bops: List[BlockOps] = [BlockOps(b, problem.order, getattr(problem, "stencil", "narrow")) for b in problem.blocks]
         self.offsets = []
         off = 0
         for bo in self.bops:
@@ -301,6 +304,7 @@ class Oracle:
                 if M[r][c] is None:
                     M[r][c] = sp.csr_matrix((self.bops[r // 2].N, self.bops[c // 2].N))
         self.A = sp.bmat(M, format="csr")
+        self._assemble_damping()
         self.wvec = np.concatenate([np.concatenate([bo.w, bo.w]) for bo in self.bops])
         self.hvec = np.concatenate([np.concatenate([bo.Hvec, bo.Hvec]) for bo in self.bops])
         self.mass = np.concatenate([np.concatenate([bo.rho * bo.J * bo.Hvec] * 2) for bo in self.bops])
@@ -321,6 +325,57 @@ class Oracle:
             full[self.offsets[s.block]:self.offsets[s.block] + 2 * bo.N] = vec.ravel()
             self.src.append((full, s))
 
+    def _assemble_damping(self):
+        """Velocity-dependent terms, J-scaled as rho J u'' = A u - (Bv + Bs) u' + data:
+        * Bv, the dissipative Robin term (remark of Sec. 5.1: T u + U u + V u' = g on a Robin face),
+          from the SAT of eq. sat_traction with U replaced by V u': H^-1 P_f J^ V;
+        * Bs, the super-grid layer dissipation (Sec. 7.3: E zero outside the layers, H E symmetric
+          negative semidefinite inside; reading: fourth-order undivided-difference dissipation
+          J E = -H^-1 sum_i Dt_i^T diag(s) Dt_i per component, Dt_i the undivided second difference
+          along direction i at the nodes 1 .. N-2 of every grid line, s >= 0 the layer profile)."""
+        nb = len(self.bops)
+        Mv = [[None] * (2 * nb) for _ in range(2 * nb)]
+        Ms = [[None] * (2 * nb) for _ in range(2 * nb)]
+        for b, bo in enumerate(self.bops):
+            blk = bo.blk
+            for f, face in enumerate(blk.faces):
+                if face.kind != "robin" or face.V is None:
+                    continue
+                fc = bo.faces[f]
+                idx, P = fc["idx"], fc["P"]
+                for J in range(2):
+                    for L in range(2):
+                        Vc = face.V[[0, 1, 2][J + L]] if (J, L) != (1, 0) else face.V[1]
+                        Vfull = np.zeros(bo.N)
+                        Vfull[idx] = fc["Jhat"] * Vc
+                        A = bo.Hinv @ P @ _diag(Vfull)
+                        r, c = 2 * b + J, 2 * b + L
+                        Mv[r][c] = A if Mv[r][c] is None else Mv[r][c] + A
+            if blk.sponge is not None:
+                sfield = blk.sponge.ravel()
+                K = sp.csr_matrix((bo.N, bo.N))
+                for i in range(2):
+                    N = bo.N1 if i == 0 else bo.N2
+                    Dt = sp.diags([np.ones(N - 2), -2 * np.ones(N - 2), np.ones(N - 2)], [0, 1, 2], shape=(N - 2, N))
+                    if i == 0:
+                        Dl = sp.kron(bo.I2, Dt, format="csr")
+                        cen = np.kron(np.arange(bo.N2) * bo.N1, np.ones(N - 2, dtype=int)) + np.tile(np.arange(1, N - 1), bo.N2)
+                    else:
+                        Dl = sp.kron(Dt, bo.I1, format="csr")
+                        cen = np.kron(np.arange(1, N - 1) * bo.N1, np.ones(bo.N1, dtype=int)) + np.tile(np.arange(bo.N1), N - 2)
+                    K = K + Dl.T @ _diag(sfield[cen]) @ Dl
+                Bs = (bo.Hinv @ K).tocsr()
+                for J in range(2):
+                    Ms[2 * b + J][2 * b + J] = Bs
+        for M in (Mv, Ms):
+            for r in range(2 * nb):
+                for c in range(2 * nb):
+                    if M[r][c] is None:
+                        M[r][c] = sp.csr_matrix((self.bops[r // 2].N, self.bops[c // 2].N))
+        self.Bv = sp.bmat(Mv, format="csr")
+        self.Bs = sp.bmat(Ms, format="csr")
+        self.damped = self.Bv.nnz > 0 or self.Bs.nnz > 0
+
     # ------------------------------------------------------------------ semidiscrete scheme
     def data(self, t):
         out = self.data_coef.T @ W.eval_time_basis(self.problem.time_basis, t) if len(self.problem.time_basis) else np.zeros(self.ndof)
@@ -339,20 +394,42 @@ class Oracle:
         return self.wvec * self.apply(u, t)
 
     def leapfrog(self, u_prev, u, t, dt, nsteps, homogeneous=False):
-        """u^{n+1} = 2 u^n - u^{n-1} + dt^2 accel(u^n, t_n)."""
+        """u^{n+1} = 2 u^n - u^{n-1} + dt^2 accel(u^n, t_n).  With velocity-dependent terms: the
+        dissipative Robin term with the centred velocity (u^{n+1} - u^{n-1}) / (2 dt) (it acts on the
+        two components of single face nodes, so the step solves a 2 x 2 system per face node), the
+        layer dissipation with the backward velocity (u^n - u^{n-1}) / dt (explicit):
+          (I + dt/2 W Bv) u^{n+1} = 2 u^n - u^{n-1} + dt^2 W (A u^n + data - Bs (u^n - u^{n-1}) / dt)
+                                    + dt/2 W Bv u^{n-1}."""
+        if self.damped:
+            Mv = (sp.identity(self.ndof, format="csr") + 0.5 * dt * _diag(self.wvec) @ self.Bv).tocsc()
+            lu = spla.splu(Mv)
         for n in range(nsteps):
             a = self.wvec * (self.A @ u) if homogeneous else self.accel(u, t)
-            u_prev, u = u, 2 * u - u_prev + dt * dt * a
+            if not self.damped:
+                u_prev, u = u, 2 * u - u_prev + dt * dt * a
+            else:
+                rhs = 2 * u - u_prev + dt * dt * a - dt * self.wvec * (self.Bs @ (u - u_prev)) \
+                    + 0.5 * dt * self.wvec * (self.Bv @ u_prev)
+                u_prev, u = u, lu.solve(rhs)
             t = t + dt
         return u_prev, u, t
 
     def rk4(self, u, v, t, dt, nsteps):
-        """Classical RK4 on (u, v) (Sec. 7.1)."""
+        """Classical RK4 on (u, v) (Sec. 7.1); v' = W (A u - (Bv + Bs) v + data)."""
+        B = self.Bv + self.Bs
+
+        def acc(uu, vv, tt):
+            a = self.accel(uu, tt)
+            return a - self.wvec * (B @ vv) if self.damped else a
+
         for n in range(nsteps):
-            k1u, k1v = v, self.accel(u, t)
-            k2u, k2v = v + 0.5 * dt * k1v, self.accel(u + 0.5 * dt * k1u, t + 0.5 * dt)
-            k3u, k3v = v + 0.5 * dt * k2v, self.accel(u + 0.5 * dt * k2u, t + 0.5 * dt)
-            k4u, k4v = v + dt * k3v, self.accel(u + dt * k3u, t + dt)
+            k1u, k1v = v, acc(u, v, t)
+            k2u = v + 0.5 * dt * k1v
+            k2v = acc(u + 0.5 * dt * k1u, k2u, t + 0.5 * dt)
+            k3u = v + 0.5 * dt * k2v
+            k3v = acc(u + 0.5 * dt * k2u, k3u, t + 0.5 * dt)
+            k4u = v + dt * k3v
+            k4v = acc(u + dt * k3u, k4u, t + dt)
             u = u + dt / 6 * (k1u + 2 * k2u + 2 * k3u + k4u)
             v = v + dt / 6 * (k1v + 2 * k2v + 2 * k3v + k4v)
             t = t + dt

@@ -24,6 +24,7 @@ FP64, FP32 = 0, 1
 BC = {"displacement": 0, "robin": 1, "interface": 2}
 FIELD_PREV, FIELD_CUR, FIELD_APPLY, FIELD_VELOCITY = 0, 1, 2, 3
 C_PAIR10, C_VOIGT6 = 0, 1
+STENCIL = {"narrow": 0, "wide": 1}
 PROF_FAMILIES = 8      # SBP_PROF_FAMILIES
 
 
@@ -44,7 +45,7 @@ class BlockDesc(C.Structure):
 
 class GridDesc(C.Structure):
     _fields_ = [("order", C.c_int), ("precision", C.c_int), ("nblocks", C.c_int),
-                ("blocks", C.POINTER(BlockDesc)), ("beta", C.c_double)]
+                ("blocks", C.POINTER(BlockDesc)), ("beta", C.c_double), ("stencil", C.c_int)]
 
 
 _lib = None
@@ -70,6 +71,8 @@ def lib():
         L.sbp_set_material.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_int]
         L.sbp_set_robin.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.sbp_set_time_basis.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), _DP]
+        L.sbp_set_robin_damping.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
+        L.sbp_set_layer_dissipation.argtypes = [C.c_void_p, C.c_int, _DP]
         L.sbp_set_boundary_data.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.sbp_set_forcing.argtypes = [C.c_void_p, C.c_int, _DP]
         L.sbp_add_point_source.argtypes = [C.c_void_p, C.c_int] + [C.c_double] * 7
@@ -94,6 +97,7 @@ def lib():
         L.sbp_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sbp_check.argtypes = [C.c_void_p]
+        L.sbp_l2_diff.argtypes = [C.c_void_p, C.c_int, C.POINTER(_DP), _DP, _DP]
         L.sbp_debug_wait_probe.argtypes = [C.c_void_p, C.c_int]
         L.sbp_batch_create.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_void_p)]
         L.sbp_batch_destroy.argtypes = [C.c_void_p]
@@ -152,7 +156,8 @@ def grid_desc(problem, precision="fp64"):
                 fd.nbr_block, fd.nbr_face, fd.reversed = -1, -1, 0
     keep.append(blocks)
     prec = FP64 if precision == "fp64" else FP32
-    return GridDesc(problem.order, prec, len(problem.blocks), blocks, problem.beta), keep
+    stencil = STENCIL[getattr(problem, "stencil", "narrow")]
+    return GridDesc(problem.order, prec, len(problem.blocks), blocks, problem.beta, stencil), keep
 
 
 def footprint_bytes(problem, precision="fp32"):
@@ -200,9 +205,15 @@ class Solver:
                 if face.kind == "robin" and face.U is not None:
                     U = _f64(face.U)
                     self._check(self.L.sbp_set_robin(self.h, b, f, _ptr(U)))
+                if face.kind == "robin" and getattr(face, "V", None) is not None:
+                    V = _f64(face.V)
+                    self._check(self.L.sbp_set_robin_damping(self.h, b, f, _ptr(V)))
                 if face.g is not None and face.kind in ("robin", "displacement"):
                     g = _f64(face.g)
                     self._check(self.L.sbp_set_boundary_data(self.h, b, f, _ptr(g)))
+            if getattr(blk, "sponge", None) is not None:
+                sp_ = _f64(blk.sponge)
+                self._check(self.L.sbp_set_layer_dissipation(self.h, b, _ptr(sp_)))
             if blk.forcing is not None:
                 fo = _f64(blk.forcing)
                 self._check(self.L.sbp_set_forcing(self.h, b, _ptr(fo)))
@@ -318,6 +329,14 @@ class Solver:
         self._check(self.L.sbp_misfit_gradient(self.h, int(nsteps), float(dt), _ptr(obs), int(checkpoint_every),
                                                C.byref(phi), pr, pc, int(layout)))
         return phi.value, gr, gc
+
+    def sbp_l2_diff(self, which, ref):
+        """(sum (u-ref)^T JH (u-ref), sum ref^T JH ref) over blocks for field `which`."""
+        arrs = [_f64(r) for r in ref]
+        ptrs = (_DP * len(arrs))(*[_ptr(a) for a in arrs])
+        e, r = C.c_double(), C.c_double()
+        self._check(self.L.sbp_l2_diff(self.h, int(which), ptrs, C.byref(e), C.byref(r)))
+        return e.value, r.value
 
     def sbp_check(self):
         self._check(self.L.sbp_check(self.h))

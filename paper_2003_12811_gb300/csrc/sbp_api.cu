@@ -18,6 +18,7 @@
 #include "sbp_kernels.cuh"
 #include "sbp_adjoint.cuh"
 #include "sbp_batch.cuh"
+#include "sbp_wide.cuh"
 
 namespace sbphost {
 #define SBP_TABLE static const
@@ -37,8 +38,10 @@ struct HostFace {
     double* jhat = nullptr;
     void* ju = nullptr;
     void* g = nullptr;
-    void* sat = nullptr;      // unused by the handle (sbp_apply_noalloc points its views at its own scratch)
+    void* sat = nullptr;      // wide stencil: SAT terms of the face nodes (k_face_sat); else unused (sbp_apply_noalloc
+                              // points its views at its own scratch)
     void* tr = nullptr;       // interface faces: trace of this side (k_face_trace), 7 x nf
+    void* jv = nullptr;       // Robin faces with damping: J^ V (3 x nf, type T)
 };
 
 struct HostBlock {
@@ -59,6 +62,11 @@ struct HostBlock {
     MarchMaps pmaps;          // marching-kernel maps over the adjoint fields
     CUtensorMap* d_smaps = nullptr;   // strip-tile band-box maps on the device: [0..2] state u0, u1, c; [3..5] adjoint
     void* rk = nullptr;       // RK4 state (u, v, V, S_u, S_v; sbp_set_state_rk4), allocated on first use
+    void* gw = nullptr;       // wide stencil: the fluxes G_1j, G_2j (4 planes, type T)
+    void* sg = nullptr;       // layer dissipation coefficient s (1 plane, type T)
+    int2* d_lnodes = nullptr; // nodes the layer dissipation reaches, (i1, i2)
+    int nln = 0;
+    void* lscr = nullptr;     // leapfrog: the dissipation of the listed nodes between the pre and post kernels
     void* mx = nullptr;       // closure matrices of D_xx^FC along x1 / x2 (k_closure_mats, type T)
     void* my = nullptr;
 };
@@ -88,6 +96,9 @@ double host_hweight(int o, int N, int i) {
 
 struct sbp_handle {
     int order = 0, precision = 0, nblocks = 0;
+    int stencil = SBP_STENCIL_NARROW;
+    bool layers = false;          // some block has layer dissipation (sbp_set_layer_dissipation)
+    bool damping = false;         // some face has Robin damping or some block layers
     double beta = 1.0;
     size_t esize = 8;
     std::vector<HostBlock> blocks;
@@ -163,6 +174,18 @@ struct sbp_handle {
     int fail(int code, const std::string& msg) {
         err = msg;
         return code;
+    }
+    // one grow-only device staging buffer for host uploads and downloads: setup and transfer calls
+    // use it instead of allocating and freeing temporaries (a free synchronises the whole device,
+    // which would stall work other streams run meanwhile, e.g. a batch of served shots)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    void* staging(size_t bytes) {
+        if (bytes <= stage_bytes) return stage;
+        if (stage) dfree(stage);
+        stage = dalloc(bytes + bytes / 4);
+        stage_bytes = stage ? bytes + bytes / 4 : 0;
+        return stage;
     }
     void* dalloc(size_t bytes) {
         void* p = nullptr;
@@ -256,9 +279,12 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
         D.g = F.g;
         D.sat = F.sat;
         D.tr = F.tr;
+        D.jv = F.jv;
+        if (F.jv) b.damped = 1;
     }
     b.smaps = hb.d_smaps;
     b.rk = hb.rk;
+    b.sg = hb.sg;
     b.mx = hb.mx;
     b.my = hb.my;
     return b;
@@ -330,6 +356,77 @@ bool make_strip_maps(const sbp_handle* h, const HostBlock& hb, void* u0, void* u
     return make_map(&dst[0], u0, hb.pitch, hb.n2, 2, bh, bw, es) &&
            make_map(&dst[1], u1, hb.pitch, hb.n2, 2, bh, bw, es) &&
            make_map(&dst[2], hb.c, hb.pitch, hb.n2, 10, bh, bw, es);
+}
+
+// interface traces of the level being read (k_face_trace), TRACE_MAX faces per launch, on stream tst
+template <typename T, int O>
+void launch_traces(sbp_handle* h, const StepArgs& a, cudaStream_t tst, bool adj) {
+    TraceArgs ta{};
+    auto flush = [&]() {
+        if (ta.nfaces == 0) return;
+        ProfScope ps(h, 2, tst, 1);
+        k_face_trace<T, O><<<grid_for(ta.total, 128), 128, 0, tst>>>(ta);
+        ta = TraceArgs{};
+    };
+    for (size_t b = 0; b < h->blocks.size(); ++b) {
+        const HostBlock& hb = h->blocks[b];
+        for (int f = 0; f < 4; ++f) {
+            const HostFace& HF = hb.f[f];
+            if (HF.kind != FACE_INTF) continue;
+            TraceFace& F = ta.f[ta.nfaces++];
+            F.u = adj ? hb.psi[a.cur] : hb.u[a.cur];
+            F.c = hb.c;
+            F.tr = HF.tr;
+            F.plane = (long long)hb.n2 * hb.pitch;
+            F.nf = HF.nf;
+            F.start = ta.total;
+            F.m = f / 2;
+            F.side = f % 2;
+            F.pitch = hb.pitch;
+            F.nm = F.m == 0 ? hb.n1 : hb.n2;
+            F.nu = (f % 2 == 0) ? -1.0 : 1.0;
+            const double hm = F.m == 0 ? hb.h1 : hb.h2, ht = F.m == 0 ? hb.h2 : hb.h1;
+            F.ihm = 1.0 / hm;
+            F.iht = 1.0 / ht;
+            F.k = h->beta * 2.0 / 4.0 * (1.0 / (hm * host_hweight(h->order, F.nm, 0)));
+            ta.total += HF.nf;
+            if (ta.nfaces == TRACE_MAX) flush();
+        }
+    }
+    flush();
+}
+
+// the wide-stencil operator (sbp_wide.cuh): traces, the SAT terms of every face node, the flux and
+// divergence passes of every block, then the point sources (every source node: the wide path has
+// no strip kernel); RK4 stages take the sources into the operator sum first
+template <typename T, int O>
+int launch_wide(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st) {
+    if (!h->src_nodes.empty() && mode == 2) {
+        ProfScope ps(h, 3, st, 1);
+        const int ns = (int)h->src_nodes.size();
+        k_sources<T, 2><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
+    }
+    if (h->ntrefs > 0) launch_traces<T, O>(h, a, st, false);
+    if (h->nface_nodes > 0) {
+        ProfScope ps(h, 1, st, 1);
+        k_face_sat<T, O><<<grid_for(h->nface_nodes), 256, 0, st>>>(h->d_blocks, h->d_refs, h->nrefs, h->nface_nodes, a, h->beta);
+    }
+    for (auto& hb : h->blocks) {
+        const BlockDev b = make_view(h, hb);
+        const long long n = (long long)hb.n1 * hb.n2;
+        ProfScope ps(h, 0, st, 2);
+        k_wide_flux<T, O><<<grid_for(n), 256, 0, st>>>(b, a, (T*)hb.gw);
+        if (mode == 0) k_wide_div<T, O, 0><<<grid_for(n), 256, 0, st>>>(b, a, (const T*)hb.gw);
+        else if (mode == 2) k_wide_div<T, O, 2><<<grid_for(n), 256, 0, st>>>(b, a, (const T*)hb.gw);
+        else k_wide_div<T, O, 1><<<grid_for(n), 256, 0, st>>>(b, a, (const T*)hb.gw);
+    }
+    if (!h->src_nodes.empty() && mode != 2) {
+        ProfScope ps(h, 3, st, 1);
+        const int ns = (int)h->src_nodes.size();
+        if (mode == 0) k_sources<T, 0><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
+        else k_sources<T, 1><<<grid_for(ns), 256, 0, st>>>(h->d_blocks, h->d_src_nodes, ns, h->d_src_params, a);
+    }
+    return check_cuda(h, "wide operator launch");
 }
 
 // one operator application (mode 1) or leapfrog step (mode 0) on the state fields, or, with adj,
@@ -404,43 +501,7 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
             }
         }
     }
-    if (h->ntrefs > 0) {
-        // interface traces of the level being read, TRACE_MAX faces per launch (enqueued after the
-        // interior kernels, so that their CTAs are placed first and the traces fill the tail)
-        TraceArgs ta{};
-        auto flush = [&]() {
-            if (ta.nfaces == 0) return;
-            ProfScope ps(h, 2, tst, 1);
-            k_face_trace<T, O><<<grid_for(ta.total, 128), 128, 0, tst>>>(ta);
-            ta = TraceArgs{};
-        };
-        for (size_t b = 0; b < h->blocks.size(); ++b) {
-            const HostBlock& hb = h->blocks[b];
-            for (int f = 0; f < 4; ++f) {
-                const HostFace& HF = hb.f[f];
-                if (HF.kind != FACE_INTF) continue;
-                TraceFace& F = ta.f[ta.nfaces++];
-                F.u = adj ? hb.psi[a.cur] : hb.u[a.cur];
-                F.c = hb.c;
-                F.tr = HF.tr;
-                F.plane = (long long)hb.n2 * hb.pitch;
-                F.nf = HF.nf;
-                F.start = ta.total;
-                F.m = f / 2;
-                F.side = f % 2;
-                F.pitch = hb.pitch;
-                F.nm = F.m == 0 ? hb.n1 : hb.n2;
-                F.nu = (f % 2 == 0) ? -1.0 : 1.0;
-                const double hm = F.m == 0 ? hb.h1 : hb.h2, ht = F.m == 0 ? hb.h2 : hb.h1;
-                F.ihm = 1.0 / hm;
-                F.iht = 1.0 / ht;
-                F.k = h->beta * 2.0 / 4.0 * (1.0 / (hm * host_hweight(h->order, F.nm, 0)));
-                ta.total += HF.nf;
-                if (ta.nfaces == TRACE_MAX) flush();
-            }
-        }
-        flush();
-    }
+    if (h->ntrefs > 0) launch_traces<T, O>(h, a, tst, adj);
     if (tr_async && !ovl) {    // the strips wait for the traces formed beside the interior
         cudaEventRecord(h->ev_join, h->aux);
         cudaStreamWaitEvent(st, h->ev_join, 0);
@@ -474,6 +535,13 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
 
 template <typename T>
 int dispatch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj) {
+    if (h->stencil == SBP_STENCIL_WIDE) {
+        switch (h->order) {
+            case 2: return launch_wide<T, 2>(h, a, mode, st);
+            case 4: return launch_wide<T, 4>(h, a, mode, st);
+            default: return launch_wide<T, 6>(h, a, mode, st);
+        }
+    }
     switch (h->order) {
         case 2: return launch_operator<T, 2>(h, a, mode, st, adj);
         case 4: return launch_operator<T, 4>(h, a, mode, st, adj);
@@ -481,9 +549,43 @@ int dispatch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t s
     }
 }
 
+// layer dissipation around the step kernels (leapfrog: the backward-velocity term is formed before
+// the step overwrites u^{n-1} and added after it; RK4: added into the stage's operator sum before)
+template <typename T, int O>
+void layer_launch(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool post) {
+    for (auto& hb : h->blocks) {
+        if (hb.nln == 0) continue;
+        const BlockDev b = make_view(h, hb);
+        const unsigned g = grid_for(hb.nln);
+        if (mode == 2) {
+            if (!post) k_layer_rk<T, O><<<g, 256, 0, st>>>(b, hb.d_lnodes, hb.nln, a.stage);
+        } else if (!post) {
+            k_layer_pre<T, O><<<g, 256, 0, st>>>(b, hb.d_lnodes, hb.nln, a.cur, 1.0 / a.dt, (T*)hb.lscr);
+        } else {
+            k_layer_post<T><<<g, 256, 0, st>>>(b, hb.d_lnodes, hb.nln, a.cur, a.dt2, (const T*)hb.lscr);
+        }
+    }
+}
+
+void run_layers(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool post) {
+    if (h->precision == SBP_FP64) {
+        if (h->order == 2) layer_launch<double, 2>(h, a, mode, st, post);
+        else if (h->order == 4) layer_launch<double, 4>(h, a, mode, st, post);
+        else layer_launch<double, 6>(h, a, mode, st, post);
+    } else {
+        if (h->order == 2) layer_launch<float, 2>(h, a, mode, st, post);
+        else if (h->order == 4) layer_launch<float, 4>(h, a, mode, st, post);
+        else layer_launch<float, 6>(h, a, mode, st, post);
+    }
+}
+
 int run_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool adj = false) {
-    return h->precision == SBP_FP64 ? dispatch_operator<double>(h, a, mode, st, adj)
-                                    : dispatch_operator<float>(h, a, mode, st, adj);
+    const bool layers = !adj && h->layers && (mode == 0 || mode == 2);
+    if (layers) run_layers(h, a, mode, st, false);
+    const int rc = h->precision == SBP_FP64 ? dispatch_operator<double>(h, a, mode, st, adj)
+                                            : dispatch_operator<float>(h, a, mode, st, adj);
+    if (rc == SBP_OK && layers && mode == 0) run_layers(h, a, mode, st, true);
+    return rc;
 }
 
 template <typename T, int O> void set_smem_attr() {
@@ -693,6 +795,7 @@ int ensure_adjoint_buffers(sbp_handle* h) {
 int step_once(sbp_handle* h, double dt, cudaStream_t st) {
     StepArgs a{};
     a.with_data = 1;
+    a.dt = dt;
     a.dt2 = dt * dt;
     a.dt2f = (float)a.dt2;
     a.cur = h->cur;
@@ -805,6 +908,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     if (desc->precision != SBP_FP64 && desc->precision != SBP_FP32) return bad(SBP_E_INVALID_ARG, "bad precision");
     if (desc->nblocks < 1 || !desc->blocks) return bad(SBP_E_INVALID_ARG, "need at least one block");
     if (desc->beta < 0 || (desc->beta > 0 && desc->beta < 1)) return bad(SBP_E_INVALID_ARG, "beta must be >= 1");
+    if (desc->stencil != SBP_STENCIL_NARROW && desc->stencil != SBP_STENCIL_WIDE) return bad(SBP_E_INVALID_ARG, "bad stencil");
     const int o = desc->order;
     for (int b = 0; b < desc->nblocks; ++b) {
         const sbp_block_desc& bd = desc->blocks[b];
@@ -836,6 +940,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     h->precision = desc->precision;
     h->esize = desc->precision == SBP_FP64 ? 8 : 4;
     h->beta = desc->beta > 0 ? desc->beta : 1.0;
+    h->stencil = desc->stencil;
     h->nblocks = desc->nblocks;
     h->blocks.resize(desc->nblocks);
     auto cleanup = [&](int code, const std::string& m) {
@@ -891,6 +996,10 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         hb.J = (double*)h->dalloc(plane * sizeof(double));
         if (!hb.u[0] || !hb.u[1] || !hb.c || !hb.w || !hb.r || !hb.X || !hb.G || !hb.J)
             return cleanup(SBP_E_OOM, "device allocation failed for block " + std::to_string(b));
+        if (h->stencil == SBP_STENCIL_WIDE) {
+            hb.gw = h->dalloc(4 * plane * es);
+            if (!hb.gw) return cleanup(SBP_E_OOM, "wide-stencil flux planes");
+        }
         for (int f = 0; f < 4; ++f) {
             HostFace& F = hb.f[f];
             F.kind = bd.faces[f].kind;
@@ -900,6 +1009,10 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
             F.nf = f < 2 ? hb.n2 : hb.n1;
             F.jhat = (double*)h->dalloc(F.nf * sizeof(double));
             if (!F.jhat) return cleanup(SBP_E_OOM, "face buffers");
+            if (h->stencil == SBP_STENCIL_WIDE) {   // SAT terms of the face nodes (k_face_sat)
+                F.sat = h->dalloc(4 * (size_t)F.nf * es);
+                if (!F.sat) return cleanup(SBP_E_OOM, "face SAT buffers");
+            }
             refs.push_back(FaceRef{b, f, start, F.nf});
             start += F.nf;
             if (F.kind == FACE_INTF) {
@@ -923,15 +1036,14 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
                 return cleanup(SBP_E_CUDA, "tensor map encoding failed (strip tiles)");
         }
         // coordinates -> pitched device planes
-        double* tmp = (double*)h->dalloc(2 * (size_t)bd.n1 * bd.n2 * sizeof(double));
+        double* tmp = (double*)h->staging(2 * (size_t)bd.n1 * bd.n2 * sizeof(double));
         if (!tmp) return cleanup(SBP_E_OOM, "staging buffer");
         const size_t n = (size_t)bd.n1 * bd.n2;
         if (cudaMemcpy(tmp, bd.x1, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(tmp + n, bd.x2, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(SBP_E_CUDA, "coordinate upload failed");
         k_to_pitched<double><<<grid_for(2 * (long long)n), 256>>>(hb.X, tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
-        const cudaError_t ce = cudaDeviceSynchronize();
-        h->dfree(tmp);
+        const cudaError_t ce = cudaStreamSynchronize(0);
         if (ce != cudaSuccess) return cleanup(SBP_E_CUDA, std::string("coordinate conversion failed: ") + cudaGetErrorString(ce));
     }
     h->nrefs = (int)refs.size();
@@ -994,7 +1106,7 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
     }
     int flag = 0;
     if (cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
         return cleanup(SBP_E_CUDA, "metric setup failed");
     if (flag) return cleanup(SBP_E_JACOBIAN_NONPOSITIVE, "non-positive Jacobian determinant");
     *out = h;
@@ -1039,19 +1151,12 @@ int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* 
         for (int p = 0; p < 10; ++p) std::memcpy(expanded.data() + p * n, C + from_voigt[p] * n, n * sizeof(double));
         C = expanded.data();
     }
-    double* d_rho = (double*)h->dalloc(n * sizeof(double));
-    double* d_C = (double*)h->dalloc(10 * n * sizeof(double));
-    if (!d_rho || !d_C) {
-        h->dfree(d_rho);
-        h->dfree(d_C);
-        return h->fail(SBP_E_OOM, "material staging");
-    }
+    double* d_rho = (double*)h->staging(11 * n * sizeof(double));
+    double* d_C = d_rho ? d_rho + n : nullptr;
+    if (!d_rho) return h->fail(SBP_E_OOM, "material staging");
     if (cudaMemcpy(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d_C, C, 10 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-        h->dfree(d_rho);
-        h->dfree(d_C);
+        cudaMemcpy(d_C, C, 10 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return h->fail(SBP_E_CUDA, "material upload failed");
-    }
     BlockDev b = make_view(h, hb);
     if (h->precision == SBP_FP64) k_material<double><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
     else k_material<float><<<grid_for((long long)n), 256>>>(b, d_rho, d_C);
@@ -1066,9 +1171,7 @@ int sbp_set_material(sbp_handle* h, int block, const double* rho, const double* 
         else if (h->order == 4) { k_closure_mats<float, 4><<<grid_for(nx), 256>>>(b, 0, (float*)hb.mx); k_closure_mats<float, 4><<<grid_for(ny), 256>>>(b, 1, (float*)hb.my); }
         else { k_closure_mats<float, 6><<<grid_for(nx), 256>>>(b, 0, (float*)hb.mx); k_closure_mats<float, 6><<<grid_for(ny), 256>>>(b, 1, (float*)hb.my); }
     }
-    cudaError_t e = cudaDeviceSynchronize();
-    h->dfree(d_rho);
-    h->dfree(d_C);
+    cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, std::string("material: ") + cudaGetErrorString(e));
     hb.material = true;
     return SBP_OK;
@@ -1084,17 +1187,98 @@ int sbp_set_robin(sbp_handle* h, int block, int face, const double* U) {
         if (!(a >= 0 && c >= 0 && a * c - b * b >= -1e-12 * (a * c + b * b))) return h->fail(SBP_E_INVALID_ARG, "U must be symmetric positive semidefinite");
     }
     if (!F.ju) F.ju = h->dalloc(3 * (size_t)F.nf * h->esize);
-    double* tmp = (double*)h->dalloc(3 * (size_t)F.nf * sizeof(double));
+    double* tmp = (double*)h->staging(3 * (size_t)F.nf * sizeof(double));
     if (!F.ju || !tmp) return h->fail(SBP_E_OOM, "robin buffers");
     if (cudaMemcpy(tmp, U, 3 * (size_t)F.nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-        h->dfree(tmp);
         return h->fail(SBP_E_CUDA, "robin upload failed");
     }
     if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for(3LL * F.nf), 256>>>((double*)F.ju, tmp, F.jhat, F.nf, 3);
     else k_scale_copy<float><<<grid_for(3LL * F.nf), 256>>>((float*)F.ju, tmp, F.jhat, F.nf, 3);
-    cudaError_t e = cudaDeviceSynchronize();
-    h->dfree(tmp);
+    cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "robin upload");
+    return sync_views(h);
+}
+
+int sbp_set_robin_damping(sbp_handle* h, int block, int face, const double* V) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || face < 0 || face > 3 || !V) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostFace& F = h->blocks[block].f[face];
+    if (F.kind != SBP_BC_ROBIN) return h->fail(SBP_E_INVALID_ARG, "face is not a Robin face");
+    for (int s = 0; s < F.nf; ++s) {
+        const double a = V[s], b = V[F.nf + s], c = V[2 * F.nf + s];
+        if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c) ||
+            !(a >= 0 && c >= 0 && a * c - b * b >= -1e-12 * (a * c + b * b)))
+            return h->fail(SBP_E_INVALID_ARG, "V must be symmetric positive semidefinite");
+    }
+    if (!F.jv) F.jv = h->dalloc(3 * (size_t)F.nf * h->esize);
+    double* tmp = (double*)h->staging(3 * (size_t)F.nf * sizeof(double));
+    if (!F.jv || !tmp) return h->fail(SBP_E_OOM, "robin damping buffers");
+    if (cudaMemcpy(tmp, V, 3 * (size_t)F.nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        return h->fail(SBP_E_CUDA, "robin damping upload failed");
+    }
+    if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for(3LL * F.nf), 256>>>((double*)F.jv, tmp, F.jhat, F.nf, 3);
+    else k_scale_copy<float><<<grid_for(3LL * F.nf), 256>>>((float*)F.jv, tmp, F.jhat, F.nf, 3);
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "robin damping upload");
+    h->damping = true;
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    return sync_views(h);
+}
+
+int sbp_set_layer_dissipation(sbp_handle* h, int block, const double* s) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (block < 0 || block >= h->nblocks || !s) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    HostBlock& hb = h->blocks[block];
+    const size_t n = (size_t)hb.n1 * hb.n2;
+    for (size_t i = 0; i < n; ++i)
+        if (!(s[i] >= 0.0) || !std::isfinite(s[i])) return h->fail(SBP_E_INVALID_ARG, "layer coefficients must be >= 0 and finite");
+    // the nodes the dissipation reaches: a centre c with s_c != 0 acts on c-1, c, c+1 along x1 and x2
+    std::vector<int2> nodes;
+    for (int i2 = 0; i2 < hb.n2; ++i2)
+        for (int i1 = 0; i1 < hb.n1; ++i1) {
+            bool hit = false;
+            for (int o = -1; o <= 1 && !hit; ++o) {
+                const int c1 = i1 + o, c2 = i2 + o;
+                if (c1 >= 1 && c1 <= hb.n1 - 2 && s[(size_t)i2 * hb.n1 + c1] != 0.0) hit = true;
+                if (c2 >= 1 && c2 <= hb.n2 - 2 && s[(size_t)c2 * hb.n1 + i1] != 0.0) hit = true;
+            }
+            if (hit) nodes.push_back(make_int2(i1, i2));
+        }
+    const size_t plane = (size_t)hb.n2 * hb.pitch;
+    if (!hb.sg) hb.sg = h->dalloc(plane * h->esize);
+    h->dfree(hb.d_lnodes);
+    h->dfree(hb.lscr);
+    hb.d_lnodes = nullptr;
+    hb.lscr = nullptr;
+    hb.nln = 0;
+    double* tmp = (double*)h->staging(n * sizeof(double));
+    if (!hb.sg || !tmp) return h->fail(SBP_E_OOM, "layer buffers");
+    if (!nodes.empty()) {
+        hb.d_lnodes = (int2*)h->dalloc(sizeof(int2) * nodes.size());
+        hb.lscr = h->dalloc(2 * nodes.size() * h->esize);
+        if (!hb.d_lnodes || !hb.lscr) {
+            return h->fail(SBP_E_OOM, "layer buffers");
+        }
+    }
+    if (cudaMemcpy(tmp, s, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!nodes.empty() && cudaMemcpy(hb.d_lnodes, nodes.data(), sizeof(int2) * nodes.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+        return h->fail(SBP_E_CUDA, "layer upload failed");
+    }
+    if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for((long long)n), 256>>>((double*)hb.sg, tmp, hb.n1, hb.n2, hb.pitch, 1, nullptr);
+    else k_to_pitched<float><<<grid_for((long long)n), 256>>>((float*)hb.sg, tmp, hb.n1, hb.n2, hb.pitch, 1, nullptr);
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "layer upload");
+    hb.nln = (int)nodes.size();
+    h->layers = false;
+    for (auto& b : h->blocks) h->layers = h->layers || b.nln > 0;
+    h->damping = h->damping || h->layers;
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
     return sync_views(h);
 }
 
@@ -1126,17 +1310,15 @@ int sbp_set_boundary_data(sbp_handle* h, int block, int face, const double* g) {
     if (F.kind == SBP_BC_INTERFACE) return h->fail(SBP_E_INVALID_ARG, "interfaces take no boundary data");
     const size_t cnt = 2 * (size_t)h->nbasis * F.nf;
     if (!F.g) F.g = h->dalloc(cnt * h->esize);
-    double* tmp = (double*)h->dalloc(cnt * sizeof(double));
+    double* tmp = (double*)h->staging(cnt * sizeof(double));
     if (!F.g || !tmp) return h->fail(SBP_E_OOM, "boundary data");
     if (cudaMemcpy(tmp, g, cnt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-        h->dfree(tmp);
         return h->fail(SBP_E_CUDA, "boundary data upload failed");
     }
     const double* scale = F.kind == SBP_BC_ROBIN ? F.jhat : nullptr;
     if (h->precision == SBP_FP64) k_scale_copy<double><<<grid_for((long long)cnt), 256>>>((double*)F.g, tmp, scale, F.nf, 2 * h->nbasis);
     else k_scale_copy<float><<<grid_for((long long)cnt), 256>>>((float*)F.g, tmp, scale, F.nf, 2 * h->nbasis);
-    cudaError_t e = cudaDeviceSynchronize();
-    h->dfree(tmp);
+    cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "boundary data upload");
     return sync_views(h);
 }
@@ -1149,16 +1331,14 @@ int sbp_set_forcing(sbp_handle* h, int block, const double* f) {
     const size_t n = (size_t)hb.n1 * hb.n2, planes = 2 * (size_t)h->nbasis;
     const size_t plane = (size_t)hb.n2 * hb.pitch;
     if (!hb.jf) hb.jf = h->dalloc(planes * plane * h->esize);
-    double* tmp = (double*)h->dalloc(planes * n * sizeof(double));
+    double* tmp = (double*)h->staging(planes * n * sizeof(double));
     if (!hb.jf || !tmp) return h->fail(SBP_E_OOM, "forcing");
     if (cudaMemcpy(tmp, f, planes * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-        h->dfree(tmp);
         return h->fail(SBP_E_CUDA, "forcing upload failed");
     }
     if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for((long long)(planes * n)), 256>>>((double*)hb.jf, tmp, hb.n1, hb.n2, hb.pitch, (int)planes, hb.J);
     else k_to_pitched<float><<<grid_for((long long)(planes * n)), 256>>>((float*)hb.jf, tmp, hb.n1, hb.n2, hb.pitch, (int)planes, hb.J);
-    cudaError_t e = cudaDeviceSynchronize();
-    h->dfree(tmp);
+    cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "forcing upload");
     return sync_views(h);
 }
@@ -1210,20 +1390,18 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
     if (block < 0 || block >= h->nblocks || !u_prev || !u_cur) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
     HostBlock& hb = h->blocks[block];
     const size_t n = (size_t)hb.n1 * hb.n2;
-    double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
+    double* tmp = (double*)h->staging(2 * n * sizeof(double));
     if (!tmp) return h->fail(SBP_E_OOM, "state staging");
     const double* src[2] = {u_prev, u_cur};
     const int dst_idx[2] = {1 - h->cur, h->cur};
     for (int k = 0; k < 2; ++k) {
         if (cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-            h->dfree(tmp);
             return h->fail(SBP_E_CUDA, "state upload failed");
         }
         if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
         else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
     }
-    cudaError_t e = cudaDeviceSynchronize();
-    h->dfree(tmp);
+    cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
     h->t = t;
     return SBP_OK;
@@ -1298,6 +1476,7 @@ int sbp_step(sbp_handle* h, int nsteps, double dt, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     StepArgs a{};
     a.with_data = 1;
+    a.dt = dt;
     a.dt2 = dt * dt;
     a.dt2f = (float)a.dt2;
     for (int n = 0; n < nsteps; ++n) {
@@ -1323,21 +1502,19 @@ int sbp_set_state_rk4(sbp_handle* h, int block, const double* u, const double* v
         int rc = sync_views(h);
         if (rc != SBP_OK) return rc;
     }
-    double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
+    double* tmp = (double*)h->staging(2 * n * sizeof(double));
     if (!tmp) return h->fail(SBP_E_OOM, "state staging");
     // u -> RK planes 0-1 and the current state buffer (the first stage input); v -> RK planes 2-3
     void* dst[3] = {hb.rk, hb.u[h->cur], (unsigned char*)hb.rk + 2 * plane * h->esize};
     const double* src[3] = {u, u, v};
     for (int k = 0; k < 3; ++k) {
         if (cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-            h->dfree(tmp);
             return h->fail(SBP_E_CUDA, "state upload failed");
         }
         if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)dst[k], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
         else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)dst[k], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
     }
-    cudaError_t e = cudaDeviceSynchronize();
-    h->dfree(tmp);
+    cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
     h->t = t;
     return SBP_OK;
@@ -1395,13 +1572,12 @@ int sbp_get_field(sbp_handle* h, int block, int which, double* dst) {
     const size_t n = (size_t)hb.n1 * hb.n2;
     if (which == SBP_FIELD_VELOCITY && !hb.rk) return h->fail(SBP_E_STATE, "no RK4 state on this block");
     void* src = field_ptr(h, hb, which);
-    double* tmp = (double*)h->dalloc(2 * n * sizeof(double));
+    double* tmp = (double*)h->staging(2 * n * sizeof(double));
     if (!tmp) return h->fail(SBP_E_OOM, "download staging");
     cudaDeviceSynchronize();
     if (h->precision == SBP_FP64) k_from_pitched<double><<<grid_for(2LL * n), 256>>>(tmp, (const double*)src, hb.n1, hb.n2, hb.pitch, 2);
     else k_from_pitched<float><<<grid_for(2LL * n), 256>>>(tmp, (const float*)src, hb.n1, hb.n2, hb.pitch, 2);
     cudaError_t e = cudaMemcpy(dst, tmp, 2 * n * sizeof(double), cudaMemcpyDeviceToHost);
-    h->dfree(tmp);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "download failed");
     return check_kernel_errors(h);
 }
@@ -1436,6 +1612,43 @@ int sbp_energy(sbp_handle* h, double dt, double* E_out) {
     int rc2 = check_kernel_errors(h);
     if (rc2 != SBP_OK) return rc2;
     if (!std::isfinite(E)) return h->fail(SBP_E_UNSTABLE, "non-finite energy");
+    return SBP_OK;
+}
+
+int sbp_l2_diff(sbp_handle* h, int which, const double* const* ref, double* err2_out, double* ref2_out) {
+    if (!h) return SBP_E_INVALID_ARG;
+    if (!ref || which < 0 || which > 3) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
+    for (int b = 0; b < h->nblocks; ++b)
+        if (!ref[b]) return h->fail(SBP_E_INVALID_ARG, "null reference array");
+    for (auto& hb : h->blocks)
+        if (which == SBP_FIELD_VELOCITY && !hb.rk) return h->fail(SBP_E_STATE, "no RK4 state");
+    if (cudaMemset(h->d_scalar, 0, 2 * sizeof(double)) != cudaSuccess) return h->fail(SBP_E_CUDA, "l2 init");
+    for (auto& hb : h->blocks) {
+        const size_t n = (size_t)hb.n1 * hb.n2;
+        double* tmp = (double*)h->staging(2 * n * sizeof(double));
+        if (!tmp) return h->fail(SBP_E_OOM, "l2 staging");
+        if (cudaMemcpy(tmp, ref[&hb - h->blocks.data()], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            return h->fail(SBP_E_CUDA, "reference upload failed");
+        }
+        const BlockDev b = make_view(h, hb);
+        const void* U = field_ptr(h, hb, which);
+        const int o = h->order;
+        if (h->precision == SBP_FP64) {
+            if (o == 2) k_l2_diff<double, 2><<<512, 256>>>(b, (const double*)U, tmp, h->d_scalar);
+            else if (o == 4) k_l2_diff<double, 4><<<512, 256>>>(b, (const double*)U, tmp, h->d_scalar);
+            else k_l2_diff<double, 6><<<512, 256>>>(b, (const double*)U, tmp, h->d_scalar);
+        } else {
+            if (o == 2) k_l2_diff<float, 2><<<512, 256>>>(b, (const float*)U, tmp, h->d_scalar);
+            else if (o == 4) k_l2_diff<float, 4><<<512, 256>>>(b, (const float*)U, tmp, h->d_scalar);
+            else k_l2_diff<float, 6><<<512, 256>>>(b, (const float*)U, tmp, h->d_scalar);
+        }
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return h->fail(SBP_E_CUDA, std::string("l2 reduction: ") + cudaGetErrorString(e));
+    }
+    double r[2] = {0, 0};
+    if (cudaMemcpy(r, h->d_scalar, sizeof(r), cudaMemcpyDeviceToHost) != cudaSuccess) return h->fail(SBP_E_CUDA, "l2 read");
+    if (err2_out) *err2_out = r[0];
+    if (ref2_out) *ref2_out = r[1];
     return SBP_OK;
 }
 
@@ -1508,6 +1721,7 @@ int sbp_apply_noalloc(sbp_handle* h, const void* u_dev, void* r_dev, int with_da
     if (!h) return SBP_E_INVALID_ARG;
     if (!u_dev || !r_dev) return h->fail(SBP_E_INVALID_ARG, "null device buffer");
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
+    if (h->stencil != SBP_STENCIL_NARROW) return h->fail(SBP_E_STATE, "sbp_apply_noalloc applies the narrow stencil");
     {
         int dev = -1;
         if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
@@ -1677,11 +1891,13 @@ int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out) {
         if (desc->order == 2 || desc->order == 4 || desc->order == 6)
             total += al((long long)closure_elems(desc->order, bd.n2) * es) + al((long long)closure_elems(desc->order, bd.n1) * es);
         total += al(6 * (long long)sizeof(CUtensorMap));
+        if (desc->stencil == SBP_STENCIL_WIDE) total += al(4 * plane * es);   // flux planes
         for (int f = 0; f < 4; ++f) {
             const long long nf = f < 2 ? bd.n2 : bd.n1;
             // J^, Robin J^U, boundary data (2 x up to 8 basis functions), interface trace (7)
             total += al(nf * 8) + al(3 * nf * es) + al(2 * 8 * nf * es);
             if (bd.faces[f].kind == SBP_BC_INTERFACE) total += al(7 * nf * es);
+            if (desc->stencil == SBP_STENCIL_WIDE) total += al(4 * nf * es);
         }
     }
     total += 4096;   // block views, face tables, source tables
@@ -1905,6 +2121,8 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     const int ncp = c_layout == SBP_C_VOIGT6 ? 6 : 10;
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
     if (h->recs.empty()) return h->fail(SBP_E_STATE, "set the receivers first");
+    if (h->stencil != SBP_STENCIL_NARROW) return h->fail(SBP_E_STATE, "the misfit gradient is built for the narrow stencil");
+    if (h->damping) return h->fail(SBP_E_STATE, "the misfit gradient is built without the velocity-dependent terms");
     for (auto& hb : h->blocks)
         for (auto& F : hb.f)
             if (F.kind == SBP_BC_DISPLACEMENT && F.g)
@@ -2228,12 +2446,13 @@ int sbp_batch_add(sbp_batch* b, sbp_handle* h, int nsteps, double dt, int* slot_
     if (!b || !h || !slot_out) return SBP_E_INVALID_ARG;
     *slot_out = -1;
     if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return b->fail(SBP_E_INVALID_ARG, "bad step arguments");
-    if (h->precision != SBP_FP32 || h->order != b->order || h->nblocks != 1)
-        return b->fail(SBP_E_INVALID_ARG, "batch shots are single-block FP32 handles of the batch's order");
+    if (h->precision != SBP_FP32 || h->order != b->order || h->nblocks != 1 || h->stencil != SBP_STENCIL_NARROW)
+        return b->fail(SBP_E_INVALID_ARG, "batch shots are single-block FP32 narrow-stencil handles of the batch's order");
     const HostBlock& hb = h->blocks[0];
     for (auto& F : hb.f)
         if (F.kind == SBP_BC_INTERFACE) return b->fail(SBP_E_INVALID_ARG, "batch shots have no interfaces");
     if (h->nbasis != 0) return b->fail(SBP_E_STATE, "batch shots take point sources only (no time-basis data)");
+    if (h->damping) return b->fail(SBP_E_STATE, "batch shots have no velocity-dependent terms");
     if (!hb.material) return b->fail(SBP_E_STATE, "set the material first");
     for (int s = 0; s < b->max_shots; ++s) if (b->shot[s] == h) return b->fail(SBP_E_STATE, "handle already in the batch");
     int slot = -1;

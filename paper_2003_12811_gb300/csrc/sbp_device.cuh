@@ -245,6 +245,7 @@ struct FaceDev {
     float facf[12];           // the same in FP32
     const double* jhat;       // surface scale factor per face node
     const void* ju;           // robin: J^ U (3 x nf), type T
+    const void* jv;           // robin with damping: J^ V (3 x nf), type T, or null
     const void* g;            // data: displacement g (2 x K x nf) or robin J^ g, type T
     void* sat;                // scratch of k_face_sat: face term (2 x nf), normal-spread amplitude (2 x nf), type T
     void* tr;                 // interface faces: this side's trace per face node (7 x nf, type T) written by
@@ -254,6 +255,7 @@ struct FaceDev {
 
 struct BlockDev {
     int n1, n2, pitch, strip;  // strip = width of the boundary strips handled by k_boundary
+    int damped;               // some face has Robin damping (FaceDev::jv)
     double h1, h2;
     double ih1, ih2;          // 1 / h1, 1 / h2
     float ih1f, ih2f;         // the same in FP32 (read directly as constant operands by FP32 kernels)
@@ -266,6 +268,7 @@ struct BlockDev {
     double* G;                // metric dX_I/dx_i (4 planes, [2 i + I])
     double* J;                // Jacobian
     void* rk;                 // RK4 state (10 planes): u, v, stage velocity V, sums S_u, S_v (2 planes each)
+    const void* sg;           // layer dissipation coefficient s (1 plane, type T) or null
     const void* smaps;        // strip-tile band-box tensor maps (CUtensorMap[3]: u[0], u[1], c)
     const void* mx;           // closure rows of D_xx^FC along x1 as matrices, type T (k_closure_mats)
     const void* my;           // the same along x2
@@ -339,6 +342,53 @@ __device__ __forceinline__ void rk4_store(const BlockDev& B, const StepArgs& a, 
         R[2 * plane + gi] = v0 + h * (sv0 + b * a0);
         R[3 * plane + gi] = v1 + h * (sv1 + b * a1);
     }
+}
+
+// Dissipative Robin term (remark of Sec. 5.1: T u + U u + V u' = g) at node (i1, i2): the sum over
+// the Robin faces with damping that the node lies on of J^ V / H_m[0] (the J-scaled SAT of the
+// term is -(J^ V / H_m[0]) u'), as the symmetric 2 x 2 (d00, d01, d11); false if there is none.
+template <typename T>
+__device__ __forceinline__ bool robin_damping_at(const BlockDev& B, int i1, int i2, T& d00, T& d01, T& d11) {
+    bool any = false;
+    d00 = d01 = d11 = T(0);
+    if (!B.damped) return false;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const FaceDev& F = B.f[f];
+        if (!F.jv) continue;
+        const int im = F.m == 0 ? i1 : i2, Nm = F.m == 0 ? B.n1 : B.n2;
+        if ((F.side ? Nm - 1 - im : im) != 0) continue;
+        const int s = F.m == 0 ? i2 : i1, nf = F.nf;
+        const T* jv = reinterpret_cast<const T*>(F.jv);
+        const T ih = T(F.inv_h0);
+        d00 += jv[s] * ih;
+        d01 += jv[nf + s] * ih;
+        d11 += jv[2 * nf + s] * ih;
+        any = true;
+    }
+    return any;
+}
+
+// leapfrog update of a node with the dissipative Robin term taken with the centred velocity
+// (u^{n+1} - u^{n-1}) / (2 dt): (I + a D) u^{n+1} = nu + a D u^{n-1}, a = dt w / 2, where nu is the
+// undamped update 2 u^n - u^{n-1} + dt^2 w r; D symmetric positive semidefinite, so I + a D is
+// invertible
+template <typename T>
+__device__ __forceinline__ void robin_damped_update(T a, T d00, T d01, T d11, T up0, T up1, T& nu0, T& nu1) {
+    const T b0 = nu0 + a * (d00 * up0 + d01 * up1), b1 = nu1 + a * (d01 * up0 + d11 * up1);
+    const T m00 = T(1) + a * d00, m01 = a * d01, m11 = T(1) + a * d11;
+    const T idet = T(1) / (m00 * m11 - m01 * m01);
+    nu0 = (m11 * b0 - m01 * b1) * idet;
+    nu1 = (m00 * b1 - m01 * b0) * idet;
+}
+
+// the stage velocity of an RK4 stage at node gi (v for the first stage, V afterwards)
+template <typename T>
+__device__ __forceinline__ void rk4_stage_velocity(const BlockDev& B, const StepArgs& a, size_t gi, size_t plane, T& v0, T& v1) {
+    const T* R = reinterpret_cast<const T*>(B.rk);
+    const size_t o = a.stage == 1 ? 2 * plane : 4 * plane;
+    v0 = R[o + gi];
+    v1 = R[o + plane + gi];
 }
 
 // the per-block and per-face step constants in the arithmetic type T (FP32 kernels read the FP32

@@ -864,10 +864,10 @@ __device__ __forceinline__ bool strip_tile_body(const BlockDev* __restrict__ blo
     // column of a side tile (lanes along the column: one closure row per warp, and the odd row
     // stride of the side staging keeps the column accesses free of bank conflicts)
     const int lane = threadIdx.x & 31;
-    for (int wid = threadIdx.x >> 5; wid < S; wid += NT / 32) {
+    auto out_node = [&](const int wid) {
         const int i1 = along_x ? x0 + lane : x0 + wid;
         const int i2 = along_x ? y0 + wid : y0 + lane;
-        if (i1 >= x0 + w || i2 >= y0 + h) continue;
+        if (i1 >= x0 + w || i2 >= y0 + h) return;
         // narrow rows: closure rows through the precomputed matrices, interior rows by edge weights
         T rx0v = T(0), rx1v = T(0), ry0v = T(0), ry1v = T(0);
         if (!dxx_closure_mat<O, T>(n1, i1, i2, n2, reinterpret_cast<const T*>(B.mx), [&](int j) { return at(0, j, i2); },
@@ -922,19 +922,35 @@ __device__ __forceinline__ bool strip_tile_body(const BlockDev* __restrict__ blo
                 r1 += T(Wt * nd.wt1);
             }
         }
+        T dd00, dd01, dd11;
+        const bool damped = MODE != 1 && robin_damping_at<T>(B, i1, i2, dd00, dd01, dd11);
         if (MODE == 0) {
             T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
             const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
-            Un[gi] = T(2) * at(0, i1, i2) - Un[gi] + dt2 * wv * r0;
-            Un[gi + plane] = T(2) * at(1, i1, i2) - Un[gi + plane] + dt2 * wv * r1;
+            const T up0 = Un[gi], up1 = Un[gi + plane];
+            T nu0 = T(2) * at(0, i1, i2) - up0 + dt2 * wv * r0;
+            T nu1 = T(2) * at(1, i1, i2) - up1 + dt2 * wv * r1;
+            if (damped) robin_damped_update<T>(T(0.5 * a.dt) * wv, dd00, dd01, dd11, up0, up1, nu0, nu1);
+            Un[gi] = nu0;
+            Un[gi + plane] = nu1;
         } else if (MODE == 2) {
+            if (damped) {
+                T v0, v1;
+                rk4_stage_velocity<T>(B, a, gi, plane, v0, v1);
+                r0 -= dd00 * v0 + dd01 * v1;
+                r1 -= dd01 * v0 + dd11 * v1;
+            }
             rk4_store<T>(B, a, gi, plane, reinterpret_cast<const T*>(B.w)[gi], r0, r1);
         } else {
             T* __restrict__ R = reinterpret_cast<T*>(B.r);
             R[gi] = r0;
             R[gi + plane] = r1;
         }
-    }
+    };
+    // one warp per output row when the CTA has 32 S threads (the strip kernel), else a loop
+    if constexpr (NT == 32 * S) out_node((int)(threadIdx.x >> 5));
+    else
+        for (int wid = threadIdx.x >> 5; wid < S; wid += NT / 32) out_node(wid);
     return true;
 }
 
@@ -988,6 +1004,114 @@ __global__ void k_wait_probe(int polls, int* err) {
     }
     __syncthreads();
     if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, polls)) atomicOr(err, ERR_SELFTEST_WAIT);
+}
+
+// ============================================================================ l2 distances
+// sum over nodes of (u_J - ref_J) (J H) (u_J - ref_J) and ref_J (J H) ref_J (FP64 accumulation);
+// ref is dense host layout (2 planes of n1*n2, x1 fastest)
+template <typename T, int O>
+__global__ void k_l2_diff(BlockDev B, const T* __restrict__ U, const double* __restrict__ ref, double* out) {
+    const long long n = (long long)B.n1 * B.n2;
+    double se = 0.0, sr = 0.0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i2 = (int)(t / B.n1), i1 = (int)(t - (long long)i2 * B.n1);
+        const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)i2 * B.pitch + i1;
+        const double wq = B.J[gi] * B.h1 * hweight<O>(B.n1, i1) * B.h2 * hweight<O>(B.n2, i2);
+        const double r0 = ref[t], r1 = ref[n + t];
+        const double e0 = (double)U[gi] - r0, e1 = (double)U[plane + gi] - r1;
+        se += wq * (e0 * e0 + e1 * e1);
+        sr += wq * (r0 * r0 + r1 * r1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        se += __shfl_down_sync(0xffffffffu, se, o);
+        sr += __shfl_down_sync(0xffffffffu, sr, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, se);
+        atomicAdd(out + 1, sr);
+    }
+}
+
+// ============================================================================ layer dissipation
+// Super-grid layer dissipation (Sec. 7.3; reading: J E = -H^-1 sum_i Dt_i^T diag(s) Dt_i per
+// component, Dt_i the undivided second difference along x_i at the nodes 1 .. N-2 of a line, s >= 0
+// the layer coefficient of the node at the difference's centre).  (H^-1 K v)(i1, i2) for a field
+// v(j1, j2, component):
+template <typename T, int O, class FV>
+__device__ __forceinline__ void layer_kv(const BlockDev& B, int i1, int i2, FV v, T& k0, T& k1) {
+    const T* __restrict__ S = reinterpret_cast<const T*>(B.sg);
+    const int P = B.pitch;
+    k0 = k1 = T(0);
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        const int N = dir == 0 ? B.n1 : B.n2, j = dir == 0 ? i1 : i2;
+#pragma unroll
+        for (int o = -1; o <= 1; ++o) {
+            const int c = j + o;
+            if (c < 1 || c > N - 2) continue;
+            const int c1 = dir == 0 ? c : i1, c2 = dir == 0 ? i2 : c;
+            const T sc = S[(size_t)c2 * P + c1];
+            if (sc == T(0)) continue;
+            const int e1 = dir == 0 ? 1 : 0, e2 = 1 - e1;
+            const T coef = o == 0 ? T(-2) : T(1);
+            const T d0 = v(c1 - e1, c2 - e2, 0) - T(2) * v(c1, c2, 0) + v(c1 + e1, c2 + e2, 0);
+            const T d1 = v(c1 - e1, c2 - e2, 1) - T(2) * v(c1, c2, 1) + v(c1 + e1, c2 + e2, 1);
+            k0 += coef * sc * d0;
+            k1 += coef * sc * d1;
+        }
+    }
+    const T ih = T(1.0 / (B.h1 * hweight<O>(B.n1, i1) * B.h2 * hweight<O>(B.n2, i2)));
+    k0 *= ih;
+    k1 *= ih;
+}
+
+// leapfrog, before the step: d = H^-1 K (u^n - u^{n-1}) / dt at the listed nodes (the backward
+// velocity; u^{n-1} is overwritten by the step kernels)
+template <typename T, int O>
+__global__ void k_layer_pre(BlockDev B, const int2* __restrict__ nodes, int n, int cur, double idt, T* __restrict__ d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int2 nd = nodes[k];
+    const size_t plane = (size_t)B.n2 * B.pitch;
+    const T* __restrict__ U = reinterpret_cast<const T*>(B.u[cur]);
+    const T* __restrict__ Up = reinterpret_cast<const T*>(B.u[1 - cur]);
+    T k0, k1;
+    layer_kv<T, O>(B, nd.x, nd.y, [&](int j1, int j2, int c) {
+        const size_t g = (size_t)c * plane + (size_t)j2 * B.pitch + j1;
+        return U[g] - Up[g];
+    }, k0, k1);
+    d[k] = k0 * T(idt);
+    d[n + k] = k1 * T(idt);
+}
+
+// leapfrog, after the step: u^{n+1} -= dt^2 w d at the listed nodes
+template <typename T>
+__global__ void k_layer_post(BlockDev B, const int2* __restrict__ nodes, int n, int cur, double dt2, const T* __restrict__ d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int2 nd = nodes[k];
+    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)nd.y * B.pitch + nd.x;
+    T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - cur]);
+    const T fac = T(dt2) * reinterpret_cast<const T*>(B.w)[gi];
+    Un[gi] -= fac * d[k];
+    Un[plane + gi] -= fac * d[n + k];
+}
+
+// RK4 stage, before the stage kernels: -H^-1 K V_s into the point-source planes of the operator
+// output (rk4_store takes them into the operator sum)
+template <typename T, int O>
+__global__ void k_layer_rk(BlockDev B, const int2* __restrict__ nodes, int n, int stage) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int2 nd = nodes[k];
+    const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)nd.y * B.pitch + nd.x;
+    const T* __restrict__ V = reinterpret_cast<const T*>(B.rk) + (stage == 1 ? 2 : 4) * plane;
+    T k0, k1;
+    layer_kv<T, O>(B, nd.x, nd.y, [&](int j1, int j2, int c) { return V[(size_t)c * plane + (size_t)j2 * B.pitch + j1]; },
+                   k0, k1);
+    T* __restrict__ R = reinterpret_cast<T*>(B.r);
+    R[gi] -= k0;
+    R[plane + gi] -= k1;
 }
 
 // ============================================================================ energy

@@ -191,7 +191,10 @@ class ServingEngine:
 
 
 def _problem_of(req):
-    return req.problem() if callable(req.problem) else req.problem
+    """The request's problem; a callable payload is made once and kept with the request."""
+    if callable(req.problem):
+        req.problem = req.problem()
+    return req.problem
 
 
 class GpuBatchBackend:
@@ -281,6 +284,12 @@ class BatchServingEngine:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
+            # the next tick of every resident shot goes to the GPU first; new shots are set up
+            # while it runs and join at the following tick
+            launched = bool(active)
+            if launched:
+                self.backend.step(self.tick)
+                self.ticks += 1
             while waiting and len(active) < self.max_active:
                 req = waiting[0]
                 prob = _problem_of(req)
@@ -296,24 +305,21 @@ class BatchServingEngine:
                 active[slot] = dict(req=req, fp=fp, admitted=self.clock() - t0, dt=dt)
                 self.peak_active = max(self.peak_active, len(active))
                 self.trace.append((self.clock() - t0, "admit", req.rid))
-            if not active:
-                if pending:
-                    wait = pending[0].arrival - (self.clock() - t0)
-                    if wait > 0:
-                        self.sleep(min(wait, 0.05))
-                continue
-            self.backend.step(self.tick)
-            self.ticks += 1
-            rem = self.backend.poll()
-            for slot in sorted(active):
-                if rem[slot] == 0:
-                    info = active.pop(slot)
-                    fields = self.backend.retire(slot)
-                    used -= info["fp"]
-                    t = self.clock() - t0
-                    req = info["req"]
-                    results.append(Result(req.rid, req.arrival, info["admitted"], t, req.nsteps, info["dt"], fields))
-                    self.trace.append((t, "finish", req.rid))
+            if launched:
+                rem = self.backend.poll()
+                for slot in sorted(active):
+                    if rem[slot] == 0:
+                        info = active.pop(slot)
+                        fields = self.backend.retire(slot)
+                        used -= info["fp"]
+                        t = self.clock() - t0
+                        req = info["req"]
+                        results.append(Result(req.rid, req.arrival, info["admitted"], t, req.nsteps, info["dt"], fields))
+                        self.trace.append((t, "finish", req.rid))
+            elif not active and pending:
+                wait = pending[0].arrival - (self.clock() - t0)
+                if wait > 0:
+                    self.sleep(min(wait, 0.05))
         return sorted(results, key=lambda r: r.rid)
 
 

@@ -207,3 +207,24 @@ def test_errors_are_reported():
     with pytest.raises(SbpError) as e:
         _solver(P)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("prec", ("fp64", "fp32"))
+def test_l2_diff_is_the_schemes_norm(prec):
+    """sbp_l2_diff: the l2 error of Table 1 (sqrt(sum e^T (J H) e)) against the oracle's l2_error of
+    the same field, and the reference norm against the oracle's J H quadrature."""
+    from paper_2003_12811_gb300.binding import FIELD_CUR
+    P = W.mms_problem(33, 6, kinds=("robin", "displacement", "robin", "displacement"), two_blocks=True)
+    O = Oracle(P)
+    u = [P.exact(b, 0.2) + 1e-3 * np.sin(3 * b.X[0] + 2 * b.X[1]) for b in P.blocks]
+    if prec == "fp32":
+        u = [np.asarray(x, np.float32).astype(np.float64) for x in u]
+    S = _solver(P, prec)
+    S.set_state(u, u, 0.0)
+    e2, r2 = S.sbp_l2_diff(FIELD_CUR, [P.exact(b, 0.2) for b in P.blocks])
+    S.close()
+    eo = O.l2_error(O.pack(u), 0.2)
+    assert math.sqrt(e2) == pytest.approx(eo, rel=1e-11)
+    ex = O.pack([P.exact(b, 0.2) for b in P.blocks])
+    assert r2 == pytest.approx(float(np.dot(ex, np.concatenate([np.tile(bo.J * bo.Hvec, 2) for bo in O.bops]) * ex)),
+                               rel=1e-12)

@@ -181,3 +181,22 @@ def test_batch_engine_admits_between_ticks_while_others_run():
     r = {x.rid: x for x in res}
     # request 1 joins while request 0 is still running and finishes first
     assert r[1].admitted < r[0].finished and r[1].finished < r[0].finished
+
+
+def test_batch_engine_makes_a_callable_payload_once():
+    """A request that waits for memory is looked at on several passes; its payload (a callable that
+    builds the problem) is made once."""
+    from paper_2003_12811_gb300.serve import BatchServingEngine
+    clk = VClock()
+    be = FakeBatchBackend(clk, {0: 80, 1: 80}, max_shots=2)
+    calls = {0: 0, 1: 0}
+
+    def make(i):
+        calls[i] += 1
+        return i
+
+    eng = BatchServingEngine(100, backend=be, tick_steps=4, max_active=2, clock=clk, sleep=clk.sleep)
+    reqs = [Request(rid=i, arrival=0.0, problem=(lambda i=i: make(i)), nsteps=20) for i in range(2)]
+    res = eng.run(reqs)
+    assert [r.fields for r in res] == [20, 20]
+    assert calls == {0: 1, 1: 1}

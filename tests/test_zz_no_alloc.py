@@ -68,7 +68,8 @@ def test_apply_noalloc_matches_apply_and_oracle_twice(prec, tol, with_data):
     for call in range(2):
         t = 0.21 + 0.07 * call if with_data else 0.0
         if with_data:
-            u = [P.exact(b, t) + 1e-3 * rng.standard_normal((2, n2, n1)) for b, (n2, n1) in zip(P.blocks, shapes)]
+            # a rough field (the FP32 bar assumes stencil terms that do not cancel), plus the data terms
+            u = [P.exact(b, t) + 0.5 * rng.standard_normal((2, n2, n1)) for b, (n2, n1) in zip(P.blocks, shapes)]
         else:
             u = [rng.standard_normal((2, n2, n1)) for (n2, n1) in shapes]
         S.set_state(u, u, 0.0)

@@ -47,6 +47,7 @@ class Face:
     U: Optional[np.ndarray] = None
     g: Optional[np.ndarray] = None
     nbr: Optional[Tuple[int, int, bool]] = None
+    V: Optional[np.ndarray] = None    # 'robin': (3, Nf) symmetric PSD damping V (V11, V12, V22) of T u + U u + V du/dt = g
 
 
 @dataclass
@@ -58,6 +59,7 @@ class Block:
     h: Optional[Tuple[float, float]] = None   # reference spacing; default 1/(N-1)
     origin: Tuple[int, int] = (0, 0)  # index of node (0,0) inside the uncropped block
     forcing: Optional[np.ndarray] = None      # (2, K, N2, N1) harmonic coefficients of f_J
+    sponge: Optional[np.ndarray] = None       # (N2, N1) >= 0: super-grid layer dissipation coefficient s
 
     @property
     def N1(self) -> int:
@@ -95,6 +97,7 @@ class Problem:
     time_basis: List[Tuple[str, float]] = field(default_factory=list)
     sources: List[PointSource] = field(default_factory=list)
     beta: float = 1.0                 # SAT penalty factor (Sec. 5.2, 6; beta = 1 in the paper)
+    stencil: str = "narrow"           # 'narrow' (D_xx^FC, the paper's scheme) or 'wide' (D_i c D_i, Sec. 7.1)
     exact: Optional[Callable] = None  # exact solution u(block, t) -> (2, N2, N1), if known
 
     @property
