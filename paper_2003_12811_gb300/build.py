@@ -7,7 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsbp.so")
 SOURCES = ["sbp_api.cu"]
-DEPS = ["sbp_api.cu", "sbp_kernels.cuh", "sbp_adjoint.cuh", "sbp_device.cuh", "sbp_interior_march.cuh", "sbp_tables.inc"]
+DEPS = ["sbp_api.cu", "sbp_kernels.cuh", "sbp_adjoint.cuh", "sbp_device.cuh", "sbp_interior_march.cuh",
+        "sbp_batch.cuh", "sbp_wide.cuh", "sbp_tables.inc"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-shared",
               "--split-compile", "0"]   # device code compiled in parallel on all host cores

@@ -553,6 +553,7 @@ int dispatch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t s
 // the step overwrites u^{n-1} and added after it; RK4: added into the stage's operator sum before)
 template <typename T, int O>
 void layer_launch(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, bool post) {
+    if (mode == 0 && !(a.dt > 0)) return;   // tuning steps advance nothing (dt = 0)
     for (auto& hb : h->blocks) {
         if (hb.nln == 0) continue;
         const BlockDev b = make_view(h, hb);
@@ -562,7 +563,7 @@ void layer_launch(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st, b
         } else if (!post) {
             k_layer_pre<T, O><<<g, 256, 0, st>>>(b, hb.d_lnodes, hb.nln, a.cur, 1.0 / a.dt, (T*)hb.lscr);
         } else {
-            k_layer_post<T><<<g, 256, 0, st>>>(b, hb.d_lnodes, hb.nln, a.cur, a.dt2, (const T*)hb.lscr);
+            k_layer_post<T><<<g, 256, 0, st>>>(b, hb.d_lnodes, hb.nln, a.cur, a.dt, (const T*)hb.lscr);
         }
     }
 }

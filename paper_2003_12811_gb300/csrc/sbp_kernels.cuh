@@ -1084,17 +1084,30 @@ __global__ void k_layer_pre(BlockDev B, const int2* __restrict__ nodes, int n, i
     d[n + k] = k1 * T(idt);
 }
 
-// leapfrog, after the step: u^{n+1} -= dt^2 w d at the listed nodes
+// leapfrog, after the step: u^{n+1} -= dt^2 w d at the listed nodes.  The layer term belongs to the
+// right-hand side of the step, so at a face node with the dissipative Robin term (where the step
+// solved (I + dt/2 w D) u^{n+1} = rhs) the correction is M^-1 (dt^2 w d), M = I + dt/2 w D.
 template <typename T>
-__global__ void k_layer_post(BlockDev B, const int2* __restrict__ nodes, int n, int cur, double dt2, const T* __restrict__ d) {
+__global__ void k_layer_post(BlockDev B, const int2* __restrict__ nodes, int n, int cur, double dt, const T* __restrict__ d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int2 nd = nodes[k];
     const size_t plane = (size_t)B.n2 * B.pitch, gi = (size_t)nd.y * B.pitch + nd.x;
     T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - cur]);
-    const T fac = T(dt2) * reinterpret_cast<const T*>(B.w)[gi];
-    Un[gi] -= fac * d[k];
-    Un[plane + gi] -= fac * d[n + k];
+    const T wv = reinterpret_cast<const T*>(B.w)[gi];
+    const T fac = T(dt * dt) * wv;
+    T c0 = fac * d[k], c1 = fac * d[n + k];
+    T d00, d01, d11;
+    if (robin_damping_at<T>(B, nd.x, nd.y, d00, d01, d11)) {
+        const T al = T(0.5 * dt) * wv;
+        const T m00 = T(1) + al * d00, m01 = al * d01, m11 = T(1) + al * d11;
+        const T idet = T(1) / (m00 * m11 - m01 * m01);
+        const T x0 = (m11 * c0 - m01 * c1) * idet, x1 = (m00 * c1 - m01 * c0) * idet;
+        c0 = x0;
+        c1 = x1;
+    }
+    Un[gi] -= c0;
+    Un[plane + gi] -= c1;
 }
 
 // RK4 stage, before the stage kernels: -H^-1 K V_s into the point-source planes of the operator
