@@ -33,7 +33,10 @@ import workloads as W  # noqa: E402
 
 METRIC = "grid-pt updates/s"
 UNIT = "node-updates/s"
-BYTES_PER_NODE = {"fp32": 68, "fp64": 136}     # 17 words: u^n 2, u^{n-1} 2, u^{n+1} 2, c 10, 1/(rho J) 1
+# algorithmic bytes per node of a leapfrog step.  FP64 (two levels): u^n 2, u^{n-1} 2, u^{n+1} 2,
+# c 10, 1/(rho J) 1 = 17 words.  FP32 (increment form): u^n 2, d^n 2, d^{n+1} 2, u^{n+1} 2, c 10,
+# 1/(rho J) 1 = 19 words
+BYTES_PER_NODE = {"fp32": 76, "fp64": 136}
 # DRAM bytes per node of one FP32 interior launch (dram__bytes_read.sum + dram__bytes_write.sum of
 # k_interior_march<6,0> captured at 2 x 1601x801, scaled by nodes).  Set to None whenever that
 # kernel changes until it is measured again.
@@ -196,11 +199,32 @@ class _ShotPrefetch:
         self.pool.shutdown(wait=True)
 
 
-def serving_bench(fp32_rate, nshots=256, side_range=(201, 2001), tick=16, hbm_cap=16e9, sample_every=8):
+def batch_capacity(specs, nprobe=32, ticks=12, tick=16):
+    """Node-updates/s of the persistent tile-queue kernel on the first nprobe shots of the served
+    mix, all resident (setup outside the timed ticks; no shot finishes within them)."""
+    import torch
+    from paper_2003_12811_gb300.serve import GpuBatchBackend
+    be = GpuBatchBackend(max_shots=nprobe)
+    sides = []
+    for (_, side, seed, n) in specs[:nprobe]:
+        be.admit(W.shot_problem(side, seed), n, 0.3)
+        sides.append(side)
+    be.step(tick)                                       # warm-up tick (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ticks):
+        be.step(tick)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    be.close()
+    return sum(s * s for s in sides) * tick * ticks / dt
+
+
+def serving_bench(nshots=256, side_range=(201, 2001), tick=16, hbm_cap=16e9, sample_every=8):
     """Served batch (config 4 as stated): nshots single-block curvilinear shots, side ~ U(side_range),
-    steps = 2 side, Poisson arrivals at 0.8 x the FP32 capacity (fp32_rate node-updates/s over the
-    mean shot work), admission under an HBM cap (16 GB: admission binds), FP32 continuous batching
-    on the persistent tile-queue kernel.  Baselines on a uniform sample (every sample_every-th
+    steps = 2 side, Poisson arrivals at 0.8 x the serving path's capacity (the batch kernel's
+    node-updates/s on the first 32 shots of the mix, over the mean shot work), admission under an
+    HBM cap (16 GB: admission binds), FP32 continuous batching on the persistent tile-queue kernel.  Baselines on a uniform sample (every sample_every-th
     request) run one solve at a time: the plain FP64 path (the target) and the same path in FP32
     (which separates the batching gain from the precision gain); their solves/s = sample size /
     sample time.  Setup (grid, material, CFL) and the result read-back are inside every arm; the
@@ -212,7 +236,8 @@ def serving_bench(fp32_rate, nshots=256, side_range=(201, 2001), tick=16, hbm_ca
     from paper_2003_12811_gb300.serve import BatchServingEngine, GpuBatchBackend, Request, percentile
     probe = W.config4_requests(nshots, side_range, rate=1.0, steps_per_side=2.0, step_multiple=2)
     work = np.mean([side * side * n for (_, side, _, n) in probe])
-    rate = 0.8 * fp32_rate / work                       # arrivals per second
+    capacity = batch_capacity(probe)
+    rate = 0.8 * capacity / work                        # arrivals per second
     specs = W.config4_requests(nshots, side_range, rate=rate, steps_per_side=2.0, step_multiple=2)
     pre = _ShotPrefetch(specs)
     reqs = [Request(rid=i, arrival=a, problem=(lambda i=i: pre.get(i)), nsteps=n) for i, (a, _, _, n) in enumerate(specs)]
@@ -249,9 +274,9 @@ def serving_bench(fp32_rate, nshots=256, side_range=(201, 2001), tick=16, hbm_ca
     seq64, n64, t64 = one_at_a_time("fp64")
     seq32, n32, t32 = one_at_a_time("fp32")
     return {"workload": f"served batch (config 4): {nshots} shots, side U{list(side_range)}, steps = 2 side, "
-                        f"Poisson arrivals {rate:.2f}/s (0.8 x FP32 capacity), FP32, HBM cap {hbm_cap / 1e9:.0f} GB, "
+                        f"Poisson arrivals {rate:.2f}/s (0.8 x the batch kernel's capacity), FP32, HBM cap {hbm_cap / 1e9:.0f} GB, "
                         f"persistent tile-queue kernel, ticks of {tick} graph-replayed steps",
-            "solves_per_s": nshots / served, "makespan_s": served,
+            "solves_per_s": nshots / served, "makespan_s": served, "batch_capacity_node_updates_per_s": capacity,
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
             "node_updates_per_s": node_updates / served,
             "fp64_one_at_a_time_solves_per_s": seq64, "fp32_one_at_a_time_solves_per_s": seq32,
@@ -337,8 +362,9 @@ def adjoint_bench(n=1001, nsteps=2000, prec="fp32"):
 # (10) and writes U_{s+1}, V, S_u, S_v (8): 31 words; four stages per step
 RK4_WORDS_PER_STAGE = 31
 # the wide operator's two passes move: fluxes u (2) + c (10) -> G (4); divergence G (4), 1/(rho J) (1),
-# u^n (2), u^{n-1} (2) -> u^{n+1} (2): 27 words, against the 17 of a fused step
-WIDE_WORDS_IMPLEMENTED = 27
+# u^n (2), u^{n-1} (2) -> u^{n+1} (2): 27 words (FP32 increment form: d^n (2) in place of u^{n-1},
+# d^{n+1} (2) written as well: 29), against the 17 (19) of a fused step
+WIDE_WORDS_IMPLEMENTED = {"fp32": 29, "fp64": 27}
 
 
 def variant_bench(P, prec, nsteps=100):
@@ -388,8 +414,8 @@ def variant_bench(P, prec, nsteps=100):
     out["wide"] = {"node_updates_per_s": nodes / (ms / 1e3), "ms_per_step": ms,
                    "algorithmic_GBs": bpn * nodes / (ms / 1e3) / 1e9,
                    "frac_of_peak_algorithmic": bpn * nodes / (ms / 1e3) / 1e9 / peak,
-                   "implemented_words_per_node": WIDE_WORDS_IMPLEMENTED,
-                   "implemented_GBs": WIDE_WORDS_IMPLEMENTED * es * nodes / (ms / 1e3) / 1e9,
+                   "implemented_words_per_node": WIDE_WORDS_IMPLEMENTED[prec],
+                   "implemented_GBs": WIDE_WORDS_IMPLEMENTED[prec] * es * nodes / (ms / 1e3) / 1e9,
                    "peak_source": src, "steps": nsteps}
     return out
 
@@ -454,6 +480,45 @@ def accuracy_table():
         table[name] = {"dt": dt, "steps": rows, "seconds": time.perf_counter() - t0}
         torch.cuda.synchronize()
     return table
+
+
+def convergence_table(Ns=(41, 81, 161, 321), T=0.5, cfl=0.25):
+    """Sec. 7.1 convergence study on the GPU: the manufactured solution and material on two blocks
+    with an interface, traction and displacement faces, to time T; the l2 error (the scheme's J H
+    norm, FP64 on the device) against the exact solution and the observed rate between successive
+    grids, for RK4 (FP64, the paper's integrator) and leapfrog (FP64 and FP32)."""
+    import torch
+    from paper_2003_12811_gb300 import Solver
+    from paper_2003_12811_gb300.binding import FIELD_CUR
+    kinds = ("robin", "displacement", "robin", "displacement")
+    out = {}
+    for order in (2, 4, 6):
+        rows = {}
+        for scheme in ("rk4 fp64", "leapfrog fp64", "leapfrog fp32"):
+            errs = []
+            for N in Ns:
+                P = W.mms_problem(N, order, kinds=kinds, two_blocks=True)
+                prec = scheme.split()[1]
+                S = Solver(P, prec)
+                dt = S.suggest_dt(cfl)
+                n = int(math.ceil(T / dt))
+                dt = T / n
+                if scheme.startswith("rk4"):
+                    v0 = [np.stack([-W.MMS_W[L] * np.cos(W.MMS_K[L, 0] * b.X[0] + W.MMS_K[L, 1] * b.X[1])
+                                    for L in range(2)]) for b in P.blocks]
+                    S.sbp_set_state_rk4([P.exact(b, 0.0) for b in P.blocks], v0, 0.0)
+                    S.sbp_step_rk4(n, dt)
+                else:
+                    S.set_state([P.exact(b, -dt) for b in P.blocks], [P.exact(b, 0.0) for b in P.blocks], 0.0)
+                    S.sbp_step(n, dt)
+                e2, _ = S.sbp_l2_diff(FIELD_CUR, [P.exact(b, S.sbp_get_time()) for b in P.blocks])
+                S.close()
+                errs.append(math.sqrt(e2))
+            rates = [math.log(errs[k] / errs[k + 1]) / math.log((Ns[k + 1] - 1) / (Ns[k] - 1)) for k in range(len(Ns) - 1)]
+            rows[scheme] = {"N": list(Ns), "l2_error": errs, "rate": rates}
+        out[f"order {order}"] = rows
+        torch.cuda.synchronize()
+    return out
 
 
 def replica_times(times, world):
@@ -537,7 +602,7 @@ def main():
 
     prec = args.precision
     if args.accuracy:
-        print(json.dumps({"accuracy": accuracy_table()}), flush=True)
+        print(json.dumps({"accuracy": accuracy_table(), "convergence": convergence_table()}), flush=True)
         return 0
     if args.adjoint_only:
         print(json.dumps(adjoint_bench(nsteps=args.adjoint_steps, prec=prec)), flush=True)
@@ -632,7 +697,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_variants:
         line["variants"] = variant_bench(P, prec)
     if rank == 0 and world == 1 and not args.no_serving:
-        line["serving"] = serving_bench(value)
+        line["serving"] = serving_bench()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_bench(nsteps=args.adjoint_steps, prec=prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -48,6 +48,7 @@ struct HostBlock {
     int n1 = 0, n2 = 0, pitch = 0;
     double h1 = 0, h2 = 0;
     void* u[2] = {nullptr, nullptr};
+    void* du = nullptr;       // FP32: the leapfrog increment u^n - u^{n-1} (2 planes)
     void* c = nullptr;
     void* w = nullptr;
     void* jf = nullptr;
@@ -245,6 +246,7 @@ BlockDev make_view(const sbp_handle* h, const HostBlock& hb) {
     b.ih2f = (float)b.ih2;
     b.u[0] = hb.u[0];
     b.u[1] = hb.u[1];
+    b.du = hb.du;
     b.c = hb.c;
     b.w = hb.w;
     b.jf = hb.jf;
@@ -295,6 +297,7 @@ BlockDev make_view_adj(const sbp_handle* h, const HostBlock& hb) {
     BlockDev b = make_view(h, hb);
     b.u[0] = hb.psi[0];
     b.u[1] = hb.psi[1];
+    b.du = nullptr;             // the adjoint fields step from their two levels
     b.smaps = hb.d_smaps ? hb.d_smaps + 3 : nullptr;
     return b;
 }
@@ -314,6 +317,14 @@ int sync_views(sbp_handle* h) {
 }
 
 inline unsigned grid_for(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+// the FP32 leapfrog increment of a block re-formed from its two levels (after the levels were
+// written by something other than a leapfrog step)
+void refresh_increment(sbp_handle* h, const HostBlock& hb, cudaStream_t st) {
+    if (!hb.du) return;
+    const long long n = 2LL * hb.n2 * hb.pitch;
+    k_diff_levels<<<grid_for(n), 256, 0, st>>>((float*)hb.du, (const float*)hb.u[h->cur], (const float*)hb.u[1 - h->cur], n);
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -463,7 +474,8 @@ int launch_operator(sbp_handle* h, const StepArgs& a, int mode, cudaStream_t st,
             mmul.start[mmul.nb] = tiles;
             ProfScope ps(h, 0, ist, 1);
             constexpr size_t msm = MarchCfg<O>::BYTES;
-            if (mode == 0) k_interior_march_multi<O, 0><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
+            if (mode == 0 && !adj) k_interior_march_multi<O, 3><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
+            else if (mode == 0) k_interior_march_multi<O, 0><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
             else if (mode == 2) k_interior_march_multi<O, 2><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
             else k_interior_march_multi<O, 1><<<tiles, MTHREADS, msm, ist>>>(mmul, a, h->d_err);
             mmul = MarchMulti{};
@@ -603,6 +615,7 @@ template <typename T, int O> void set_smem_attr() {
         cudaFuncSetAttribute(k_interior_march<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march<O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march_multi<O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
+        cudaFuncSetAttribute(k_interior_march_multi<O, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march_multi<O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
         cudaFuncSetAttribute(k_interior_march_multi<O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<O>::BYTES);
     }
@@ -986,6 +999,10 @@ int sbp_grid_create(const sbp_grid_desc* desc, sbp_handle** out) {
         const size_t es = h->esize;
         hb.u[0] = h->dalloc(2 * plane * es);
         hb.u[1] = h->dalloc(2 * plane * es);
+        if (h->precision == SBP_FP32) {
+            hb.du = h->dalloc(2 * plane * es);
+            if (!hb.du) return cleanup(SBP_E_OOM, "device allocation failed for block " + std::to_string(b));
+        }
         hb.c = h->dalloc(10 * plane * es);
         hb.w = h->dalloc(plane * es);
         hb.r = h->dalloc(2 * plane * es);
@@ -1391,17 +1408,20 @@ int sbp_set_state(sbp_handle* h, int block, const double* u_prev, const double* 
     if (block < 0 || block >= h->nblocks || !u_prev || !u_cur) return h->fail(SBP_E_INVALID_ARG, "bad arguments");
     HostBlock& hb = h->blocks[block];
     const size_t n = (size_t)hb.n1 * hb.n2;
-    double* tmp = (double*)h->staging(2 * n * sizeof(double));
+    double* tmp = (double*)h->staging(4 * n * sizeof(double));
     if (!tmp) return h->fail(SBP_E_OOM, "state staging");
     const double* src[2] = {u_prev, u_cur};
     const int dst_idx[2] = {1 - h->cur, h->cur};
     for (int k = 0; k < 2; ++k) {
-        if (cudaMemcpy(tmp, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        double* tk = tmp + 2 * n * k;
+        if (cudaMemcpy(tk, src[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
             return h->fail(SBP_E_CUDA, "state upload failed");
         }
-        if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
-        else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)hb.u[dst_idx[k]], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+        if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)hb.u[dst_idx[k]], tk, hb.n1, hb.n2, hb.pitch, 2, nullptr);
+        else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)hb.u[dst_idx[k]], tk, hb.n1, hb.n2, hb.pitch, 2, nullptr);
     }
+    // FP32 increment u^n - u^{n-1}: formed from the FP64 levels and rounded once
+    if (hb.du) k_diff_to_pitched<<<grid_for(2LL * n), 256>>>((float*)hb.du, tmp + 2 * n, tmp, hb.n1, hb.n2, hb.pitch, 2);
     cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
     h->t = t;
@@ -1451,8 +1471,9 @@ int sbp_set_state_device(sbp_handle* h, int block, const void* u_prev, const voi
         if (cudaMemcpy2DAsync(dst[k], hb.pitch * es, src[k], (size_t)pitch * es, hb.n1 * es, 2 * (size_t)hb.n2,
                               cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return h->fail(SBP_E_CUDA, "device state copy failed");
+    refresh_increment(h, hb, st);
     h->t = t;
-    return SBP_OK;
+    return check_cuda(h, "device state copy");
 }
 
 int sbp_get_field_device(sbp_handle* h, int block, int which, void* dst, long long pitch, void* stream) {
@@ -1515,6 +1536,7 @@ int sbp_set_state_rk4(sbp_handle* h, int block, const double* u, const double* v
         if (h->precision == SBP_FP64) k_to_pitched<double><<<grid_for(2LL * n), 256>>>((double*)dst[k], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
         else k_to_pitched<float><<<grid_for(2LL * n), 256>>>((float*)dst[k], tmp, hb.n1, hb.n2, hb.pitch, 2, nullptr);
     }
+    refresh_increment(h, hb, 0);   // a later leapfrog step continues from the two state buffers
     cudaError_t e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return h->fail(SBP_E_CUDA, "state upload");
     h->t = t;
@@ -1549,7 +1571,8 @@ int sbp_step_rk4(sbp_handle* h, int nsteps, double dt, void* stream) {
         }
         h->t += dt;
     }
-    return SBP_OK;
+    for (auto& hb : h->blocks) refresh_increment(h, hb, st);
+    return check_cuda(h, "RK4 steps");
 }
 
 int sbp_apply(sbp_handle* h, int with_data, double t) {
@@ -1885,8 +1908,10 @@ int sbp_grid_footprint(const sbp_grid_desc* desc, long long* bytes_out) {
         if (bd.n1 < 2 || bd.n2 < 2) return SBP_E_INVALID_ARG;
         const long long pitch = (bd.n1 + 31) / 32 * 32;
         const long long plane = (long long)bd.n2 * pitch;
-        // u (2 x 2), c (10), w (1), r (2) in the field precision; X (2), G (4), J (1) in FP64
+        // u (2 x 2), c (10), w (1), r (2) in the field precision, the FP32 leapfrog increment (2);
+        // X (2), G (4), J (1) in FP64
         total += al(2 * plane * es) * 2 + al(10 * plane * es) + al(plane * es) + al(2 * plane * es);
+        if (desc->precision == SBP_FP32) total += al(2 * plane * es);
         total += al(2 * plane * 8) + al(4 * plane * 8) + al(plane * 8);
         // closure matrices of D_xx^FC along x1 and x2, strip-tile tensor maps
         if (desc->order == 2 || desc->order == 4 || desc->order == 6)
@@ -1941,10 +1966,11 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
     a.with_data = 0;
     a.dt2 = 0.0;
     a.dt2f = 0.f;
+    // (u^{n-1}, and the FP32 increment, which the timed steps rewrite with its own value)
     std::vector<void*> keep;
     for (auto& hb : h->blocks) {
         const size_t bytes = 2 * (size_t)hb.n2 * hb.pitch * h->esize;
-        void* p = h->dalloc(bytes);
+        void* p = h->dalloc(hb.du ? 2 * bytes : bytes);
         if (!p) {
             for (void* q : keep) h->dfree(q);
             cudaEventDestroy(e0);
@@ -1952,7 +1978,8 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
             return h->fail(SBP_E_OOM, "autotune state copy");
         }
         keep.push_back(p);
-        if (cudaMemcpy(p, hb.u[1 - h->cur], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+        if (cudaMemcpy(p, hb.u[1 - h->cur], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            (hb.du && cudaMemcpy((unsigned char*)p + bytes, hb.du, bytes, cudaMemcpyDeviceToDevice) != cudaSuccess)) {
             for (void* q : keep) h->dfree(q);
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
@@ -1963,7 +1990,9 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
     auto put_back = [&]() {
         for (size_t b = 0; b < h->blocks.size(); ++b) {
             const HostBlock& hb = h->blocks[b];
-            if (cudaMemcpy(hb.u[1 - h->cur], keep[b], 2 * (size_t)hb.n2 * hb.pitch * h->esize, cudaMemcpyDeviceToDevice) != cudaSuccess)
+            const size_t bytes = 2 * (size_t)hb.n2 * hb.pitch * h->esize;
+            if (cudaMemcpy(hb.u[1 - h->cur], keep[b], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+                (hb.du && cudaMemcpy(hb.du, (unsigned char*)keep[b] + bytes, bytes, cudaMemcpyDeviceToDevice) != cudaSuccess))
                 restored = false;
             h->dfree(keep[b]);
         }
@@ -2139,15 +2168,17 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     GradScratch sc(h);
     std::vector<void*> ck(nb), seg(nb), pseg(nb), fin(nb);
     std::vector<size_t> lvl_bytes(nb);
+    // a checkpoint holds (u_{n-1}, u_n) and, for FP32, the leapfrog increment
+    const int nck = h->precision == SBP_FP32 ? 3 : 2;
     std::vector<GradDev> grads(nb);
     for (int b = 0; b < nb; ++b) {
         HostBlock& hb = h->blocks[b];
         const size_t plane = (size_t)hb.n2 * hb.pitch;
         lvl_bytes[b] = 2 * plane * es;
-        ck[b] = sc.get((size_t)nseg * 2 * lvl_bytes[b]);
+        ck[b] = sc.get((size_t)nseg * nck * lvl_bytes[b]);
         seg[b] = sc.get((size_t)(K + 2) * lvl_bytes[b]);
         pseg[b] = sc.get((size_t)K * lvl_bytes[b]);
-        fin[b] = sc.get(2 * lvl_bytes[b]);
+        fin[b] = sc.get(nck * lvl_bytes[b]);
         GradDev& G = grads[b];
         G.seg = seg[b];
         G.pseg = pseg[b];
@@ -2174,15 +2205,33 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     };
     auto lvl_ptr = [&](std::vector<void*>& base, int b, size_t l) { return (unsigned char*)base[b] + l * lvl_bytes[b]; };
+    // the state (u_{n-1}, u_n[, increment]) of every block to / from slot `slot` of `base`
+    auto save_state = [&](std::vector<void*>& base, size_t slot) {
+        for (int b = 0; b < nb; ++b) {
+            const HostBlock& hb = h->blocks[b];
+            if (!copy(lvl_ptr(base, b, nck * slot), hb.u[1 - h->cur], lvl_bytes[b]) ||
+                !copy(lvl_ptr(base, b, nck * slot + 1), hb.u[h->cur], lvl_bytes[b]) ||
+                (hb.du && !copy(lvl_ptr(base, b, nck * slot + 2), hb.du, lvl_bytes[b])))
+                return false;
+        }
+        return true;
+    };
+    auto load_state = [&](std::vector<void*>& base, size_t slot) {
+        for (int b = 0; b < nb; ++b) {
+            const HostBlock& hb = h->blocks[b];
+            if (!copy(hb.u[1 - h->cur], lvl_ptr(base, b, nck * slot), lvl_bytes[b]) ||
+                !copy(hb.u[h->cur], lvl_ptr(base, b, nck * slot + 1), lvl_bytes[b]) ||
+                (hb.du && !copy(hb.du, lvl_ptr(base, b, nck * slot + 2), lvl_bytes[b])))
+                return false;
+        }
+        return true;
+    };
     // forward pass: checkpoints (u_{n-1}, u_n) at the start of every segment, receiver traces
     std::vector<double> ck_t(nseg);
     for (int n = 0; n < nsteps; ++n) {
         if (n % K == 0) {
             const int c = n / K;
-            for (int b = 0; b < nb; ++b)
-                if (!copy(lvl_ptr(ck, b, 2 * c), h->blocks[b].u[1 - h->cur], lvl_bytes[b]) ||
-                    !copy(lvl_ptr(ck, b, 2 * c + 1), h->blocks[b].u[h->cur], lvl_bytes[b]))
-                    return h->fail(SBP_E_CUDA, "checkpoint copy");
+            if (!save_state(ck, c)) return h->fail(SBP_E_CUDA, "checkpoint copy");
             ck_t[c] = h->t;
         }
         rc = step_once(h, dt, st);
@@ -2191,10 +2240,7 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     }
     const int cur_final = h->cur;
     const double t_final = h->t;
-    for (int b = 0; b < nb; ++b)
-        if (!copy(lvl_ptr(fin, b, 0), h->blocks[b].u[1 - h->cur], lvl_bytes[b]) ||
-            !copy(lvl_ptr(fin, b, 1), h->blocks[b].u[h->cur], lvl_bytes[b]))
-            return h->fail(SBP_E_CUDA, "final state copy");
+    if (!save_state(fin, 0)) return h->fail(SBP_E_CUDA, "final state copy");
     // misfit: 1/2 dt sum (traces - observed)^2
     {
         ProfScope ps(h, 7, st, 2);
@@ -2219,11 +2265,10 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     for (int s = nseg - 1; s >= 0; --s) {
         const int a0 = s * K, a1 = std::min(a0 + K, nsteps) - 1;   // 0-based steps of the segment
         // recompute the segment's levels u_{a0} .. u_{a1+2} from its checkpoint
+        if (!load_state(ck, s)) return h->fail(SBP_E_CUDA, "checkpoint restore");
         for (int b = 0; b < nb; ++b) {
-            if (!copy(h->blocks[b].u[1 - h->cur], lvl_ptr(ck, b, 2 * s), lvl_bytes[b]) ||
-                !copy(h->blocks[b].u[h->cur], lvl_ptr(ck, b, 2 * s + 1), lvl_bytes[b]) ||
-                !copy(lvl_ptr(seg, b, 0), lvl_ptr(ck, b, 2 * s), lvl_bytes[b]) ||
-                !copy(lvl_ptr(seg, b, 1), lvl_ptr(ck, b, 2 * s + 1), lvl_bytes[b]))
+            if (!copy(lvl_ptr(seg, b, 0), lvl_ptr(ck, b, (size_t)nck * s), lvl_bytes[b]) ||
+                !copy(lvl_ptr(seg, b, 1), lvl_ptr(ck, b, (size_t)nck * s + 1), lvl_bytes[b]))
                 return h->fail(SBP_E_CUDA, "checkpoint restore");
         }
         h->t = ck_t[s];
@@ -2278,10 +2323,7 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     // leave the state where the forward pass ended
     h->cur = cur_final;
     h->t = t_final;
-    for (int b = 0; b < nb; ++b)
-        if (!copy(h->blocks[b].u[1 - h->cur], lvl_ptr(fin, b, 0), lvl_bytes[b]) ||
-            !copy(h->blocks[b].u[h->cur], lvl_ptr(fin, b, 1), lvl_bytes[b]))
-            return h->fail(SBP_E_CUDA, "final state restore");
+    if (!load_state(fin, 0)) return h->fail(SBP_E_CUDA, "final state restore");
     if (cudaMemcpy(misfit, d_phi, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
         return h->fail(SBP_E_CUDA, "misfit download");
     rc = check_cuda(h, "misfit gradient");

@@ -1,4 +1,5 @@
-// Persistent tile-queue step over a batch of resident shots (FP32, one block per shot).
+// Persistent tile-queue step over a batch of resident shots (FP32 in increment form, one block per
+// shot).
 //
 // One launch advances every active shot of the batch by one leapfrog step.  Its CTAs (a fixed
 // number per SM) pull work items from one device-wide queue -- an interior tile of a shot (128
@@ -51,6 +52,20 @@ template <int O> constexpr size_t batch_smem_bytes() {
                                                                         : StripTile<O>::template bytes<float>();
 }
 
+// an interior item and a strip item, each compiled as a function of its own so that their
+// registers are allocated apart from each other and from the queue loop
+template <int O>
+__device__ __noinline__ bool batch_interior_item(const BatchShot& sh, int tile, const StepArgs& a, int* err,
+                                                 unsigned char* smem) {
+    return march_tile<O, 3>(sh.maps, sh.view, a, sh.rows, tile, err, smem);
+}
+
+template <int O>
+__device__ __noinline__ bool batch_strip_item(const BatchShot& sh, int tile, const StepArgs& a, int* err,
+                                              unsigned char* smem) {
+    return strip_tile_body<float, O, 0, MTHREADS>(&sh.view, sh.tiles[tile], a, sh.beta, err, sh.ssrc, sh.spar, smem);
+}
+
 template <int O>
 __global__ void __launch_bounds__(MTHREADS, 4) k_batch_step(BatchHead* __restrict__ H, int* err) {
     extern __shared__ __align__(128) unsigned char batch_smem[];
@@ -75,9 +90,8 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_batch_step(BatchHead* __restric
         a.dt2 = sh.dt2;
         a.dt2f = sh.dt2f;
         bool ok;
-        if (w.y == 0) ok = march_tile<O, 0>(sh.maps, sh.view, a, sh.rows, w.z, err, batch_smem);
-        else ok = strip_tile_body<float, O, 0, MTHREADS>(&sh.view, sh.tiles[w.z], a, sh.beta, err, sh.ssrc, sh.spar,
-                                                        batch_smem);
+        if (w.y == 0) ok = batch_interior_item<O>(sh, w.z, a, err, batch_smem);
+        else ok = batch_strip_item<O>(sh, w.z, a, err, batch_smem);
         __syncthreads();                                    // the next item reuses the shared memory
         if (!ok) break;                                     // uniform: set by a CTA-wide vote
     }
@@ -96,6 +110,7 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_batch_step(BatchHead* __restric
         a.t = st.t;
         const size_t plane = (size_t)sh.view.n2 * sh.view.pitch;
         float* Un = reinterpret_cast<float*>(sh.view.u[1 - st.cur]);
+        float* DU = reinterpret_cast<float*>(sh.view.du);
         const float* Wv = reinterpret_cast<const float*>(sh.view.w);
         for (int k = tx; k < sh.nisrc; k += blockDim.x) {     // as k_sources (leapfrog mode)
             const SrcNode nd = sh.isrc[k];
@@ -103,6 +118,8 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_batch_step(BatchHead* __restric
             const double fac = sh.dt2 * (double)Wv[nd.gi] * Wt;
             atomicAdd(Un + nd.gi, float(fac * nd.wt0));
             atomicAdd(Un + plane + nd.gi, float(fac * nd.wt1));
+            atomicAdd(DU + nd.gi, float(fac * nd.wt0));
+            atomicAdd(DU + plane + nd.gi, float(fac * nd.wt1));
         }
     }
     __syncthreads();

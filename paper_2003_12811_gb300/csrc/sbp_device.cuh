@@ -264,6 +264,7 @@ struct BlockDev {
     const void* w;            // 1/(rho J)
     const void* jf;           // J f harmonic planes (2 x K) or null
     void* r;                  // operator output (apply mode), 2 planes
+    void* du;                 // FP32 leapfrog: the increment u^n - u^{n-1} (2 planes), else null
     const double* X;          // coordinates (2 planes)
     double* G;                // metric dX_I/dx_i (4 planes, [2 i + I])
     double* J;                // Jacobian
@@ -369,19 +370,6 @@ __device__ __forceinline__ bool robin_damping_at(const BlockDev& B, int i1, int 
     return any;
 }
 
-// leapfrog update of a node with the dissipative Robin term taken with the centred velocity
-// (u^{n+1} - u^{n-1}) / (2 dt): (I + a D) u^{n+1} = nu + a D u^{n-1}, a = dt w / 2, where nu is the
-// undamped update 2 u^n - u^{n-1} + dt^2 w r; D symmetric positive semidefinite, so I + a D is
-// invertible
-template <typename T>
-__device__ __forceinline__ void robin_damped_update(T a, T d00, T d01, T d11, T up0, T up1, T& nu0, T& nu1) {
-    const T b0 = nu0 + a * (d00 * up0 + d01 * up1), b1 = nu1 + a * (d01 * up0 + d11 * up1);
-    const T m00 = T(1) + a * d00, m01 = a * d01, m11 = T(1) + a * d11;
-    const T idet = T(1) / (m00 * m11 - m01 * m01);
-    nu0 = (m11 * b0 - m01 * b1) * idet;
-    nu1 = (m00 * b1 - m01 * b0) * idet;
-}
-
 // the stage velocity of an RK4 stage at node gi (v for the first stage, V afterwards)
 template <typename T>
 __device__ __forceinline__ void rk4_stage_velocity(const BlockDev& B, const StepArgs& a, size_t gi, size_t plane, T& v0, T& v1) {
@@ -404,6 +392,45 @@ template <typename T> __device__ __forceinline__ T facT(const FaceDev& F, int d)
 }
 template <typename T> __device__ __forceinline__ T dt2T(const StepArgs& a) {
     if constexpr (sizeof(T) == 4) return a.dt2f; else return a.dt2;
+}
+
+// leapfrog step of one node, u^{n+1} = 2 u^n - u^{n-1} + dt^2 w r (w = 1/(rho J)), written in
+// increment form: d^{n+1} = d^n + dt^2 w r, u^{n+1} = u^n + d^{n+1}, d^n = u^n - u^{n-1}.  With
+// B.du (the FP32 state) the increment is a field of its own, so dt^2 w r is added to a number of
+// the size of u^n - u^{n-1} instead of u^n and is not lost below half an ulp of u^n (for dt small
+// against h it is of that size); without it (FP64, adjoint fields) d^n is formed from the levels.
+// On a face node with the dissipative Robin term, taken with the centred velocity
+// (u^{n+1} - u^{n-1}) / (2 dt), the increment solves the 2 x 2 system
+// (I + al D) d^{n+1} = (I - al D) d^n + dt^2 w r, al = dt w / 2 (D from robin_damping_at).
+template <typename T>
+__device__ __forceinline__ void leapfrog_store(const BlockDev& B, const StepArgs& a, size_t gi, size_t plane, T u0, T u1,
+                                               T wv, T r0, T r1, bool damped, T dd00, T dd01, T dd11) {
+    T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+    T* __restrict__ DU = reinterpret_cast<T*>(B.du);
+    T v0, v1;
+    if (DU) {
+        v0 = DU[gi];
+        v1 = DU[gi + plane];
+    } else {
+        v0 = u0 - Un[gi];
+        v1 = u1 - Un[gi + plane];
+    }
+    const T f = dt2T<T>(a) * wv;
+    T d0 = v0 + f * r0, d1 = v1 + f * r1;
+    if (damped) {
+        const T al = T(0.5 * a.dt) * wv;
+        const T b0 = d0 - al * (dd00 * v0 + dd01 * v1), b1 = d1 - al * (dd01 * v0 + dd11 * v1);
+        const T m00 = T(1) + al * dd00, m01 = al * dd01, m11 = T(1) + al * dd11;
+        const T idet = T(1) / (m00 * m11 - m01 * m01);
+        d0 = (m11 * b0 - m01 * b1) * idet;
+        d1 = (m00 * b1 - m01 * b0) * idet;
+    }
+    Un[gi] = u0 + d0;
+    Un[gi + plane] = u1 + d1;
+    if (DU) {
+        DU[gi] = d0;
+        DU[gi + plane] = d1;
+    }
 }
 
 

@@ -16,7 +16,9 @@
 //  * the x-direction fluxes g1 = c_1j2l D_2 u_l of the current row are exchanged through a
 //    double-buffered shared row (one barrier per row);
 //  * 1/(rho J) and u^{n-1} of the output row are loaded from global memory two rows ahead;
-//  * MODE 0: leapfrog update; 1: operator output r; 2: RK4 stage (rk4_store);
+//  * MODE 0: leapfrog update from the two levels; 3: leapfrog update in increment form (the
+//    FP32 state: d^{n+1} = d^n + dt^2 w r, u^{n+1} = u^n + d^{n+1}, see leapfrog_store);
+//    1: operator output r; 2: RK4 stage (rk4_store);
 //  * the two components of the displacement and of every flux are carried as float2 and
 //    combined with packed FP32x2 instructions (one issue slot for both).
 #pragma once
@@ -162,16 +164,17 @@ __device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BlockDev
     // threads 0..2Q-1 also follow one halo column each (x0-Q..x0-1, x0+128..x0+127+Q) for g1
     const int hc = tx < Q ? MXOFF - Q + tx : MXOFF + MTHREADS + (tx - Q);
     const bool halo = tx < 2 * Q;
-    // prefetched 1/(rho J) and u^{n-1}: *_c for the row being output, *_n for the next row
+    // prefetched 1/(rho J) and u^{n-1} (MODE 3: the increment d^n): *_c for the row being output,
+    // *_n for the next row
     float w_c = 0.f, w_n = 0.f;
     float2 up_c = make_float2(0.f, 0.f), up_n = make_float2(0.f, 0.f);
     auto load_row = [&](int r, float& wv, float2& v) {
         if (MODE != 1 && col_ok && r >= ys && r < ye) {
             const size_t gi = (size_t)r * P + gx;
             wv = __ldg(reinterpret_cast<const float*>(B.w) + gi);
-            if (MODE == 0) {
-                const float* Un = reinterpret_cast<const float*>(B.u[1 - a.cur]);
-                v = make_float2(Un[gi], Un[gi + plane]);
+            if (MODE == 0 || MODE == 3) {
+                const float* Up = reinterpret_cast<const float*>(MODE == 3 ? B.du : B.u[1 - a.cur]);
+                v = make_float2(Up[gi], Up[gi + plane]);
             }
         }
     };
@@ -358,6 +361,15 @@ __device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BlockDev
             const float2 nu = ffma2(bc2(a.dt2f * w_c), make_float2(r0, r1), fsub2(fadd2(uc, uc), up_c));
             Un[gi] = nu.x;
             Un[gi + plane] = nu.y;
+        } else if (MODE == 3) {
+            float* __restrict__ Un = reinterpret_cast<float*>(B.u[1 - a.cur]);
+            float* __restrict__ DU = reinterpret_cast<float*>(B.du);
+            const float2 d = ffma2(bc2(a.dt2f * w_c), make_float2(r0, r1), up_c);
+            const float2 nu = fadd2(uc, d);
+            Un[gi] = nu.x;
+            Un[gi + plane] = nu.y;
+            DU[gi] = d.x;
+            DU[gi + plane] = d.y;
         } else if (MODE == 2) {
             rk4_store<float>(B, a, gi, plane, w_c, r0, r1);
         } else {

@@ -925,14 +925,8 @@ __device__ __forceinline__ bool strip_tile_body(const BlockDev* __restrict__ blo
         T dd00, dd01, dd11;
         const bool damped = MODE != 1 && robin_damping_at<T>(B, i1, i2, dd00, dd01, dd11);
         if (MODE == 0) {
-            T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
-            const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
-            const T up0 = Un[gi], up1 = Un[gi + plane];
-            T nu0 = T(2) * at(0, i1, i2) - up0 + dt2 * wv * r0;
-            T nu1 = T(2) * at(1, i1, i2) - up1 + dt2 * wv * r1;
-            if (damped) robin_damped_update<T>(T(0.5 * a.dt) * wv, dd00, dd01, dd11, up0, up1, nu0, nu1);
-            Un[gi] = nu0;
-            Un[gi + plane] = nu1;
+            leapfrog_store<T>(B, a, gi, plane, at(0, i1, i2), at(1, i1, i2), reinterpret_cast<const T*>(B.w)[gi], r0, r1,
+                              damped, dd00, dd01, dd11);
         } else if (MODE == 2) {
             if (damped) {
                 T v0, v1;
@@ -975,10 +969,16 @@ __global__ void k_sources(const BlockDev* __restrict__ blocks, const SrcNode* __
     const BlockDev& B = blocks[nd.block];
     const size_t plane = (size_t)B.n2 * B.pitch;
     if (MODE == 0) {
+        // the source's share of dt^2 w r, into u^{n+1} and, in increment form, into d^{n+1}
         T* Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
+        T* DU = reinterpret_cast<T*>(B.du);
         const double fac = a.dt2 * (double)reinterpret_cast<const T*>(B.w)[nd.gi] * Wt;
         atomicAdd(Un + nd.gi, T(fac * nd.wt0));
         atomicAdd(Un + plane + nd.gi, T(fac * nd.wt1));
+        if (DU) {
+            atomicAdd(DU + nd.gi, T(fac * nd.wt0));
+            atomicAdd(DU + plane + nd.gi, T(fac * nd.wt1));
+        }
     } else if (MODE == 2) {
         // RK4 stage: J f at the node into the (otherwise zero) operator-output planes, which the
         // stage's kernels add to the operator sum before forming the acceleration (rk4_store)
@@ -1075,16 +1075,17 @@ __global__ void k_layer_pre(BlockDev B, const int2* __restrict__ nodes, int n, i
     const size_t plane = (size_t)B.n2 * B.pitch;
     const T* __restrict__ U = reinterpret_cast<const T*>(B.u[cur]);
     const T* __restrict__ Up = reinterpret_cast<const T*>(B.u[1 - cur]);
+    const T* __restrict__ DU = reinterpret_cast<const T*>(B.du);
     T k0, k1;
     layer_kv<T, O>(B, nd.x, nd.y, [&](int j1, int j2, int c) {
         const size_t g = (size_t)c * plane + (size_t)j2 * B.pitch + j1;
-        return U[g] - Up[g];
+        return DU ? DU[g] : U[g] - Up[g];
     }, k0, k1);
     d[k] = k0 * T(idt);
     d[n + k] = k1 * T(idt);
 }
 
-// leapfrog, after the step: u^{n+1} -= dt^2 w d at the listed nodes.  The layer term belongs to the
+// leapfrog, after the step: u^{n+1} -= dt^2 w d at the listed nodes (and d^{n+1} in increment form).  The layer term belongs to the
 // right-hand side of the step, so at a face node with the dissipative Robin term (where the step
 // solved (I + dt/2 w D) u^{n+1} = rhs) the correction is M^-1 (dt^2 w d), M = I + dt/2 w D.
 template <typename T>
@@ -1108,6 +1109,11 @@ __global__ void k_layer_post(BlockDev B, const int2* __restrict__ nodes, int n, 
     }
     Un[gi] -= c0;
     Un[plane + gi] -= c1;
+    if (B.du) {
+        T* __restrict__ DU = reinterpret_cast<T*>(B.du);
+        DU[gi] -= c0;
+        DU[plane + gi] -= c1;
+    }
 }
 
 // RK4 stage, before the stage kernels: -H^-1 K V_s into the point-source planes of the operator
@@ -1243,6 +1249,25 @@ __global__ void k_scale_copy(T* out, const double* __restrict__ in, const double
 }
 
 // pitched plane <-> dense double (optionally multiplied by the block's J)
+// FP32 leapfrog increment from two dense FP64 levels: dst = (float)(cur - prev), rounded once
+__global__ void k_diff_to_pitched(float* dst, const double* __restrict__ cur, const double* __restrict__ prev, int n1,
+                                  int n2, int pitch, int planes) {
+    const long long n = (long long)n1 * n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * planes) return;
+    const int p = (int)(t / n);
+    const long long node = t - (long long)p * n;
+    const int i2 = (int)(node / n1), i1 = (int)(node - (long long)i2 * n1);
+    dst[(size_t)p * n2 * pitch + (size_t)i2 * pitch + i1] = (float)(cur[t] - prev[t]);
+}
+
+// FP32 leapfrog increment from the two levels held in the state buffers (n elements each)
+__global__ void k_diff_levels(float* __restrict__ du, const float* __restrict__ cur, const float* __restrict__ prev,
+                              long long n) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) du[t] = cur[t] - prev[t];
+}
+
 template <typename T>
 __global__ void k_to_pitched(T* dst, const double* __restrict__ src, int n1, int n2, int pitch, int planes,
                              const double* __restrict__ Jmul) {

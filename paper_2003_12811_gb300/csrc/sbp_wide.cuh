@@ -87,14 +87,8 @@ __global__ void k_wide_div(BlockDev B, StepArgs a, const T* __restrict__ G) {
     const bool damped = MODE != 1 && robin_damping_at<T>(B, i1, i2, dd00, dd01, dd11);
     if (MODE == 0) {
         const T* __restrict__ U = reinterpret_cast<const T*>(B.u[a.cur]);
-        T* __restrict__ Un = reinterpret_cast<T*>(B.u[1 - a.cur]);
-        const T wv = reinterpret_cast<const T*>(B.w)[gi], dt2 = dt2T<T>(a);
-        const T up0 = Un[gi], up1 = Un[gi + plane];
-        T nu0 = T(2) * U[gi] - up0 + dt2 * wv * r0;
-        T nu1 = T(2) * U[gi + plane] - up1 + dt2 * wv * r1;
-        if (damped) robin_damped_update<T>(T(0.5 * a.dt) * wv, dd00, dd01, dd11, up0, up1, nu0, nu1);
-        Un[gi] = nu0;
-        Un[gi + plane] = nu1;
+        leapfrog_store<T>(B, a, gi, plane, U[gi], U[gi + plane], reinterpret_cast<const T*>(B.w)[gi], r0, r1, damped,
+                          dd00, dd01, dd11);
     } else if (MODE == 2) {
         if (damped) {
             T v0, v1;
