@@ -52,46 +52,54 @@ template <int O> constexpr size_t batch_smem_bytes() {
                                                                         : StripTile<O>::template bytes<float>();
 }
 
-// an interior item and a strip item, each compiled as a function of its own so that their
-// registers are allocated apart from each other and from the queue loop
-template <int O>
-__device__ __noinline__ bool batch_interior_item(const BatchShot& sh, int tile, const StepArgs& a, int* err,
-                                                 unsigned char* smem) {
-    return march_tile<O, 3>(sh.maps, sh.view, a, sh.rows, tile, err, smem);
-}
-
-template <int O>
-__device__ __noinline__ bool batch_strip_item(const BatchShot& sh, int tile, const StepArgs& a, int* err,
-                                              unsigned char* smem) {
-    return strip_tile_body<float, O, 0, MTHREADS>(&sh.view, sh.tiles[tile], a, sh.beta, err, sh.ssrc, sh.spar, smem);
-}
-
 template <int O>
 __global__ void __launch_bounds__(MTHREADS, 4) k_batch_step(BatchHead* __restrict__ H, int* err) {
     extern __shared__ __align__(128) unsigned char batch_smem[];
-    __shared__ int s_item;
+    // the item's step arguments and (interior items) the block fields the march reads, kept in
+    // shared memory for the item: the launch-per-step kernels read them from the constant bank,
+    // here they would otherwise be re-read from global memory inside the row loop
+    __shared__ StepArgs s_a;
+    __shared__ MarchView s_v;
+    __shared__ int4 s_w;
+    __shared__ int s_item, s_run;
     __shared__ int s_last;
     const int tx = threadIdx.x;
     for (;;) {
-        if (tx == 0) s_item = atomicAdd(&H->next, 1);
+        if (tx == 0) {
+            const int it = atomicAdd(&H->next, 1);
+            int run = 0;
+            if (it < H->nitems) {
+                const int4 w = H->items[it];
+                const BatchState st = H->state[w.x];
+                if (st.remaining > 0) {
+                    run = 1;
+                    const BatchShot& sh = H->shots[w.x];
+                    StepArgs a{};
+                    a.cur = st.cur;
+                    a.with_data = 1;
+                    a.t = st.t;
+                    a.dt = sh.dt;
+                    a.dt2 = sh.dt2;
+                    a.dt2f = sh.dt2f;
+                    s_a = a;
+                    if (w.y == 0) s_v = march_view(sh.view);
+                }
+                s_w = w;
+            }
+            s_item = it;
+            s_run = run;
+        }
         __syncthreads();
-        const int it = s_item;
-        __syncthreads();                                    // s_item is rewritten only after every thread read it
+        const int it = s_item, run = s_run;
+        const int4 w = s_w;
+        __syncthreads();                                    // s_item, s_run, s_w are rewritten only after every thread read them
         if (it >= H->nitems) break;
-        const int4 w = H->items[it];
+        if (!run) continue;
         const BatchShot& sh = H->shots[w.x];
-        const BatchState st = H->state[w.x];
-        if (st.remaining <= 0) continue;
-        StepArgs a{};
-        a.cur = st.cur;
-        a.with_data = 1;
-        a.t = st.t;
-        a.dt = sh.dt;
-        a.dt2 = sh.dt2;
-        a.dt2f = sh.dt2f;
         bool ok;
-        if (w.y == 0) ok = batch_interior_item<O>(sh, w.z, a, err, batch_smem);
-        else ok = batch_strip_item<O>(sh, w.z, a, err, batch_smem);
+        if (w.y == 0) ok = march_tile<O, 3>(sh.maps, s_v, s_a, sh.rows, w.z, err, batch_smem);
+        else ok = strip_tile_body<float, O, 0, MTHREADS>(&sh.view, sh.tiles[w.z], s_a, sh.beta, err, sh.ssrc, sh.spar,
+                                                        batch_smem);
         __syncthreads();                                    // the next item reuses the shared memory
         if (!ok) break;                                     // uniform: set by a CTA-wide vote
     }

@@ -70,14 +70,42 @@ __host__ __device__ inline int march_x0(int strip) { return (strip / 4) * 4; }
 // columns-of-128 tiles across the interior of a block (the host sizes grids and work lists with it)
 __host__ __device__ inline int march_ncx(int n1, int strip) { return (n1 - strip - march_x0(strip) + MTHREADS - 1) / MTHREADS; }
 
+// The block fields the tile reads, as a compact copy (a persistent caller keeps it in shared memory;
+// the launch-per-step kernels read the BlockDev kernel parameter directly).
+struct MarchView {
+    int n1, n2, pitch, strip;
+    float ih1f, ih2f;
+    void* u[2];
+    void* du;
+    const void* w;
+    const void* jf;
+    void* r;
+};
+__host__ __device__ inline MarchView march_view(const BlockDev& B) {
+    MarchView v;
+    v.n1 = B.n1;
+    v.n2 = B.n2;
+    v.pitch = B.pitch;
+    v.strip = B.strip;
+    v.ih1f = B.ih1f;
+    v.ih2f = B.ih2f;
+    v.u[0] = B.u[0];
+    v.u[1] = B.u[1];
+    v.du = B.du;
+    v.w = B.w;
+    v.jf = B.jf;
+    v.r = B.r;
+    return v;
+}
+
 // One interior tile: the 128 columns of column tile `tile % ncx` and the rows_per_cta rows of row
 // band `tile / ncx`, by the 128 threads of the calling CTA, with `smem` (MarchCfg<O>::BYTES, 128-byte
 // aligned) as its ring, flux row and mbarriers.  Returns false when a bounded wait ran out (the
 // error word is set; the tile's copies have been drained).  The mbarriers are invalidated before
 // the return, so a persistent caller can reuse the shared memory for its next tile after a
 // CTA barrier.
-template <int O, int MODE>
-__device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BlockDev& B, const StepArgs& a, int rows_per_cta,
+template <int O, int MODE, class BV = BlockDev>
+__device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BV& B, const StepArgs& a, int rows_per_cta,
                                            int tile, int* err, unsigned char* march_smem) {
     using MC = MarchCfg<O>;
     constexpr int Q = MC::Q, W = MBOXW, L = 2 * Q + 1;
@@ -370,7 +398,7 @@ __device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BlockDev
             Un[gi + plane] = nu.y;
             DU[gi] = d.x;
             DU[gi + plane] = d.y;
-        } else if (MODE == 2) {
+        } else if constexpr (MODE == 2) {
             rk4_store<float>(B, a, gi, plane, w_c, r0, r1);
         } else {
             float* __restrict__ R = reinterpret_cast<float*>(B.r);
