@@ -199,73 +199,61 @@ class _ShotPrefetch:
         self.pool.shutdown(wait=True)
 
 
-def batch_capacity(specs, nprobe=32, ticks=12, tick=16):
-    """Node-updates/s of the persistent tile-queue kernel on the first nprobe shots of the served
-    mix, all resident (setup outside the timed ticks; no shot finishes within them)."""
-    import torch
-    from paper_2003_12811_gb300.serve import GpuBatchBackend
-    be = GpuBatchBackend(max_shots=nprobe)
-    sides = []
-    for (_, side, seed, n) in specs[:nprobe]:
-        be.admit(W.shot_problem(side, seed), n, 0.3)
-        sides.append(side)
-    be.step(tick)                                       # warm-up tick (graph capture)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(ticks):
-        be.step(tick)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    be.close()
-    return sum(s * s for s in sides) * tick * ticks / dt
-
-
-def serving_bench(nshots=256, side_range=(201, 2001), tick=16, hbm_cap=16e9, sample_every=8):
+def serving_bench(nshots=256, side_range=(201, 2001), tick=16, hbm_cap=16e9, sample_every=16):
     """Served batch (config 4 as stated): nshots single-block curvilinear shots, side ~ U(side_range),
-    steps = 2 side, Poisson arrivals at 0.8 x the serving path's capacity (the batch kernel's
-    node-updates/s on the first 32 shots of the mix, over the mean shot work), admission under an
-    HBM cap (16 GB: admission binds), FP32 continuous batching on the persistent tile-queue kernel.  Baselines on a uniform sample (every sample_every-th
-    request) run one solve at a time: the plain FP64 path (the target) and the same path in FP32
-    (which separates the batching gain from the precision gain); their solves/s = sample size /
-    sample time.  Setup (grid, material, CFL) and the result read-back are inside every arm; the
-    host-side shot construction is not (prefetched on worker threads for the batch, done before
-    each timed solve for the baselines)."""
+    steps = 2 side, admission under an HBM cap (16 GB: admission binds), FP32 continuous batching
+    on the persistent tile-queue kernel.  Two runs of the same requests:
+      * saturated: every request is waiting at t = 0; solves/s = nshots / makespan is the serving
+        path's capacity (the number compared with the one-at-a-time arms);
+      * loaded: Poisson arrivals at 0.8 x that capacity; p50 / p99 latency (arrival to result).
+    Baselines on a uniform sample (every sample_every-th request) run one solve at a time, back to
+    back: the plain FP64 path (the target) and the same path in FP32 (which separates the batching
+    gain from the precision gain); their solves/s = sample size / sample time.  Setup (grid,
+    material, CFL) and the result read-back are inside every arm; the host-side shot construction
+    is not (prefetched on worker threads for the batch, done before each timed solve for the
+    baselines)."""
     import numpy as np
     import torch
     from paper_2003_12811_gb300 import Solver
+    from paper_2003_12811_gb300.binding import FIELD_CUR
     from paper_2003_12811_gb300.serve import BatchServingEngine, GpuBatchBackend, Request, percentile
-    probe = W.config4_requests(nshots, side_range, rate=1.0, steps_per_side=2.0, step_multiple=2)
-    work = np.mean([side * side * n for (_, side, _, n) in probe])
-    capacity = batch_capacity(probe)
-    rate = 0.8 * capacity / work                        # arrivals per second
-    specs = W.config4_requests(nshots, side_range, rate=rate, steps_per_side=2.0, step_multiple=2)
-    pre = _ShotPrefetch(specs)
-    reqs = [Request(rid=i, arrival=a, problem=(lambda i=i: pre.get(i)), nsteps=n) for i, (a, _, _, n) in enumerate(specs)]
-    be = GpuBatchBackend(max_shots=nshots)
-    eng = BatchServingEngine(int(hbm_cap), backend=be, tick_steps=tick, max_active=nshots)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    res = eng.run(reqs)
-    torch.cuda.synchronize()
-    served = time.perf_counter() - t0
-    be.close()
-    pre.close()
-    lat = [r.latency for r in res]
-    node_updates = int(sum(side * side * n for (_, side, _, n) in specs))
+    base = W.config4_requests(nshots, side_range, rate=1.0, steps_per_side=2.0, step_multiple=2)
+    work = float(np.mean([side * side * n for (_, side, _, n) in base]))
+    node_updates = int(sum(side * side * n for (_, side, _, n) in base))
+
+    def serve(arrivals):
+        specs = [(a, side, seed, n) for a, (_, side, seed, n) in zip(arrivals, base)]
+        pre = _ShotPrefetch(specs)
+        reqs = [Request(rid=i, arrival=a, problem=(lambda i=i: pre.get(i)), nsteps=n)
+                for i, (a, _, _, n) in enumerate(specs)]
+        be = GpuBatchBackend(max_shots=nshots)
+        eng = BatchServingEngine(int(hbm_cap), backend=be, tick_steps=tick, max_active=nshots)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = eng.run(reqs)
+        torch.cuda.synchronize()
+        served = time.perf_counter() - t0
+        be.close()
+        pre.close()
+        return served, [r.latency for r in res], eng
+
+    sat_s, sat_lat, sat_eng = serve([0.0] * nshots)
+    capacity = nshots / sat_s                            # solves/s at saturation
+    rate = 0.8 * capacity                                # arrivals per second of the loaded run
+    loaded = W.config4_requests(nshots, side_range, rate=rate, steps_per_side=2.0, step_multiple=2)
+    load_s, lat, eng = serve([a for (a, _, _, _) in loaded])
 
     def one_at_a_time(prec):
         tot = 0.0
-        sample = specs[::sample_every]
+        sample = base[::sample_every]
         for (_, side, seed, n) in sample:
             P = W.shot_problem(side, seed)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            S = Solver(P, prec)
+            S = Solver(P, prec)                         # state zero at t = 0, as for the batch
             dt = S.suggest_dt(0.3)
-            z = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
-            S.set_state(z, z, 0.0)
             S.sbp_step(n, dt)
-            S.state()
+            S.sbp_get_field(FIELD_CUR)
             S.close()
             torch.cuda.synchronize()
             tot += time.perf_counter() - t1
@@ -273,17 +261,21 @@ def serving_bench(nshots=256, side_range=(201, 2001), tick=16, hbm_cap=16e9, sam
 
     seq64, n64, t64 = one_at_a_time("fp64")
     seq32, n32, t32 = one_at_a_time("fp32")
-    return {"workload": f"served batch (config 4): {nshots} shots, side U{list(side_range)}, steps = 2 side, "
-                        f"Poisson arrivals {rate:.2f}/s (0.8 x the batch kernel's capacity), FP32, HBM cap {hbm_cap / 1e9:.0f} GB, "
-                        f"persistent tile-queue kernel, ticks of {tick} graph-replayed steps",
-            "solves_per_s": nshots / served, "makespan_s": served, "batch_capacity_node_updates_per_s": capacity,
+    return {"workload": f"served batch (config 4): {nshots} shots, side U{list(side_range)}, steps = 2 side, FP32, "
+                        f"HBM cap {hbm_cap / 1e9:.0f} GB, persistent tile-queue kernel, ticks of {tick} graph-replayed "
+                        f"steps; saturated run (all requests at t = 0) and loaded run (Poisson arrivals "
+                        f"{rate:.2f}/s = 0.8 x the saturated solves/s)",
+            "solves_per_s": capacity, "makespan_s": sat_s, "node_updates_per_s": node_updates / sat_s,
+            "mean_shot_node_updates": work,
+            "loaded": {"arrivals_per_s": rate, "makespan_s": load_s, "solves_per_s": nshots / load_s,
+                       "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
+                       "peak_active": eng.peak_active, "peak_bytes": eng.peak_bytes, "ticks": eng.ticks},
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
-            "node_updates_per_s": node_updates / served,
             "fp64_one_at_a_time_solves_per_s": seq64, "fp32_one_at_a_time_solves_per_s": seq32,
             "baseline_sample": f"every {sample_every}th request ({n64} shots): FP64 {t64:.1f} s, FP32 {t32:.1f} s",
-            "speedup_vs_fp64_one_at_a_time": (nshots / served) / seq64,
-            "speedup_vs_fp32_one_at_a_time": (nshots / served) / seq32,
-            "peak_active": eng.peak_active, "peak_bytes": eng.peak_bytes, "ticks": eng.ticks,
+            "speedup_vs_fp64_one_at_a_time": capacity / seq64,
+            "speedup_vs_fp32_one_at_a_time": capacity / seq32,
+            "peak_active": sat_eng.peak_active, "peak_bytes": sat_eng.peak_bytes, "ticks": sat_eng.ticks,
             "node_updates": node_updates}
 
 

@@ -23,6 +23,7 @@
 //    combined with packed FP32x2 instructions (one issue slot for both).
 #pragma once
 #include <cuda.h>
+#include <type_traits>
 #include "sbp_device.cuh"
 
 namespace sbp {
@@ -36,7 +37,8 @@ template <int O> struct MarchCfg {
     static constexpr int UPAD = ((2 * MR * MBOXW * 4 + 127) / 128) * 128 / 4;
     static constexpr int CHUNK = ((UPAD + 10 * MR * MBOXW) * 4 + 127) / 128 * 128 / 4;
     static constexpr int G1 = 2 * 2 * MBOXW;                 // [row parity][col][component] (float2)
-    static constexpr size_t BYTES = (size_t)(MNCH * CHUNK + G1) * 4 + 64;
+    static constexpr int HQ = 6 * 8 * 2;                      // halo queues [2q][8] (float2), persistent callers
+    static constexpr size_t BYTES = (size_t)(MNCH * CHUNK + G1 + HQ) * 4 + 64;
 };
 
 struct MarchMaps {
@@ -111,7 +113,12 @@ __device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BV& B, c
     constexpr int Q = MC::Q, W = MBOXW, L = 2 * Q + 1;
     float* ring = reinterpret_cast<float*>(march_smem);
     float* g1s = ring + MNCH * MC::CHUNK;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(g1s + MC::G1);
+    float2* hqs = reinterpret_cast<float2*>(g1s + MC::G1);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(g1s + MC::G1 + MC::HQ);
+    // a persistent caller (view type other than the BlockDev kernel parameter) keeps the halo
+    // columns' displacement queues in shared memory (rows indexed mod 8) instead of registers:
+    // its block fields live in registers, not in the constant bank
+    constexpr bool HS = !std::is_same<BV, BlockDev>::value;
 
     const int S = B.strip, n1 = B.n1, n2 = B.n2, P = B.pitch;
     const int lim1 = n1 - S, lim2 = n2 - S;
@@ -252,9 +259,13 @@ __device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BV& B, c
             // g2_1 = c_1121 D_1 u_1 + c_1221 D_1 u_2,  g2_2 = c_1122 D_1 u_1 + c_1222 D_1 u_2
             qg[L - 1] = ffma2(make_float2(m6, m7), bc2(d.x), fmul2(make_float2(m8, m9), bc2(d.y)));
             if (halo) {
+                if constexpr (HS) {
+                    hqs[tx * 8 + ((unsigned)Lr & 7u)] = make_float2(at(0, Lr, hc), at(1, Lr, hc));
+                } else {
 #pragma unroll
-                for (int k = 0; k < L - 1; ++k) qh[k] = qh[k + 1];
-                qh[L - 1] = make_float2(at(0, Lr, hc), at(1, Lr, hc));
+                    for (int k = 0; k < L - 1; ++k) qh[k] = qh[k + 1];
+                    qh[L - 1] = make_float2(at(0, Lr, hc), at(1, Lr, hc));
+                }
             }
         }
     };
@@ -311,7 +322,12 @@ __device__ __forceinline__ bool march_tile(const MarchMaps& maps, const BV& B, c
         if (halo) {
             float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 1; k <= Q; ++k) d = ffma2(bc2(ak[k - 1]), fsub2(qh[Q + k], qh[Q - k]), d);
+            for (int k = 1; k <= Q; ++k) {
+                if constexpr (HS)
+                    d = ffma2(bc2(ak[k - 1]), fsub2(hqs[tx * 8 + ((unsigned)(r + k) & 7u)], hqs[tx * 8 + ((unsigned)(r - k) & 7u)]), d);
+                else
+                    d = ffma2(bc2(ak[k - 1]), fsub2(qh[Q + k], qh[Q - k]), d);
+            }
             d = fmul2(d, bc2(ih2));
             const float m6 = at(8, r, hc), m7 = at(9, r, hc), m8 = at(10, r, hc), m9 = at(11, r, hc);
             const float2 g = ffma2(make_float2(m6, m8), bc2(d.x), fmul2(make_float2(m7, m9), bc2(d.y)));

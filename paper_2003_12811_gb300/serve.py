@@ -212,6 +212,8 @@ class GpuBatchBackend:
         if rows:
             self.batch.sbp_batch_set_rows(rows)
         self.stream = torch.cuda.Stream()
+        self._ev0 = torch.cuda.Event(enable_timing=True)
+        self._ev1 = torch.cuda.Event(enable_timing=True)
         self.max_shots = max_shots
         self.shots = {}
 
@@ -219,26 +221,32 @@ class GpuBatchBackend:
         return self.footprint_bytes(problem, "fp32")
 
     def admit(self, problem, nsteps, cfl, dt=None):
-        import numpy as np
+        # a new handle's state is zero at t = 0 (its buffers are cleared when allocated): a shot
+        # that starts at rest needs no state upload
         S = self.Solver(problem, "fp32")
         if dt is None:
             dt = S.suggest_dt(cfl)
-        z = [np.zeros((2, b.N2, b.N1)) for b in problem.blocks]
-        S.set_state(z, z, 0.0)
         slot = self.batch.sbp_batch_add(S, nsteps, dt)
         self.shots[slot] = S
         return slot, dt
 
     def step(self, k):
+        self._ev0.record(self.stream)
         self.batch.sbp_batch_step(k, self.stream.cuda_stream)
+        self._ev1.record(self.stream)
 
     def poll(self):
         return self.batch.sbp_batch_poll(self.stream.cuda_stream)
 
+    def tick_seconds(self):
+        """Device time of the last tick (valid after poll)."""
+        return self._ev0.elapsed_time(self._ev1) / 1e3
+
     def retire(self, slot):
+        from .binding import FIELD_CUR
         self.batch.sbp_batch_remove(slot, self.stream.cuda_stream)
         S = self.shots.pop(slot)
-        _, u = S.state()
+        u = S.sbp_get_field(FIELD_CUR)
         S.close()
         return u
 
@@ -252,13 +260,15 @@ class GpuBatchBackend:
 class BatchServingEngine:
     """Continuous batching on the persistent tile-queue kernel (see the module docstring).
 
-    Between ticks the engine retires finished shots (reading their results), admits waiting
-    requests first come first served while slots and the HBM cap allow, and launches the next
-    tick for every resident shot; each shot advances by its own step count."""
+    The engine launches the next tick of every resident shot, admits waiting requests first come
+    first served while slots and the HBM cap allow and while the tick runs (for about one tick's
+    device time, at least one request: admission is host-side setup, so the GPU is kept busy), then
+    waits for the tick and retires finished shots (reading their results).  Each shot advances by
+    its own step count."""
 
     def __init__(self, hbm_cap_bytes: int, backend=None, tick_steps: int = 32, max_active: int = 256,
                  cfl: float = 0.3, clock: Callable[[], float] = time.perf_counter,
-                 sleep: Callable[[float], None] = time.sleep):
+                 sleep: Callable[[float], None] = time.sleep, min_admit_budget: float = 2e-3):
         if tick_steps < 1:
             raise ValueError("tick_steps must be >= 1")
         self.cap = int(hbm_cap_bytes)
@@ -268,6 +278,7 @@ class BatchServingEngine:
         self.cfl = cfl
         self.clock = clock
         self.sleep = sleep
+        self.min_admit_budget = min_admit_budget
         self.peak_bytes = 0
         self.peak_active = 0
         self.ticks = 0
@@ -279,17 +290,20 @@ class BatchServingEngine:
         active = {}                       # slot -> dict(req, fp, admitted, dt)
         used = 0
         results = []
+        tick_est = 0.0                    # device time of the last tick
         t0 = self.clock()
         while pending or waiting or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
             # the next tick of every resident shot goes to the GPU first; new shots are set up
-            # while it runs and join at the following tick
+            # while it runs (for about the tick's duration) and join at the following tick
             launched = bool(active)
             if launched:
                 self.backend.step(self.tick)
                 self.ticks += 1
+            budget = max(self.min_admit_budget, tick_est if launched else 0.0)
+            t_adm = self.clock()
             while waiting and len(active) < self.max_active:
                 req = waiting[0]
                 prob = _problem_of(req)
@@ -305,8 +319,12 @@ class BatchServingEngine:
                 active[slot] = dict(req=req, fp=fp, admitted=self.clock() - t0, dt=dt)
                 self.peak_active = max(self.peak_active, len(active))
                 self.trace.append((self.clock() - t0, "admit", req.rid))
+                if self.clock() - t_adm >= budget:
+                    break
             if launched:
                 rem = self.backend.poll()
+                if hasattr(self.backend, "tick_seconds"):
+                    tick_est = self.backend.tick_seconds()
                 for slot in sorted(active):
                     if rem[slot] == 0:
                         info = active.pop(slot)
