@@ -340,8 +340,10 @@ int sbp_batch_step(sbp_batch* b, int ksteps, void* stream);
  * kernel ran out since the last poll. */
 int sbp_batch_poll(sbp_batch* b, int* remaining, void* stream);
 
-/* Retire the shot in `slot` (finished or not): synchronises `stream`, hands its level parity and
- * time back to its handle and frees the slot. */
+/* Retire the shot in `slot` (finished or not) and free the slot: hands its level parity and time
+ * back to its handle.  A shot that the last sbp_batch_poll saw finished no longer changes, so its
+ * state is taken from that poll without touching the device (later launches may already be queued
+ * on `stream`); otherwise `stream` is synchronised and the state read. */
 int sbp_batch_remove(sbp_batch* b, int slot, void* stream);
 
 /* Rows of an interior work item (the tile shape; 0 = default 64).  Only while the batch is empty. */
@@ -377,14 +379,16 @@ int sbp_record(sbp_handle* h, int nsteps, double dt, double* traces);
  *                the pair entries it sets).
  * Either array pointer (or an entry) may be null to skip that output; `observed` is host FP64
  * [nsteps][nrec][2]; *misfit receives Phi.  Method: a forward pass that stores the state every
- * `checkpoint_every` steps (0: ceil(sqrt(nsteps))), then, segment by segment from the last, a
- * recomputation of the segment's levels and the adjoint recursion psi_n = 2 psi_{n+1} - psi_{n+2}
+ * `checkpoint_every` steps (0: every level, when the forward and adjoint levels of the whole run
+ * fit in 60 % of the free device memory, else ceil(sqrt(nsteps))), then, segment by segment from
+ * the last, a recomputation of the segment's levels (none with a single segment: the forward pass
+ * keeps them) and the adjoint recursion psi_n = 2 psi_{n+1} - psi_{n+2}
  * + dt^2 W L psi_{n+1} + H^-1 W dPhi/du_{n+1} with the forward kernels (psi = H^-1 W lambda, lambda
  * the Lagrange multipliers of the step equations), accumulating
  *   dPhi/dc_p(x) += dt^2 (H psi_n)^T dL/dc_p(x) u_n,  dPhi/drho(x) -= H J psi_n . (u_{n+1} - 2u_n + u_{n-1}),
  * (the terms of a segment are accumulated in registers over its levels and added once), and
  * finally dPhi/dC from dPhi/dc through c_ijkl = J F_Ii C_IjKl F_Kk.  Device workspace: about
- * (2 nsteps / K + 2 K + 4) field levels per block plus 11 accumulator planes, allocated for the call.
+ * (3 nsteps / K + 2 K + 5) field levels per block plus 11 accumulator planes, allocated for the call.
  * On return the state is the one after nsteps steps (as sbp_step would leave it).  Synchronous.
  * Errors: SBP_E_STATE without receivers or when a displacement face carries boundary data (the
  * data would then depend on C); SBP_E_OOM when the workspace does not fit. */

@@ -508,7 +508,7 @@ __device__ __forceinline__ void grad_strip_node(const BlockDev& B, long long t, 
 
 // strip nodes, phase 1: level chunk blockIdx.y of nchunk; partial sums to G.part
 template <typename T, int O>
-__global__ void __launch_bounds__(256) k_grad_strip(BlockDev B, GradDev G, int nl, int nchunk, long long nstrip) {
+__global__ void __launch_bounds__(256, 2) k_grad_strip(BlockDev B, GradDev G, int nl, int nchunk, long long nstrip) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nstrip) return;
     int i1, i2;

@@ -1890,7 +1890,7 @@ int sbp_step_graph(sbp_handle* h, int nsteps, double dt, void* stream) {
         const int nb = (int)h->blocks.size();
         const int nint = h->precision == SBP_FP32 ? (nb + MARCH_MAX_BLOCKS - 1) / MARCH_MAX_BLOCKS : nb;
         h->launches[0] += (long long)nsteps * nint;
-        h->launches[1] += (long long)nsteps * nb;
+        h->launches[1] += (long long)nsteps;
         if (h->n_src_int > 0) h->launches[3] += nsteps;
     }
     h->t = tt;
@@ -2159,9 +2159,21 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
                 return h->fail(SBP_E_STATE, "displacement faces with boundary data make the data depend on C; not supported");
     int rc = ensure_adjoint_buffers(h);
     if (rc != SBP_OK) return rc;
-    const int K = checkpoint_every > 0 ? std::min(checkpoint_every, nsteps)
-                                       : std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+    // checkpoint interval: given, or (0) every level kept on the device when the forward and
+    // adjoint levels of the whole run fit in 60 % of the free memory (no recomputation), else
+    // ceil(sqrt(nsteps))
+    int K = checkpoint_every > 0 ? std::min(checkpoint_every, nsteps) : 0;
+    if (K == 0) {
+        size_t lvl_all = 0, freeb = 0, totalb = 0;
+        for (auto& hb : h->blocks) lvl_all += 2 * (size_t)hb.n2 * hb.pitch * h->esize;
+        if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess && (double)(2 * (size_t)nsteps + 8) * lvl_all <= 0.6 * (double)freeb)
+            K = nsteps;
+        else
+            K = std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+    }
     const int nseg = (nsteps + K - 1) / K;
+    // one segment: the forward pass stores the levels as it makes them, so none is recomputed
+    const bool keep_all = nseg == 1;
     const size_t es = h->esize;
     const size_t per = 2 * h->recs.size();
     const int nb = (int)h->blocks.size();
@@ -2233,10 +2245,19 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
             const int c = n / K;
             if (!save_state(ck, c)) return h->fail(SBP_E_CUDA, "checkpoint copy");
             ck_t[c] = h->t;
+            if (keep_all)
+                for (int b = 0; b < nb; ++b)
+                    if (!copy(lvl_ptr(seg, b, 0), h->blocks[b].u[1 - h->cur], lvl_bytes[b]) ||
+                        !copy(lvl_ptr(seg, b, 1), h->blocks[b].u[h->cur], lvl_bytes[b]))
+                        return h->fail(SBP_E_CUDA, "level copy");
         }
         rc = step_once(h, dt, st);
         if (rc != SBP_OK) return rc;
         record_receivers(h, d_tr + (size_t)n * per, st);
+        if (keep_all)
+            for (int b = 0; b < nb; ++b)
+                if (!copy(lvl_ptr(seg, b, (size_t)n + 2), h->blocks[b].u[h->cur], lvl_bytes[b]))
+                    return h->fail(SBP_E_CUDA, "level copy");
     }
     const int cur_final = h->cur;
     const double t_final = h->t;
@@ -2264,20 +2285,23 @@ int sbp_misfit_gradient(sbp_handle* h, int nsteps, double dt, const double* obse
     const int nr = (int)h->recs.size();
     for (int s = nseg - 1; s >= 0; --s) {
         const int a0 = s * K, a1 = std::min(a0 + K, nsteps) - 1;   // 0-based steps of the segment
-        // recompute the segment's levels u_{a0} .. u_{a1+2} from its checkpoint
-        if (!load_state(ck, s)) return h->fail(SBP_E_CUDA, "checkpoint restore");
-        for (int b = 0; b < nb; ++b) {
-            if (!copy(lvl_ptr(seg, b, 0), lvl_ptr(ck, b, (size_t)nck * s), lvl_bytes[b]) ||
-                !copy(lvl_ptr(seg, b, 1), lvl_ptr(ck, b, (size_t)nck * s + 1), lvl_bytes[b]))
-                return h->fail(SBP_E_CUDA, "checkpoint restore");
-        }
-        h->t = ck_t[s];
-        for (int q = a0; q <= a1; ++q) {
-            rc = step_once(h, dt, st);
-            if (rc != SBP_OK) return rc;
-            for (int b = 0; b < nb; ++b)
-                if (!copy(lvl_ptr(seg, b, (size_t)(q - a0 + 2)), h->blocks[b].u[h->cur], lvl_bytes[b]))
-                    return h->fail(SBP_E_CUDA, "segment copy");
+        // recompute the segment's levels u_{a0} .. u_{a1+2} from its checkpoint (one segment: the
+        // forward pass kept them)
+        if (!keep_all) {
+            if (!load_state(ck, s)) return h->fail(SBP_E_CUDA, "checkpoint restore");
+            for (int b = 0; b < nb; ++b) {
+                if (!copy(lvl_ptr(seg, b, 0), lvl_ptr(ck, b, (size_t)nck * s), lvl_bytes[b]) ||
+                    !copy(lvl_ptr(seg, b, 1), lvl_ptr(ck, b, (size_t)nck * s + 1), lvl_bytes[b]))
+                    return h->fail(SBP_E_CUDA, "checkpoint restore");
+            }
+            h->t = ck_t[s];
+            for (int q = a0; q <= a1; ++q) {
+                rc = step_once(h, dt, st);
+                if (rc != SBP_OK) return rc;
+                for (int b = 0; b < nb; ++b)
+                    if (!copy(lvl_ptr(seg, b, (size_t)(q - a0 + 2)), h->blocks[b].u[h->cur], lvl_bytes[b]))
+                        return h->fail(SBP_E_CUDA, "segment copy");
+            }
         }
         // adjoint steps n = q + 1 (1-based) from the last step of the segment down to the first
         for (int q = a1; q >= a0; --q) {
@@ -2348,6 +2372,8 @@ struct sbp_batch {
     std::vector<sbp::BatchShot> mirror;     // host copies of the immutable descriptions
     std::vector<sbp::BatchState> pending;   // state of slots admitted since the last launch
     std::vector<char> pending_set;
+    std::vector<BatchState> finished;       // device state of slots a poll saw finished (it no longer changes)
+    std::vector<char> finished_set;
     std::vector<int> nint, nstrip;          // work items per slot
     bool dirty = false;
     int graph_k = 0;
@@ -2437,6 +2463,8 @@ int sbp_batch_create(int order, int max_shots, sbp_batch** out) {
     b->mirror.assign(max_shots, BatchShot{});
     b->pending.assign(max_shots, BatchState{});
     b->pending_set.assign(max_shots, 0);
+    b->finished.assign(max_shots, BatchState{});
+    b->finished_set.assign(max_shots, 0);
     b->nint.assign(max_shots, 0);
     b->nstrip.assign(max_shots, 0);
     int dev = 0;
@@ -2523,6 +2551,7 @@ int sbp_batch_add(sbp_batch* b, sbp_handle* h, int nsteps, double dt, int* slot_
     b->nstrip[slot] = h->ntiles;
     b->pending[slot] = BatchState{nsteps, h->cur, h->t};
     b->pending_set[slot] = 1;
+    b->finished_set[slot] = 0;
     b->shot[slot] = h;
     b->dirty = true;
     *slot_out = slot;
@@ -2569,6 +2598,10 @@ int sbp_batch_poll(sbp_batch* b, int* remaining, void* stream) {
     for (int s = 0; s < b->max_shots; ++s) {
         if (!b->shot[s]) remaining[s] = -1;
         else remaining[s] = b->pending_set[s] ? b->pending[s].remaining : v[s].remaining;
+        if (b->shot[s] && !b->pending_set[s] && v[s].remaining <= 0) {
+            b->finished[s] = v[s];
+            b->finished_set[s] = 1;
+        }
     }
     if (e) {
         cudaMemset(b->d_err, 0, sizeof(int));
@@ -2585,6 +2618,8 @@ int sbp_batch_remove(sbp_batch* b, int slot, void* stream) {
     BatchState cur{};
     if (b->pending_set[slot]) {
         cur = b->pending[slot];
+    } else if (b->finished_set[slot]) {
+        cur = b->finished[slot];              // finished shots are skipped by later launches: no read needed
     } else if (cudaMemcpyAsync(&cur, b->d_state + slot, sizeof(cur), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                cudaStreamSynchronize(st) != cudaSuccess) {
         return b->fail(SBP_E_CUDA, "batch state read");
@@ -2595,6 +2630,7 @@ int sbp_batch_remove(sbp_batch* b, int slot, void* stream) {
     b->shot[slot] = nullptr;
     b->pending[slot] = BatchState{0, 0, 0.0};
     b->pending_set[slot] = 1;               // the slot's device state is cleared at the next launch
+    b->finished_set[slot] = 0;
     b->mirror[slot] = BatchShot{};
     b->nint[slot] = b->nstrip[slot] = 0;
     b->dirty = true;

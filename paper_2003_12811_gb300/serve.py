@@ -212,6 +212,7 @@ class GpuBatchBackend:
         if rows:
             self.batch.sbp_batch_set_rows(rows)
         self.stream = torch.cuda.Stream()
+        self.side = torch.cuda.Stream()
         self._ev0 = torch.cuda.Event(enable_timing=True)
         self._ev1 = torch.cuda.Event(enable_timing=True)
         self.max_shots = max_shots
@@ -243,12 +244,35 @@ class GpuBatchBackend:
         return self._ev0.elapsed_time(self._ev1) / 1e3
 
     def retire(self, slot):
+        return self.collect(self.retire_async(slot))
+
+    def retire_async(self, slot):
+        """Free the slot and start reading the shot's u^n back on a side stream (the next tick may
+        already be queued on the batch stream; a finished shot no longer changes).  collect() waits
+        for the copy, releases the handle and returns the fields."""
         from .binding import FIELD_CUR
+        torch = self.torch
         self.batch.sbp_batch_remove(slot, self.stream.cuda_stream)
         S = self.shots.pop(slot)
-        u = S.sbp_get_field(FIELD_CUR)
+        outs = []
+        with torch.cuda.stream(self.side):
+            for b, blk in enumerate(S.problem.blocks):
+                pitch = (blk.N1 + 3) // 4 * 4                  # 16-byte rows
+                dev = torch.empty((2, blk.N2, pitch), dtype=torch.float32, device="cuda")
+                S.sbp_get_field_device(b, FIELD_CUR, dev.data_ptr(), pitch, self.side.cuda_stream)
+                host = torch.empty(dev.shape, dtype=torch.float32, pin_memory=True)
+                host.copy_(dev, non_blocking=True)
+                outs.append((host, blk.N1, dev))
+            ev = torch.cuda.Event()
+            ev.record(self.side)
+        return S, outs, ev
+
+    def collect(self, pending):
+        S, outs, ev = pending
+        ev.synchronize()
+        fields = [host[:, :, :n1].numpy().astype("float64") for host, n1, _ in outs]
         S.close()
-        return u
+        return fields
 
     def close(self):
         for S in self.shots.values():
@@ -282,17 +306,39 @@ class BatchServingEngine:
         self.peak_bytes = 0
         self.peak_active = 0
         self.ticks = 0
+        # host time per phase of the loop: tick launch, admissions, waiting for the tick, retirement
+        self.phase_s = {"launch": 0.0, "admit": 0.0, "poll": 0.0, "retire": 0.0}
         self.trace: List[tuple] = []
 
     def run(self, requests: List[Request]) -> List[Result]:
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting: collections.deque = collections.deque()
         active = {}                       # slot -> dict(req, fp, admitted, dt)
+        retiring = []                     # (info, backend handle) of results being read back
+        asynchronous = hasattr(self.backend, "retire_async")
         used = 0
         results = []
         tick_est = 0.0                    # device time of the last tick
         t0 = self.clock()
-        while pending or waiting or active:
+
+        def finish(info, fields):
+            nonlocal used
+            used -= info["fp"]
+            t = self.clock() - t0
+            req = info["req"]
+            results.append(Result(req.rid, req.arrival, info["admitted"], t, req.nsteps, info["dt"], fields))
+            self.trace.append((t, "finish", req.rid))
+
+        def collect():
+            # release the shots retired at the previous poll: their read-back ran beside the
+            # current tick; freeing their device memory waits for the device, as the poll does
+            t_c = self.clock()
+            for info, hnd in retiring:
+                finish(info, self.backend.collect(hnd))
+            retiring.clear()
+            self.phase_s["retire"] += self.clock() - t_c
+
+        while pending or waiting or active or retiring:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
@@ -300,8 +346,10 @@ class BatchServingEngine:
             # while it runs (for about the tick's duration) and join at the following tick
             launched = bool(active)
             if launched:
+                t_l = self.clock()
                 self.backend.step(self.tick)
                 self.ticks += 1
+                self.phase_s["launch"] += self.clock() - t_l
             budget = max(self.min_admit_budget, tick_est if launched else 0.0)
             t_adm = self.clock()
             while waiting and len(active) < self.max_active:
@@ -321,20 +369,24 @@ class BatchServingEngine:
                 self.trace.append((self.clock() - t0, "admit", req.rid))
                 if self.clock() - t_adm >= budget:
                     break
+            self.phase_s["admit"] += self.clock() - t_adm
+            collect()
             if launched:
+                t_p = self.clock()
                 rem = self.backend.poll()
                 if hasattr(self.backend, "tick_seconds"):
                     tick_est = self.backend.tick_seconds()
+                t_r = self.clock()
+                self.phase_s["poll"] += t_r - t_p
                 for slot in sorted(active):
                     if rem[slot] == 0:
                         info = active.pop(slot)
-                        fields = self.backend.retire(slot)
-                        used -= info["fp"]
-                        t = self.clock() - t0
-                        req = info["req"]
-                        results.append(Result(req.rid, req.arrival, info["admitted"], t, req.nsteps, info["dt"], fields))
-                        self.trace.append((t, "finish", req.rid))
-            elif not active and pending:
+                        if asynchronous:
+                            retiring.append((info, self.backend.retire_async(slot)))
+                        else:
+                            finish(info, self.backend.retire(slot))
+                self.phase_s["retire"] += self.clock() - t_r
+            elif not active and pending and not retiring:
                 wait = pending[0].arrival - (self.clock() - t0)
                 if wait > 0:
                     self.sleep(min(wait, 0.05))

@@ -200,3 +200,39 @@ def test_batch_engine_makes_a_callable_payload_once():
     res = eng.run(reqs)
     assert [r.fields for r in res] == [20, 20]
     assert calls == {0: 1, 1: 1}
+
+
+class FakeAsyncBatchBackend(FakeBatchBackend):
+    """Retirement in two halves, as the GPU backend does it: retire_async frees the slot and starts
+    the read-back, collect (one poll later) returns the fields and releases the memory."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.open = 0
+
+    def retire_async(self, slot):
+        out = self.retire(slot)
+        self.open += 1
+        return out
+
+    def collect(self, h):
+        self.open -= 1
+        self.log.append(("collect", h))
+        return h
+
+
+def test_batch_engine_asynchronous_retirement_matches_and_respects_the_cap():
+    from paper_2003_12811_gb300.serve import BatchServingEngine
+    sizes = {0: 40, 1: 40, 2: 40, 3: 10, 4: 10}
+    arrivals, nsteps = [0.0] * 5, [40, 40, 8, 8, 8]
+    clk = VClock()
+    be = FakeAsyncBatchBackend(clk, sizes, max_shots=4)
+    eng = BatchServingEngine(90, backend=be, tick_steps=4, max_active=4, clock=clk, sleep=clk.sleep)
+    res = eng.run([Request(rid=i, arrival=a, problem=i, nsteps=n) for i, (a, n) in enumerate(zip(arrivals, nsteps))])
+    assert [r.fields for r in res] == nsteps
+    assert be.open == 0 and eng.peak_bytes <= 90
+    # a shot's memory counts until its result is collected: request 2 (40) is admitted only after
+    # one of the first two is collected
+    first_collect = next(i for i, e in enumerate(be.log) if e[0] == "collect")
+    admit2 = next(i for i, e in enumerate(be.log) if e[0] == "admit" and e[1] == 2)
+    assert admit2 > first_collect
