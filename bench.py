@@ -525,6 +525,27 @@ def convergence_table(Ns=(41, 81, 161, 321), T=0.5, cfl=0.25):
     return out
 
 
+def batch_profile_run(nshots=8, side=801, nsteps=6, tick=3):
+    """A small served batch for profile captures: nshots shots of side^2 held resident, nsteps
+    steps in ticks of `tick` persistent launches."""
+    import torch
+    from paper_2003_12811_gb300 import Batch, Solver
+    B = Batch(6, nshots)
+    st = torch.cuda.Stream()
+    shots = []
+    for i in range(nshots):
+        S = Solver(W.shot_problem(side, 70 + i), "fp32")
+        B.sbp_batch_add(S, nsteps, S.suggest_dt(0.3))
+        shots.append(S)
+    for _ in range(nsteps // tick):
+        B.sbp_batch_step(tick, st.cuda_stream)
+    rem = B.sbp_batch_poll(st.cuda_stream)
+    for S in shots:
+        S.close()
+    B.close()
+    return {"batch_profile": {"shots": nshots, "side": side, "steps": nsteps, "remaining": list(rem)[:nshots]}}
+
+
 def replica_times(times, world):
     """Job times of `world` independent replicas (one process per GPU, no data exchange): each
     entry is the slowest rank's (MAX over ranks).  torch.distributed must be initialised when
@@ -582,6 +603,8 @@ def main():
     ap.add_argument("--accuracy", action="store_true",
                     help="print the FP32-against-FP64 accuracy table of configs 1-3 and exit")
     ap.add_argument("--adjoint-only", action="store_true", help="print the misfit-gradient measurement alone")
+    ap.add_argument("--batch-profile", action="store_true",
+                    help="run a small served batch (8 shots of 801^2, 6 steps) for a profile capture and exit")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="leapfrog steps of the misfit-gradient workload")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -605,6 +628,9 @@ def main():
     from paper_2003_12811_gb300 import Solver
 
     prec = args.precision
+    if args.batch_profile:
+        print(json.dumps(batch_profile_run()), flush=True)
+        return
     if args.accuracy:
         print(json.dumps({"accuracy": accuracy_table(), "convergence": convergence_table()}), flush=True)
         return 0
