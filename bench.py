@@ -38,9 +38,9 @@ UNIT = "node-updates/s"
 # 1/(rho J) 1 = 19 words
 BYTES_PER_NODE = {"fp32": 76, "fp64": 136}
 # DRAM bytes per node of one FP32 interior launch (dram__bytes_read.sum + dram__bytes_write.sum of
-# k_interior_march<6,0> captured at 2 x 1601x801, scaled by nodes).  Set to None whenever that
+# k_interior_march_multi<6,3> captured at 2 x 1601x801, scaled by nodes).  Set to None whenever that
 # kernel changes until it is measured again.
-TRAFFIC_BYTES_PER_NODE = {"fp32": None, "fp64": None}
+TRAFFIC_BYTES_PER_NODE = {"fp32": 71.75, "fp64": None}
 FALLBACK_HBM_GBS = 6800.0
 N1, N2 = 4001, 2001
 # crop of the workload the oracle is timed on: a 401-column window around the source spanning
