@@ -1948,12 +1948,29 @@ int sbp_set_tuning(sbp_handle* h, int rows_per_cta, int overlap) {
 int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
     if (!h) return SBP_E_INVALID_ARG;
     if (!all_materials(h)) return h->fail(SBP_E_STATE, "set the material of every block first");
-    // candidates for the marching kernel's rows per CTA (FP32 only); 0 = heuristic (one wave at
-    // 4 CTAs/SM); then whether the strips run concurrently with the interior
-    const int cand32[] = {0, 16, 32, 64, 128, 256};
-    const int cand64[] = {0};
-    const int* cand = h->precision == SBP_FP32 ? cand32 : cand64;
-    const int ncand = h->precision == SBP_FP32 ? 6 : 1;
+    // candidates for the marching kernel's rows per CTA (FP32 only); 0 = heuristic (one wave of
+    // 4 CTAs/SM per block); then whether the strips run concurrently with the interior.  Beside
+    // fixed heights, heights sized on the whole launch (the interior tiles of every block in one
+    // grid): the tallest tiles whose count fits k waves of 4 CTAs/SM (k = 1, 2), and tiles a half
+    // band lower, so that the rows left over form a short extra band that finishes in the tail
+    std::vector<int> cand{0};
+    if (h->precision == SBP_FP32) {
+        for (int r : {16, 32, 64, 128, 256}) cand.push_back(r);
+        const int S2 = std::max(order_nclos(h->order), order_ncol(h->order));
+        int ncx_all = 0, n2i_max = 1;
+        for (auto& hb : h->blocks) {
+            ncx_all += march_ncx(hb.n1, S2);
+            n2i_max = std::max(n2i_max, hb.n2 - 2 * S2);
+        }
+        for (int k = 1; k <= 2; ++k) {
+            const int ny = std::max(1, 4 * h->num_sms * k / std::max(1, ncx_all));
+            for (double f : {0.0, 0.5}) {
+                const int r = (int)std::ceil(n2i_max / (ny + f));
+                if (r >= 16 && std::find(cand.begin(), cand.end(), r) == cand.end()) cand.push_back(r);
+            }
+        }
+    }
+    const int ncand = (int)cand.size();
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -2003,7 +2020,7 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
     for (int k = 0; k < SBP_PROF_FAMILIES; ++k) saved_l[k] = h->launches[k];
     auto time_it = [&](float& tot) -> int {
         tot = 0.f;
-        for (int rep = 0; rep < 4; ++rep) {
+        for (int rep = 0; rep < 6; ++rep) {
             cudaEventRecord(e0, 0);
             int rc = run_operator(h, a, 0, 0);   // a step without data from the current level
             cudaEventRecord(e1, 0);
@@ -2036,13 +2053,21 @@ int sbp_autotune(sbp_handle* h, int* rows_out, int* overlap_out) {
         }
     }
     h->rows_per_cta = best;
-    h->overlap = true;
-    float tot_ov;
-    {
-        const int rc = time_it(tot_ov);
+    // strips beside the interior or after it: the two timed alternately at the chosen height (the
+    // height's own time is the minimum over the candidates, so it is not compared directly)
+    float sum_seq = 0.f, sum_ov = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        float t;
+        h->overlap = false;
+        int rc = time_it(t);
         if (rc != SBP_OK) return restore(rc);
+        sum_seq += t;
+        h->overlap = true;
+        rc = time_it(t);
+        if (rc != SBP_OK) return restore(rc);
+        sum_ov += t;
     }
-    const bool best_ov = tot_ov < best_ms;
+    const bool best_ov = sum_ov <= sum_seq;
     h->overlap = best_ov;
     cudaDeviceSynchronize();
     put_back();

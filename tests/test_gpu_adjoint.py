@@ -82,11 +82,11 @@ def test_gradient_matches_oracle_fp64(order):
     assert phi == pytest.approx(ref["misfit"], rel=1e-12)
     for b in range(2):
         scale = np.max(np.abs(ref["grad_rho"][b]))
-        assert np.max(np.abs(gr[b] - ref["grad_rho"][b])) <= 1e-9 * scale, b
+        assert np.max(np.abs(gr[b] - ref["grad_rho"][b])) <= 1e-12 * scale, b
     got = np.array([gc[b][Pp, i2, i1] for (b, Pp, i1, i2) in params])
     scale = np.max(np.abs(ref["grad_C"]))
     err = np.abs(got - ref["grad_C"])
-    assert np.all(err <= 1e-9 * scale), [(params[k], got[k], ref["grad_C"][k]) for k in np.argsort(-err)[:5]]
+    assert np.all(err <= 1e-12 * scale), [(params[k], got[k], ref["grad_C"][k]) for k in np.argsort(-err)[:5]]
 
 
 @pytest.mark.parametrize("order", (4, 6))
@@ -166,10 +166,13 @@ def test_misfit_gradient_workload_small():
     phi, gr, gc = S.sbp_misfit_gradient(nsteps, dt, obs)
     S.close()
     assert ref["misfit"] > 0 and phi == pytest.approx(ref["misfit"], rel=1e-12)
+    # 60 steps; the density term sums psi_n . (u_{n+1} - 2 u_n + u_{n-1}), a second difference in
+    # time that cancels about two digits of the FP64 levels (measured: 2.4e-12 of the largest entry)
     scale = np.max(np.abs(ref["grad_rho"][0]))
-    assert np.max(np.abs(gr[0] - ref["grad_rho"][0])) <= 1e-9 * scale
+    assert np.max(np.abs(gr[0] - ref["grad_rho"][0])) <= 1e-11 * scale
     got = np.array([gc[0][Pp, i2, i1] for (_, Pp, i1, i2) in params])
-    assert np.max(np.abs(got - ref["grad_C"])) <= 1e-9 * np.max(np.abs(ref["grad_C"]))
+    # the scale is the largest of five sampled entries, not of the field (measured: 4.1e-12 of it)
+    assert np.max(np.abs(got - ref["grad_C"])) <= 1e-11 * np.max(np.abs(ref["grad_C"]))
 
 
 def test_autograd_bridge_and_gpu_central_differences():
@@ -231,4 +234,4 @@ def test_voigt_gradient_matches_oracle_fp64():
     assert gc[0].shape == (6, n2, n1)
     got = np.array([gc[b][V, i2, i1] for (b, (_, V), i1, i2) in params])
     scale = np.max(np.abs(ref["grad_C"]))
-    assert np.all(np.abs(got - ref["grad_C"]) <= 1e-9 * scale)
+    assert np.all(np.abs(got - ref["grad_C"]) <= 1e-12 * scale)
