@@ -371,6 +371,50 @@ RK4_WORDS_PER_STAGE = 31
 WIDE_WORDS_IMPLEMENTED = {"fp32": 29, "fp64": 27}
 
 
+# FP64 operations of k_interior<double, 6, 0> per interior node (ncu thread-level counts
+# 2 x DFMA + DADD + DMUL over the 299,889 interior nodes of one 801 x 401 block) and the FP64 peak
+# of the part: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz
+FP64_FLOPS_PER_NODE = 431.6
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_bench(P, nsteps=20):
+    """The FP64 path on the bench workload: node updates/s, the interior kernel's share, and its
+    rooflines: HBM at 136 B/node and the FP64 ALU (the bound this path actually meets)."""
+    import torch
+    from paper_2003_12811_gb300 import Solver
+    nodes = P.n_nodes
+    S = Solver(P, "fp64")
+    dt = S.suggest_dt(0.3)
+    zero = [np.zeros((2, b.N2, b.N1)) for b in P.blocks]
+    S.set_state(zero, zero, 0.0)
+    S.sbp_step(2, dt)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.sbp_step(nsteps, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    S.sbp_profile(True)
+    S.sbp_step(4, dt)
+    fam_ms, fam_n = S.sbp_profile_read()
+    S.sbp_profile(False)
+    S.close()
+    inner = sum((b.N1 - 18) * (b.N2 - 18) for b in P.blocks)
+    k_ms = fam_ms[0] / 4
+    peak, src = peaks()
+    tflops = FP64_FLOPS_PER_NODE * inner / (k_ms / 1e3) / 1e12
+    return {"node_updates_per_s": nodes / (ms / 1e3), "ms_per_step": ms, "interior_ms_per_step": k_ms,
+            "hbm": {"bytes_per_node": BYTES_PER_NODE["fp64"], "achieved_GBs": BYTES_PER_NODE["fp64"] * inner / (k_ms / 1e3) / 1e9,
+                    "frac": BYTES_PER_NODE["fp64"] * inner / (k_ms / 1e3) / 1e9 / peak, "peak_source": src},
+            "alu": {"bound": "alu", "kernel": "k_interior<double,6,0>", "flops_per_node": FP64_FLOPS_PER_NODE,
+                    "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz"},
+            "steps": nsteps}
+
+
 def variant_bench(P, prec, nsteps=100):
     """The time integrator and operator variants on the bench workload: RK4 steps (the paper's
     integrator; four fused stage passes per step) and leapfrog steps of the wide-stencil operator,
@@ -726,6 +770,8 @@ def main():
     S.close()
     if rank == 0 and world == 1 and not args.no_variants:
         line["variants"] = variant_bench(P, prec)
+        if prec == "fp32":
+            line["variants"]["fp64"] = fp64_bench(P)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_bench()
     if rank == 0 and world == 1 and not args.no_adjoint:
