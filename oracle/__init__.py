@@ -16,6 +16,8 @@ scheme  metric (Sec. 3.2-3.3), transformed stiffness, the discrete elastic opera
         (Sec. 4.6-4.7), boundary SATs (Sec. 5), interface SATs (Sec. 6), leapfrog and RK4
         time stepping, discrete energy, CFL time step (Sec. 7), Ricker wavelet and
         discrete delta point sources (Sec. 7.4).
+scheme3d the same operator and boundary SATs in three dimensions on one curvilinear block
+        (Sec. 3.3 with eq. surfj_app_3d, Sec. 4.3-4.7 and 5 for d = 3), leapfrog and energy.
 adjoint discrete adjoint of the leapfrog scheme with explicit transposes, receiver misfit and its
         gradient with respect to density and stiffness (Sec. 5.2 remark, Theorems 3 and 5).
 
