@@ -415,6 +415,74 @@ def fp64_bench(P, nsteps=20):
             "steps": nsteps}
 
 
+# 3-D operator: words per node each bulk kernel must move (FP32 words; FP64 doubles them)
+#   k3_flux: u (3) and the 27 mixed coefficients in, the 9 fluxes q out            = 39
+#   k3_div:  q (9), the 18 narrow coefficients, w, u (3), du (3) in; du, u^{n+1} out = 40
+#   one fused pass at the minimum: u, du, 45 coefficients, w in; du, u^{n+1} out     = 58
+OP3D_WORDS = {"k3_flux": 39, "k3_div": 40, "fused_min": 58}
+
+
+def bench3d(n=256, nsteps=40, prec="fp32"):
+    """The 3-D operator on one curvilinear block of n^3 nodes (order 6; tilted transversely
+    isotropic medium with smooth heterogeneity; topography-like top face with traction, five
+    displacement faces): leapfrog node updates/s and the rooflines of the two bulk kernels
+    (CUDA events on the launch stream)."""
+    import torch
+    from workloads import box3d as B3
+    from paper_2003_12811_gb300 import Solver3D
+    N = (n, n, n)
+    faces = ("displacement",) * 5 + ("traction",)
+    X = B3.block3_coords(N)
+    S = Solver3D(X, faces, 6, prec)
+    for k0 in range(0, n, 32):
+        k1 = min(n, k0 + 32)
+        rho, Pm = B3.material3_planes(N, k0=k0, k1=k1)
+        S.sbp3_set_material(k0, k1 - k0, rho, Pm)
+    # a stable step for the medium: 0.2 x (smallest spacing of the deformed box) / (fastest P speed)
+    hmin = min(np.abs(np.diff(X[0], axis=2)).min(), np.abs(np.diff(X[1], axis=1)).min(),
+               np.abs(np.diff(X[2], axis=0)).min())
+    del X
+    dt = 0.2 * hmin / (2.3 * np.sqrt(1.3))
+    g1, g2, g3 = B3.ref_grid3(*N)
+    u = np.array([np.sin(np.pi * g1) * np.sin(np.pi * g2) * np.sin(np.pi * g3 / 2)] * 3)
+    del g1, g2, g3
+    S.set_state(u, u)
+    del u
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    S.step(3, dt, sh)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.step(nsteps, dt, sh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    S.profile(True)
+    S.step(4, dt, sh)
+    fam_ms, fam_n = S.profile_read()
+    S.profile(False)
+    a, b = S.state()
+    finite = bool(np.isfinite(b).all())
+    S.close()
+    nodes = n ** 3
+    es = 4 if prec == "fp32" else 8
+    peak, src = peaks()
+    kern = {}
+    for f, name in enumerate(("k3_flux", "k3_div", "k3_face")):
+        kms = fam_ms[f] / 4
+        kern[name] = {"ms_per_step": kms}
+        if name in OP3D_WORDS:
+            gbs = OP3D_WORDS[name] * es * nodes / (kms / 1e3) / 1e9
+            kern[name].update({"bytes_per_node": OP3D_WORDS[name] * es, "achieved_GBs": gbs, "frac": gbs / peak})
+    fused = OP3D_WORDS["fused_min"] * es * nodes / (ms / 1e3) / 1e9
+    return {"workload": f"3-D block {n}^3 nodes, order 6, {prec.upper()}, leapfrog in increment form",
+            "node_updates_per_s": nodes / (ms / 1e3), "ms_per_step": ms, "kernels": kern,
+            "step_vs_fused_minimum": {"bytes_per_node": OP3D_WORDS["fused_min"] * es, "achieved_GBs": fused,
+                                      "frac": fused / peak},
+            "peak_GBs": peak, "peak_source": src, "launches_per_step": 5, "steps": nsteps, "state_finite": finite}
+
+
 def variant_bench(P, prec, nsteps=100):
     """The time integrator and operator variants on the bench workload: RK4 steps (the paper's
     integrator; four fused stage passes per step) and leapfrog steps of the wide-stencil operator,
@@ -650,6 +718,8 @@ def main():
     ap.add_argument("--batch-profile", action="store_true",
                     help="run a small served batch (8 shots of 801^2, 6 steps) for a profile capture and exit")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="leapfrog steps of the misfit-gradient workload")
+    ap.add_argument("--op3d-only", action="store_true", help="print the 3-D operator measurement alone")
+    ap.add_argument("--n3d", type=int, default=256, help="nodes per direction of the 3-D operator workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -680,6 +750,9 @@ def main():
         return 0
     if args.adjoint_only:
         print(json.dumps(adjoint_bench(nsteps=args.adjoint_steps, prec=prec)), flush=True)
+        return 0
+    if args.op3d_only:
+        print(json.dumps(bench3d(n=args.n3d, prec=prec)), flush=True)
         return 0
     P = W.config3(n1=args.n1, n2=args.n2)
     S = Solver(P, prec)
@@ -770,6 +843,7 @@ def main():
     S.close()
     if rank == 0 and world == 1 and not args.no_variants:
         line["variants"] = variant_bench(P, prec)
+        line["variants"]["op3d"] = bench3d(n=args.n3d, prec=prec)
         if prec == "fp32":
             line["variants"]["fp64"] = fp64_bench(P)
     if rank == 0 and world == 1 and not args.no_serving:

@@ -1,0 +1,85 @@
+/*
+ * libsbp, 3-D operator -- C-ABI of the GB300 (sm_103a) SBP-SAT elastic operator in three
+ * dimensions on one curvilinear block (the paper states the scheme for d dimensions:
+ * Sec. 3.2-3.3 with eq. surfj_app_3d for the metric, Sec. 4.3-4.7 for the operator, Sec. 5 for
+ * the boundary SATs with the penalty of Theorem 3 at d = 3).
+ *
+ * Per node the scheme is rho J u_j'' = sum_ik DD_ik(c_ijkl) u_l + J SAT_j with
+ * c_ijkl = J F_Ii C_IjKl F_Kk (F = G^-1, G_iI = D_i X_I), DD_ii the narrow operator D_xx^FC(c)
+ * along direction i and DD_ik = D_i c D_k for i != k.  Faces carry either the traction SAT
+ * (Robin face of eq. sat_traction with U = 0, g = 0) or the displacement SAT (eq.
+ * dirichlet_ansatz with g = 0, J^ Z_JL = beta d / h1 c_mJmL, d = 3).  Time stepping is leapfrog,
+ * u^{n+1} = 2 u^n - u^{n-1} + dt^2 (rho J)^-1 [ DD(c) u^n + J SAT(u^n) ].
+ *
+ * Conventions
+ *  - Status codes, precisions and sbp_last_error-style messages as in sbp.h; every call returns
+ *    SBP_OK or a negative SBP_E_* code and never aborts.  sbp3_last_error describes the last
+ *    failure of a handle (or of sbp3_create when passed NULL).
+ *  - The block has n1 x n2 x n3 nodes; node (i1, i2, i3) of a host array sits at index
+ *    (i3 * n2 + i2) * n1 + i1 (x1 fastest).  Vector fields hold their three components one after
+ *    the other (component stride n1 n2 n3).  Faces: 0: x1=0, 1: x1=1, 2: x2=0, 3: x2=1,
+ *    4: x3=0, 5: x3=1.
+ *  - Host arrays passed in are copied (the caller keeps ownership); host arrays written out are
+ *    caller-allocated.  Host values are double precision.  Device memory is owned by the handle.
+ *  - Orders 2, 4, 6 need n_i >= 5, 18, 27 nodes per direction.
+ */
+#ifndef SBP3_H
+#define SBP3_H
+
+#include "sbp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBP3_BC_DISPLACEMENT 0   /* u = 0 weakly, SAT of eq. dirichlet_ansatz */
+#define SBP3_BC_TRACTION 1       /* traction-free, SAT of eq. sat_traction with U = 0 */
+
+#define SBP3_PROF_FAMILIES 3     /* 0: k3_flux, 1: k3_div, 2: k3_face */
+
+typedef struct sbp3_handle sbp3_handle;
+
+/* Create the block and compute its metric on the device.  X: 3 * n1*n2*n3 physical node
+ * coordinates (X_1, X_2, X_3 one after the other); face_kinds: six SBP3_BC_* values;
+ * beta >= 1 the penalty factor.  The material must then be set for every x3-plane
+ * (sbp3_set_material) before sbp3_step or sbp3_apply. */
+int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* X, const int* face_kinds,
+                double beta, sbp3_handle** out);
+int sbp3_destroy(sbp3_handle* h);
+const char* sbp3_last_error(const sbp3_handle* h);
+
+/* Device bytes a handle of this size holds (material, state, fluxes, metric staging). */
+int sbp3_footprint(int precision, int n1, int n2, int n3, long long* bytes_out);
+
+/* Density and stiffness of the x3-planes i3_begin <= i3 < i3_begin + i3_count (any chunking).
+ * rho: i3_count*n2*n1 values; C45: 45 * (i3_count*n2*n1) values, entry t of the upper triangle
+ * (row-major) of the 9 x 9 pair matrix M[3I+J][3K+L] = C_IJKL, t = 9p - p(p-1)/2 + (q - p) for
+ * p <= q.  The transformed c_ijkl (45 entries per node) and 1/(rho J) are formed on the device.
+ * SBP_E_JACOBIAN_NONPOSITIVE if J <= 0 at a node of these planes (Sec. 3.3). */
+int sbp3_set_material(sbp3_handle* h, int i3_begin, int i3_count, const double* rho, const double* C45);
+
+/* Leapfrog levels u^{n-1}, u^n (3 * n1*n2*n3 each).  In FP32 the handle keeps the increment
+ * u^n - u^{n-1}, formed here in double precision, beside u^n. */
+int sbp3_set_state(sbp3_handle* h, const double* u_prev, const double* u_cur);
+int sbp3_get_state(sbp3_handle* h, double* u_prev, double* u_cur);
+
+/* accel = (rho J)^-1 [ DD(c) u + J SAT(u) ] for the host field u (3 * n1*n2*n3); the state is
+ * left untouched. */
+int sbp3_apply(sbp3_handle* h, const double* u, double* accel);
+
+/* nsteps leapfrog steps of size dt on the given CUDA stream (NULL: the default stream); the call
+ * returns once the launches are queued. */
+int sbp3_step(sbp3_handle* h, int nsteps, double dt, void* stream);
+
+/* Per-family device time (CUDA events on the launch stream) of the launches made while enabled,
+ * and the launch counts since create (always counted).  ms and launches hold
+ * SBP3_PROF_FAMILIES entries; sbp3_profile_read synchronizes the device. */
+int sbp3_profile(sbp3_handle* h, int enable);
+int sbp3_profile_read(sbp3_handle* h, double* ms, long long* launches);
+
+int sbp3_get_info(const sbp3_handle* h, long long* nodes_out, int* precision_out, int* order_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -44,7 +44,8 @@ class Oracle3D:
         N1, N2, N3 = blk.N
         self.Ns = (N1, N2, N3)
         self.N = N1 * N2 * N3
-        self.op = [SBP1D(blk.order, n, 1.0 / (n - 1)) for n in self.Ns]
+        hs = blk.h if getattr(blk, "h", None) is not None else tuple(1.0 / (n - 1) for n in self.Ns)
+        self.op = [SBP1D(blk.order, n, h) for n, h in zip(self.Ns, hs)]
         self.I = [sp.identity(n, format="csr") for n in self.Ns]
         self.Dr = [self.kr(i, self.op[i].D) for i in range(3)]
         self.Hvec = np.kron(self.op[2].H, np.kron(self.op[1].H, self.op[0].H))
@@ -164,6 +165,8 @@ class Oracle3D:
         for f, kind in enumerate(self.blk.faces):
             fc = self.faces[f]
             m, P = fc["m"], fc["P"]
+            if kind == "open":
+                continue                       # a crop edge: no SAT (oracle windows of a larger block)
             if kind == "traction":
                 T = self.traction_rows(f)
                 for J in range(3):

@@ -15,6 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsbp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "sbp.h")
+HEADER3 = os.path.join(os.path.dirname(HERE), "include", "sbp3.h")
 
 SBP_OK = 0
 STATUS = {0: "SBP_OK", -1: "SBP_E_INVALID_ARG", -2: "SBP_E_JACOBIAN_NONPOSITIVE",
@@ -53,9 +54,9 @@ _DP = C.POINTER(C.c_double)
 
 
 def header_functions():
-    """Names of the functions declared in include/sbp.h."""
-    txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s+(sbp_\w+)\s*\(", txt, re.M)))
+    """Names of the functions declared in include/sbp.h and include/sbp3.h."""
+    txt = open(HEADER).read() + open(HEADER3).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s+(sbp3?_\w+)\s*\(", txt, re.M)))
 
 
 def lib():
@@ -113,6 +114,20 @@ def lib():
         L.sbp_record.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP]
         L.sbp_misfit_gradient.argtypes = [C.c_void_p, C.c_int, C.c_double, _DP, C.c_int, _DP,
                                           C.POINTER(_DP), C.POINTER(_DP), C.c_int]
+        L.sbp3_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DP, C.POINTER(C.c_int), C.c_double,
+                                  C.POINTER(C.c_void_p)]
+        L.sbp3_destroy.argtypes = [C.c_void_p]
+        L.sbp3_last_error.argtypes = [C.c_void_p]
+        L.sbp3_last_error.restype = C.c_char_p
+        L.sbp3_footprint.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
+        L.sbp3_set_material.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP, _DP]
+        L.sbp3_set_state.argtypes = [C.c_void_p, _DP, _DP]
+        L.sbp3_get_state.argtypes = [C.c_void_p, _DP, _DP]
+        L.sbp3_apply.argtypes = [C.c_void_p, _DP, _DP]
+        L.sbp3_step.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+        L.sbp3_profile.argtypes = [C.c_void_p, C.c_int]
+        L.sbp3_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
+        L.sbp3_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -433,3 +448,100 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- 3-D operator (include/sbp3.h)
+BC3 = {"displacement": 0, "traction": 1}
+PROF3_FAMILIES = 3     # SBP3_PROF_FAMILIES: k3_flux, k3_div, k3_face
+
+
+def footprint3_bytes(N, precision="fp32"):
+    out = C.c_longlong()
+    rc = lib().sbp3_footprint(FP64 if precision == "fp64" else FP32, N[0], N[1], N[2], C.byref(out))
+    if rc != SBP_OK:
+        raise SbpError(rc, lib().sbp3_last_error(None).decode())
+    return int(out.value)
+
+
+class Solver3D:
+    """A 3-D libsbp handle (include/sbp3.h) for one block.  ``X`` is (3, N3, N2, N1); the material
+    is given per chunk of x3-planes with ``sbp3_set_material`` (rho (k, N2, N1), C45 (45, k, N2, N1)),
+    or at once from a ``workloads.box3d.Block3D`` through ``from_block``."""
+
+    def __init__(self, X, faces, order=6, precision="fp64", beta=1.0):
+        self.L = lib()
+        X = _f64(X)
+        self.shape = X.shape[1:]
+        self.N = (X.shape[3], X.shape[2], X.shape[1])
+        self.precision = FP64 if precision == "fp64" else FP32
+        kinds = (C.c_int * 6)(*[BC3[f] for f in faces])
+        h = C.c_void_p()
+        rc = self.L.sbp3_create(order, self.precision, self.N[0], self.N[1], self.N[2], _ptr(X), kinds, float(beta),
+                                C.byref(h))
+        if rc != SBP_OK:
+            raise SbpError(rc, self.L.sbp3_last_error(None).decode())
+        self.h = h
+
+    @classmethod
+    def from_block(cls, blk, precision="fp64", pair45=None):
+        S = cls(blk.X, blk.faces, blk.order, precision, blk.beta)
+        try:
+            P = pair45(blk.C) if pair45 is not None else _pair45(blk.C)
+            S.sbp3_set_material(0, blk.shape[0], blk.rho, P)
+        except Exception:
+            S.close()
+            raise
+        return S
+
+    def _check(self, rc):
+        if rc != SBP_OK:
+            raise SbpError(rc, self.L.sbp3_last_error(self.h).decode())
+
+    def sbp3_set_material(self, i3_begin, i3_count, rho, C45):
+        rho, C45 = _f64(rho), _f64(C45)
+        self._check(self.L.sbp3_set_material(self.h, i3_begin, i3_count, _ptr(rho), _ptr(C45)))
+
+    def set_state(self, u_prev, u_cur):
+        a, b = _f64(u_prev), _f64(u_cur)
+        self._check(self.L.sbp3_set_state(self.h, _ptr(a), _ptr(b)))
+
+    def state(self):
+        a = np.empty((3,) + tuple(self.shape))
+        b = np.empty_like(a)
+        self._check(self.L.sbp3_get_state(self.h, _ptr(a), _ptr(b)))
+        return a, b
+
+    def apply(self, u):
+        u = _f64(u)
+        out = np.empty_like(u)
+        self._check(self.L.sbp3_apply(self.h, _ptr(u), _ptr(out)))
+        return out
+
+    def step(self, nsteps, dt, stream=None):
+        self._check(self.L.sbp3_step(self.h, int(nsteps), float(dt), stream))
+
+    def profile(self, enable):
+        self._check(self.L.sbp3_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        ms = (C.c_double * PROF3_FAMILIES)()
+        n = (C.c_longlong * PROF3_FAMILIES)()
+        self._check(self.L.sbp3_profile_read(self.h, ms, n))
+        return list(ms), list(n)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sbp3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _pair45(Cfull):
+    """Full tensor C[I,J,K,L,...] -> 45 planes: upper triangle of M[p][q], p = 3I+J, q = 3K+L."""
+    M = Cfull.reshape((9, 9) + Cfull.shape[4:])
+    return np.stack([M[p, q] for p in range(9) for q in range(p, 9)])

@@ -86,3 +86,27 @@ def test_footprint_covers_every_device_buffer(L, prec):
         need += sum(7 * (blk.N2 if f < 2 else blk.N1) * es for f, face in enumerate(blk.faces) if face.kind == "interface")
     fp = footprint_bytes(P, prec)
     assert need <= fp <= 1.05 * need + (1 << 20), (need, fp)
+
+
+def test_sbp3_validation_before_device_work(L):
+    """sbp3_create rejects bad arguments before any CUDA call (so this runs without a GPU)."""
+    n = 27
+    X = np.zeros(3 * n * n * n)
+    kinds = (C.c_int * 6)(*([1] * 6))
+    h = C.c_void_p()
+    P = C.POINTER(C.c_double)
+    xp = X.ctypes.data_as(P)
+    assert L.sbp3_create(5, 0, n, n, n, xp, kinds, 1.0, C.byref(h)) == -1          # order
+    assert L.sbp3_create(6, 3, n, n, n, xp, kinds, 1.0, C.byref(h)) == -1          # precision
+    assert L.sbp3_create(6, 0, 26, n, n, xp, kinds, 1.0, C.byref(h)) == -1         # too few nodes
+    assert L.sbp3_create(6, 0, n, n, n, None, kinds, 1.0, C.byref(h)) == -1        # no coordinates
+    bad = (C.c_int * 6)(*([1] * 5 + [2]))
+    assert L.sbp3_create(6, 0, n, n, n, xp, bad, 1.0, C.byref(h)) == -1            # face kind
+    assert L.sbp3_create(6, 0, n, n, n, xp, kinds, 0.0, C.byref(h)) == -1          # beta
+    X[5] = np.nan
+    assert L.sbp3_create(6, 0, n, n, n, xp, kinds, 1.0, C.byref(h)) == -1          # non-finite X
+    assert b"non-finite" in L.sbp3_last_error(None)
+    out = C.c_longlong()
+    assert L.sbp3_footprint(1, 256, 256, 256, C.byref(out)) == 0
+    # 64 FP32 fields + 3 FP64 coordinate fields per node
+    assert out.value == 256 ** 3 * (64 * 4 + 3 * 8)

@@ -176,3 +176,25 @@ def test_leapfrog_conserves_energy():
     E1 = O.energy(a, c, dt)
     assert E0 > 0
     assert abs(E1 - E0) < 1e-11 * E0
+
+
+def test_crop_window_matches_whole_block_at_its_centre():
+    """The oracle on a crop with 'open' cut faces and the whole block's spacing gives the whole
+    block's accelerations wherever the stencils (and the metric rows they read) stay inside the
+    crop: here the crop's central node.  This is what the full-size sampled parity relies on."""
+    N = (40, 38, 41)
+    b = B.random_block3(N=N, order=6)
+    u = B.smooth_state3(b)
+    a = Oracle3D(b).accel(u)
+    for lo in ((6, 5, 7), (0, 11, 14), (13, 0, 14)):
+        hi = tuple(l + 27 for l in lo)
+        c = B.crop_block3(b, lo, hi)
+        sub = u[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        ac = Oracle3D(c).accel(sub)
+        for node in ((13, 13, 13), (2, 13, 13) if lo[0] == 0 else (13, 13, 13), (13, 1, 13) if lo[1] == 0 else (13, 13, 13)):
+            i1, i2, i3 = node
+            got = ac[:, i3, i2, i1]
+            ref = a[:, lo[2] + i3, lo[1] + i2, lo[0] + i1]
+            assert np.abs(got - ref).max() < 1e-10 * np.abs(a).max()
+        cc = B.random_block3_crop(N, lo, hi, order=6, faces=b.faces)
+        assert np.array_equal(cc.X, c.X) and np.allclose(cc.C, c.C, rtol=1e-15, atol=0) and cc.faces == c.faces

@@ -8,7 +8,7 @@ Conventions
 * Fields are numpy arrays of shape ``(N3, N2, N1)`` (x1 fastest); vector fields ``(3, N3, N2, N1)``.
 * Faces are numbered 0: x1=0, 1: x1=1, 2: x2=0, 3: x2=1, 4: x3=0, 5: x3=1 (reference coordinates).
   A face is 'traction' (the Robin face of Sec. 5.1 with U = 0 and g = 0) or 'displacement'
-  (Sec. 5.2 with g = 0).
+  (Sec. 5.2 with g = 0); 'open' marks the cut edge of a crop (no SAT; oracle windows only).
 * The stiffness is stored in full, ``C[I, J, K, L]`` of shape ``(3, 3, 3, 3, N3, N2, N1)`` (major
   symmetry; minor symmetry not assumed).  ``pair45`` packs it into the 45 entries of the upper
   triangle of the 9 x 9 pair matrix over (IJ) = 11, 12, 13, 21, ..., 33, the layout the C-ABI takes.
@@ -16,7 +16,7 @@ Conventions
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import Tuple
+from typing import Optional, Tuple
 
 import numpy as np
 
@@ -33,6 +33,7 @@ class Block3D:
     faces: Tuple[str, ...]            # six kinds, 'traction' or 'displacement'
     order: int = 6
     beta: float = 1.0                 # SAT penalty factor (beta = 1 in the paper)
+    h: Optional[Tuple[float, float, float]] = None   # reference spacing; default 1/(N_i - 1)
 
     @property
     def shape(self) -> Tuple[int, int, int]:
@@ -240,3 +241,38 @@ def bench_block3(n=(256, 256, 256), order=6, seed=SEED) -> Block3D:
     """The 3-D bench workload: a deformed box with topography on x3 = 1, tilted TTI medium with
     smooth heterogeneity, traction on the top face and displacement faces elsewhere."""
     return random_block3(N=n, order=order, faces=("displacement",) * 5 + ("traction",), seed=seed)
+
+
+def crop_block3(b: Block3D, lo, hi) -> Block3D:
+    """The nodes lo[i] <= i_i < hi[i] of ``b`` as a block of its own, keeping the spacing of ``b``.
+    A face that cuts through ``b`` becomes 'open'; a face on the boundary of ``b`` keeps its kind."""
+    N = b.N
+    sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    faces = []
+    for f in range(6):
+        m, side = f // 2, f % 2
+        on_bdry = lo[m] == 0 if side == 0 else hi[m] == N[m]
+        faces.append(b.faces[f] if on_bdry else "open")
+    h = b.h if b.h is not None else tuple(1.0 / (n - 1) for n in N)
+    return Block3D(X=b.X[(slice(None),) + sl].copy(), rho=b.rho[sl].copy(), C=b.C[(slice(None),) * 4 + sl].copy(),
+                   faces=tuple(faces), order=b.order, beta=b.beta, h=h)
+
+
+def random_block3_crop(N, lo, hi, order=6, faces=("displacement",) * 5 + ("traction",), seed=SEED,
+                       curved=True, aniso=True, beta=1.0) -> Block3D:
+    """crop_block3 of random_block3(N, ...) without forming the whole block's stiffness."""
+    X = block3_coords(N, seed, curved)
+    rho, P = material3_planes(N, seed, lo[2], hi[2], aniso)
+    sl = (slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    rho = rho[(slice(None),) + sl]
+    C = tensor_from_pair45(P[(slice(None), slice(None)) + sl])
+    full = Block3D(X=X[:, lo[2]:hi[2]][(slice(None), slice(None)) + sl], rho=rho, C=C, faces=tuple(faces),
+                   order=order, beta=beta)
+    out = []
+    for f in range(6):
+        m, side = f // 2, f % 2
+        on_bdry = lo[m] == 0 if side == 0 else hi[m] == N[m]
+        out.append(faces[f] if on_bdry else "open")
+    full.faces = tuple(out)
+    full.h = tuple(1.0 / (n - 1) for n in N)
+    return full
