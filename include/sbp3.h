@@ -35,7 +35,7 @@ extern "C" {
 #define SBP3_BC_DISPLACEMENT 0   /* u = 0 weakly, SAT of eq. dirichlet_ansatz */
 #define SBP3_BC_TRACTION 1       /* traction-free, SAT of eq. sat_traction with U = 0 */
 
-#define SBP3_PROF_FAMILIES 3     /* 0: k3_flux, 1: k3_div, 2: k3_face */
+#define SBP3_PROF_FAMILIES 3     /* 0: k3_flux, 1: k3_div_int, 2: k3_div_shell (with the face SATs) */
 
 typedef struct sbp3_handle sbp3_handle;
 
@@ -48,8 +48,10 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
 int sbp3_destroy(sbp3_handle* h);
 const char* sbp3_last_error(const sbp3_handle* h);
 
-/* Device bytes a handle of this size holds (material, state, fluxes, metric staging). */
-int sbp3_footprint(int precision, int n1, int n2, int n3, long long* bytes_out);
+/* Device bytes a handle of this order, precision and size holds: 64 words per node (45 coefficients,
+ * 1/(rho J), two levels, the increment, 9 fluxes), the FP64 coordinates and the x1 closure
+ * matrices of D_xx^FC (2 x NCLOS x NCLOSJ x 6 words per x1 line). */
+int sbp3_footprint(int order, int precision, int n1, int n2, int n3, long long* bytes_out);
 
 /* Density and stiffness of the x3-planes i3_begin <= i3 < i3_begin + i3_count (any chunking).
  * rho: i3_count*n2*n1 values; C45: 45 * (i3_count*n2*n1) values, entry t of the upper triangle

@@ -119,7 +119,7 @@ def lib():
         L.sbp3_destroy.argtypes = [C.c_void_p]
         L.sbp3_last_error.argtypes = [C.c_void_p]
         L.sbp3_last_error.restype = C.c_char_p
-        L.sbp3_footprint.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
+        L.sbp3_footprint.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
         L.sbp3_set_material.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP, _DP]
         L.sbp3_set_state.argtypes = [C.c_void_p, _DP, _DP]
         L.sbp3_get_state.argtypes = [C.c_void_p, _DP, _DP]
@@ -452,12 +452,12 @@ class Batch:
 
 # ----------------------------------------------------------------------------- 3-D operator (include/sbp3.h)
 BC3 = {"displacement": 0, "traction": 1}
-PROF3_FAMILIES = 3     # SBP3_PROF_FAMILIES: k3_flux, k3_div, k3_face
+PROF3_FAMILIES = 3     # SBP3_PROF_FAMILIES: k3_flux, k3_div_int, k3_div_shell (with the face SATs)
 
 
-def footprint3_bytes(N, precision="fp32"):
+def footprint3_bytes(N, precision="fp32", order=6):
     out = C.c_longlong()
-    rc = lib().sbp3_footprint(FP64 if precision == "fp64" else FP32, N[0], N[1], N[2], C.byref(out))
+    rc = lib().sbp3_footprint(order, FP64 if precision == "fp64" else FP32, N[0], N[1], N[2], C.byref(out))
     if rc != SBP_OK:
         raise SbpError(rc, lib().sbp3_last_error(None).decode())
     return int(out.value)

@@ -1,9 +1,10 @@
 // libsbp 3-D operator kernels: one curvilinear block of n1 x n2 x n3 nodes (the d = 3 form of
 // Sec. 3.3, 4.3-4.7 and 5).  A leapfrog step is three kernel families:
 //   k3_flux  -- the mixed fluxes q_ij = sum_{k != i} c_ijkl D_k u_l (9 fields) from u^n;
-//   k3_div   -- r_j = sum_i D_i q_ij + sum_i D_ii^FC(c_ijil) u_l, then the leapfrog store;
-//   k3_face  -- the traction / displacement SATs of the two faces x_m = 0, 1 (one launch per m),
-//               added to the stored step (they are linear in r, so they can follow k3_div).
+//   k3_div_int / k3_div_shell -- r_j = sum_i D_i q_ij + sum_i D_ii^FC(c_ijil) u_l, then the leapfrog
+//               store (MODE 0: increment form, d = du + dt^2 w r, un = u + d; MODE 1: out = w r), on
+//               the interior box (interior rows only) and on the boundary shell (closure rows and
+//               the traction / displacement SATs of every face that reaches the node).
 // Layout: every scalar field is [n3][n2][pitch] in the arithmetic type T, pitch = n1 rounded up
 // to 128 bytes; field f of a group starts at f * fs (fs = n3 * n2 * pitch).
 //   cm: 27 fields, M^{ik}_{jl} = c_ijkl for the pairs (i, k) = (1,2), (1,3), (2,3), field 9p + 3j + l
@@ -11,6 +12,8 @@
 //   cd: 18 fields, c_ijil of direction i as a symmetric 3 x 3 (jl = 11 12 13 22 23 33), field 6i + s;
 //   w : 1 / (rho J).
 #pragma once
+#include <utility>
+
 #include "sbp_device.cuh"
 
 namespace sbp3 {
@@ -46,44 +49,172 @@ __device__ __forceinline__ T cfull(const T* __restrict__ cm, const T* __restrict
 
 // ------------------------------------------------------------------ narrow D_xx^FC for 3 components
 // r_j += h^2 sum_l D_xx^FC(b_jl) u_l along one grid line; u(l, t) and b(s, t) read index t of
-// the line, b symmetric with s = sym3(j, l).  Closure rows from the coefficient table, interior
-// rows through the edge weights E_m (the same splitting as the 2-component rows).
-template <int O, typename T, class FU, class FB>
-__device__ __forceinline__ void dxx3(int N, int i, FU u, FB b, T r[3]) {
-    using P = Ord<O>;
-    if (i < P::NCLOS || i >= N - P::NCLOS) {
-        const bool right = i >= N - P::NCLOS;
-        const int row = right ? N - 1 - i : i;
-        for (int t = P::cstart(row); t < P::cstart(row + 1); ++t) {
-            int j = P::cj(t), k = P::ck(t);
-            if (right) { j = N - 1 - j; k = N - 1 - k; }
-            const T c = P::template ccT<T>(t);
-            const T b00 = b(0, k), b01 = b(1, k), b02 = b(2, k), b11 = b(3, k), b12 = b(4, k), b22 = b(5, k);
-            const T u0 = u(0, j), u1 = u(1, j), u2 = u(2, j);
-            r[0] += c * (b00 * u0 + b01 * u1 + b02 * u2);
-            r[1] += c * (b01 * u0 + b11 * u1 + b12 * u2);
-            r[2] += c * (b02 * u0 + b12 * u1 + b22 * u2);
-        }
-    } else {
-        const T uc0 = u(0, i), uc1 = u(1, i), uc2 = u(2, i);
-#pragma unroll
-        for (int m = 1; m <= P::Q; ++m) {
-            T ep[6], em[6];
-#pragma unroll
-            for (int s = 0; s < 6; ++s) {
-                ep[s] = Edge<O>::template e<T>(m, [&](int k) { return b(s, i + k); });
-                em[s] = Edge<O>::template e<T>(m, [&](int k) { return b(s, i - m + k); });
+// the line, b symmetric with s = sym3(j, l).  Closure rows come from the coefficient table.  An
+// interior row is sum_m E_m(i) (u_{i+m} - u_i) + E_m(i-m) (u_{i-m} - u_i) with the edge weights
+// E_m(i) = sum_t e_{m,t} b_{i+t}; collecting the terms of each b_{i+k} (k = -Q..Q) gives
+//   h^2 D_xx(b) u |_i = sum_k b_{i+k} L_k(u),  L_k(u) = sum_m e_{m,k} (u_{i+m} - u_i) + e_{m,k+m} (u_{i-m} - u_i),
+// so every b value of the window is read once and the e's fold into compile-time constants.
+template <int O, typename T> __device__ __forceinline__ T edge_wT(int m, int kk) {
+    return Edge<O>::template e<T>(m, [&](int q) { return q == kk ? T(1) : T(0); });
+}
+
+// Closure rows of D_xx^FC, unrolled at compile time.  Row ROW of the table is a list of terms
+// c_t b(k_t) u(j_t); grouping them by k gives r_j += sum_k sum_l b_jl(k) V_k(u_l) with
+// V_k(u) = sum_{t: k_t = k} c_t u(j_t), so the u window (NCLOSJ columns) and each b column are
+// read once and every c_t, j_t, k_t is a constant.
+namespace tab {
+#define SBP_TABLE static constexpr
+#include "sbp_tables.inc"
+#undef SBP_TABLE
+}  // namespace tab
+
+template <int O> struct CTab;
+#define SBP3_CTAB(O)                                                                                   \
+    template <> struct CTab<O> {                                                                       \
+        static constexpr int NCLOS = SBP##O##_NCLOS, NJ = SBP##O##_NCLOSJ;                             \
+        static constexpr const int* start = tab::sbp##O##_CLOS_START;                                  \
+        static constexpr const int* cj = tab::sbp##O##_CLOS_J;                                         \
+        static constexpr const int* ck = tab::sbp##O##_CLOS_K;                                         \
+        static constexpr const double* cc = tab::sbp##O##_CLOS_C;                                      \
+    };
+SBP3_CTAB(2)
+SBP3_CTAB(4)
+SBP3_CTAB(6)
+#undef SBP3_CTAB
+
+template <int O> constexpr bool clos_has_k(int row, int k) {
+    for (int t = CTab<O>::start[row]; t < CTab<O>::start[row + 1]; ++t)
+        if (CTab<O>::ck[t] == k) return true;
+    return false;
+}
+
+template <int O, int ROW, int K, typename T, int... I>
+__device__ __forceinline__ void clos_vk(const T (&uw)[3][CTab<O>::NJ], T V[3], std::integer_sequence<int, I...>) {
+    constexpr int T0 = CTab<O>::start[ROW];
+    (
+        [&] {
+            if constexpr (CTab<O>::ck[T0 + I] == K) {
+                constexpr int j = CTab<O>::cj[T0 + I];
+                const T c = T(CTab<O>::cc[T0 + I]);
+                V[0] += c * uw[0][j];
+                V[1] += c * uw[1][j];
+                V[2] += c * uw[2][j];
             }
-            const T p0 = u(0, i + m) - uc0, p1 = u(1, i + m) - uc1, p2 = u(2, i + m) - uc2;
-            const T m0 = u(0, i - m) - uc0, m1 = u(1, i - m) - uc1, m2 = u(2, i - m) - uc2;
-            r[0] += ep[0] * p0 + ep[1] * p1 + ep[2] * p2 + em[0] * m0 + em[1] * m1 + em[2] * m2;
-            r[1] += ep[1] * p0 + ep[3] * p1 + ep[4] * p2 + em[1] * m0 + em[3] * m1 + em[4] * m2;
-            r[2] += ep[2] * p0 + ep[4] * p1 + ep[5] * p2 + em[2] * m0 + em[4] * m1 + em[5] * m2;
+        }(),
+        ...);
+}
+
+template <int O, int ROW, typename T, class FB, int... K>
+__device__ __forceinline__ void clos_row_k(const T (&uw)[3][CTab<O>::NJ], FB b, T r[3],
+                                           std::integer_sequence<int, K...>) {
+    constexpr int NT = CTab<O>::start[ROW + 1] - CTab<O>::start[ROW];
+    (
+        [&] {
+            if constexpr (clos_has_k<O>(ROW, K)) {
+                T V[3] = {T(0), T(0), T(0)};
+                clos_vk<O, ROW, K>(uw, V, std::make_integer_sequence<int, NT>());
+                const T b00 = b(0, K), b01 = b(1, K), b02 = b(2, K), b11 = b(3, K), b12 = b(4, K), b22 = b(5, K);
+                r[0] += b00 * V[0] + b01 * V[1] + b02 * V[2];
+                r[1] += b01 * V[0] + b11 * V[1] + b12 * V[2];
+                r[2] += b02 * V[0] + b12 * V[1] + b22 * V[2];
+            }
+        }(),
+        ...);
+}
+
+// one closure row, shared by the three directions and both ends: the node's pointers up (u) and
+// cp (the 6 narrow coefficients of the direction), column c of the line (counted from the nearer
+// end) at offset (c - ROW) * Ss from the node, Ss = +stride at the left end and -stride at the right
+template <int O, int ROW, typename T>
+__device__ __noinline__ void clos_row(const T* __restrict__ up, const T* __restrict__ cp, long long fs, int Ss,
+                                      T* __restrict__ r) {
+    constexpr int NJ = CTab<O>::NJ;
+    T uw[3][NJ];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) uw[l][c] = ldg(up + l * fs + (c - ROW) * Ss);
+    T rr[3] = {T(0), T(0), T(0)};
+    auto b = [&](int s6, int c) { return ldg(cp + s6 * fs + (c - ROW) * Ss); };
+    clos_row_k<O, ROW>(uw, b, rr, std::make_integer_sequence<int, NJ>());
+    r[0] += rr[0];
+    r[1] += rr[1];
+    r[2] += rr[2];
+}
+
+template <int O, typename T, int... R>
+__device__ __forceinline__ void clos_dispatch(int row, const T* up, const T* cp, long long fs, int Ss, T* r,
+                                              std::integer_sequence<int, R...>) {
+    ((row == R ? clos_row<O, R>(up, cp, fs, Ss, r) : void()), ...);
+}
+
+// h^2 D_xx^FC rows of the closure (i < NCLOS or i >= N - NCLOS) for the node at index i of a line
+// with stride S
+template <int O, typename T>
+__device__ __forceinline__ void dxx3_closure_ptr(int N, int i, const T* up, const T* cp, long long fs, int S,
+                                                 T r[3]) {
+    using P = Ord<O>;
+    const bool right = i >= N - P::NCLOS;
+    const int row = right ? N - 1 - i : i;
+    clos_dispatch<O, T>(row, up, cp, fs, right ? -S : S, r, std::make_integer_sequence<int, P::NCLOS>());
+}
+
+template <int O, typename T, class FU, class FB>
+__device__ __forceinline__ void dxx3_interior(int i, FU u, FB b, T r[3]) {
+    constexpr int Q = Ord<O>::Q;
+    T dp[3][Q], dm[3][Q];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const T uc = u(l, i);
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            dp[l][m - 1] = u(l, i + m) - uc;
+            dm[l][m - 1] = u(l, i - m) - uc;
         }
+    }
+#pragma unroll
+    for (int k = -Q; k <= Q; ++k) {
+        T L[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            const T cp = edge_wT<O, T>(m, k), cn = edge_wT<O, T>(m, k + m);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                if (cp != T(0)) L[l] += cp * dp[l][m - 1];
+                if (cn != T(0)) L[l] += cn * dm[l][m - 1];
+            }
+        }
+        const T b00 = b(0, i + k), b01 = b(1, i + k), b02 = b(2, i + k), b11 = b(3, i + k), b12 = b(4, i + k),
+                b22 = b(5, i + k);
+        r[0] += b00 * L[0] + b01 * L[1] + b02 * L[2];
+        r[1] += b01 * L[0] + b11 * L[1] + b12 * L[2];
+        r[2] += b02 * L[0] + b12 * L[1] + b22 * L[2];
     }
 }
 
 constexpr int BX = 32, BY = 8;
+
+// element stride of direction D as a 32-bit int (a plane of the grid holds fewer than 2^31
+// elements, checked at create): 1 along x1 (a compile-time constant), pitch or plane otherwise.
+// Neighbour reads go through the node's own pointer plus (t - i) * stride, so interior stencil
+// offsets fold into constants shared by every field.
+template <int D> __device__ __forceinline__ int dstride(const Grid3& g) {
+    if constexpr (D == 0) return 1;
+    else return (int)g.s[D];
+}
+
+// D_D u_l (l = 0..2) at the node (index i along D), u at the node's pointer
+template <typename T, int O, int D>
+__device__ __forceinline__ void grad_dir(const Grid3& g, int i, const T* __restrict__ up, T gr[3]) {
+    const int S = dstride<D>(g);
+    const int N = g.n[D];
+    const T ih = T(g.ih[D]);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const T* p = up + l * g.fs;
+        gr[l] = ih * dsum<O, T>(N, i, [&](int t) { return ldg(p + (t - i) * S); });
+    }
+}
 
 // ------------------------------------------------------------------ mixed fluxes
 template <typename T, int O>
@@ -91,24 +222,18 @@ __global__ void __launch_bounds__(BX * BY) k3_flux(Grid3 g, const T* __restrict_
                                                    T* __restrict__ q) {
     const int i1 = blockIdx.x * BX + threadIdx.x, i2 = blockIdx.y * BY + threadIdx.y, i3 = blockIdx.z;
     if (i1 >= g.n[0] || i2 >= g.n[1]) return;
-    const int idx[3] = {i1, i2, i3};
     const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
+    const T* up = u + o;
     T gr[3][3];                                   // gr[k][l] = D_k u_l
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const T ihk = T(g.ih[k]);
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-            const T* line = u + l * g.fs + o - idx[k] * g.s[k];
-            const long long sk = g.s[k];
-            gr[k][l] = ihk * dsum<O, T>(g.n[k], idx[k], [&](int t) { return ldg(line + t * sk); });
-        }
-    }
+    grad_dir<T, O, 0>(g, i1, up, gr[0]);
+    grad_dir<T, O, 1>(g, i2, up, gr[1]);
+    grad_dir<T, O, 2>(g, i3, up, gr[2]);
     T qq[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) qq[i][j] = T(0);
+    const T* cmo = cm + o;
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const int i = p == 2 ? 1 : 0, k = p == 0 ? 1 : 2;
@@ -116,199 +241,533 @@ __global__ void __launch_bounds__(BX * BY) k3_flux(Grid3 g, const T* __restrict_
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                const T M = ldg(cm + (long long)(9 * p + 3 * j + l) * g.fs + o);
+                const T M = ldg(cmo + (9 * p + 3 * j + l) * g.fs);
                 qq[i][j] += M * gr[k][l];             // c_ijkl D_k u_l
                 qq[k][l] += M * gr[i][j];             // c_klij D_i u_j (= c_kl ij, major symmetry)
             }
     }
+    T* qo = q + o;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) q[(long long)(3 * i + j) * g.fs + o] = qq[i][j];
+        for (int j = 0; j < 3; ++j) qo[(3 * i + j) * g.fs] = qq[i][j];
 }
 
 // ------------------------------------------------------------------ divergence and leapfrog store
-// MODE 0: leapfrog in increment form, d = du + dt^2 w r, un = u + d (du updated in place);
-// MODE 1: apply, out = w r.
-template <typename T, int O, int MODE>
-__global__ void __launch_bounds__(BX * BY) k3_div(Grid3 g, const T* __restrict__ u, const T* __restrict__ q,
-                                                  const T* __restrict__ cd, const T* __restrict__ w,
-                                                  T* __restrict__ du, T* __restrict__ un, T dt2) {
-    const int i1 = blockIdx.x * BX + threadIdx.x, i2 = blockIdx.y * BY + threadIdx.y, i3 = blockIdx.z;
-    if (i1 >= g.n[0] || i2 >= g.n[1]) return;
-    const int idx[3] = {i1, i2, i3};
-    const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
-    T r[3] = {T(0), T(0), T(0)};
+// r_j += D_D q_Dj + D_DD^FC(c_DjDl) u_l for one direction D
+// x1 closure rows as matrices: row rho of the line (i2, i3) at side s is
+//   h^2 D_xx^FC(b) u |_rho = sum_c sum_l M_{s,rho,c}(b_jl) u_l(col_s(c)),  M(b) = sum_{t in row: j_t = c} c_t b(k_t)
+// (symmetric in jl like b), formed once from the material by k3_xclos.  Layout
+// xm[(((s * NJ + c) * 6 + s6) * nlines + line) * NCLOS + rho]: the row index is fastest, so the lanes
+// of a warp (consecutive i1, hence consecutive rows) read consecutive words, and every lane runs
+// the same code whatever its row.
+struct XClos {
+    const void* m;
+    long long nlines;
+};
+
+template <typename T, int O>
+__device__ __forceinline__ void xclos_apply(const XClos& xc, int N, int i, int line, const T* __restrict__ up,
+                                            long long fs, T rr[3]) {
+    using P = Ord<O>;
+    constexpr int NJ = CTab<O>::NJ, NC = P::NCLOS;
+    const bool right = i >= N - NC;
+    const int rho = right ? N - 1 - i : i;
+    const T* mp = static_cast<const T*>(xc.m) + ((long long)(right ? NJ : 0) * 6 * xc.nlines + line) * NC + rho;
+    const long long cs = xc.nlines * NC;            // stride of one (c, s6) slot
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const T ihi = T(g.ih[i]);
-        const long long si = g.s[i];
-        const long long base = o - idx[i] * si;
+    for (int c = 0; c < NJ; ++c) {
+        const int off = right ? (N - 1 - c) - i : c - i;
+        const T u0 = ldg(up + off), u1 = ldg(up + fs + off), u2 = ldg(up + 2 * fs + off);
+        T m6[6];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T* line = q + (long long)(3 * i + j) * g.fs + base;
-            r[j] += ihi * dsum<O, T>(g.n[i], idx[i], [&](int t) { return ldg(line + t * si); });
-        }
-        T rr[3] = {T(0), T(0), T(0)};
-        const T* cdi = cd + (long long)(6 * i) * g.fs + base;
-        const T* ul = u + base;
-        const long long fs = g.fs;
-        dxx3<O, T>(g.n[i], idx[i], [&](int l, int t) { return ldg(ul + l * fs + t * si); },
-                   [&](int s, int t) { return ldg(cdi + s * fs + t * si); }, rr);
-        const T ih2 = ihi * ihi;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) r[j] += ih2 * rr[j];
-    }
-    const T wv = ldg(w + o);
-    if constexpr (MODE == 0) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const long long oj = j * g.fs + o;
-            const T d = du[oj] + dt2 * wv * r[j];
-            du[oj] = d;
-            un[oj] = ldg(u + oj) + d;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) un[j * g.fs + o] = wv * r[j];
+        for (int s6 = 0; s6 < 6; ++s6) m6[s6] = ldg(mp + (long long)(c * 6 + s6) * cs);
+        rr[0] += m6[0] * u0 + m6[1] * u1 + m6[2] * u2;
+        rr[1] += m6[1] * u0 + m6[3] * u1 + m6[4] * u2;
+        rr[2] += m6[2] * u0 + m6[4] * u1 + m6[5] * u2;
     }
 }
 
+template <typename T, int O, int D>
+__device__ __forceinline__ void div_dir(const Grid3& g, int i, const T* __restrict__ qo, const T* __restrict__ cdo,
+                                        const T* __restrict__ up, T r[3], const XClos* xc = nullptr, int line = 0) {
+    const int S = dstride<D>(g);
+    const int N = g.n[D];
+    const long long fs = g.fs;
+    const T ih = T(g.ih[D]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const T* p = qo + (3 * D + j) * fs;
+        r[j] += ih * dsum<O, T>(N, i, [&](int t) { return ldg(p + (t - i) * S); });
+    }
+    T rr[3] = {T(0), T(0), T(0)};
+    const T* cp = cdo + 6 * D * fs;
+    if (i < Ord<O>::NCLOS || i >= N - Ord<O>::NCLOS) {
+        if constexpr (D == 0) xclos_apply<T, O>(*xc, N, i, line, up, fs, rr);
+        else dxx3_closure_ptr<O, T>(N, i, up, cp, fs, S, rr);
+    } else {
+        dxx3_interior<O, T>(i, [&](int l, int t) { return ldg(up + l * fs + (t - i) * S); },
+                            [&](int s, int t) { return ldg(cp + s * fs + (t - i) * S); }, rr);
+    }
+    const T ih2 = ih * ih;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r[j] += ih2 * rr[j];
+}
+
+// the x1 closure matrices of the lines of x3-planes k0 <= i3 < k0 + nk (one thread per line, side, row)
+template <typename T, int O>
+__global__ void __launch_bounds__(128) k3_xclos(Grid3 g, int k0, int nk, const T* __restrict__ cd, T* __restrict__ xm) {
+    using P = Ord<O>;
+    constexpr int NJ = CTab<O>::NJ, NC = P::NCLOS;
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i3 = k0 + blockIdx.y;
+    const int rho = blockIdx.z % NC, side = blockIdx.z / NC;
+    if (i2 >= g.n[1] || blockIdx.y >= (unsigned)nk) return;
+    const int N = g.n[0];
+    const long long nlines = (long long)g.n[1] * g.n[2];
+    const long long line = (long long)i3 * g.n[1] + i2;
+    const long long base = i2 * g.s[1] + i3 * g.s[2];
+    for (int c = 0; c < NJ; ++c)
+        for (int s6 = 0; s6 < 6; ++s6) {
+            double m = 0.0;
+            for (int t = P::cstart(rho); t < P::cstart(rho + 1); ++t) {
+                if (P::cj(t) != c) continue;
+                const int k = side ? N - 1 - P::ck(t) : P::ck(t);
+                m += P::cc(t) * double(cd[s6 * g.fs + base + k]);
+            }
+            xm[((((long long)side * NJ + c) * 6 + s6) * nlines + line) * NC + rho] = T(m);
+        }
+}
+
+// ------------------------------------------------------------------ divergence: interior box and boundary shell
+// Nodes at least NCLOS from every face use only interior rows in all three directions.  They form
+// the box [x1lo, x1hi) x [y0, y1) x [z0, z1) (x1lo a multiple of NV), handled by k3_div_int: no
+// closure branches, and NV consecutive x1 nodes per thread read as one vector (float2 for FP32).
+// Every other node (the shell) goes to k3_div_shell, the general per-node code above.
+struct Box3 {
+    int x1lo, x1hi, y0, y1, z0, z1;
+};
+
+template <typename T, int NV> __device__ __forceinline__ void vld(const T* p, T v[NV]) {
+    if constexpr (NV == 2 && sizeof(T) == 4) {
+        const float2 x = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) v[n] = __ldg(p + n);
+    }
+}
+template <typename T, int NV> __device__ __forceinline__ void vst(T* p, const T v[NV]) {
+    if constexpr (NV == 2 && sizeof(T) == 4) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) p[n] = v[n];
+    }
+}
+
+// x2 / x3 direction (stride S) for NV nodes: r[n][j] += ih D q_Dj + ih^2 D_xx(b) u, interior rows
+template <typename T, int O, int NV>
+__device__ __forceinline__ void div_int_strided(const T* __restrict__ qD, const T* __restrict__ cdD,
+                                                const T* __restrict__ up, long long fs, int S, T ih, T r[NV][3]) {
+    constexpr int Q = Ord<O>::Q;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T acc[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) acc[n] = T(0);
+        const T* p = qD + j * fs;
+#pragma unroll
+        for (int k = 1; k <= Q; ++k) {
+            T a[NV], b[NV];
+            vld<T, NV>(p + k * S, a);
+            vld<T, NV>(p - k * S, b);
+            const T ak = Ord<O>::template aT<T>(k - 1);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) acc[n] += ak * (a[n] - b[n]);
+        }
+#pragma unroll
+        for (int n = 0; n < NV; ++n) r[n][j] += ih * acc[n];
+    }
+    T dp[3][Q][NV], dm[3][Q][NV];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        T uc[NV];
+        vld<T, NV>(up + l * fs, uc);
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            T a[NV], b[NV];
+            vld<T, NV>(up + l * fs + m * S, a);
+            vld<T, NV>(up + l * fs - m * S, b);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                dp[l][m - 1][n] = a[n] - uc[n];
+                dm[l][m - 1][n] = b[n] - uc[n];
+            }
+        }
+    }
+    const T ih2 = ih * ih;
+#pragma unroll
+    for (int k = -Q; k <= Q; ++k) {
+        T L[3][NV];
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int n = 0; n < NV; ++n) L[l][n] = T(0);
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            const T cp = edge_wT<O, T>(m, k), cn = edge_wT<O, T>(m, k + m);
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    if (cp != T(0)) L[l][n] += cp * dp[l][m - 1][n];
+                    if (cn != T(0)) L[l][n] += cn * dm[l][m - 1][n];
+                }
+        }
+        T bb[6][NV];
+#pragma unroll
+        for (int s6 = 0; s6 < 6; ++s6) vld<T, NV>(cdD + s6 * fs + k * S, bb[s6]);
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            r[n][0] += ih2 * (bb[0][n] * L[0][n] + bb[1][n] * L[1][n] + bb[2][n] * L[2][n]);
+            r[n][1] += ih2 * (bb[1][n] * L[0][n] + bb[3][n] * L[1][n] + bb[4][n] * L[2][n]);
+            r[n][2] += ih2 * (bb[2][n] * L[0][n] + bb[4][n] * L[1][n] + bb[5][n] * L[2][n]);
+        }
+    }
+}
+
+// x1 direction for NV consecutive nodes: windows of WN = NV + 2 QA values from i1 - QA (QA = Q
+// rounded up to NV, so the window loads stay vector-aligned); node n sits at window index QA + n
+template <typename T, int O, int NV>
+__device__ __forceinline__ void div_int_x1(const T* __restrict__ q0, const T* __restrict__ cd0,
+                                           const T* __restrict__ up, long long fs, T ih, T r[NV][3]) {
+    constexpr int Q = Ord<O>::Q;
+    constexpr int QA = (Q + NV - 1) / NV * NV;
+    constexpr int WN = NV + 2 * QA;
+    auto window = [&](const T* p, T w[WN]) {
+#pragma unroll
+        for (int v = 0; v < WN / NV; ++v) vld<T, NV>(p - QA + v * NV, w + v * NV);
+    };
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T w[WN];
+        window(q0 + j * fs, w);
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 1; k <= Q; ++k) acc += Ord<O>::template aT<T>(k - 1) * (w[QA + n + k] - w[QA + n - k]);
+            r[n][j] += ih * acc;
+        }
+    }
+    T L[2 * Q + 1][3][NV];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        T w[WN];
+        window(up + l * fs, w);
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            const T uc = w[QA + n];
+#pragma unroll
+            for (int k = -Q; k <= Q; ++k) {
+                T acc = T(0);
+#pragma unroll
+                for (int m = 1; m <= Q; ++m) {
+                    const T cp = edge_wT<O, T>(m, k), cn = edge_wT<O, T>(m, k + m);
+                    if (cp != T(0)) acc += cp * (w[QA + n + m] - uc);
+                    if (cn != T(0)) acc += cn * (w[QA + n - m] - uc);
+                }
+                L[k + Q][l][n] = acc;
+            }
+        }
+    }
+    const T ih2 = ih * ih;
+    T rr[NV][3];
+#pragma unroll
+    for (int n = 0; n < NV; ++n)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) rr[n][j] = T(0);
+#pragma unroll
+    for (int s6 = 0; s6 < 6; ++s6) {
+        const int j = s6 < 3 ? 0 : (s6 < 5 ? 1 : 2);
+        const int l = s6 < 3 ? s6 : (s6 < 5 ? s6 - 2 : 2);
+        T w[WN];
+        window(cd0 + s6 * fs, w);
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+#pragma unroll
+            for (int k = -Q; k <= Q; ++k) {
+                const T bk = w[QA + n + k];
+                rr[n][j] += bk * L[k + Q][l][n];
+                if (j != l) rr[n][l] += bk * L[k + Q][j][n];
+            }
+    }
+#pragma unroll
+    for (int n = 0; n < NV; ++n)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r[n][j] += ih2 * rr[n][j];
+}
+
+// MODE 0: leapfrog in increment form, d = du + dt^2 w r, un = u + d (du updated in place);
+// MODE 1: apply, out = w r.
+template <typename T, int O, int MODE, int NV>
+__global__ void __launch_bounds__(128) k3_div_int(Grid3 g, Box3 bx, const T* __restrict__ u, const T* __restrict__ q,
+                                                  const T* __restrict__ cd, const T* __restrict__ w,
+                                                  T* __restrict__ du, T* __restrict__ un, T dt2) {
+    const int gx = blockIdx.x * 32 + threadIdx.x;
+    const int i1 = bx.x1lo + gx * NV, i2 = bx.y0 + blockIdx.y * 4 + threadIdx.y, i3 = bx.z0 + blockIdx.z;
+    if (i1 >= bx.x1hi || i2 >= bx.y1) return;
+    const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
+    const long long fs = g.fs;
+    const T* up = u + o;
+    T r[NV][3];
+#pragma unroll
+    for (int n = 0; n < NV; ++n) r[n][0] = r[n][1] = r[n][2] = T(0);
+    div_int_x1<T, O, NV>(q + o, cd + o, up, fs, T(g.ih[0]), r);
+    div_int_strided<T, O, NV>(q + 3 * fs + o, cd + 6 * fs + o, up, fs, (int)g.s[1], T(g.ih[1]), r);
+    div_int_strided<T, O, NV>(q + 6 * fs + o, cd + 12 * fs + o, up, fs, (int)g.s[2], T(g.ih[2]), r);
+    T wv[NV];
+    vld<T, NV>(w + o, wv);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const long long oj = j * fs + o;
+        T out[NV];
+        if constexpr (MODE == 0) {
+            T d[NV], uc[NV];
+            vld<T, NV>(du + oj, d);
+            vld<T, NV>(up + j * fs, uc);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                d[n] += dt2 * wv[n] * r[n][j];
+                out[n] = uc[n] + d[n];
+            }
+            vst<T, NV>(du + oj, d);
+        } else {
+#pragma unroll
+            for (int n = 0; n < NV; ++n) out[n] = wv[n] * r[n][j];
+        }
+        vst<T, NV>(un + oj, out);
+    }
+}
+
+// the shell: every node outside the box, lanes along x1 (coalesced), in three parts:
+//   Z: the planes i3 < z0, i3 >= z1 (whole planes);
+//   Y: within the box's planes, the rows i2 < y0, i2 >= y1 (whole rows);
+//   X: within the box's planes and rows, the x1 runs i1 < x1lo and i1 >= x1hi.
+struct Shell3 {
+    long long cZ, cY, cX;   // node counts of the three parts
+};
+
+__device__ __forceinline__ bool shell_node(const Grid3& g, const Box3& bx, const Shell3& sh, long long t, int& i1,
+                                           int& i2, int& i3) {
+    const long long n1 = g.n[0], n2 = g.n[1];
+    const long long plane = n1 * n2;
+    if (t < sh.cZ) {
+        const long long pz = t / plane;
+        const long long rem = t - pz * plane;
+        i3 = (int)(pz < bx.z0 ? pz : bx.z1 + (pz - bx.z0));
+        i2 = (int)(rem / n1);
+        i1 = (int)(rem - (long long)i2 * n1);
+        return true;
+    }
+    t -= sh.cZ;
+    if (t < sh.cY) {
+        const long long rowsB = bx.y0 + (n2 - bx.y1);
+        const long long row = t / n1;
+        i1 = (int)(t - row * n1);
+        const long long pz = row / rowsB, ry = row - pz * rowsB;
+        i3 = (int)(bx.z0 + pz);
+        i2 = (int)(ry < bx.y0 ? ry : bx.y1 + (ry - bx.y0));
+        return true;
+    }
+    t -= sh.cY;
+    if (t >= sh.cX) return false;
+    const long long ny = bx.y1 - bx.y0;
+    const long long runs = bx.x1lo + (n1 - bx.x1hi);
+    const long long row = t / runs, rx = t - row * runs;
+    const long long pz = row / ny, py = row - pz * ny;
+    i3 = (int)(bx.z0 + pz);
+    i2 = (int)(bx.y0 + py);
+    i1 = (int)(rx < bx.x1lo ? rx : bx.x1hi + (rx - bx.x1lo));
+    return true;
+}
+
 // ------------------------------------------------------------------ boundary SATs of the faces x_m = 0, 1
-// One thread per face node (a, b) along the two tangential directions (p < t), blockIdx.z = side.
+// Computed by the shell kernel for the nodes they reach, so no node is written twice:
 //   traction:     J SAT_J = -H^-1 P_f nu c_mJkL D_k u_L              (face node only)
 //   displacement: J SAT_J = H^-1 [ sum_k D_k^T (nu c_mLkJ P_f u_L) - P_f (beta d / h1) c_mJmL u_L ]
 // H^-1 P_f is 1 / (h_m hw_0) at a face node; D_m^T spreads the normal term over the first NCOL
 // nodes of the normal line (H^-1 D_m^T at depth t: D_m[face][t] / (h_m hw_t)); the tangential
-// D_k^T stays on the face, weighted by hw_k(a') / hw_k(a).  MODE 0 adds dt^2 w SAT to du and un,
-// MODE 1 adds w SAT to the applied field.
-template <typename T, int O, int MODE>
-__global__ void __launch_bounds__(128) k3_face(Grid3 g, int m, int kind0, int kind1, double beta,
-                                               const T* __restrict__ u, const T* __restrict__ cm,
-                                               const T* __restrict__ cd, const T* __restrict__ w,
-                                               T* __restrict__ du, T* __restrict__ un, T dt2) {
+// D_k^T stays on the face, weighted by hw_k(a') / hw_k(a).
+// tangential transpose along direction K of face direction M: (H_K^-1 D_K^T H_K v)(a) with
+// v_J = nu c_MLKJ u_L on the face; away from the ends of the line (every row that reads column a
+// is an interior row and every weight there is 1) this is -(D_K v)(a).
+template <typename T, int O, int M, int K>
+__device__ __forceinline__ void face_tangential(const Grid3& g, int ak, const T* __restrict__ up,
+                                               const T* __restrict__ cm, const T* __restrict__ cd, long long o,
+                                               T base, T rs[3]) {
     using P = Ord<O>;
-    const int pd = m == 0 ? 1 : 0, td = m == 2 ? 1 : 2;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
-    const int side = blockIdx.z;
-    if (a >= g.n[pd] || b >= g.n[td]) return;
-    const int kind = side ? kind1 : kind0;
-    const int Nm = g.n[m];
-    const int im = side ? Nm - 1 : 0;
-    const T nu = side ? T(1) : T(-1);
-    int idx[3];
-    idx[m] = im;
-    idx[pd] = a;
-    idx[td] = b;
-    const long long o = idx[0] + idx[1] * g.s[1] + idx[2] * g.s[2];
+    const int Nk = g.n[K];
+    const int S = dstride<K>(g);
     const long long fs = g.fs;
-    const T ihb = T(g.ih[m] / hweight<O>(Nm, im));        // H^-1 P_f at the face node
-    T rs[3] = {T(0), T(0), T(0)};
-    if (kind == BC_TRACTION) {
-        T gr[3][3];
+    auto vJ = [&](int off, T out[3]) {
+        T v[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const T ihk = T(g.ih[k]);
-            const long long sk = g.s[k];
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                const T* line = u + l * fs + o - idx[k] * sk;
-                gr[k][l] = ihk * dsum<O, T>(g.n[k], idx[k], [&](int t) { return ldg(line + t * sk); });
-            }
-        }
+        for (int L = 0; L < 3; ++L) v[L] = ldg(up + L * fs + off);
 #pragma unroll
         for (int J = 0; J < 3; ++J) {
             T s = T(0);
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+            for (int L = 0; L < 3; ++L) s += cfull(cm, cd, fs, M, L, K, J, o + off) * v[L];
+            out[J] = s;
+        }
+    };
+    if (ak >= P::NCOL && ak >= P::NB + P::Q && ak <= Nk - 1 - P::NCOL && ak <= Nk - 1 - P::NB - P::Q) {
 #pragma unroll
-                for (int L = 0; L < 3; ++L) s += cfull(cm, cd, fs, m, J, k, L, o) * gr[k][L];
-            rs[J] = -ihb * nu * s;
+        for (int mm = 1; mm <= P::Q; ++mm) {
+            const T am = P::template aT<T>(mm - 1) * base;
+            T vp[3], vm[3];
+            vJ(mm * S, vp);
+            vJ(-mm * S, vm);
+#pragma unroll
+            for (int J = 0; J < 3; ++J) rs[J] += am * (vm[J] - vp[J]);
         }
     } else {
-        T uf[3];
-#pragma unroll
-        for (int L = 0; L < 3; ++L) uf[L] = ldg(u + L * fs + o);
-        // penalty -H^-1 P_f (beta d / h1) c_mJmL u_L, h1 = h_m hw_0
-        const T pen = T(beta * 3.0) * ihb * ihb;
-#pragma unroll
-        for (int J = 0; J < 3; ++J) {
-            T s = T(0);
-#pragma unroll
-            for (int L = 0; L < 3; ++L) s += cfull(cm, cd, fs, m, J, m, L, o) * uf[L];
-            rs[J] = -pen * s;
-        }
-        // tangential transposes
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-            const int k = kk ? td : pd;
-            const int Nk = g.n[k], ak = idx[k];
-            const long long sk = g.s[k];
-            const int W = P::NCOL - 1 > P::Q ? P::NCOL - 1 : P::Q;
-            const int lo = ak - W < 0 ? 0 : ak - W, hi = ak + W > Nk - 1 ? Nk - 1 : ak + W;
-            const T iwa = T(1.0 / hweight<O>(Nk, ak));
-            for (int a2 = lo; a2 <= hi; ++a2) {
-                const T dc = dcoefT<O, T>(Nk, a2, ak);
-                if (dc == T(0)) continue;
-                const T coef = ihb * T(g.ih[k]) * dc * hweightT<O, T>(Nk, a2) * iwa * nu;
-                const long long o2 = o + (long long)(a2 - ak) * sk;
-                T v[3];
-#pragma unroll
-                for (int L = 0; L < 3; ++L) v[L] = ldg(u + L * fs + o2);
-#pragma unroll
-                for (int J = 0; J < 3; ++J) {
-                    T s = T(0);
-#pragma unroll
-                    for (int L = 0; L < 3; ++L) s += cfull(cm, cd, fs, m, L, k, J, o2) * v[L];
-                    rs[J] += coef * s;
-                }
-            }
-        }
-        // normal transpose: depth t = 0 .. NCOL-1 along the normal line
-        T vn[3];
-#pragma unroll
-        for (int J = 0; J < 3; ++J) {
-            T s = T(0);
-#pragma unroll
-            for (int L = 0; L < 3; ++L) s += cfull(cm, cd, fs, m, L, m, J, o) * uf[L];
-            vn[J] = nu * s;
-        }
-        const T ihm = T(g.ih[m]);
-        for (int t = 0; t < P::NCOL; ++t) {
-            const int col = side ? Nm - 1 - t : t;
-            const T dc = dcoefT<O, T>(Nm, im, col);
+        constexpr int W = P::NCOL - 1 > P::Q ? P::NCOL - 1 : P::Q;
+        const int lo = ak - W < 0 ? 0 : ak - W, hi = ak + W > Nk - 1 ? Nk - 1 : ak + W;
+        const T iwa = T(1.0 / hweight<O>(Nk, ak));
+        for (int a2 = lo; a2 <= hi; ++a2) {
+            const T dc = dcoefT<O, T>(Nk, a2, ak);
             if (dc == T(0)) continue;
-            const T coef = ihm * ihm * dc / hweightT<O, T>(Nm, col);
-            const long long on = o + (long long)(col - im) * g.s[m];
-            const T wv = ldg(w + on);
-            if (t == 0) {
+            const T coef = base * dc * hweightT<O, T>(Nk, a2) * iwa;
+            T v[3];
+            vJ((a2 - ak) * S, v);
 #pragma unroll
-                for (int J = 0; J < 3; ++J) rs[J] += coef * vn[J];
-                continue;
-            }
-#pragma unroll
-            for (int J = 0; J < 3; ++J) {
-                const long long oj = J * fs + on;
-                if constexpr (MODE == 0) {
-                    const T dlt = dt2 * wv * coef * vn[J];
-                    du[oj] += dlt;
-                    un[oj] += dlt;
-                } else {
-                    un[oj] += wv * coef * vn[J];
-                }
-            }
+            for (int J = 0; J < 3; ++J) rs[J] += coef * v[J];
         }
     }
+}
+
+struct Faces3 {
+    int kind[6];            // BC_DISPLACEMENT or BC_TRACTION per face
+    double beta;
+};
+
+// r += the SAT terms of the faces x_M = 0 and x_M = 1 that reach the node (index im along M):
+// at a face node the face's own terms, at depth 1 .. NCOL-1 below a displacement face the
+// normal transpose D_M^T of that face's node on the same line.
+template <typename T, int O, int M>
+__device__ __noinline__ void face_terms(const Grid3& g, const Faces3& fc, int im, int ia, int ib, long long o,
+                                           const T* __restrict__ u, const T* __restrict__ cm,
+                                           const T* __restrict__ cd, T r[3]) {
+    using P = Ord<O>;
+    constexpr int PD = M == 0 ? 1 : 0, TD = M == 2 ? 1 : 2;
+    const int Nm = g.n[M];
+    const int SM = dstride<M>(g);
+    const long long fs = g.fs;
+    const T ihm = T(g.ih[M]);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int depth = side ? Nm - 1 - im : im;
+        if (depth >= P::NCOL) continue;
+        const int kind = fc.kind[2 * M + side];
+        const T nu = side ? T(1) : T(-1);
+        const int frow = side ? Nm - 1 : 0;                 // the face's row along M
+        if (depth > 0) {
+            if (kind != BC_DISPLACEMENT) continue;
+            const T dc = dcoefT<O, T>(Nm, frow, im);
+            if (dc == T(0)) continue;
+            const long long of = o + (long long)(frow - im) * SM;
+            T uf[3];
+#pragma unroll
+            for (int L = 0; L < 3; ++L) uf[L] = ldg(u + L * fs + of);
+            const T coef = ihm * ihm * dc / hweightT<O, T>(Nm, im) * nu;
+#pragma unroll
+            for (int J = 0; J < 3; ++J) {
+                T sm = T(0);
+#pragma unroll
+                for (int L = 0; L < 3; ++L) sm += cfull(cm, cd, fs, M, L, M, J, of) * uf[L];
+                r[J] += coef * sm;
+            }
+            continue;
+        }
+        const T* up = u + o;
+        const T ihb = ihm / hweightT<O, T>(Nm, im);         // H^-1 P_f at the face node
+        if (kind == BC_TRACTION) {
+            T gr[3][3];
+            const int ix[3] = {M == 0 ? im : ia, M == 1 ? im : (M == 0 ? ia : ib), M == 2 ? im : ib};
+            grad_dir<T, O, 0>(g, ix[0], up, gr[0]);
+            grad_dir<T, O, 1>(g, ix[1], up, gr[1]);
+            grad_dir<T, O, 2>(g, ix[2], up, gr[2]);
+#pragma unroll
+            for (int J = 0; J < 3; ++J) {
+                T sm = T(0);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int L = 0; L < 3; ++L) sm += cfull(cm, cd, fs, M, J, k, L, o) * gr[k][L];
+                r[J] -= ihb * nu * sm;
+            }
+        } else {
+            T uf[3];
+#pragma unroll
+            for (int L = 0; L < 3; ++L) uf[L] = ldg(up + L * fs);
+            // penalty -H^-1 P_f (beta d / h1) c_mJmL u_L (h1 = h_m hw_0), and the normal transpose at
+            // depth 0, H^-1 D_M[face][face] nu c_MLMJ u_L
+            const T pen = T(fc.beta * 3.0) * ihb * ihb;
+            const T cn = ihm * ihm * dcoefT<O, T>(Nm, frow, im) / hweightT<O, T>(Nm, im) * nu;
+#pragma unroll
+            for (int J = 0; J < 3; ++J) {
+                T sp = T(0), sn = T(0);
+#pragma unroll
+                for (int L = 0; L < 3; ++L) {
+                    sp += cfull(cm, cd, fs, M, J, M, L, o) * uf[L];
+                    sn += cfull(cm, cd, fs, M, L, M, J, o) * uf[L];
+                }
+                r[J] += cn * sn - pen * sp;
+            }
+            const T base = ihb * nu;
+            face_tangential<T, O, M, PD>(g, ia, up, cm, cd, o, base * T(g.ih[PD]), r);
+            face_tangential<T, O, M, TD>(g, ib, up, cm, cd, o, base * T(g.ih[TD]), r);
+        }
+    }
+}
+
+// the boundary shell: volume terms with closure rows, then every face SAT reaching the node, then
+// the leapfrog store (MODE as in k3_div_int)
+template <typename T, int O, int MODE>
+__global__ void __launch_bounds__(128) k3_div_shell(Grid3 g, Box3 bx, Shell3 sh, XClos xc, Faces3 fc, long long count,
+                                                    const T* __restrict__ u, const T* __restrict__ q,
+                                                    const T* __restrict__ cm, const T* __restrict__ cd,
+                                                    const T* __restrict__ w, T* __restrict__ du,
+                                                    T* __restrict__ un, T dt2) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    int i1, i2, i3;
+    if (!shell_node(g, bx, sh, t, i1, i2, i3)) return;
+    const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
+    const T* up = u + o;
+    const T* qo = q + o;
+    const T* cdo = cd + o;
+    T r[3] = {T(0), T(0), T(0)};
+    div_dir<T, O, 0>(g, i1, qo, cdo, up, r, &xc, i3 * g.n[1] + i2);
+    div_dir<T, O, 1>(g, i2, qo, cdo, up, r);
+    div_dir<T, O, 2>(g, i3, qo, cdo, up, r);
+    face_terms<T, O, 0>(g, fc, i1, i2, i3, o, u, cm, cd, r);
+    face_terms<T, O, 1>(g, fc, i2, i1, i3, o, u, cm, cd, r);
+    face_terms<T, O, 2>(g, fc, i3, i1, i2, o, u, cm, cd, r);
     const T wv = ldg(w + o);
 #pragma unroll
-    for (int J = 0; J < 3; ++J) {
-        const long long oj = J * fs + o;
+    for (int j = 0; j < 3; ++j) {
+        const long long oj = j * g.fs + o;
         if constexpr (MODE == 0) {
-            const T dlt = dt2 * wv * rs[J];
-            du[oj] += dlt;
-            un[oj] += dlt;
+            const T d = du[oj] + dt2 * wv * r[j];
+            du[oj] = d;
+            un[oj] = ldg(up + j * g.fs) + d;
         } else {
-            un[oj] += wv * rs[J];
+            un[oj] = wv * r[j];
         }
     }
 }

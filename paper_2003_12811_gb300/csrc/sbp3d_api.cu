@@ -34,8 +34,11 @@ struct sbp3_handle {
     long long pitch = 0, fs = 0;
     size_t es = 8;
     double beta = 1.0;
-    int faces[6] = {0, 0, 0, 0, 0, 0};
     Grid3 g{};
+    Box3 box{};                              // nodes with interior rows in every direction (k3_div_int)
+    long long shell = 0;                     // nodes outside the box (k3_div_shell)
+    Shell3 sh{};
+    Faces3 fc{};
     double* X = nullptr;                     // pitched FP64 coordinates (3 fields)
     void* cm = nullptr;                      // 27 fields
     void* cd = nullptr;                      // 18 fields
@@ -43,6 +46,7 @@ struct sbp3_handle {
     void* u[2] = {nullptr, nullptr};         // leapfrog levels (3 fields each), u[cur] = u^n
     void* du = nullptr;                      // increment u^n - u^{n-1} (3 fields)
     void* q = nullptr;                       // mixed fluxes (9 fields)
+    void* xm = nullptr;                      // x1 closure matrices of D_xx^FC (k3_xclos)
     void* ain = nullptr;                     // sbp3_apply input / output (3 fields each), on first use
     void* aout = nullptr;
     int cur = 0;
@@ -121,15 +125,21 @@ int launch_operator(sbp3_handle* h, const T* u, T* du, T* un, double dt, cudaStr
     prof_begin(h, 0, st, &stop);
     k3_flux<T, O><<<grd, blk, 0, st>>>(g, u, cm, q);
     prof_end(stop, st);
-    prof_begin(h, 1, st, &stop);
-    k3_div<T, O, MODE><<<grd, blk, 0, st>>>(g, u, q, cd, w, du, un, dt2);
-    prof_end(stop, st);
-    for (int m = 0; m < 3; ++m) {
-        const int pd = m == 0 ? 1 : 0, td = m == 2 ? 1 : 2;
-        const dim3 fb(32, 4), fg((g.n[pd] + 31) / 32, (g.n[td] + 3) / 4, 2);
+    {
+        constexpr int NV = sizeof(T) == 4 ? 2 : 1;
+        const Box3& bx = h->box;
+        const int ngx = (bx.x1hi - bx.x1lo) / NV;
+        const dim3 ib(32, 4), ig((ngx + 31) / 32, (bx.y1 - bx.y0 + 3) / 4, bx.z1 - bx.z0);
+        if (ngx > 0) {             // the box is empty only for order 2 on the smallest grids
+            prof_begin(h, 1, st, &stop);
+            k3_div_int<T, O, MODE, NV><<<ig, ib, 0, st>>>(g, bx, u, q, cd, w, du, un, dt2);
+            prof_end(stop, st);
+        }
+        const long long cnt = h->shell;
         prof_begin(h, 2, st, &stop);
-        k3_face<T, O, MODE><<<fg, fb, 0, st>>>(g, m, h->faces[2 * m], h->faces[2 * m + 1], h->beta, u, cm, cd, w, du,
-                                                un, dt2);
+        const XClos xc{h->xm, (long long)h->n[1] * h->n[2]};
+        k3_div_shell<T, O, MODE><<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(g, bx, h->sh, xc, h->fc, cnt, u, q,
+                                                                             cm, cd, w, du, un, dt2);
         prof_end(stop, st);
     }
     cudaError_t e = cudaGetLastError();
@@ -159,6 +169,8 @@ int material_impl(sbp3_handle* h, int k0, int nk, const double* rho_d, const dou
     const dim3 blk(128), grd((h->n[0] + 127) / 128, h->n[1], nk);
     k3_material<T, O><<<grd, blk>>>(h->g, h->X, k0, nk, rho_d, c_d, static_cast<T*>(h->cm), static_cast<T*>(h->cd),
                                      static_cast<T*>(h->w), h->d_err);
+    const dim3 xg((h->n[1] + 127) / 128, nk, 2 * Ord<O>::NCLOS);
+    k3_xclos<T, O><<<xg, 128>>>(h->g, k0, nk, static_cast<const T*>(h->cd), static_cast<T*>(h->xm));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "k3_material");
     return SBP_OK;
@@ -181,12 +193,18 @@ template <typename F> int dispatch(sbp3_handle* h, F f) {
 }
 
 void free_all(sbp3_handle* h) {
-    void* bufs[] = {h->X, h->cm, h->cd, h->w, h->u[0], h->u[1], h->du, h->q, h->ain, h->aout, h->d_err};
+    void* bufs[] = {h->X, h->cm, h->cd, h->w, h->u[0], h->u[1], h->du, h->q, h->xm, h->ain, h->aout, h->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& v : h->prof.ev)
         for (cudaEvent_t e : v)
             if (e) cudaEventDestroy(e);
+}
+
+size_t xclos_bytes(int order, size_t es, int n2, int n3) {
+    const int nclos = order == 2 ? SBP2_NCLOS : (order == 4 ? SBP4_NCLOS : SBP6_NCLOS);
+    const int nj = order == 2 ? SBP2_NCLOSJ : (order == 4 ? SBP4_NCLOSJ : SBP6_NCLOSJ);
+    return (size_t)2 * nj * 6 * nclos * (size_t)n2 * n3 * es;
 }
 
 long long field_bytes(int precision, const int n[3]) {
@@ -204,13 +222,15 @@ extern "C" {
 
 const char* sbp3_last_error(const sbp3_handle* h) { return h ? h->err.c_str() : g3_create_error.c_str(); }
 
-int sbp3_footprint(int precision, int n1, int n2, int n3, long long* bytes_out) {
-    if (!bytes_out || n1 <= 0 || n2 <= 0 || n3 <= 0 || (precision != SBP_FP64 && precision != SBP_FP32))
+int sbp3_footprint(int order, int precision, int n1, int n2, int n3, long long* bytes_out) {
+    if (!bytes_out || n1 <= 0 || n2 <= 0 || n3 <= 0 || (precision != SBP_FP64 && precision != SBP_FP32) ||
+        (order != 2 && order != 4 && order != 6))
         return fail(nullptr, SBP_E_INVALID_ARG, "sbp3_footprint: bad arguments");
     const int n[3] = {n1, n2, n3};
     const long long f = field_bytes(precision, n);
     const long long x = pitch_of(n1, precision == SBP_FP32 ? 4 : 8) * n2 * n3 * 8LL;
-    *bytes_out = f * (NCM + NCD + 1 + 6 + 3 + 9) + 3 * x;
+    *bytes_out = f * (NCM + NCD + 1 + 6 + 3 + 9) + 3 * x +
+                 (long long)xclos_bytes(order, precision == SBP_FP32 ? 4 : 8, n2, n3);
     return SBP_OK;
 }
 
@@ -226,6 +246,8 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
         return fail(nullptr, SBP_E_INVALID_ARG, "need n1, n2, n3 >= " + std::to_string(mn) + " for order " +
                                                     std::to_string(order));
     if (n3 > 65535 || n2 > 65535) return fail(nullptr, SBP_E_INVALID_ARG, "n2, n3 must be <= 65535");
+    if (pitch_of(n1, precision == SBP_FP32 ? 4 : 8) * (long long)n2 >= (1LL << 31))
+        return fail(nullptr, SBP_E_INVALID_ARG, "an x3-plane must hold fewer than 2^31 elements");
     if (!X || !face_kinds) return fail(nullptr, SBP_E_INVALID_ARG, "X and face_kinds are required");
     for (int f = 0; f < 6; ++f)
         if (face_kinds[f] != SBP3_BC_DISPLACEMENT && face_kinds[f] != SBP3_BC_TRACTION)
@@ -245,7 +267,8 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
     h->pitch = pitch_of(n1, h->es);
     h->fs = h->pitch * n2 * n3;
     h->beta = beta;
-    for (int f = 0; f < 6; ++f) h->faces[f] = face_kinds[f];
+    for (int f = 0; f < 6; ++f) h->fc.kind[f] = face_kinds[f];
+    h->fc.beta = beta;
     h->planes_set.assign(n3, 0);
     cudaGetDevice(&h->device);
     Grid3& g = h->g;
@@ -257,6 +280,28 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
     g.s[1] = h->pitch;
     g.s[2] = h->pitch * n2;
     g.fs = h->fs;
+    {
+        const int nclos = order == 2 ? SBP2_NCLOS : (order == 4 ? SBP4_NCLOS : SBP6_NCLOS);
+        const int q = order / 2, nv = precision == SBP_FP32 ? 2 : 1;
+        const int qa = (q + nv - 1) / nv * nv;            // the x1 window of k3_div_int reaches qa nodes out
+        const int ncol = order == 2 ? SBP2_NCOL : (order == 4 ? SBP4_NCOL : SBP6_NCOL);
+        // the shell holds every node with a closure row, a normal SAT term (depth < NCOL) or an x1
+        // window of k3_div_int that would leave the row
+        const int ey = nclos > ncol ? nclos : ncol;
+        const int e = ey > qa ? ey : qa;
+        Box3& bx = h->box;
+        bx.x1lo = (e + nv - 1) / nv * nv;
+        bx.x1hi = n1 - e > bx.x1lo ? bx.x1lo + (n1 - e - bx.x1lo) / nv * nv : bx.x1lo;
+        bx.y0 = ey;
+        bx.y1 = n2 - ey;
+        bx.z0 = ey;
+        bx.z1 = n3 - ey;
+        Shell3& sh = h->sh;
+        sh.cZ = (long long)(bx.z0 + (n3 - bx.z1)) * n2 * n1;
+        sh.cY = (long long)(bx.z1 - bx.z0) * (bx.y0 + (n2 - bx.y1)) * n1;
+        sh.cX = (long long)(bx.z1 - bx.z0) * (bx.y1 - bx.y0) * (bx.x1lo + (n1 - bx.x1hi));
+        h->shell = sh.cX + sh.cZ + sh.cY;
+    }
     auto alloc = [&](void** p, size_t bytes) -> bool {
         if (cudaMalloc(p, bytes) != cudaSuccess) return false;
         return cudaMemset(*p, 0, bytes) == cudaSuccess;
@@ -267,7 +312,8 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
     const size_t xfs = (size_t)h->fs;
     bool ok = alloc((void**)&h->X, 3 * xfs * 8) && alloc(&h->cm, NCM * fb) && alloc(&h->cd, NCD * fb) &&
               alloc(&h->w, fb) && alloc(&h->u[0], 3 * fb) && alloc(&h->u[1], 3 * fb) && alloc(&h->du, 3 * fb) &&
-              alloc(&h->q, 9 * fb) && alloc((void**)&h->d_err, sizeof(int));
+              alloc(&h->q, 9 * fb) && alloc(&h->xm, xclos_bytes(order, h->es, n2, n3)) &&
+              alloc((void**)&h->d_err, sizeof(int));
     if (!ok) {
         cudaGetLastError();
         free_all(h);

@@ -42,7 +42,8 @@ def test_apply_fp64(order, N, faces):
     assert np.abs(got - ref).max() < 1e-12 * _term_scale(O, u)
 
 
-@pytest.mark.parametrize("order,N", [(6, (30, 28, 27)), (4, (37, 18, 21))])
+@pytest.mark.parametrize("order,N", [(6, (30, 28, 27)), (6, (64, 29, 31)), (4, (37, 18, 21)), (2, (9, 7, 8)),
+                                     (2, (5, 6, 5))])
 @pytest.mark.parametrize("smooth", [True, False])
 def test_apply_fp32(order, N, smooth):
     from paper_2003_12811_gb300 import Solver3D

@@ -107,6 +107,8 @@ def test_sbp3_validation_before_device_work(L):
     assert L.sbp3_create(6, 0, n, n, n, xp, kinds, 1.0, C.byref(h)) == -1          # non-finite X
     assert b"non-finite" in L.sbp3_last_error(None)
     out = C.c_longlong()
-    assert L.sbp3_footprint(1, 256, 256, 256, C.byref(out)) == 0
-    # 64 FP32 fields + 3 FP64 coordinate fields per node
-    assert out.value == 256 ** 3 * (64 * 4 + 3 * 8)
+    assert L.sbp3_footprint(6, 1, 256, 256, 256, C.byref(out)) == 0
+    # 64 FP32 fields + 3 FP64 coordinate fields per node, and per x1 line the order-6 closure
+    # matrices: 2 sides x 9 rows x 12 columns x 6 coefficients
+    assert out.value == 256 ** 3 * (64 * 4 + 3 * 8) + 256 ** 2 * 2 * 9 * 12 * 6 * 4
+    assert L.sbp3_footprint(5, 1, 256, 256, 256, C.byref(out)) == -1
