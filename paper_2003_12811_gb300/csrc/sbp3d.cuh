@@ -462,58 +462,52 @@ __device__ __forceinline__ void div_int_x1(const T* __restrict__ q0, const T* __
             r[n][j] += ih * acc;
         }
     }
-    T L[2 * Q + 1][3][NV];
+    // narrow rows one displacement component at a time (L_k of u_l for the NV nodes, then every
+    // coefficient field b_jl that multiplies u_l), so only one component's L's are live
+    const T ih2 = ih * ih;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        T w[WN];
-        window(up + l * fs, w);
+        T L[2 * Q + 1][NV];
+        {
+            T w[WN];
+            window(up + l * fs, w);
 #pragma unroll
-        for (int n = 0; n < NV; ++n) {
-            const T uc = w[QA + n];
+            for (int n = 0; n < NV; ++n) {
+                const T uc = w[QA + n];
 #pragma unroll
-            for (int k = -Q; k <= Q; ++k) {
+                for (int k = -Q; k <= Q; ++k) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 1; m <= Q; ++m) {
+                        const T cp = edge_wT<O, T>(m, k), cn = edge_wT<O, T>(m, k + m);
+                        if (cp != T(0)) acc += cp * (w[QA + n + m] - uc);
+                        if (cn != T(0)) acc += cn * (w[QA + n - m] - uc);
+                    }
+                    L[k + Q][n] = acc;
+                }
+            }
+        }
+        // fields b_jl with this l: (j, l) for j = 0..2, s6 = sym3 index
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int s6 = j <= l ? (j == 0 ? l : (j == 1 ? 2 + l : 5)) : (l == 0 ? j : (l == 1 ? 2 + j : 5));
+            T w[WN];
+            window(cd0 + s6 * fs, w);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
                 T acc = T(0);
 #pragma unroll
-                for (int m = 1; m <= Q; ++m) {
-                    const T cp = edge_wT<O, T>(m, k), cn = edge_wT<O, T>(m, k + m);
-                    if (cp != T(0)) acc += cp * (w[QA + n + m] - uc);
-                    if (cn != T(0)) acc += cn * (w[QA + n - m] - uc);
-                }
-                L[k + Q][l][n] = acc;
+                for (int k = -Q; k <= Q; ++k) acc += w[QA + n + k] * L[k + Q][n];
+                r[n][j] += ih2 * acc;
             }
         }
     }
-    const T ih2 = ih * ih;
-    T rr[NV][3];
-#pragma unroll
-    for (int n = 0; n < NV; ++n)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) rr[n][j] = T(0);
-#pragma unroll
-    for (int s6 = 0; s6 < 6; ++s6) {
-        const int j = s6 < 3 ? 0 : (s6 < 5 ? 1 : 2);
-        const int l = s6 < 3 ? s6 : (s6 < 5 ? s6 - 2 : 2);
-        T w[WN];
-        window(cd0 + s6 * fs, w);
-#pragma unroll
-        for (int n = 0; n < NV; ++n)
-#pragma unroll
-            for (int k = -Q; k <= Q; ++k) {
-                const T bk = w[QA + n + k];
-                rr[n][j] += bk * L[k + Q][l][n];
-                if (j != l) rr[n][l] += bk * L[k + Q][j][n];
-            }
-    }
-#pragma unroll
-    for (int n = 0; n < NV; ++n)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) r[n][j] += ih2 * rr[n][j];
 }
 
 // MODE 0: leapfrog in increment form, d = du + dt^2 w r, un = u + d (du updated in place);
 // MODE 1: apply, out = w r.
 template <typename T, int O, int MODE, int NV>
-__global__ void __launch_bounds__(128) k3_div_int(Grid3 g, Box3 bx, const T* __restrict__ u, const T* __restrict__ q,
+__global__ void __launch_bounds__(128, 5) k3_div_int(Grid3 g, Box3 bx, const T* __restrict__ u, const T* __restrict__ q,
                                                   const T* __restrict__ cd, const T* __restrict__ w,
                                                   T* __restrict__ du, T* __restrict__ un, T dt2) {
     const int gx = blockIdx.x * 32 + threadIdx.x;
