@@ -340,10 +340,12 @@ __global__ void __launch_bounds__(128) k3_xclos(Grid3 g, int k0, int nk, const T
 }
 
 // ------------------------------------------------------------------ divergence: interior box and boundary shell
-// Nodes at least NCLOS from every face use only interior rows in all three directions.  They form
-// the box [x1lo, x1hi) x [y0, y1) x [z0, z1) (x1lo a multiple of NV), handled by k3_div_int: no
-// closure branches, and NV consecutive x1 nodes per thread read as one vector (float2 for FP32).
-// Every other node (the shell) goes to k3_div_shell, the general per-node code above.
+// Nodes at least max(NCLOS, NCOL) from the x1 faces use interior rows along x1 and no x1-face
+// SAT.  They form the box [x1lo, x1hi) x [y0, y1) x [z0, z1) (x1lo a multiple of NV; the box
+// spans every i2 and i3), handled by k3_div_int: NV consecutive x1 nodes per thread read as one
+// vector (float2 for FP32); the x2 and x3 rows are interior vector code or, on the closure planes
+// and rows (the same for the whole warp), the general rows.  The x1 slabs outside the box (the
+// shell) go to k3_div_shell.
 struct Box3 {
     int x1lo, x1hi, y0, y1, z0, z1;
 };
@@ -504,90 +506,6 @@ __device__ __forceinline__ void div_int_x1(const T* __restrict__ q0, const T* __
     }
 }
 
-// MODE 0: leapfrog in increment form, d = du + dt^2 w r, un = u + d (du updated in place);
-// MODE 1: apply, out = w r.
-template <typename T, int O, int MODE, int NV>
-__global__ void __launch_bounds__(128, 5) k3_div_int(Grid3 g, Box3 bx, const T* __restrict__ u, const T* __restrict__ q,
-                                                  const T* __restrict__ cd, const T* __restrict__ w,
-                                                  T* __restrict__ du, T* __restrict__ un, T dt2) {
-    const int gx = blockIdx.x * 32 + threadIdx.x;
-    const int i1 = bx.x1lo + gx * NV, i2 = bx.y0 + blockIdx.y * 4 + threadIdx.y, i3 = bx.z0 + blockIdx.z;
-    if (i1 >= bx.x1hi || i2 >= bx.y1) return;
-    const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
-    const long long fs = g.fs;
-    const T* up = u + o;
-    T r[NV][3];
-#pragma unroll
-    for (int n = 0; n < NV; ++n) r[n][0] = r[n][1] = r[n][2] = T(0);
-    div_int_x1<T, O, NV>(q + o, cd + o, up, fs, T(g.ih[0]), r);
-    div_int_strided<T, O, NV>(q + 3 * fs + o, cd + 6 * fs + o, up, fs, (int)g.s[1], T(g.ih[1]), r);
-    div_int_strided<T, O, NV>(q + 6 * fs + o, cd + 12 * fs + o, up, fs, (int)g.s[2], T(g.ih[2]), r);
-    T wv[NV];
-    vld<T, NV>(w + o, wv);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const long long oj = j * fs + o;
-        T out[NV];
-        if constexpr (MODE == 0) {
-            T d[NV], uc[NV];
-            vld<T, NV>(du + oj, d);
-            vld<T, NV>(up + j * fs, uc);
-#pragma unroll
-            for (int n = 0; n < NV; ++n) {
-                d[n] += dt2 * wv[n] * r[n][j];
-                out[n] = uc[n] + d[n];
-            }
-            vst<T, NV>(du + oj, d);
-        } else {
-#pragma unroll
-            for (int n = 0; n < NV; ++n) out[n] = wv[n] * r[n][j];
-        }
-        vst<T, NV>(un + oj, out);
-    }
-}
-
-// the shell: every node outside the box, lanes along x1 (coalesced), in three parts:
-//   Z: the planes i3 < z0, i3 >= z1 (whole planes);
-//   Y: within the box's planes, the rows i2 < y0, i2 >= y1 (whole rows);
-//   X: within the box's planes and rows, the x1 runs i1 < x1lo and i1 >= x1hi.
-struct Shell3 {
-    long long cZ, cY, cX;   // node counts of the three parts
-};
-
-__device__ __forceinline__ bool shell_node(const Grid3& g, const Box3& bx, const Shell3& sh, long long t, int& i1,
-                                           int& i2, int& i3) {
-    const long long n1 = g.n[0], n2 = g.n[1];
-    const long long plane = n1 * n2;
-    if (t < sh.cZ) {
-        const long long pz = t / plane;
-        const long long rem = t - pz * plane;
-        i3 = (int)(pz < bx.z0 ? pz : bx.z1 + (pz - bx.z0));
-        i2 = (int)(rem / n1);
-        i1 = (int)(rem - (long long)i2 * n1);
-        return true;
-    }
-    t -= sh.cZ;
-    if (t < sh.cY) {
-        const long long rowsB = bx.y0 + (n2 - bx.y1);
-        const long long row = t / n1;
-        i1 = (int)(t - row * n1);
-        const long long pz = row / rowsB, ry = row - pz * rowsB;
-        i3 = (int)(bx.z0 + pz);
-        i2 = (int)(ry < bx.y0 ? ry : bx.y1 + (ry - bx.y0));
-        return true;
-    }
-    t -= sh.cY;
-    if (t >= sh.cX) return false;
-    const long long ny = bx.y1 - bx.y0;
-    const long long runs = bx.x1lo + (n1 - bx.x1hi);
-    const long long row = t / runs, rx = t - row * runs;
-    const long long pz = row / ny, py = row - pz * ny;
-    i3 = (int)(bx.z0 + pz);
-    i2 = (int)(bx.y0 + py);
-    i1 = (int)(rx < bx.x1lo ? rx : bx.x1hi + (rx - bx.x1lo));
-    return true;
-}
-
 // ------------------------------------------------------------------ boundary SATs of the faces x_m = 0, 1
 // Computed by the shell kernel for the nodes they reach, so no node is written twice:
 //   traction:     J SAT_J = -H^-1 P_f nu c_mJkL D_k u_L              (face node only)
@@ -727,6 +645,128 @@ __device__ __noinline__ void face_terms(const Grid3& g, const Faces3& fc, int im
             face_tangential<T, O, M, TD>(g, ib, up, cm, cd, o, base * T(g.ih[TD]), r);
         }
     }
+}
+
+// the general row code of one node as a call of its own, so the closure planes do not weigh on
+// the register allocation of the vector path
+template <typename T, int O, int D>
+__device__ __noinline__ void div_dir_call(const Grid3& g, int i, const T* __restrict__ qo, const T* __restrict__ cdo,
+                                          const T* __restrict__ up, T* __restrict__ rn) {
+    T r3[3] = {T(0), T(0), T(0)};
+    div_dir<T, O, D>(g, i, qo, cdo, up, r3);
+    rn[0] += r3[0];
+    rn[1] += r3[1];
+    rn[2] += r3[2];
+}
+
+// direction D = x2 or x3 for the NV nodes of a thread: interior rows through the vector code,
+// closure rows (the same for every lane of a warp, whose lanes share i2 and i3) node by node
+template <typename T, int O, int NV, int D>
+__device__ __forceinline__ void div_int_dir(const Grid3& g, int i, const T* __restrict__ qo,
+                                            const T* __restrict__ cdo, const T* __restrict__ up, T r[NV][3]) {
+    const int N = g.n[D];
+    const long long fs = g.fs;
+    if (i >= Ord<O>::NCLOS && i < N - Ord<O>::NCLOS) {
+        div_int_strided<T, O, NV>(qo + 3 * D * fs, cdo + 6 * D * fs, up, fs, dstride<D>(g), T(g.ih[D]), r);
+        return;
+    }
+#pragma unroll
+    for (int n = 0; n < NV; ++n) div_dir_call<T, O, D>(g, i, qo + n, cdo + n, up + n, r[n]);
+}
+
+// MODE 0: leapfrog in increment form, d = du + dt^2 w r, un = u + d (du updated in place);
+// MODE 1: apply, out = w r.
+template <typename T, int O, int MODE, int NV>
+__global__ void __launch_bounds__(128, 5) k3_div_int(Grid3 g, Box3 bx, Faces3 fc, const T* __restrict__ u,
+                                                     const T* __restrict__ q, const T* __restrict__ cm,
+                                                     const T* __restrict__ cd, const T* __restrict__ w,
+                                                     T* __restrict__ du, T* __restrict__ un, T dt2) {
+    using P = Ord<O>;
+    const int gx = blockIdx.x * 32 + threadIdx.x;
+    const int i1 = bx.x1lo + gx * NV, i2 = bx.y0 + blockIdx.y * 4 + threadIdx.y, i3 = bx.z0 + blockIdx.z;
+    if (i1 >= bx.x1hi || i2 >= bx.y1) return;
+    const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
+    const long long fs = g.fs;
+    const T* up = u + o;
+    T r[NV][3];
+#pragma unroll
+    for (int n = 0; n < NV; ++n) r[n][0] = r[n][1] = r[n][2] = T(0);
+    div_int_x1<T, O, NV>(q + o, cd + o, up, fs, T(g.ih[0]), r);
+    div_int_dir<T, O, NV, 1>(g, i2, q + o, cd + o, up, r);
+    div_int_dir<T, O, NV, 2>(g, i3, q + o, cd + o, up, r);
+    // SATs of the x2 and x3 faces that reach these nodes (the x1 faces lie in the shell)
+    if (i2 < P::NCOL || i2 >= g.n[1] - P::NCOL) {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) face_terms<T, O, 1>(g, fc, i2, i1 + n, i3, o + n, u, cm, cd, r[n]);
+    }
+    if (i3 < P::NCOL || i3 >= g.n[2] - P::NCOL) {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) face_terms<T, O, 2>(g, fc, i3, i1 + n, i2, o + n, u, cm, cd, r[n]);
+    }
+    T wv[NV];
+    vld<T, NV>(w + o, wv);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const long long oj = j * fs + o;
+        T out[NV];
+        if constexpr (MODE == 0) {
+            T d[NV], uc[NV];
+            vld<T, NV>(du + oj, d);
+            vld<T, NV>(up + j * fs, uc);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                d[n] += dt2 * wv[n] * r[n][j];
+                out[n] = uc[n] + d[n];
+            }
+            vst<T, NV>(du + oj, d);
+        } else {
+#pragma unroll
+            for (int n = 0; n < NV; ++n) out[n] = wv[n] * r[n][j];
+        }
+        vst<T, NV>(un + oj, out);
+    }
+}
+
+// the shell: every node outside the box, lanes along x1 (coalesced), in three parts:
+//   Z: the planes i3 < z0, i3 >= z1 (whole planes);
+//   Y: within the box's planes, the rows i2 < y0, i2 >= y1 (whole rows);
+//   X: within the box's planes and rows, the x1 runs i1 < x1lo and i1 >= x1hi.
+struct Shell3 {
+    long long cZ, cY, cX;   // node counts of the three parts
+};
+
+__device__ __forceinline__ bool shell_node(const Grid3& g, const Box3& bx, const Shell3& sh, long long t, int& i1,
+                                           int& i2, int& i3) {
+    const long long n1 = g.n[0], n2 = g.n[1];
+    const long long plane = n1 * n2;
+    if (t < sh.cZ) {
+        const long long pz = t / plane;
+        const long long rem = t - pz * plane;
+        i3 = (int)(pz < bx.z0 ? pz : bx.z1 + (pz - bx.z0));
+        i2 = (int)(rem / n1);
+        i1 = (int)(rem - (long long)i2 * n1);
+        return true;
+    }
+    t -= sh.cZ;
+    if (t < sh.cY) {
+        const long long rowsB = bx.y0 + (n2 - bx.y1);
+        const long long row = t / n1;
+        i1 = (int)(t - row * n1);
+        const long long pz = row / rowsB, ry = row - pz * rowsB;
+        i3 = (int)(bx.z0 + pz);
+        i2 = (int)(ry < bx.y0 ? ry : bx.y1 + (ry - bx.y0));
+        return true;
+    }
+    t -= sh.cY;
+    if (t >= sh.cX) return false;
+    const long long ny = bx.y1 - bx.y0;
+    const long long runs = bx.x1lo + (n1 - bx.x1hi);
+    const long long row = t / runs, rx = t - row * runs;
+    const long long pz = row / ny, py = row - pz * ny;
+    i3 = (int)(bx.z0 + pz);
+    i2 = (int)(bx.y0 + py);
+    i1 = (int)(rx < bx.x1lo ? rx : bx.x1hi + (rx - bx.x1lo));
+    return true;
 }
 
 // the boundary shell: volume terms with closure rows, then every face SAT reaching the node, then

@@ -132,7 +132,7 @@ int launch_operator(sbp3_handle* h, const T* u, T* du, T* un, double dt, cudaStr
         const dim3 ib(32, 4), ig((ngx + 31) / 32, (bx.y1 - bx.y0 + 3) / 4, bx.z1 - bx.z0);
         if (ngx > 0) {             // the box is empty only for order 2 on the smallest grids
             prof_begin(h, 1, st, &stop);
-            k3_div_int<T, O, MODE, NV><<<ig, ib, 0, st>>>(g, bx, u, q, cd, w, du, un, dt2);
+            k3_div_int<T, O, MODE, NV><<<ig, ib, 0, st>>>(g, bx, h->fc, u, q, cm, cd, w, du, un, dt2);
             prof_end(stop, st);
         }
         const long long cnt = h->shell;
@@ -292,10 +292,10 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
         Box3& bx = h->box;
         bx.x1lo = (e + nv - 1) / nv * nv;
         bx.x1hi = n1 - e > bx.x1lo ? bx.x1lo + (n1 - e - bx.x1lo) / nv * nv : bx.x1lo;
-        bx.y0 = ey;
-        bx.y1 = n2 - ey;
-        bx.z0 = ey;
-        bx.z1 = n3 - ey;
+        bx.y0 = 0;
+        bx.y1 = n2;
+        bx.z0 = 0;
+        bx.z1 = n3;
         Shell3& sh = h->sh;
         sh.cZ = (long long)(bx.z0 + (n3 - bx.z1)) * n2 * n1;
         sh.cY = (long long)(bx.z1 - bx.z0) * (bx.y0 + (n2 - bx.y1)) * n1;
