@@ -448,6 +448,7 @@ def bench3d(n=256, nsteps=40, prec="fp32"):
     del g1, g2, g3
     S.set_state(u, u)
     del u
+    variant, variant_ms = S.sbp3_autotune()           # launch shape of the interior kernel
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     S.step(3, dt, sh)
@@ -481,7 +482,8 @@ def bench3d(n=256, nsteps=40, prec="fp32"):
             "node_updates_per_s": nodes / (ms / 1e3), "ms_per_step": ms, "kernels": kern,
             "step_vs_fused_minimum": {"bytes_per_node": OP3D_WORDS["fused_min"] * es, "achieved_GBs": fused,
                                       "frac": fused / peak},
-            "peak_GBs": peak, "peak_source": src, "launches_per_step": 3, "steps": nsteps, "state_finite": finite}
+            "peak_GBs": peak, "peak_source": src, "launches_per_step": 3, "steps": nsteps, "state_finite": finite,
+            "tuning": {"variant": variant, "apply_ms_per_variant": variant_ms}}
 
 
 def variant_bench(P, prec, nsteps=100):

@@ -76,6 +76,17 @@ int sbp3_step(sbp3_handle* h, int nsteps, double dt, void* stream);
 /* Per-family device time (CUDA events on the launch stream) of the launches made while enabled,
  * and the launch counts since create (always counted).  ms and launches hold
  * SBP3_PROF_FAMILIES entries; sbp3_profile_read synchronizes the device. */
+/* Launch shape of the interior divergence kernel (x2 rows per block and the register cap that
+ * follows from the minimum resident blocks): variant 0 .. SBP3_TUNING_VARIANTS-1, order 6 only
+ * (other orders keep variant 0).  Every variant computes bitwise the same field.
+ * sbp3_autotune times each variant on operator applications of the current level (zeros before
+ * any state; the state is not changed), selects the fastest and returns it; ms_out (optional,
+ * SBP3_TUNING_VARIANTS entries) receives the time of one application per variant (-1: not built
+ * for this order). */
+#define SBP3_TUNING_VARIANTS 4
+int sbp3_set_tuning(sbp3_handle* h, int variant);
+int sbp3_autotune(sbp3_handle* h, int* variant_out, double* ms_out);
+
 int sbp3_profile(sbp3_handle* h, int enable);
 int sbp3_profile_read(sbp3_handle* h, double* ms, long long* launches);
 

@@ -126,6 +126,8 @@ def lib():
         L.sbp3_apply.argtypes = [C.c_void_p, _DP, _DP]
         L.sbp3_step.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.sbp3_profile.argtypes = [C.c_void_p, C.c_int]
+        L.sbp3_set_tuning.argtypes = [C.c_void_p, C.c_int]
+        L.sbp3_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int), _DP]
         L.sbp3_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_longlong)]
         L.sbp3_get_info.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
@@ -519,6 +521,16 @@ class Solver3D:
 
     def step(self, nsteps, dt, stream=None):
         self._check(self.L.sbp3_step(self.h, int(nsteps), float(dt), stream))
+
+    def sbp3_set_tuning(self, variant):
+        self._check(self.L.sbp3_set_tuning(self.h, int(variant)))
+
+    def sbp3_autotune(self):
+        """Selects the fastest launch shape of the interior kernel; returns (variant, ms per variant)."""
+        v = C.c_int()
+        ms = (C.c_double * 4)()
+        self._check(self.L.sbp3_autotune(self.h, C.byref(v), ms))
+        return int(v.value), list(ms)
 
     def profile(self, enable):
         self._check(self.L.sbp3_profile(self.h, int(enable)))

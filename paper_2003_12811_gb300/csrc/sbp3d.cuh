@@ -676,14 +676,21 @@ __device__ __forceinline__ void div_int_dir(const Grid3& g, int i, const T* __re
 
 // MODE 0: leapfrog in increment form, d = du + dt^2 w r, un = u + d (du updated in place);
 // MODE 1: apply, out = w r.
-template <typename T, int O, int MODE, int NV>
-__global__ void __launch_bounds__(128, 5) k3_div_int(Grid3 g, Box3 bx, Faces3 fc, const T* __restrict__ u,
-                                                     const T* __restrict__ q, const T* __restrict__ cm,
-                                                     const T* __restrict__ cd, const T* __restrict__ w,
-                                                     T* __restrict__ du, T* __restrict__ un, T dt2) {
+// launch shapes of k3_div_int (sbp3_set_tuning / sbp3_autotune): x2 rows per block and the
+// minimum resident blocks per SM, which sets the register cap (65536 / (32 BY MINB))
+struct DivShape {
+    int by, minb;
+};
+constexpr DivShape kDivShapes[4] = {{4, 5}, {4, 6}, {8, 3}, {2, 10}};
+
+template <typename T, int O, int MODE, int NV, int BY, int MINB>
+__global__ void __launch_bounds__(32 * BY, MINB) k3_div_int(Grid3 g, Box3 bx, Faces3 fc, const T* __restrict__ u,
+                                                            const T* __restrict__ q, const T* __restrict__ cm,
+                                                            const T* __restrict__ cd, const T* __restrict__ w,
+                                                            T* __restrict__ du, T* __restrict__ un, T dt2) {
     using P = Ord<O>;
     const int gx = blockIdx.x * 32 + threadIdx.x;
-    const int i1 = bx.x1lo + gx * NV, i2 = bx.y0 + blockIdx.y * 4 + threadIdx.y, i3 = bx.z0 + blockIdx.z;
+    const int i1 = bx.x1lo + gx * NV, i2 = bx.y0 + blockIdx.y * BY + threadIdx.y, i3 = bx.z0 + blockIdx.z;
     if (i1 >= bx.x1hi || i2 >= bx.y1) return;
     const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
     const long long fs = g.fs;

@@ -39,6 +39,7 @@ struct sbp3_handle {
     long long shell = 0;                     // nodes outside the box (k3_div_shell)
     Shell3 sh{};
     Faces3 fc{};
+    int div_variant = 0;                     // launch shape of k3_div_int (kDivShapes)
     double* X = nullptr;                     // pitched FP64 coordinates (3 fields)
     void* cm = nullptr;                      // 27 fields
     void* cd = nullptr;                      // 18 fields
@@ -129,10 +130,20 @@ int launch_operator(sbp3_handle* h, const T* u, T* du, T* un, double dt, cudaStr
         constexpr int NV = sizeof(T) == 4 ? 2 : 1;
         const Box3& bx = h->box;
         const int ngx = (bx.x1hi - bx.x1lo) / NV;
-        const dim3 ib(32, 4), ig((ngx + 31) / 32, (bx.y1 - bx.y0 + 3) / 4, bx.z1 - bx.z0);
         if (ngx > 0) {             // the box is empty only for order 2 on the smallest grids
+            auto run = [&](auto vc) {
+                constexpr int V = decltype(vc)::value;
+                constexpr int BY = kDivShapes[V].by, MINB = kDivShapes[V].minb;
+                const dim3 ib(32, BY), ig((ngx + 31) / 32, (bx.y1 - bx.y0 + BY - 1) / BY, bx.z1 - bx.z0);
+                k3_div_int<T, O, MODE, NV, BY, MINB><<<ig, ib, 0, st>>>(g, bx, h->fc, u, q, cm, cd, w, du, un, dt2);
+            };
             prof_begin(h, 1, st, &stop);
-            k3_div_int<T, O, MODE, NV><<<ig, ib, 0, st>>>(g, bx, h->fc, u, q, cm, cd, w, du, un, dt2);
+            // every shape is built for order 6; orders 2 and 4 keep the first
+            const int v = O == 6 ? h->div_variant : 0;
+            if (v == 1) run(std::integral_constant<int, O == 6 ? 1 : 0>());
+            else if (v == 2) run(std::integral_constant<int, O == 6 ? 2 : 0>());
+            else if (v == 3) run(std::integral_constant<int, O == 6 ? 3 : 0>());
+            else run(std::integral_constant<int, 0>());
             prof_end(stop, st);
         }
         const long long cnt = h->shell;
@@ -477,6 +488,74 @@ int sbp3_step(sbp3_handle* h, int nsteps, double dt, void* stream) {
         constexpr int O = decltype(oc)::value;
         return step_impl<T, O>(h, nsteps, dt, st);
     });
+}
+
+int sbp3_set_tuning(sbp3_handle* h, int variant) {
+    if (!h) return fail(nullptr, SBP_E_INVALID_ARG, "null handle");
+    if (variant < 0 || variant >= SBP3_TUNING_VARIANTS) return fail(h, SBP_E_INVALID_ARG, "bad tuning variant");
+    h->div_variant = h->order == 6 ? variant : 0;
+    return SBP_OK;
+}
+
+int sbp3_autotune(sbp3_handle* h, int* variant_out, double* ms_out) {
+    if (!h) return fail(nullptr, SBP_E_INVALID_ARG, "null handle");
+    if (!check_range(h)) return fail(h, SBP_E_STATE, "material not set for every x3-plane");
+    DeviceGuard dg(h->device);
+    const size_t fb = (size_t)h->fs * h->es;
+    if (!h->ain) CK3(h, cudaMalloc(&h->ain, 3 * fb));
+    if (!h->aout) CK3(h, cudaMalloc(&h->aout, 3 * fb));
+    // operator applications on the current level (or on zeros before any state): the state is untouched
+    if (h->state) CK3(h, cudaMemcpy(h->ain, h->u[h->cur], 3 * fb, cudaMemcpyDeviceToDevice));
+    else CK3(h, cudaMemset(h->ain, 0, 3 * fb));
+    const int nv = h->order == 6 ? SBP3_TUNING_VARIANTS : 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = h->prof_on;
+    h->prof_on = false;
+    int best = 0;
+    double best_ms = 1e300;
+    for (int v = 0; v < nv; ++v) {
+        h->div_variant = v;
+        int rc = SBP_OK;
+        for (int rep = 0; rep < 2 && rc == SBP_OK; ++rep)
+            rc = dispatch(h, [&](auto tag, auto oc) {
+                using T = decltype(tag);
+                constexpr int O = decltype(oc)::value;
+                return apply_impl<T, O>(h, 0);
+            });
+        cudaEventRecord(e0, 0);
+        for (int rep = 0; rep < 5 && rc == SBP_OK; ++rep)
+            rc = dispatch(h, [&](auto tag, auto oc) {
+                using T = decltype(tag);
+                constexpr int O = decltype(oc)::value;
+                return apply_impl<T, O>(h, 0);
+            });
+        cudaEventRecord(e1, 0);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (rc != SBP_OK || e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            h->prof_on = prof;
+            h->div_variant = 0;
+            return rc != SBP_OK ? rc : cuda_fail(h, e, "sbp3_autotune");
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (ms_out) ms_out[v] = t / 5.0;
+        if (t < best_ms) {
+            best_ms = t;
+            best = v;
+        }
+    }
+    for (int v = nv; v < SBP3_TUNING_VARIANTS; ++v)
+        if (ms_out) ms_out[v] = -1.0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->prof_on = prof;
+    h->div_variant = best;
+    if (variant_out) *variant_out = best;
+    return SBP_OK;
 }
 
 int sbp3_profile(sbp3_handle* h, int enable) {

@@ -161,3 +161,29 @@ def test_fullsize_sampled_parity():
         ref = ac[:, i3, i2, i1]
         g = got[:, node[2], node[1], node[0]]
         assert np.abs(g - ref).max() < 1e-5 * _term_scale(O, sub), (node, g, ref)
+
+
+def test_tuning_variants_bitwise_equal():
+    """Every launch shape of the interior kernel computes bitwise the same step; the autotuner picks
+    one of them and leaves the state alone."""
+    from paper_2003_12811_gb300 import Solver3D
+    b = B.random_block3(N=(40, 37, 33), order=6, faces=MIXED)
+    u0 = B.smooth_state3(b, seed=1)
+    u1 = u0 + 1e-3 * B.smooth_state3(b, seed=2)
+    outs = []
+    for v in range(4):
+        S = Solver3D.from_block(b, "fp32")
+        S.set_state(u0, u1)
+        S.sbp3_set_tuning(v)
+        S.step(3, 2e-3)
+        outs.append(S.state())
+        S.close()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+    S = Solver3D.from_block(b, "fp32")
+    S.set_state(u0, u1)
+    v, ms = S.sbp3_autotune()
+    assert 0 <= v < 4 and all(m > 0 for m in ms)
+    a, c = S.state()
+    S.close()
+    assert np.array_equal(c, u1.astype(np.float32).astype(np.float64))
