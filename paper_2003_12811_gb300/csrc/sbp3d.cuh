@@ -216,23 +216,128 @@ __device__ __forceinline__ void grad_dir(const Grid3& g, int i, const T* __restr
     }
 }
 
+template <typename T, int NV> __device__ __forceinline__ void vld(const T* p, T v[NV]) {
+    if constexpr (NV == 2 && sizeof(T) == 4) {
+        const float2 x = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) v[n] = __ldg(p + n);
+    }
+}
+template <typename T, int NV> __device__ __forceinline__ void vst(T* p, const T v[NV]) {
+    if constexpr (NV == 2 && sizeof(T) == 4) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) p[n] = v[n];
+    }
+}
+
+// D_D u_l of one node as a call of its own (the closure rows of the paired flux kernel)
+template <typename T, int O, int D>
+__device__ __noinline__ void grad_call(const Grid3& g, int i, const T* __restrict__ up, T* __restrict__ out) {
+    T gr[3];
+    grad_dir<T, O, D>(g, i, up, gr);
+    out[0] = gr[0];
+    out[1] = gr[1];
+    out[2] = gr[2];
+}
+
 // ------------------------------------------------------------------ mixed fluxes
-template <typename T, int O>
-__global__ void __launch_bounds__(BX * BY) k3_flux(Grid3 g, const T* __restrict__ u, const T* __restrict__ cm,
+// Two x1-adjacent nodes per thread (FP32; one node in FP64).  A pair whose x1 rows are interior
+// reads its x1 stencil as aligned vector windows; its x2 / x3 rows are vector loads at +-k
+// strides (interior) or the general rows node by node (closure rows, the same for a whole warp).
+// A pair near the x1 faces takes the general rows for everything.
+template <typename T, int O, int NV>
+__device__ __forceinline__ void flux_pair(const Grid3& g, int i1, int i2, int i3, const T* __restrict__ up,
+                                          T gr[NV][3][3]) {
+    using P = Ord<O>;
+    constexpr int Q = P::Q;
+    constexpr int QA = (Q + NV - 1) / NV * NV;
+    constexpr int WN = NV + 2 * QA;
+    const long long fs = g.fs;
+    const bool x1int = i1 >= P::NB && i1 + NV - 1 <= g.n[0] - 1 - P::NB && i1 >= QA;
+    if (x1int) {
+        const T ih = T(g.ih[0]);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            T w[WN];
+#pragma unroll
+            for (int v = 0; v < WN / NV; ++v) vld<T, NV>(up + l * fs - QA + v * NV, w + v * NV);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                T acc = T(0);
+#pragma unroll
+                for (int k = 1; k <= Q; ++k) acc += P::template aT<T>(k - 1) * (w[QA + n + k] - w[QA + n - k]);
+                gr[n][0][l] = ih * acc;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < NV; ++n) grad_call<T, O, 0>(g, i1 + n, up + n, gr[n][0]);
+    }
+    auto strided = [&](auto dc, int i) {
+        constexpr int D = decltype(dc)::value;
+        const int N = g.n[D];
+        if (i >= P::NB && i <= N - 1 - P::NB) {
+            const int S = dstride<D>(g);
+            const T ih = T(g.ih[D]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                T acc[NV];
+#pragma unroll
+                for (int n = 0; n < NV; ++n) acc[n] = T(0);
+#pragma unroll
+                for (int k = 1; k <= Q; ++k) {
+                    T a[NV], b[NV];
+                    vld<T, NV>(up + l * fs + k * S, a);
+                    vld<T, NV>(up + l * fs - k * S, b);
+                    const T ak = P::template aT<T>(k - 1);
+#pragma unroll
+                    for (int n = 0; n < NV; ++n) acc[n] += ak * (a[n] - b[n]);
+                }
+#pragma unroll
+                for (int n = 0; n < NV; ++n) gr[n][D][l] = ih * acc[n];
+            }
+        } else {
+#pragma unroll
+            for (int n = 0; n < NV; ++n) grad_call<T, O, D>(g, i, up + n, gr[n][D]);
+        }
+    };
+    strided(std::integral_constant<int, 1>(), i2);
+    strided(std::integral_constant<int, 2>(), i3);
+}
+
+template <typename T, int O, int NV>
+__global__ void __launch_bounds__(BX * BY, 3) k3_flux(Grid3 g, const T* __restrict__ u, const T* __restrict__ cm,
                                                    T* __restrict__ q) {
-    const int i1 = blockIdx.x * BX + threadIdx.x, i2 = blockIdx.y * BY + threadIdx.y, i3 = blockIdx.z;
+    const int i1 = (blockIdx.x * BX + threadIdx.x) * NV, i2 = blockIdx.y * BY + threadIdx.y, i3 = blockIdx.z;
     if (i1 >= g.n[0] || i2 >= g.n[1]) return;
     const long long o = i1 + i2 * g.s[1] + i3 * g.s[2];
+    const long long fs = g.fs;
     const T* up = u + o;
-    T gr[3][3];                                   // gr[k][l] = D_k u_l
-    grad_dir<T, O, 0>(g, i1, up, gr[0]);
-    grad_dir<T, O, 1>(g, i2, up, gr[1]);
-    grad_dir<T, O, 2>(g, i3, up, gr[2]);
-    T qq[3][3];
+    // the last pair of an odd row has one node: it runs alone through the general rows
+    const bool full = i1 + NV - 1 < g.n[0];
+    T gr[NV][3][3];                               // gr[n][k][l] = D_k u_l at node n
+    if (full) {
+        flux_pair<T, O, NV>(g, i1, i2, i3, up, gr);
+    } else {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int n = 0; n < NV; ++n) {
+            grad_call<T, O, 0>(g, i1, up, gr[n][0]);
+            grad_call<T, O, 1>(g, i2, up, gr[n][1]);
+            grad_call<T, O, 2>(g, i3, up, gr[n][2]);
+        }
+    }
+    T qq[NV][3][3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) qq[i][j] = T(0);
+    for (int n = 0; n < NV; ++n)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) qq[n][i][j] = T(0);
     const T* cmo = cm + o;
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
@@ -241,16 +346,36 @@ __global__ void __launch_bounds__(BX * BY) k3_flux(Grid3 g, const T* __restrict_
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                const T M = ldg(cmo + (9 * p + 3 * j + l) * g.fs);
-                qq[i][j] += M * gr[k][l];             // c_ijkl D_k u_l
-                qq[k][l] += M * gr[i][j];             // c_klij D_i u_j (= c_kl ij, major symmetry)
+                T M[NV];
+                if (full) {
+                    vld<T, NV>(cmo + (9 * p + 3 * j + l) * fs, M);
+                } else {
+                    M[0] = ldg(cmo + (9 * p + 3 * j + l) * fs);
+#pragma unroll
+                    for (int n = 1; n < NV; ++n) M[n] = T(0);
+                }
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    qq[n][i][j] += M[n] * gr[n][k][l];       // c_ijkl D_k u_l
+                    qq[n][k][l] += M[n] * gr[n][i][j];       // c_klij D_i u_j (major symmetry)
+                }
             }
     }
     T* qo = q + o;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) qo[(3 * i + j) * g.fs] = qq[i][j];
+        for (int j = 0; j < 3; ++j) {
+            const long long f = (3 * i + j) * fs;
+            if (full) {
+                T v[NV];
+#pragma unroll
+                for (int n = 0; n < NV; ++n) v[n] = qq[n][i][j];
+                vst<T, NV>(qo + f, v);
+            } else {
+                qo[f] = qq[0][i][j];
+            }
+        }
 }
 
 // ------------------------------------------------------------------ divergence and leapfrog store
@@ -349,25 +474,6 @@ __global__ void __launch_bounds__(128) k3_xclos(Grid3 g, int k0, int nk, const T
 struct Box3 {
     int x1lo, x1hi, y0, y1, z0, z1;
 };
-
-template <typename T, int NV> __device__ __forceinline__ void vld(const T* p, T v[NV]) {
-    if constexpr (NV == 2 && sizeof(T) == 4) {
-        const float2 x = __ldg(reinterpret_cast<const float2*>(p));
-        v[0] = x.x;
-        v[1] = x.y;
-    } else {
-#pragma unroll
-        for (int n = 0; n < NV; ++n) v[n] = __ldg(p + n);
-    }
-}
-template <typename T, int NV> __device__ __forceinline__ void vst(T* p, const T v[NV]) {
-    if constexpr (NV == 2 && sizeof(T) == 4) {
-        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-    } else {
-#pragma unroll
-        for (int n = 0; n < NV; ++n) p[n] = v[n];
-    }
-}
 
 // x2 / x3 direction (stride S) for NV nodes: r[n][j] += ih D q_Dj + ih^2 D_xx(b) u, interior rows
 template <typename T, int O, int NV>

@@ -116,7 +116,8 @@ void prof_end(cudaEvent_t stop, cudaStream_t st) {
 template <typename T, int O, int MODE>
 int launch_operator(sbp3_handle* h, const T* u, T* du, T* un, double dt, cudaStream_t st) {
     const Grid3& g = h->g;
-    const dim3 blk(BX, BY), grd((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, g.n[2]);
+    constexpr int NVF = sizeof(T) == 4 ? 2 : 1;
+    const dim3 blk(BX, BY), grd((g.n[0] + BX * NVF - 1) / (BX * NVF), (g.n[1] + BY - 1) / BY, g.n[2]);
     const T* cm = static_cast<const T*>(h->cm);
     const T* cd = static_cast<const T*>(h->cd);
     const T* w = static_cast<const T*>(h->w);
@@ -124,7 +125,7 @@ int launch_operator(sbp3_handle* h, const T* u, T* du, T* un, double dt, cudaStr
     const T dt2 = T(dt * dt);
     cudaEvent_t stop;
     prof_begin(h, 0, st, &stop);
-    k3_flux<T, O><<<grd, blk, 0, st>>>(g, u, cm, q);
+    k3_flux<T, O, NVF><<<grd, blk, 0, st>>>(g, u, cm, q);
     prof_end(stop, st);
     {
         constexpr int NV = sizeof(T) == 4 ? 2 : 1;
