@@ -2,9 +2,9 @@
 // Sec. 3.3, 4.3-4.7 and 5).  A leapfrog step is three kernel families:
 //   k3_flux  -- the mixed fluxes q_ij = sum_{k != i} c_ijkl D_k u_l (9 fields) from u^n;
 //   k3_div_int / k3_div_shell -- r_j = sum_i D_i q_ij + sum_i D_ii^FC(c_ijil) u_l, then the leapfrog
-//               store (MODE 0: increment form, d = du + dt^2 w r, un = u + d; MODE 1: out = w r), on
-//               the interior box (interior rows only) and on the boundary shell (closure rows and
-//               the traction / displacement SATs of every face that reaches the node).
+//               store (MODE 0: increment form, d = du + dt^2 w r, un = u + d; MODE 1: out = w r),
+//               on the x1-interior columns at every i2, i3 (with the x2 / x3 face SATs) and on the
+//               x1 slabs near the x1 faces (with every face SAT that reaches the node).
 // Layout: every scalar field is [n3][n2][pitch] in the arithmetic type T, pitch = n1 rounded up
 // to 128 bytes; field f of a group starts at f * fs (fs = n3 * n2 * pitch).
 //   cm: 27 fields, M^{ik}_{jl} = c_ijkl for the pairs (i, k) = (1,2), (1,3), (2,3), field 9p + 3j + l
