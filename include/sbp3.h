@@ -21,7 +21,8 @@
  *    4: x3=0, 5: x3=1.
  *  - Host arrays passed in are copied (the caller keeps ownership); host arrays written out are
  *    caller-allocated.  Host values are double precision.  Device memory is owned by the handle.
- *  - Orders 2, 4, 6 need n_i >= 5, 18, 27 nodes per direction.
+ *  - Orders 2, 4, 6 need n_i >= 5, 18, 27 nodes per direction; n2, n3 <= 65535 and an x3-plane
+ *    (n1 rounded up to 128 bytes, times n2) below 2^27 elements (SBP_E_INVALID_ARG otherwise).
  */
 #ifndef SBP3_H
 #define SBP3_H

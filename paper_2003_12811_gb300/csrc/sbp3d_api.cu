@@ -258,8 +258,9 @@ int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* 
         return fail(nullptr, SBP_E_INVALID_ARG, "need n1, n2, n3 >= " + std::to_string(mn) + " for order " +
                                                     std::to_string(order));
     if (n3 > 65535 || n2 > 65535) return fail(nullptr, SBP_E_INVALID_ARG, "n2, n3 must be <= 65535");
-    if (pitch_of(n1, precision == SBP_FP32 ? 4 : 8) * (long long)n2 >= (1LL << 31))
-        return fail(nullptr, SBP_E_INVALID_ARG, "an x3-plane must hold fewer than 2^31 elements");
+    // neighbour offsets are 32-bit: up to 16 planes away from a node must stay below 2^31 elements
+    if (pitch_of(n1, precision == SBP_FP32 ? 4 : 8) * (long long)n2 * 16 >= (1LL << 31))
+        return fail(nullptr, SBP_E_INVALID_ARG, "an x3-plane must hold fewer than 2^27 elements");
     if (!X || !face_kinds) return fail(nullptr, SBP_E_INVALID_ARG, "X and face_kinds are required");
     for (int f = 0; f < 6; ++f)
         if (face_kinds[f] != SBP3_BC_DISPLACEMENT && face_kinds[f] != SBP3_BC_TRACTION)

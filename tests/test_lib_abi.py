@@ -103,6 +103,9 @@ def test_sbp3_validation_before_device_work(L):
     bad = (C.c_int * 6)(*([1] * 5 + [2]))
     assert L.sbp3_create(6, 0, n, n, n, xp, bad, 1.0, C.byref(h)) == -1            # face kind
     assert L.sbp3_create(6, 0, n, n, n, xp, kinds, 0.0, C.byref(h)) == -1          # beta
+    # a plane of 2^27 elements or more is rejected before X is read (X here is far too short)
+    assert L.sbp3_create(6, 1, 1 << 17, 1024, n, xp, kinds, 1.0, C.byref(h)) == -1
+    assert b"2^27" in L.sbp3_last_error(None)
     X[5] = np.nan
     assert L.sbp3_create(6, 0, n, n, n, xp, kinds, 1.0, C.byref(h)) == -1          # non-finite X
     assert b"non-finite" in L.sbp3_last_error(None)
