@@ -9,7 +9,8 @@ none of which reuses the 3-D oracle's own formulas:
 * rigid translations (any grid) and rigid rotations (affine grid, constant C) are in the kernel
   of the operator with traction faces;
 * the volume operator is exact for quadratic displacements on an affine grid with constant C
-  (orders 4 and 6: their boundary closures differentiate quadratics exactly);
+  (orders 4 and 6: their boundary closures differentiate quadratics exactly), and away from the
+  closures it converges to the continuous operator at the interior order 2q;
 * leapfrog conserves the discrete energy of the scheme.
 """
 import numpy as np
@@ -198,3 +199,29 @@ def test_crop_window_matches_whole_block_at_its_centre():
             assert np.abs(got - ref).max() < 1e-10 * np.abs(a).max()
         cc = B.random_block3_crop(N, lo, hi, order=6, faces=b.faces)
         assert np.array_equal(cc.X, c.X) and np.allclose(cc.C, c.C, rtol=1e-15, atol=0) and cc.faces == c.faces
+
+
+@pytest.mark.parametrize("order,ns,margin,rate", [(2, (12, 23), 2, 1.9), (4, (19, 37), 7, 3.3)])
+def test_volume_operator_interior_convergence(order, ns, margin, rate):
+    """Affine grid, constant C, u_l = sin(k . X + phi_l): away from the closure rows the volume
+    operator converges to the continuous J C_IjKl d_I d_K u_l = -J C_IjKl k_I k_K u_l at the
+    interior order 2q (Sec. 4: order 2q in the interior)."""
+    def max_err(n):
+        N = (n, n, n)
+        g = np.array(B.ref_grid3(*N))
+        Aff = np.array([[1.0, 0.1, 0.05], [0.2, 1.3, 0.0], [0.1, -0.1, 0.8]])
+        X = np.einsum("Ii,i...->I...", Aff, g)
+        rho, C = B.random_material3(N)
+        C = np.broadcast_to(C[..., 3:4, 3:4, 3:4], C.shape).copy()
+        O = Oracle3D(B.Block3D(X=X, rho=np.ones_like(rho), C=C, faces=("traction",) * 6, order=order))
+        K = O.volume_operator()
+        kv = np.array([1.3, -0.7, 0.9])
+        u = np.array([np.sin(np.einsum("I,I...->...", kv, X) + ph) for ph in (0.3, 1.1, -0.4)])
+        got = np.array([sum(K[j][l] @ u[l].ravel() for l in range(3)) for j in range(3)])
+        c0 = C[..., 0, 0, 0]
+        exact = -O.J * np.einsum("IjKl,I,K,l...->j...", c0, kv, kv, u).reshape(3, -1)
+        e = np.abs(got - exact).reshape(3, n, n, n)
+        m = margin
+        return e[:, m:n - m, m:n - m, m:n - m].max()
+    e1, e2 = max_err(ns[0]), max_err(ns[1])
+    assert np.log(e1 / e2) / np.log((ns[1] - 1) / (ns[0] - 1)) > rate
