@@ -601,6 +601,44 @@ def accuracy_table():
     return table
 
 
+def accuracy3d(n=96, nsteps=(200, 1000)):
+    """The 3-D operator in FP32 (increment form) against FP64 on a curvilinear n^3 block (order 6,
+    the bench medium and faces), relative l2 of u after each mark; the FP64 path is the reference
+    (the parity tests hold it to the 3-D oracle at 1e-12)."""
+    from workloads import box3d as B3
+    from paper_2003_12811_gb300 import Solver3D
+    N = (n, n, n)
+    faces = ("displacement",) * 5 + ("traction",)
+    X = B3.block3_coords(N)
+    rho, P45 = B3.material3_planes(N)
+    hmin = min(np.abs(np.diff(X[0], axis=2)).min(), np.abs(np.diff(X[1], axis=1)).min(),
+               np.abs(np.diff(X[2], axis=0)).min())
+    dt = 0.2 * hmin / (2.3 * np.sqrt(1.3))
+    g1, g2, g3 = B3.ref_grid3(*N)
+    u0 = np.array([np.sin(np.pi * g1) * np.sin(np.pi * g2) * np.sin(np.pi * g3 / 2),
+                   np.sin(2 * np.pi * g1) * np.sin(np.pi * g2) * np.sin(np.pi * g3 / 2),
+                   np.sin(np.pi * g1) * np.sin(2 * np.pi * g2) * np.sin(np.pi * g3 / 2)])
+    u0 = u0.astype(np.float32).astype(np.float64)
+    out = {}
+    runs = {}
+    for prec in ("fp64", "fp32"):
+        S = Solver3D(X, faces, 6, prec)
+        S.sbp3_set_material(0, n, rho, P45)
+        S.set_state(u0, u0)
+        done = 0
+        runs[prec] = {}
+        for mark in nsteps:
+            S.step(mark - done, dt)
+            done = mark
+            runs[prec][mark] = S.state()[1]
+        S.close()
+    for mark in nsteps:
+        a, b = runs["fp32"][mark], runs["fp64"][mark]
+        out[str(mark)] = float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+    return {"workload": f"3-D block {n}^3, order 6, bench medium and faces, dt = 0.2 h_min / v_max",
+            "fp32_vs_fp64_rel_l2": out}
+
+
 def convergence_table(Ns=(41, 81, 161, 321), T=0.5, cfl=0.25):
     """Sec. 7.1 convergence study on the GPU: the manufactured solution and material on two blocks
     with an interface, traction and displacement faces, to time T; the l2 error (the scheme's J H
@@ -722,6 +760,8 @@ def main():
                     help="run a small served batch (8 shots of 801^2, 6 steps) for a profile capture and exit")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="leapfrog steps of the misfit-gradient workload")
     ap.add_argument("--op3d-only", action="store_true", help="print the 3-D operator measurement alone")
+    ap.add_argument("--accuracy3d", action="store_true",
+                    help="print the 3-D FP32-against-FP64 accuracy (96^3, 1000 steps) and exit")
     ap.add_argument("--n3d", type=int, default=256, help="nodes per direction of the 3-D operator workload")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -753,6 +793,9 @@ def main():
         return 0
     if args.adjoint_only:
         print(json.dumps(adjoint_bench(nsteps=args.adjoint_steps, prec=prec)), flush=True)
+        return 0
+    if args.accuracy3d:
+        print(json.dumps({"accuracy3d": accuracy3d()}), flush=True)
         return 0
     if args.op3d_only:
         print(json.dumps(bench3d(n=args.n3d, prec=prec)), flush=True)
