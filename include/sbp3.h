@@ -46,7 +46,10 @@ typedef struct sbp3_handle sbp3_handle;
  * (sbp3_set_material) before sbp3_step or sbp3_apply. */
 int sbp3_create(int order, int precision, int n1, int n2, int n3, const double* X, const int* face_kinds,
                 double beta, sbp3_handle** out);
+/* Synchronizes the device and frees every buffer of the handle; h is invalid afterwards. */
 int sbp3_destroy(sbp3_handle* h);
+/* Message of the last failed call on h (of the last failed sbp3_create when h is NULL); owned by
+ * the library, valid until the next call on the same handle. */
 const char* sbp3_last_error(const sbp3_handle* h);
 
 /* Device bytes a handle of this order, precision and size holds: 64 words per node (45 coefficients,
@@ -61,17 +64,22 @@ int sbp3_footprint(int order, int precision, int n1, int n2, int n3, long long* 
  * SBP_E_JACOBIAN_NONPOSITIVE if J <= 0 at a node of these planes (Sec. 3.3). */
 int sbp3_set_material(sbp3_handle* h, int i3_begin, int i3_count, const double* rho, const double* C45);
 
-/* Leapfrog levels u^{n-1}, u^n (3 * n1*n2*n3 each).  In FP32 the handle keeps the increment
- * u^n - u^{n-1}, formed here in double precision, beside u^n. */
+/* Leapfrog levels u^{n-1}, u^n (3 * n1*n2*n3 each, host FP64, copied).  In FP32 the handle keeps
+ * the increment u^n - u^{n-1}, formed here in double precision, beside u^n.  sbp3_get_state
+ * writes the two current levels (after a step: the levels before and after it) into caller
+ * arrays; SBP_E_STATE before any sbp3_set_state.  Both synchronize the device. */
 int sbp3_set_state(sbp3_handle* h, const double* u_prev, const double* u_cur);
 int sbp3_get_state(sbp3_handle* h, double* u_prev, double* u_cur);
 
-/* accel = (rho J)^-1 [ DD(c) u + J SAT(u) ] for the host field u (3 * n1*n2*n3); the state is
- * left untouched. */
+/* accel = (rho J)^-1 [ DD(c) u + J SAT(u) ] for the host field u (3 * n1*n2*n3, FP64, rounded to
+ * the handle's precision on the device); the state is left untouched; SBP_E_STATE until the
+ * material covers every x3-plane.  Synchronizes the device. */
 int sbp3_apply(sbp3_handle* h, const double* u, double* accel);
 
 /* nsteps leapfrog steps of size dt on the given CUDA stream (NULL: the default stream); the call
- * returns once the launches are queued. */
+ * returns once the launches are queued (three kernels per step).  SBP_E_STATE without a complete
+ * material or a state; SBP_E_INVALID_ARG for nsteps < 0 or dt <= 0.  The caller picks a stable dt
+ * (no CFL estimate in 3-D). */
 int sbp3_step(sbp3_handle* h, int nsteps, double dt, void* stream);
 
 /* Per-family device time (CUDA events on the launch stream) of the launches made while enabled,
@@ -91,6 +99,7 @@ int sbp3_autotune(sbp3_handle* h, int* variant_out, double* ms_out);
 int sbp3_profile(sbp3_handle* h, int enable);
 int sbp3_profile_read(sbp3_handle* h, double* ms, long long* launches);
 
+/* Node count, precision and order of the handle (any output pointer may be NULL). */
 int sbp3_get_info(const sbp3_handle* h, long long* nodes_out, int* precision_out, int* order_out);
 
 #ifdef __cplusplus
