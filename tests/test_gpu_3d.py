@@ -126,32 +126,36 @@ def test_state_roundtrip_and_errors():
 
 
 def test_fullsize_sampled_parity():
-    """The bench workload (256^3 nodes, order 6, FP32) in the configuration the bench times: the
-    accelerations at sampled nodes -- interior, next to the displacement faces x1 = 0 and
-    x2 = 1, under the traction top face x3 = 1, and at the corner of three faces -- against the
-    oracle on a 27^3 crop around each sample ('open' cut faces, the whole block's spacing)."""
+    """The bench workload (256^3 nodes, order 6) in FP32 (the configuration the bench times) and in
+    FP64: the accelerations at sampled nodes -- interior, next to the displacement faces x1 = 0
+    and x2 = 1, under the traction top face x3 = 1, and at the corner of three faces -- against
+    the oracle on a 27^3 crop around each sample ('open' cut faces, the whole block's spacing)."""
     from paper_2003_12811_gb300 import Solver3D
     N = (256, 256, 256)
     faces = ("displacement",) * 5 + ("traction",)
-    X = B.block3_coords(N)
-    S = Solver3D(X, faces, 6, "fp32")
-    for k0 in range(0, 256, 64):
-        rho, P = B.material3_planes(N, k0=k0, k1=k0 + 64)
-        S.sbp3_set_material(k0, 64, rho, P)
-    del X
     g1, g2, g3 = B.ref_grid3(*N)
     u = np.array([np.sin(2.1 * g1 + 0.3) * np.cos(1.7 * g2) * np.sin(1.3 * g3 + 0.5),
                   np.cos(1.1 * g1) * np.sin(2.3 * g2 + 0.2) * np.cos(0.9 * g3),
                   np.sin(1.5 * g1 + 0.7) * np.sin(1.2 * g2) * np.cos(2.0 * g3 + 0.1)])
     del g1, g2, g3
-    got = S.apply(u)
-    S.close()
     samples = [((100, 117, 140), (113, 130, 153)),     # (crop lo, node)
                ((0, 60, 90), (2, 73, 103)),
                ((70, 229, 30), (83, 254, 43)),
                ((140, 40, 229), (153, 53, 255)),
                ((0, 229, 229), (0, 255, 255))]
-    for lo, node in samples:
+    got = {}
+    for prec in ("fp32", "fp64"):
+        X = B.block3_coords(N)
+        S = Solver3D(X, faces, 6, prec)
+        del X
+        for k0 in range(0, 256, 64):
+            rho, P = B.material3_planes(N, k0=k0, k1=k0 + 64)
+            S.sbp3_set_material(k0, 64, rho, P)
+        a = S.apply(u)
+        S.close()
+        got[prec] = np.array([a[:, n3, n2, n1] for _, (n1, n2, n3) in samples])
+        del a
+    for s_i, (lo, node) in enumerate(samples):
         hi = tuple(l + 27 for l in lo)
         c = B.random_block3_crop(N, lo, hi, order=6, faces=faces)
         sub = u[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
@@ -159,8 +163,9 @@ def test_fullsize_sampled_parity():
         ac = O.accel(sub)
         i1, i2, i3 = (node[0] - lo[0], node[1] - lo[1], node[2] - lo[2])
         ref = ac[:, i3, i2, i1]
-        g = got[:, node[2], node[1], node[0]]
-        assert np.abs(g - ref).max() < 1e-5 * _term_scale(O, sub), (node, g, ref)
+        t = _term_scale(O, sub)
+        assert np.abs(got["fp32"][s_i] - ref).max() < 1e-5 * t, (node, got["fp32"][s_i], ref)
+        assert np.abs(got["fp64"][s_i] - ref).max() < 1e-12 * t, (node, got["fp64"][s_i], ref)
 
 
 def test_tuning_variants_bitwise_equal():
