@@ -115,3 +115,16 @@ def test_sbp3_validation_before_device_work(L):
     # matrices: 2 sides x 9 rows x 12 columns x 6 coefficients
     assert out.value == 256 ** 3 * (64 * 4 + 3 * 8) + 256 ** 2 * 2 * 9 * 12 * 6 * 4
     assert L.sbp3_footprint(5, 1, 256, 256, 256, C.byref(out)) == -1
+    # every call rejects a NULL handle before any device work
+    d = np.zeros(3 * 27 ** 3)
+    dp = d.ctypes.data_as(P)
+    assert L.sbp3_set_material(None, 0, 1, dp, dp) == -1
+    assert L.sbp3_set_state(None, dp, dp) == -1
+    assert L.sbp3_get_state(None, dp, dp) == -1
+    assert L.sbp3_apply(None, dp, dp) == -1
+    assert L.sbp3_step(None, 1, 1e-3, None) == -1
+    assert L.sbp3_set_tuning(None, 0) == -1
+    assert L.sbp3_autotune(None, None, None) == -1
+    assert L.sbp3_profile(None, 1) == -1
+    assert L.sbp3_destroy(None) == -1
+    assert L.sbp3_get_info(None, None, None, None) == -1
