@@ -546,6 +546,68 @@ __device__ __forceinline__ void div_int_strided(const T* __restrict__ qD, const 
     }
 }
 
+// the same for FP32 node pairs, in packed FP32x2 arithmetic (one instruction for both nodes)
+__device__ __forceinline__ float2 p2ffma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2fmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2fsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p2s(float a) { return make_float2(a, a); }
+
+template <int O>
+__device__ __forceinline__ void div_int_strided_f2(const float* __restrict__ qD, const float* __restrict__ cdD,
+                                                   const float* __restrict__ up, long long fs, int S, float ih,
+                                                   float r[2][3]) {
+    constexpr int Q = Ord<O>::Q;
+    auto ld2 = [](const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); };
+    float2 R[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float* p = qD + j * fs;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k <= Q; ++k)
+            acc = p2ffma(p2s(Ord<O>::template aT<float>(k - 1)), p2fsub(ld2(p + k * S), ld2(p - k * S)), acc);
+        R[j] = p2fmul(p2s(ih), acc);
+    }
+    float2 dp[3][Q], dm[3][Q];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const float2 uc = ld2(up + l * fs);
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            dp[l][m - 1] = p2fsub(ld2(up + l * fs + m * S), uc);
+            dm[l][m - 1] = p2fsub(ld2(up + l * fs - m * S), uc);
+        }
+    }
+    const float2 ih2 = p2s(ih * ih);
+#pragma unroll
+    for (int k = -Q; k <= Q; ++k) {
+        float2 L[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) {
+            const float cp = edge_wT<O, float>(m, k), cn = edge_wT<O, float>(m, k + m);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                if (cp != 0.f) L[l] = p2ffma(p2s(cp), dp[l][m - 1], L[l]);
+                if (cn != 0.f) L[l] = p2ffma(p2s(cn), dm[l][m - 1], L[l]);
+            }
+        }
+        float2 bb[6];
+#pragma unroll
+        for (int s6 = 0; s6 < 6; ++s6) bb[s6] = ld2(cdD + s6 * fs + k * S);
+        const float2 t0 = p2ffma(bb[2], L[2], p2ffma(bb[1], L[1], p2fmul(bb[0], L[0])));
+        const float2 t1 = p2ffma(bb[4], L[2], p2ffma(bb[3], L[1], p2fmul(bb[1], L[0])));
+        const float2 t2 = p2ffma(bb[5], L[2], p2ffma(bb[4], L[1], p2fmul(bb[2], L[0])));
+        R[0] = p2ffma(ih2, t0, R[0]);
+        R[1] = p2ffma(ih2, t1, R[1]);
+        R[2] = p2ffma(ih2, t2, R[2]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        r[0][j] += R[j].x;
+        r[1][j] += R[j].y;
+    }
+}
+
 // x1 direction for NV consecutive nodes: windows of WN = NV + 2 QA values from i1 - QA (QA = Q
 // rounded up to NV, so the window loads stay vector-aligned); node n sits at window index QA + n
 template <typename T, int O, int NV>
@@ -773,7 +835,10 @@ __device__ __forceinline__ void div_int_dir(const Grid3& g, int i, const T* __re
     const int N = g.n[D];
     const long long fs = g.fs;
     if (i >= Ord<O>::NCLOS && i < N - Ord<O>::NCLOS) {
-        div_int_strided<T, O, NV>(qo + 3 * D * fs, cdo + 6 * D * fs, up, fs, dstride<D>(g), T(g.ih[D]), r);
+        if constexpr (NV == 2 && sizeof(T) == 4)
+            div_int_strided_f2<O>(qo + 3 * D * fs, cdo + 6 * D * fs, up, fs, dstride<D>(g), float(g.ih[D]), r);
+        else
+            div_int_strided<T, O, NV>(qo + 3 * D * fs, cdo + 6 * D * fs, up, fs, dstride<D>(g), T(g.ih[D]), r);
         return;
     }
 #pragma unroll
